@@ -1,0 +1,299 @@
+"""Benchmark: molecule-steps/s of the cavity-MD hot path on one GB300 (or N replicas).
+
+Workload (default "c2"): 4096 synthetic waters (12,288 atoms) in a 919 x 30 x 30 bohr slab at
+liquid density, 512 real cavity modes on an in-plane line of wave vectors, g = 0.001 a.u.,
+dt = 0.5 fs, FP64 SCC-DFTB with Mulliken charges, photons initially at rest.
+
+One timed step = one cavmd_step(ctx, 1) call: the whole hot path (SCC-DFTB of every cell,
+dipoles, forward contraction, photon half-flows, field on every cell, kicks and drift,
+energies). Each step is bracketed by CUDA events on the library's stream; a 256 MB buffer
+(larger than the 129 MB L2) is rewritten between steps, outside the events.
+
+Multi-GPU (torchrun): every rank propagates its own independent replica (its own velocities),
+no data-path collective; value = all ranks' molecule-steps / max-over-ranks time (weak scaling).
+
+--impl reference times the FP64 oracle (oracle/) on the host cores instead: each step runs the
+oracle's full time step on a bounded sample of the same workload (its first 512 cells).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP64_FLOPS_PER_CLK_SM = 4.0      # 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal at 2.07 GHz)
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+FLUSH_BYTES = 256 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _dftb_flops_per_cell(iters):
+    """Algorithmic FP64 flops of one water (n = 6 orbitals, 4 occupied) per time step:
+    per SCC iteration 2n^3 (basis transform) + 9n^3 (symmetric eigensolve with vectors)
+    + 2 n^2 n_occ (density) + 2 n^2 (Mulliken) = 2736, plus 3000 for the Slater-Koster build
+    and the analytic forces."""
+    n, nocc = 6, 4
+    per_iter = 2 * n ** 3 + 9 * n ** 3 + 2 * n * n * nocc + 2 * n * n
+    return per_iter * np.asarray(iters, float) + 3000.0
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(workload, seconds=12.0, n_sample=None):
+    """The oracle as it stands, on a bounded sample of the workload, on this host."""
+    import cavmd_synth as cs
+    from oracle import cavity as OC
+    w = cs.make_workload(workload, n_cells=n_sample)
+    sy, mo, pa = w["system"], w["modes"], w["params"]
+    mat = OC.DFTBMatter(pa, sy)
+    md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
+    md.step()                                   # warm start of the charges
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        md.step()
+        n += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and n >= 3) or n >= 1000:
+            break
+    return {"value": sy.n_cells * n / el, "unit": "molecule-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sy.n_cells} cells x {mo.n_modes} modes of workload {workload}, {n} oracle time "
+                      f"steps after one warm-up step ({el:.1f} s, NumPy, one thread)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import cavmd_synth as cs
+    from oracle import cavity as OC
+    n_sample = 512
+    w = cs.make_workload(args.workload)
+    sub = cs.make_workload(args.workload, n_cells=n_sample)
+    sy, mo, pa = sub["system"], w["modes"], sub["params"]
+    mat = OC.DFTBMatter(pa, sy)
+    md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
+    for _ in range(args.warmup):
+        md.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        md.step()
+    el = time.perf_counter() - t0
+    value = n_sample * args.steps / el
+    line = {
+        "impl": "reference", "metric": "molecule-steps/s", "value": value, "unit": "molecule-steps/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(args.workload, w),
+        "cpu_baseline": {"value": value, "unit": "molecule-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n_sample} of {w['system'].n_cells} cells, all {mo.n_modes} modes, "
+                                   f"one oracle time step per step (NumPy FP64, one thread)"},
+        "e2e": {"value": value, "unit": "molecule-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(workload, w):
+    sy, mo = w["system"], w["modes"]
+    return {"workload": f"{workload}: {sy.n_cells} water x {mo.n_modes} modes, FP64 SCC-DFTB, Mulliken, dt 0.5 fs",
+            "n_cells": sy.n_cells, "n_atoms": sy.n_atoms, "n_modes": mo.n_modes, "precision": "fp64",
+            "charge_model": "mulliken", "l2": "256 MB buffer rewritten between timed steps (L2 flush)",
+            "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import cavmd_synth as cs
+    import paper_2512_03277_gb300 as P
+    from paper_2512_03277_gb300 import build
+    from paper_2512_03277_gb300 import cavmd as B
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    build.build()
+    w = cs.make_workload(args.workload)
+    if rank > 0:   # independent replica: its own Maxwell-Boltzmann velocities
+        w["system"].p = cs.mb_momenta(np.random.default_rng(1000 + rank), w["system"])
+    opt = P.default_options()
+    opt.device = local
+    ctx = P.Context(w["system"], w["params"], w["modes"], opt)
+    stream = ctx.stream
+    N = w["system"].n_cells
+    for _ in range(args.warmup):
+        ctx.cavmd_step(1)
+    ctx.cavmd_observables(want_arrays=False)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    ctx.cavmd_phase_times(True, reset=True)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            ctx.cavmd_step(1)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    phase_ms, phase_cnt = ctx.cavmd_phase_times(False, reset=True)
+    obs = ctx.cavmd_observables(want_arrays=False)
+    ev = ctx.cavmd_get_eval()
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    total_ms = float(step_ms.sum())
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = N * args.steps * ws / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel (SCC-DFTB, FP64-ALU bound)
+    dftb_ms = phase_ms[0] / max(phase_cnt[0], 1)
+    flops = float(_dftb_flops_per_cell(ev["scc_iters"]).sum())
+    achieved = flops / (dftb_ms * 1e-3) / 1e12
+    peak = N_SM * FP64_FLOPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    shares = {name: float(phase_ms[i] / max(phase_ms.sum(), 1e-30))
+              for i, name in enumerate(["dftb", "photon_forward", "field_kick_drift", "other"])}
+
+    # end to end through the C ABI: step + observables into pinned host buffers, wall clock
+    pin = {k: torch.empty(n, dtype=torch.float64, pin_memory=True)
+           for k, n in (("M", N), ("q", ctx.n_modes), ("p", ctx.n_modes), ("D", ctx.n_modes))}
+    o = B.cavmd_obs()
+    import ctypes as C
+    for k, t in pin.items():
+        setattr(o, k, C.cast(t.data_ptr(), C.POINTER(C.c_double)))
+    ctx.cavmd_step(1)
+    ctx.cavmd_observables_into(o)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.cavmd_step(1)
+        ctx.cavmd_observables_into(o)
+    e2e_s = time.perf_counter() - t0
+    d2h = 8 * (N + 3 * ctx.n_modes) + 8 * 8 + 4 * N + 4
+    e2e = {"value": N * args.e2e_steps * ws / e2e_s, "unit": "molecule-steps/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": d2h,
+           "note": "cavmd_step(1) + cavmd_observables (energies, per-cell dipoles, photon q/p/D) every step; "
+                   "the MD state stays on the device between steps, so no host input is copied per step"}
+
+    line = {
+        "metric": "molecule-steps/s", "value": value, "unit": "molecule-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(args.workload, w),
+        "roofline": {"bound": "alu", "kernel": "dftb_kernel<3,6>", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "flops_per_launch": flops, "avg_launch_ms": dftb_ms,
+                     "mean_scc_iters": float(np.mean(ev["scc_iters"])),
+                     "peak_note": "FP64 ALU: 152 SMs x 4 FP64 flop/clk x 2070 MHz (derived, 1.26 TFLOP/s)"},
+        "phase_share": shares,
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": t_wall,
+        "energy_total": obs["e_total"], "temperature_K": obs["temperature"],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.cavmd_destroy()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

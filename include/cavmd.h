@@ -1,0 +1,227 @@
+/*
+ * cavmd.h - C ABI of the GB300 cavity molecular-dynamics hot path.
+ *
+ * One context propagates N independent cells (molecules or clusters, the batch
+ * dimension; the paper's non-interacting cells of Eq. hm) coupled to M cavity
+ * modes through the multimode dipole-gauge Hamiltonian beyond the long-wavelength
+ * approximation (Eq. hlm_bigin / hlm2, written with real modes). Every time step
+ * runs, on one GPU:
+ *   - an SCC-DFTB evaluation of every cell (Slater-Koster H0/S, self-consistent
+ *     charges, generalised eigensolve, Mulliken charges, analytic forces; the
+ *     method the paper's "Computational details" names, second-order SCC-DFTB);
+ *   - the cell dipoles M_n = pol . mu_n and their derivatives b_j = dM_n/dr_j
+ *     (Mulliken charges or finite-difference Born charges, Results section);
+ *   - the forward contraction D_a = lambda_a sum_n u_a(R_n) M_n and the field on
+ *     every cell E_n = sum_a lambda_a u_a(R_n) Y_a (k-space form of Eq. dpj);
+ *   - one symmetric velocity-Verlet-like step with the analytic photon rotation
+ *     of Eq. qknk (Step 3), integrated as described for CAVMD_SPLIT_PHOTON_EXACT.
+ *
+ * Units: atomic units throughout (bohr, Hartree, electron masses, a.u. of time).
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer in the structs below is a HOST pointer unless its comment
+ *     says otherwise. The library copies what it reads during the call; the
+ *     caller keeps ownership of all its arrays.
+ *   - Arrays of 3-vectors are atom-major: x[3*i + k] is component k of atom i.
+ *   - Return value: CAVMD_OK (0) or a negative CAVMD_ERR_* code. The message of
+ *     the last failure is available from cavmd_last_error(ctx) (or
+ *     cavmd_last_error(NULL) when cavmd_init itself failed). No exception or
+ *     abort crosses the ABI.
+ *   - One context belongs to one GPU and one CUDA stream. A context is not
+ *     thread safe; distinct contexts are independent.
+ */
+#ifndef CAVMD_H
+#define CAVMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CAVMD_OK 0
+#define CAVMD_ERR_INVALID_ARG -1   /* a size, pointer or option is out of range            */
+#define CAVMD_ERR_CUDA -2          /* a CUDA runtime call failed (message has the name)    */
+#define CAVMD_ERR_SCC_NOCONV -3    /* a cell's charges did not converge in scc_max_iter    */
+#define CAVMD_ERR_NONFINITE -4     /* a NaN or Inf appeared in the state                   */
+#define CAVMD_ERR_S_NOT_PD -5      /* an overlap matrix was not positive definite          */
+#define CAVMD_ERR_ZERO_GAP -6      /* HOMO-LUMO gap below the closed-shell threshold       */
+#define CAVMD_ERR_DEVICE_TIMEOUT -7/* a bounded device loop ran out of iterations          */
+#define CAVMD_ERR_UNSUPPORTED -8   /* valid request that this build does not implement     */
+#define CAVMD_ERR_NOMEM -9         /* device allocation failed                             */
+
+#define CAVMD_MAX_ELEM 4           /* element ids 0..3                                    */
+#define CAVMD_MAX_ATOMS_PER_CELL 3 /* cells with more atoms return CAVMD_ERR_UNSUPPORTED  */
+
+/* Integral kinds of a Slater-Koster table entry [eA][eB][kind]: SP means an s
+ * orbital on the first element and a p orbital on the second. */
+enum { CAVMD_SK_SS = 0, CAVMD_SK_SP = 1, CAVMD_SK_PPS = 2, CAVMD_SK_PPP = 3 };
+
+enum { CAVMD_PREC_FP64 = 0, CAVMD_PREC_MIXED_TF32 = 1, CAVMD_PREC_MIXED_BF16X3 = 2 };
+enum { CAVMD_CHARGE_MULLIKEN = 0, CAVMD_CHARGE_BORN_FD = 1, CAVMD_CHARGE_BORN_CENTRAL = 2,
+       CAVMD_CHARGE_BORN_MLP = 3 };
+enum { CAVMD_SPLIT_PHOTON_EXACT = 0, CAVMD_SPLIT_STRANG = 1, CAVMD_SPLIT_PAPER = 2 };
+enum { CAVMD_PHOTON_RELAXED = 0, CAVMD_PHOTON_ZERO = 1 };
+
+/* The cells. Cell c owns atoms cell_offset[c] .. cell_offset[c+1]-1. Cells are
+ * neutral and closed shell (sum of valence charges even). */
+typedef struct {
+    int32_t n_cells;
+    int32_t n_atoms;
+    const int32_t *cell_offset; /* [n_cells + 1], non-decreasing, [0] = 0, [n_cells] = n_atoms */
+    const int32_t *species;     /* [n_atoms] element ids < n_elem of the tables                */
+    const double *r;            /* [3 n_atoms] positions, bohr                                  */
+    const double *p;            /* [3 n_atoms] momenta                                          */
+    const double *R_ref;        /* [3 n_cells] fixed mode-function centres R_n, or NULL for the
+                                   initial centre of mass of each cell                           */
+} cavmd_system;
+
+/* Slater-Koster parameter set. Every radial integral is
+ *   V(r) = a exp(-b r) (1 + c1 r + c2 r^2) f_cut(r)   with params {a, b, c1, c2},
+ * f_cut = 1 below r_cut - taper, then 1/2 (1 + cos(pi x)), x = (r - r_cut + taper)/taper,
+ * and 0 from r_cut on. Entries of kinds that do not exist for a pair (p orbitals
+ * on an s-only element) are ignored. Klopman-Ohno gamma uses hubbard[]. */
+typedef struct {
+    int32_t n_elem;                                       /* 1..CAVMD_MAX_ELEM                */
+    int32_t norb[CAVMD_MAX_ELEM];                         /* 1 (s) or 4 (s, px, py, pz)       */
+    double onsite[CAVMD_MAX_ELEM][2];                     /* eps_s, eps_p, Hartree            */
+    double hubbard[CAVMD_MAX_ELEM];                       /* U, Hartree                       */
+    double zval[CAVMD_MAX_ELEM];                          /* valence electrons                */
+    double mass[CAVMD_MAX_ELEM];                          /* electron masses                  */
+    double h0[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][4][4];      /* [eA][eB][kind][a,b,c1,c2]        */
+    double s[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][4][4];       /* same layout, overlap             */
+    double rep[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][2];        /* pair repulsion a exp(-b r) f_cut */
+    double r_cut;                                         /* bohr                             */
+    double taper;                                         /* bohr, > 0                        */
+} cavmd_sk_tables;
+
+/* Real cavity modes u_a(R) = cos(k_a . R + phi_a) with frequency omega_a > 0 and
+ * amplitude lambda_a (2 g0 for each real member of a travelling +-k pair,
+ * sqrt(2) g0 for a single real mode; see Eq. hlm2). */
+typedef struct {
+    int32_t n_modes;            /* M >= 1                                   */
+    const double *k;            /* [3 M] wave vectors, 1/bohr               */
+    const double *omega;        /* [M]                                      */
+    const double *lambda;       /* [M]                                      */
+    const double *phi;          /* [M]                                      */
+    double pol[3];              /* polarisation, the same for every mode    */
+} cavmd_modes;
+
+typedef void *(*cavmd_alloc_fn)(size_t bytes, void *user);
+typedef void (*cavmd_free_fn)(void *device_ptr, void *user);
+
+typedef struct {
+    double dt;                  /* time step, a.u.                                            */
+    int32_t precision;          /* CAVMD_PREC_*                                               */
+    int32_t charge_model;       /* CAVMD_CHARGE_*                                             */
+    int32_t born_interval;      /* refresh finite-difference Born charges every this many steps */
+    double fd_step;             /* finite-difference displacement, bohr                      */
+    double scc_tol;             /* max |q_out - q_in| per atom at convergence                */
+    int32_t scc_max_iter;
+    double mixing;              /* linear part of the charge mixing                           */
+    int32_t splitting;          /* CAVMD_SPLIT_*                                              */
+    int32_t photon_init;        /* CAVMD_PHOTON_*                                             */
+    int32_t graph_chunk;        /* steps per captured CUDA graph; 0 = no graph                */
+    int32_t device;             /* CUDA device ordinal                                        */
+    void *stream;               /* cudaStream_t to run on, or NULL for a library-owned stream */
+    cavmd_alloc_fn dev_alloc;   /* optional device allocator (e.g. a framework's); NULL = cudaMalloc */
+    cavmd_free_fn dev_free;     /* its matching free                                          */
+    void *alloc_user;           /* passed back to dev_alloc / dev_free                        */
+    int32_t energy_history;     /* steps of energy history kept on the device (>= 1)          */
+} cavmd_options;
+
+/* Observables at the current (synchronised) time. Optional arrays may be NULL. */
+typedef struct {
+    double e_kin, e_dftb, e_photon, e_coupling, e_dse, e_photon_free, e_total, temperature;
+    int64_t step;               /* steps taken since cavmd_init                   */
+    int32_t scc_iter_max;       /* largest SCC iteration count of the last step   */
+    double *M;                  /* out [n_cells] projected cell dipoles, or NULL  */
+    double *q;                  /* out [M] photon coordinates, or NULL            */
+    double *p;                  /* out [M] photon momenta, or NULL                */
+    double *D;                  /* out [M] D_a, or NULL                           */
+} cavmd_obs;
+
+/* The propagated state. All arrays host, caller-owned, sized as noted. */
+typedef struct {
+    double *r;                  /* [3 n_atoms] */
+    double *p;                  /* [3 n_atoms] */
+    double *q;                  /* [M]         */
+    double *pq;                 /* [M]         */
+    int64_t step;
+} cavmd_state;
+
+/* The last evaluation (at the current positions). Optional arrays may be NULL. */
+typedef struct {
+    double *F_dftb;             /* [3 n_atoms] -dE_DFTB/dr                                */
+    double *F_total;            /* [3 n_atoms] F_dftb + E_n b_j with the instantaneous
+                                   field E_n = sum_a lambda_a u_a(R_n)(omega_a q_a - D_a) */
+    double *b;                  /* [3 n_atoms] dM_n/dr_j used by the step                 */
+    double *q_pop;              /* [n_atoms] Mulliken populations                         */
+    double *E_cell;             /* [n_cells] E_DFTB of every cell                         */
+    double *M;                  /* [n_cells] projected dipoles                            */
+    int32_t *scc_iters;         /* [n_cells] SCC iterations of the last evaluation        */
+} cavmd_eval;
+
+/* Opaque context: one propagated system on one GPU. */
+typedef struct cavmd_ctx cavmd_ctx;
+
+/* Fills *opt with the defaults: dt = 0.5 fs, FP64, Mulliken, born_interval 3, fd_step 1e-3,
+ * scc_tol 1e-12, scc_max_iter 200, mixing 0.5, PHOTON_EXACT, relaxed photons, graph_chunk 50,
+ * device 0, library stream, cudaMalloc, energy_history 1024. */
+void cavmd_default_options(cavmd_options *opt);
+
+/* Creates a context: validates and copies the inputs to the device, evaluates every cell at
+ * the initial positions, initialises the photons (CAVMD_PHOTON_RELAXED: p_a = 0,
+ * q_a = D_a / omega_a, the minimum of the photon energy at the initial matter, the
+ * zero-temperature end point of the paper's Step 0) and records the energies of step 0.
+ * On success *ctx owns its device memory until cavmd_destroy. Blocks until done. */
+int cavmd_init(cavmd_ctx **ctx, const cavmd_system *sys, const cavmd_sk_tables *sk,
+               const cavmd_modes *modes, const cavmd_options *opt);
+
+/* Advances nsteps >= 0 time steps (Steps 1-4 of the paper's loop, in k-space form). The work is
+ * queued on the context's stream; the call returns once it is queued, with the status of the
+ * work queued by the previous call (a non-convergence or a non-finite value found there). */
+int cavmd_step(cavmd_ctx *ctx, int64_t nsteps);
+
+/* Waits for the queued work and copies the observables of the current time into *out. */
+int cavmd_observables(cavmd_ctx *ctx, cavmd_obs *out);
+
+/* Copies the energy history: up to n most recent steps, 8 doubles each
+ * (e_kin, e_dftb, e_photon, e_coupling, e_dse, e_photon_free, e_total, step), oldest first.
+ * *n_out receives the number written. Waits for the queued work. */
+int cavmd_energy_history(cavmd_ctx *ctx, double *out, int32_t n, int32_t *n_out);
+
+/* Waits, then copies the state into / out of the caller's host buffers. cavmd_set_state
+ * re-evaluates every cell at the new positions (as cavmd_init does, without touching the
+ * photons), so a run resumed from a saved state repeats the original one exactly. */
+int cavmd_get_state(cavmd_ctx *ctx, cavmd_state *st);
+int cavmd_set_state(cavmd_ctx *ctx, const cavmd_state *st);
+
+/* Waits, then copies the last evaluation into the caller's host buffers. */
+int cavmd_get_eval(cavmd_ctx *ctx, cavmd_eval *out);
+
+/* Per-phase device timers. enable = 1 starts recording CUDA events around every kernel
+ * phase of later steps (on the context's stream); enable = 0 stops. ms_out[CAVMD_N_PHASES]
+ * receives the summed durations and counts[CAVMD_N_PHASES] the launches since the last
+ * reset (reset = 1 clears both after reading). Either output may be NULL. */
+#define CAVMD_N_PHASES 4        /* 0: SCC-DFTB, 1: forward contraction + photons,
+                                   2: field + kicks + drift, 3: other                    */
+int cavmd_phase_times(cavmd_ctx *ctx, int32_t enable, double *ms_out, int64_t *counts,
+                      int32_t reset);
+
+/* Message of the last failure on ctx (or of the last failed cavmd_init when ctx is NULL).
+ * The string stays valid until the next call on the same context. */
+const char *cavmd_last_error(const cavmd_ctx *ctx);
+
+/* Frees every device buffer and the context itself. NULL is allowed. */
+void cavmd_destroy(cavmd_ctx *ctx);
+
+/* Size of one of the library's structs, for bindings that lay them out by hand. */
+size_t cavmd_struct_size(int32_t which); /* 0 system, 1 sk_tables, 2 modes, 3 options,
+                                            4 obs, 5 state, 6 eval */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAVMD_H */

@@ -1,0 +1,639 @@
+// Host implementation of the C ABI declared in include/cavmd.h.
+//
+// One step of the loop (the paper's Steps 1-4 in k-space form) is three kernels:
+//   dftb      SCC-DFTB of every cell at the drifted positions (forces, charges, dipoles);
+//   photon    D_a from the new dipoles, second half-flow of every mode, energies, and the first
+//             half-flow of the next step;
+//   field     E_n for both half-flows in one pass over u_a(R_n), the two nuclear kicks and the
+//             drift to the next positions, and the energy record of the synchronised state.
+// A call of cavmd_step(n) opens with the first half-flow (photon + field kernels without the
+// forward contraction) and closes with a second half-flow only, so the state between calls is
+// synchronised. Chunks of graph_chunk steps are captured once as a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cavmd_internal.cuh"
+
+namespace {
+thread_local std::string g_init_error;
+}
+
+struct cavmd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cavmd_options opt{};
+    int N = 0, n_atoms = 0, M = 0;
+    std::vector<int> h_off, h_species;
+    double pol[3] = {1, 0, 0};
+    // device buffers
+    DevSK *d_sk = nullptr;
+    int *d_off = nullptr, *d_species = nullptr, *d_iters = nullptr;
+    double *d_r = nullptr, *d_p = nullptr, *d_F = nullptr, *d_b = nullptr, *d_qpop = nullptr;
+    double *d_C = nullptr, *d_E = nullptr, *d_Mc = nullptr, *d_mass = nullptr, *d_imass = nullptr;
+    double *d_U = nullptr, *d_k = nullptr, *d_phi = nullptr, *d_R = nullptr;
+    double *d_omega = nullptr, *d_lam = nullptr, *d_iomega = nullptr;
+    double *d_cos = nullptr, *d_sin = nullptr, *d_omc = nullptr;
+    double *d_q = nullptr, *d_pq = nullptr, *d_qs = nullptr, *d_pqs = nullptr, *d_D = nullptr;
+    double *d_W1 = nullptr, *d_W2 = nullptr, *d_emode = nullptr, *d_Einst = nullptr;
+    double *d_ekp = nullptr, *d_edp = nullptr, *d_hist = nullptr;
+    unsigned *d_done = nullptr, *d_status = nullptr;
+    long long *d_step = nullptr;
+    std::vector<void *> allocs;
+    // host-side bookkeeping
+    unsigned *h_status = nullptr;   // pinned
+    cudaEvent_t status_ev = nullptr;
+    bool status_pending = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    int64_t step = 0;
+    std::string err;
+    // phase timers
+    bool timing = false;
+    struct Pending { cudaEvent_t a, b; int phase; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> ev_free;
+    double phase_ms[CAVMD_N_PHASES] = {0, 0, 0, 0};
+    int64_t phase_cnt[CAVMD_N_PHASES] = {0, 0, 0, 0};
+    StepArgs sa{};
+    DftbArgs da{};
+};
+
+namespace {
+
+int fail(cavmd_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg; else g_init_error = msg;
+    return code;
+}
+
+int cuda_fail(cavmd_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, CAVMD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                       cudaGetErrorString(e) + ")");
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+int dalloc(cavmd_ctx *c, void **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void *q = nullptr;
+    if (c->opt.dev_alloc) {
+        q = c->opt.dev_alloc(bytes, c->opt.alloc_user);
+        if (!q) return fail(c, CAVMD_ERR_NOMEM, "device allocator callback returned NULL");
+    } else {
+        cudaError_t e = cudaMalloc(&q, bytes);
+        if (e != cudaSuccess) return fail(c, CAVMD_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    *p = q;
+    return CAVMD_OK;
+}
+
+template <typename T>
+int dalloc_n(cavmd_ctx *c, T **p, size_t n) {
+    return dalloc(c, reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+#define AL(ptr, n)                                   \
+    do {                                             \
+        int rc_ = dalloc_n(c, &(ptr), (size_t)(n));  \
+        if (rc_) return rc_;                         \
+    } while (0)
+
+int status_to_code(cavmd_ctx *c, unsigned st) {
+    if (!st) return CAVMD_OK;
+    if (st & ERRBIT_NONFINITE) return fail(c, CAVMD_ERR_NONFINITE, "non-finite energy in the state");
+    if (st & ERRBIT_S_NOT_PD) return fail(c, CAVMD_ERR_S_NOT_PD, "an overlap matrix is not positive definite");
+    if (st & ERRBIT_ZERO_GAP) return fail(c, CAVMD_ERR_ZERO_GAP, "HOMO-LUMO gap below threshold");
+    if (st & ERRBIT_SCC_NOCONV) return fail(c, CAVMD_ERR_SCC_NOCONV, "SCC charges did not converge within scc_max_iter");
+    if (st & ERRBIT_TIMEOUT) return fail(c, CAVMD_ERR_DEVICE_TIMEOUT, "Jacobi sweep limit reached");
+    return fail(c, CAVMD_ERR_CUDA, "unknown device status");
+}
+
+// Waits for the queued work, reads and clears the device status word.
+int sync_status(cavmd_ctx *c) {
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    const unsigned st = *c->h_status;
+    c->status_pending = false;
+    if (st) {
+        CK(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+        return status_to_code(c, st);
+    }
+    return CAVMD_OK;
+}
+
+cudaEvent_t get_event(cavmd_ctx *c) {
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseScope {
+    cavmd_ctx *c;
+    cavmd_ctx::Pending pd{};
+    bool on;
+    PhaseScope(cavmd_ctx *c_, int phase) : c(c_), on(c_->timing) {
+        if (on) {
+            pd.a = get_event(c);
+            pd.b = get_event(c);
+            pd.phase = phase;
+            cudaEventRecord(pd.a, c->stream);
+        }
+    }
+    ~PhaseScope() {
+        if (on) {
+            cudaEventRecord(pd.b, c->stream);
+            c->pending.push_back(pd);
+        }
+    }
+};
+
+void collect_phase_times(cavmd_ctx *c) {
+    for (auto &pd : c->pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(pd.b);
+        cudaEventElapsedTime(&ms, pd.a, pd.b);
+        c->phase_ms[pd.phase] += ms;
+        c->phase_cnt[pd.phase] += 1;
+        c->ev_free.push_back(pd.a);
+        c->ev_free.push_back(pd.b);
+    }
+    c->pending.clear();
+}
+
+cudaError_t run_dftb(cavmd_ctx *c, int have_warm) {
+    PhaseScope ps(c, 0);
+    c->da.have_warm = have_warm;
+    return launch_dftb_water(c->d_sk, c->da, c->stream);
+}
+
+cudaError_t run_photon(cavmd_ctx *c, int flags) {
+    PhaseScope ps(c, 1);
+    return launch_photon(c->sa, flags, c->stream);
+}
+
+cudaError_t run_field(cavmd_ctx *c, int flags) {
+    PhaseScope ps(c, 2);
+    return launch_field(c->sa, flags, c->stream);
+}
+
+// Queues n >= 1 steps starting and ending at a synchronised state.
+cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n) {
+    cudaError_t e;
+    if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
+    if ((e = run_field(c, FLD_FIRST)) != cudaSuccess) return e;
+    for (int64_t s = 0; s < n; ++s) {
+        const bool last = (s == n - 1);
+        if ((e = run_dftb(c, 1)) != cudaSuccess) return e;
+        if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
+        if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+int initial_evaluation(cavmd_ctx *c, bool init_photons) {
+    CK(run_dftb(c, 0));
+    if (init_photons) {
+        const int pf = (c->opt.photon_init == CAVMD_PHOTON_ZERO) ? PH_INIT_ZERO : PH_INIT_RELAXED;
+        CK(run_photon(c, PH_FORWARD | pf | PH_ENERGY));
+    } else {
+        CK(run_photon(c, PH_FORWARD | PH_ENERGY));   // keeps q_sync / pq_sync
+    }
+    CK(run_field(c, FLD_ENERGY));
+    return sync_status(c);
+}
+
+void fill_devsk(const cavmd_sk_tables *t, DevSK *d) {
+    std::memset(d, 0, sizeof(*d));
+    for (int e = 0; e < CAVMD_MAX_ELEM; ++e) {
+        d->onsite[e][0] = t->onsite[e][0];
+        d->onsite[e][1] = t->onsite[e][1];
+        d->hubbard[e] = t->hubbard[e];
+        d->zval[e] = t->zval[e];
+        d->norb[e] = t->norb[e];
+    }
+    std::memcpy(d->h0, t->h0, sizeof(d->h0));
+    std::memcpy(d->s, t->s, sizeof(d->s));
+    std::memcpy(d->rep, t->rep, sizeof(d->rep));
+    d->r_cut = t->r_cut;
+    d->taper = t->taper;
+    d->inv_taper = 1.0 / t->taper;
+}
+
+int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_modes *md,
+             const cavmd_options *o) {
+    cavmd_ctx *c = nullptr;
+    if (!sys || !sk || !md || !o) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    if (sys->n_cells < 1 || sys->n_atoms < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "need n_cells >= 1 and n_atoms >= 1");
+    if (!sys->cell_offset || !sys->species || !sys->r || !sys->p) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL system array");
+    if (sk->n_elem < 1 || sk->n_elem > CAVMD_MAX_ELEM) return fail(c, CAVMD_ERR_INVALID_ARG, "n_elem out of range");
+    for (int e = 0; e < sk->n_elem; ++e)
+        if (sk->norb[e] != 1 && sk->norb[e] != 4) return fail(c, CAVMD_ERR_INVALID_ARG, "norb must be 1 or 4");
+    if (!(sk->taper > 0.0) || !(sk->r_cut > sk->taper)) return fail(c, CAVMD_ERR_INVALID_ARG, "need r_cut > taper > 0");
+    if (sys->cell_offset[0] != 0 || sys->cell_offset[sys->n_cells] != sys->n_atoms)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "cell_offset must start at 0 and end at n_atoms");
+    for (int i = 0; i < sys->n_atoms; ++i)
+        if (sys->species[i] < 0 || sys->species[i] >= sk->n_elem) return fail(c, CAVMD_ERR_INVALID_ARG, "species id out of range");
+    for (int i = 0; i < 3 * sys->n_atoms; ++i)
+        if (!std::isfinite(sys->r[i]) || !std::isfinite(sys->p[i])) return fail(c, CAVMD_ERR_INVALID_ARG, "non-finite position or momentum");
+    for (int n = 0; n < sys->n_cells; ++n) {
+        const int a0 = sys->cell_offset[n], a1 = sys->cell_offset[n + 1];
+        if (a1 < a0) return fail(c, CAVMD_ERR_INVALID_ARG, "cell_offset not non-decreasing");
+        if (a1 - a0 != 3) return fail(c, CAVMD_ERR_UNSUPPORTED, "this build evaluates cells of exactly 3 atoms with 6 orbitals");
+        int norb = 0;
+        double nel = 0;
+        for (int i = a0; i < a1; ++i) { norb += sk->norb[sys->species[i]]; nel += sk->zval[sys->species[i]]; }
+        if (norb != 6) return fail(c, CAVMD_ERR_UNSUPPORTED, "this build evaluates cells of exactly 3 atoms with 6 orbitals");
+        const long ne = std::lround(nel);
+        if (std::fabs(nel - ne) > 1e-12 || (ne & 1) || ne <= 0 || ne > 2 * norb)
+            return fail(c, CAVMD_ERR_INVALID_ARG, "cells must be neutral and closed shell");
+    }
+    if (md->n_modes < 1 || !md->k || !md->omega || !md->lambda || !md->phi)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "need n_modes >= 1 and all mode arrays");
+    for (int a = 0; a < md->n_modes; ++a)
+        if (!(md->omega[a] > 0.0) || !std::isfinite(md->omega[a]) || !std::isfinite(md->lambda[a]) ||
+            !std::isfinite(md->phi[a]))
+            return fail(c, CAVMD_ERR_INVALID_ARG, "mode frequencies must be positive and finite");
+    if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(c, CAVMD_ERR_INVALID_ARG, "dt must be positive");
+    if (!(o->scc_tol > 0.0) || o->scc_max_iter < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad SCC tolerance or iteration limit");
+    if (!(o->mixing > 0.0 && o->mixing <= 1.0)) return fail(c, CAVMD_ERR_INVALID_ARG, "mixing must be in (0, 1]");
+    if (o->precision != CAVMD_PREC_FP64) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_PREC_FP64 in this build");
+    if (o->charge_model != CAVMD_CHARGE_MULLIKEN) return fail(c, CAVMD_ERR_UNSUPPORTED, "only Mulliken charges in this build");
+    if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_SPLIT_PHOTON_EXACT in this build");
+    if (o->photon_init != CAVMD_PHOTON_RELAXED && o->photon_init != CAVMD_PHOTON_ZERO)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
+    if (o->graph_chunk < 0 || o->energy_history < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad graph_chunk or energy_history");
+    if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return fail(c, CAVMD_ERR_INVALID_ARG, "dev_alloc and dev_free go together");
+    return CAVMD_OK;
+}
+
+void release(cavmd_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
+    for (auto e : c->ev_free) cudaEventDestroy(e);
+    for (void *p : c->allocs) {
+        if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_user);
+        else cudaFree(p);
+    }
+    if (c->status_ev) cudaEventDestroy(c->status_ev);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_modes *md) {
+    const int N = c->N, NA = c->n_atoms, M = c->M;
+    CK(cudaSetDevice(c->device));
+    if (c->opt.stream) {
+        c->stream = (cudaStream_t)c->opt.stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    CK(cudaMallocHost(&c->h_status, sizeof(unsigned)));
+    CK(cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming));
+
+    // host-side derived arrays
+    std::vector<double> mass(NA), imass(NA), R(3 * N);
+    for (int i = 0; i < NA; ++i) { mass[i] = sk->mass[sys->species[i]]; imass[i] = 1.0 / mass[i]; }
+    for (int n = 0; n < N; ++n) {
+        if (sys->R_ref) {
+            for (int k = 0; k < 3; ++k) R[3 * n + k] = sys->R_ref[3 * n + k];
+        } else {
+            double mt = 0, x[3] = {0, 0, 0};
+            for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) {
+                mt += mass[i];
+                for (int k = 0; k < 3; ++k) x[k] += mass[i] * sys->r[3 * i + k];
+            }
+            for (int k = 0; k < 3; ++k) R[3 * n + k] = x[k] / mt;
+        }
+    }
+    std::vector<double> iw(M), cw(M), sw(M), omc(M);
+    const double tau = 0.5 * c->opt.dt;
+    for (int a = 0; a < M; ++a) {
+        const double w = md->omega[a];
+        iw[a] = 1.0 / w;
+        cw[a] = std::cos(w * tau);
+        sw[a] = std::sin(w * tau);
+        omc[a] = (1.0 - cw[a]) / w;
+    }
+    DevSK hsk;
+    fill_devsk(sk, &hsk);
+
+    AL(c->d_sk, 1);
+    AL(c->d_off, N + 1); AL(c->d_species, NA); AL(c->d_iters, N);
+    AL(c->d_r, 3 * NA); AL(c->d_p, 3 * NA); AL(c->d_F, 3 * NA); AL(c->d_b, 3 * NA);
+    AL(c->d_qpop, NA); AL(c->d_C, (size_t)N * 36); AL(c->d_E, N); AL(c->d_Mc, N);
+    AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N);
+    AL(c->d_U, (size_t)M * N); AL(c->d_k, 3 * M); AL(c->d_phi, M); AL(c->d_R, 3 * N);
+    AL(c->d_omega, M); AL(c->d_lam, M); AL(c->d_iomega, M); AL(c->d_cos, M); AL(c->d_sin, M); AL(c->d_omc, M);
+    AL(c->d_q, M); AL(c->d_pq, M); AL(c->d_qs, M); AL(c->d_pqs, M); AL(c->d_D, M);
+    AL(c->d_W1, M); AL(c->d_W2, M); AL(c->d_emode, 4 * M);
+    const int fb = field_blocks(N);
+    AL(c->d_ekp, fb); AL(c->d_edp, fb); AL(c->d_hist, 8 * (size_t)c->opt.energy_history);
+    AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1);
+
+    cudaStream_t st = c->stream;
+    CK(cudaMemcpyAsync(c->d_sk, &hsk, sizeof(DevSK), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_off, sys->cell_offset, sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_species, sys->species, sizeof(int) * NA, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_r, sys->r, sizeof(double) * 3 * NA, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_p, sys->p, sizeof(double) * 3 * NA, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_mass, mass.data(), sizeof(double) * NA, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_imass, imass.data(), sizeof(double) * NA, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_R, R.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_k, md->k, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_phi, md->phi, sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_omega, md->omega, sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_lam, md->lambda, sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_iomega, iw.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_cos, cw.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_sin, sw.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_omc, omc.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(c->d_step, 0, sizeof(long long), st));
+    CK(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 8 * c->opt.energy_history, st));
+    CK(cudaMemsetAsync(c->d_q, 0, sizeof(double) * M, st));
+    CK(cudaMemsetAsync(c->d_pq, 0, sizeof(double) * M, st));
+    CK(launch_mode_functions(c->d_k, c->d_phi, c->d_R, M, N, c->d_U, st));
+
+    DftbArgs &d = c->da;
+    d.n_cells = N;
+    d.cell_list = nullptr;
+    d.cell_offset = c->d_off;
+    d.species = c->d_species;
+    d.r = c->d_r;
+    d.F = c->d_F;
+    d.b = c->d_b;
+    d.qpop = c->d_qpop;
+    d.Cwarm = c->d_C;
+    d.E_cell = c->d_E;
+    d.M_cell = c->d_Mc;
+    d.iters = c->d_iters;
+    d.status = c->d_status;
+    d.pol0 = c->pol[0];
+    d.pol1 = c->pol[1];
+    d.pol2 = c->pol[2];
+    d.scc_tol = c->opt.scc_tol;
+    d.beta = c->opt.mixing;
+    d.max_iter = c->opt.scc_max_iter;
+    d.have_warm = 0;
+    d.write_b = 1;
+
+    StepArgs &s = c->sa;
+    s.N = N; s.M = M; s.n_atoms = NA;
+    s.cell_offset = c->d_off; s.U = c->d_U; s.M_cell = c->d_Mc; s.E_cell = c->d_E;
+    s.inv_mass = c->d_imass; s.mass = c->d_mass; s.F = c->d_F; s.b = c->d_b; s.r = c->d_r; s.p = c->d_p;
+    s.omega = c->d_omega; s.lam = c->d_lam; s.inv_omega = c->d_iomega;
+    s.cos_h = c->d_cos; s.sin_h = c->d_sin; s.omc_h = c->d_omc;
+    s.q = c->d_q; s.pq = c->d_pq; s.q_sync = c->d_qs; s.pq_sync = c->d_pqs; s.D = c->d_D;
+    s.W1 = c->d_W1; s.W2 = c->d_W2; s.e_mode = c->d_emode; s.e_kin_part = c->d_ekp; s.e_dftb_part = c->d_edp;
+    s.done_counter = c->d_done; s.hist = c->d_hist; s.hist_cap = c->opt.energy_history;
+    s.step_counter = c->d_step; s.status = c->d_status; s.dt = c->opt.dt; s.tau = tau;
+    return CAVMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cavmd_default_options(cavmd_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->dt = 0.5 * 41.341373335;
+    o->precision = CAVMD_PREC_FP64;
+    o->charge_model = CAVMD_CHARGE_MULLIKEN;
+    o->born_interval = 3;
+    o->fd_step = 1e-3;
+    o->scc_tol = 1e-12;
+    o->scc_max_iter = 200;
+    o->mixing = 0.5;
+    o->splitting = CAVMD_SPLIT_PHOTON_EXACT;
+    o->photon_init = CAVMD_PHOTON_RELAXED;
+    o->graph_chunk = 50;
+    o->device = 0;
+    o->energy_history = 1024;
+}
+
+int cavmd_init(cavmd_ctx **out, const cavmd_system *sys, const cavmd_sk_tables *sk,
+               const cavmd_modes *md, const cavmd_options *opt) {
+    if (!out) return fail(nullptr, CAVMD_ERR_INVALID_ARG, "ctx pointer is NULL");
+    *out = nullptr;
+    int rc = validate(sys, sk, md, opt);
+    if (rc) return rc;
+    cavmd_ctx *c = new cavmd_ctx();
+    c->opt = *opt;
+    c->device = opt->device;
+    c->N = sys->n_cells;
+    c->n_atoms = sys->n_atoms;
+    c->M = md->n_modes;
+    c->h_off.assign(sys->cell_offset, sys->cell_offset + sys->n_cells + 1);
+    c->h_species.assign(sys->species, sys->species + sys->n_atoms);
+    for (int k = 0; k < 3; ++k) c->pol[k] = md->pol[k];
+    rc = build_context(c, sys, sk, md);
+    if (!rc) rc = initial_evaluation(c, true);
+    if (rc) {
+        g_init_error = c->err;
+        release(c);
+        return rc;
+    }
+    *out = c;
+    return CAVMD_OK;
+}
+
+int cavmd_step(cavmd_ctx *c, int64_t nsteps) {
+    if (!c) return fail(nullptr, CAVMD_ERR_INVALID_ARG, "NULL context");
+    if (nsteps < 0) return fail(c, CAVMD_ERR_INVALID_ARG, "nsteps < 0");
+    int rc = CAVMD_OK;
+    if (c->status_pending) {
+        CK(cudaEventSynchronize(c->status_ev));
+        c->status_pending = false;
+        const unsigned st = *c->h_status;
+        if (st) {
+            CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+            rc = status_to_code(c, st);
+        }
+    }
+    if (nsteps == 0) return rc;
+    CK(cudaSetDevice(c->device));
+    int64_t left = nsteps;
+    const int G = c->opt.graph_chunk;
+    if (G > 0 && !c->timing && left >= G) {
+        if (!c->graph) {
+            cudaGraph_t g;
+            CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_steps(c, G);
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+            if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch during graph capture");
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+            CK(cudaGraphInstantiate(&c->graph, g, 0));
+            cudaGraphDestroy(g);
+            c->graph_steps = G;
+        }
+        while (left >= c->graph_steps) {
+            CK(cudaGraphLaunch(c->graph, c->stream));
+            left -= c->graph_steps;
+        }
+    }
+    if (left > 0) {
+        cudaError_t e = enqueue_steps(c, left);
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    }
+    c->step += nsteps;
+    CK(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->status_ev, c->stream));
+    c->status_pending = true;
+    return rc;
+}
+
+int cavmd_observables(cavmd_ctx *c, cavmd_obs *o) {
+    if (!c || !o) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    int rc = sync_status(c);
+    double h[8];
+    const int slot = (int)(c->step % c->opt.energy_history);
+    CK(cudaMemcpy(h, c->d_hist + 8 * (size_t)slot, sizeof(h), cudaMemcpyDeviceToHost));
+    o->e_kin = h[0];
+    o->e_dftb = h[1];
+    o->e_photon = h[2];
+    o->e_coupling = h[3];
+    o->e_dse = h[4];
+    o->e_photon_free = h[5];
+    o->e_total = h[6];
+    o->temperature = 2.0 * h[0] / (3.0 * c->n_atoms * 3.166811563e-6);
+    o->step = c->step;
+    std::vector<int> it(c->N);
+    CK(cudaMemcpy(it.data(), c->d_iters, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
+    int mx = 0;
+    for (int v : it) mx = v > mx ? v : mx;
+    o->scc_iter_max = mx;
+    if (o->M) CK(cudaMemcpy(o->M, c->d_Mc, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
+    if (o->q) CK(cudaMemcpy(o->q, c->d_qs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+    if (o->p) CK(cudaMemcpy(o->p, c->d_pqs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+    if (o->D) CK(cudaMemcpy(o->D, c->d_D, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+    return rc;
+}
+
+int cavmd_energy_history(cavmd_ctx *c, double *out, int32_t n, int32_t *n_out) {
+    if (!c || !out || n < 0) return fail(c, CAVMD_ERR_INVALID_ARG, "bad argument");
+    int rc = sync_status(c);
+    const int64_t cap = c->opt.energy_history;
+    const int64_t avail = (c->step + 1 < cap) ? c->step + 1 : cap;
+    const int64_t cnt = n < avail ? n : avail;
+    std::vector<double> all(8 * (size_t)cap);
+    CK(cudaMemcpy(all.data(), c->d_hist, sizeof(double) * 8 * cap, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < cnt; ++i) {
+        const int64_t stp = c->step - cnt + 1 + i;
+        std::memcpy(out + 8 * i, all.data() + 8 * (stp % cap), 8 * sizeof(double));
+    }
+    if (n_out) *n_out = (int32_t)cnt;
+    return rc;
+}
+
+int cavmd_get_state(cavmd_ctx *c, cavmd_state *s) {
+    if (!c || !s) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    int rc = sync_status(c);
+    if (s->r) CK(cudaMemcpy(s->r, c->d_r, sizeof(double) * 3 * c->n_atoms, cudaMemcpyDeviceToHost));
+    if (s->p) CK(cudaMemcpy(s->p, c->d_p, sizeof(double) * 3 * c->n_atoms, cudaMemcpyDeviceToHost));
+    if (s->q) CK(cudaMemcpy(s->q, c->d_qs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+    if (s->pq) CK(cudaMemcpy(s->pq, c->d_pqs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+    s->step = c->step;
+    return rc;
+}
+
+int cavmd_set_state(cavmd_ctx *c, const cavmd_state *s) {
+    if (!c || !s || !s->r || !s->p || !s->q || !s->pq) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    int rc = sync_status(c);
+    if (rc) return rc;
+    for (int i = 0; i < 3 * c->n_atoms; ++i)
+        if (!std::isfinite(s->r[i]) || !std::isfinite(s->p[i])) return fail(c, CAVMD_ERR_INVALID_ARG, "non-finite state");
+    CK(cudaMemcpy(c->d_r, s->r, sizeof(double) * 3 * c->n_atoms, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_p, s->p, sizeof(double) * 3 * c->n_atoms, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_qs, s->q, sizeof(double) * c->M, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_pqs, s->pq, sizeof(double) * c->M, cudaMemcpyHostToDevice));
+    long long stp = s->step;
+    CK(cudaMemcpy(c->d_step, &stp, sizeof(long long), cudaMemcpyHostToDevice));
+    c->step = s->step;
+    return initial_evaluation(c, false);
+}
+
+int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
+    if (!c || !o) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    int rc = sync_status(c);
+    const size_t NA = c->n_atoms, N = c->N;
+    if (o->F_dftb) CK(cudaMemcpy(o->F_dftb, c->d_F, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
+    if (o->b) CK(cudaMemcpy(o->b, c->d_b, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
+    if (o->q_pop) CK(cudaMemcpy(o->q_pop, c->d_qpop, sizeof(double) * NA, cudaMemcpyDeviceToHost));
+    if (o->E_cell) CK(cudaMemcpy(o->E_cell, c->d_E, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    if (o->M) CK(cudaMemcpy(o->M, c->d_Mc, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    if (o->scc_iters) CK(cudaMemcpy(o->scc_iters, c->d_iters, sizeof(int) * N, cudaMemcpyDeviceToHost));
+    if (o->F_total) {
+        // instantaneous field with W_a = lambda_a (omega_a q_a - D_a), on the device
+        std::vector<double> q(c->M), D(c->M), w(c->M), lam(c->M), W(c->M);
+        CK(cudaMemcpy(q.data(), c->d_qs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(D.data(), c->d_D, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(w.data(), c->d_omega, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(lam.data(), c->d_lam, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+        for (int a = 0; a < c->M; ++a) W[a] = lam[a] * (w[a] * q[a] - D[a]);
+        CK(cudaMemcpy(c->d_W1, W.data(), sizeof(double) * c->M, cudaMemcpyHostToDevice));
+        CK(launch_field_only(c->d_U, c->d_W1, c->M, c->N, c->d_Einst, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::vector<double> E(N), F(3 * NA), b(3 * NA);
+        CK(cudaMemcpy(E.data(), c->d_Einst, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(F.data(), c->d_F, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(b.data(), c->d_b, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
+        for (size_t n = 0; n < N; ++n)
+            for (int i = c->h_off[n]; i < c->h_off[n + 1]; ++i)
+                for (int k = 0; k < 3; ++k) o->F_total[3 * i + k] = F[3 * i + k] + E[n] * b[3 * i + k];
+    }
+    return rc;
+}
+
+int cavmd_phase_times(cavmd_ctx *c, int32_t enable, double *ms, int64_t *cnt, int32_t reset) {
+    if (!c) return fail(nullptr, CAVMD_ERR_INVALID_ARG, "NULL context");
+    CK(cudaStreamSynchronize(c->stream));
+    collect_phase_times(c);
+    for (int i = 0; i < CAVMD_N_PHASES; ++i) {
+        if (ms) ms[i] = c->phase_ms[i];
+        if (cnt) cnt[i] = c->phase_cnt[i];
+        if (reset) { c->phase_ms[i] = 0; c->phase_cnt[i] = 0; }
+    }
+    c->timing = enable != 0;
+    return CAVMD_OK;
+}
+
+const char *cavmd_last_error(const cavmd_ctx *c) {
+    return c ? c->err.c_str() : g_init_error.c_str();
+}
+
+void cavmd_destroy(cavmd_ctx *c) { release(c); }
+
+size_t cavmd_struct_size(int32_t which) {
+    switch (which) {
+        case 0: return sizeof(cavmd_system);
+        case 1: return sizeof(cavmd_sk_tables);
+        case 2: return sizeof(cavmd_modes);
+        case 3: return sizeof(cavmd_options);
+        case 4: return sizeof(cavmd_obs);
+        case 5: return sizeof(cavmd_state);
+        case 6: return sizeof(cavmd_eval);
+        default: return 0;
+    }
+}
+
+}  // extern "C"

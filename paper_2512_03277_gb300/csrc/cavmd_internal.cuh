@@ -1,0 +1,122 @@
+// Internal declarations shared by the CUDA translation units of the cavity-MD library.
+// Nothing here is part of the public ABI (include/cavmd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cavmd.h"
+
+#define CAVMD_FULL_MASK 0xffffffffu
+
+// Device copy of the Slater-Koster set (kept in global memory, read through the L1 cache).
+struct DevSK {
+    double onsite[CAVMD_MAX_ELEM][2];
+    double hubbard[CAVMD_MAX_ELEM];
+    double zval[CAVMD_MAX_ELEM];
+    double h0[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][4][4];
+    double s[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][4][4];
+    double rep[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][2];
+    int norb[CAVMD_MAX_ELEM];
+    double r_cut, taper, inv_taper;
+};
+
+// Error bits OR-ed into the context's device status word by any kernel.
+enum {
+    ERRBIT_SCC_NOCONV = 1,
+    ERRBIT_S_NOT_PD = 2,
+    ERRBIT_ZERO_GAP = 4,
+    ERRBIT_NONFINITE = 8,
+    ERRBIT_TIMEOUT = 16,
+};
+
+// Arguments of one batched SCC-DFTB evaluation (cells of one composition).
+struct DftbArgs {
+    int n_cells;               // cells in this launch
+    const int *cell_list;      // [n_cells] cell ids, or NULL for 0..n_cells-1
+    const int *cell_offset;    // [N+1] first atom of each cell
+    const int *species;        // [n_atoms]
+    const double *r;           // [3 n_atoms]
+    double *F;                 // [3 n_atoms] out: -dE/dr
+    double *b;                 // [3 n_atoms] out: Mulliken b_j = Q_j pol (charge_model 0)
+    double *qpop;              // [n_atoms] in/out: Mulliken populations (warm start)
+    double *Cwarm;             // [n_cells_total][NORB*NORB] in/out eigenvectors (column-major)
+    double *E_cell;            // [N] out
+    double *M_cell;            // [N] out
+    int *iters;                // [N] out
+    unsigned *status;          // device error word
+    double pol0, pol1, pol2;
+    double scc_tol;
+    double beta;
+    int max_iter;
+    int have_warm;             // 1: Cwarm and qpop hold a previous solution
+    int write_b;               // 1: write Mulliken b
+};
+
+// Arguments of the coupling / integrator kernels.
+struct StepArgs {
+    int N, M, n_atoms;
+    const int *cell_offset;
+    const double *U;           // [M][N] u_a(R_n), row-major
+    const double *M_cell;      // [N]
+    const double *E_cell;      // [N]
+    const double *inv_mass;    // [n_atoms]
+    const double *mass;        // [n_atoms]
+    const double *F;           // [3 n_atoms]
+    const double *b;           // [3 n_atoms]
+    double *r, *p;             // [3 n_atoms]
+    // photons
+    const double *omega, *lam, *inv_omega;
+    const double *cos_h, *sin_h, *omc_h;   // cos(w tau), sin(w tau), (1 - cos(w tau)) / w, tau = dt/2
+    double *q, *pq;            // running photon state (mid-step when a first half-flow is applied)
+    double *q_sync, *pq_sync;  // photon state at the last full step
+    double *D;                 // [M]
+    double *W1, *W2;           // [M] field weights of the first / second half-flow
+    double *e_mode;            // [M][4] photon, coupling, dse, free-photon energy of each mode
+    double *e_kin_part;        // [n_blocks] partial kinetic energies
+    double *e_dftb_part;       // [n_blocks]
+    unsigned *done_counter;    // last-block counter of the field kernel
+    double *hist;              // [hist_cap][8] energy history
+    int hist_cap;
+    long long *step_counter;   // device step counter
+    unsigned *status;
+    double dt, tau;
+};
+
+// |x| < y for finite doubles and y > 0, by the ordering of the IEEE bit patterns: an integer
+// comparison that leaves the FP64 pipe free.
+__device__ __forceinline__ bool abs_lt(double x, double y) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) < __double_as_longlong(y);
+}
+
+// Total order key of a double (same order as the numeric value for non-NaN inputs).
+__device__ __forceinline__ long long order_key(double x) {
+    long long b = __double_as_longlong(x);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+// 1/sqrt(d) for d > 0 within FP64 rounding: single-precision seed, then two Newton-Raphson
+// steps y <- y (3 - d y^2) / 2, each of which doubles the number of correct bits (24 -> 48 -> 96).
+__device__ __forceinline__ double rsqrt_nr(double d) {
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    return y;
+}
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st);
+cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
+                                  double *U, cudaStream_t st);
+// forward contraction of M_cell into D plus the photon half-flows (flags below)
+enum { PH_FORWARD = 1, PH_SECOND = 2, PH_FIRST = 4, PH_INIT_RELAXED = 8, PH_INIT_ZERO = 16,
+       PH_ENERGY = 32 };
+cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st);
+// field on the cells with weights W2 (second half-flow kick) and/or W1 (first half-flow kick +
+// drift); always records the energies of the synchronised state when FLD_ENERGY is set
+enum { FLD_SECOND = 1, FLD_FIRST = 2, FLD_ENERGY = 4 };
+cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st);
+int field_blocks(int N);
+// instantaneous field E_n = sum_a u_a(R_n) W_a for a caller-supplied weight vector
+cudaError_t launch_field_only(const double *U, const double *W, int M, int N, double *E,
+                              cudaStream_t st);

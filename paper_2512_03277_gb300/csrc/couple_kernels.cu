@@ -1,0 +1,241 @@
+// Light-matter coupling and time-step kernels (FP64).
+//
+// With real modes u_a(R) = cos(k_a . R + phi_a) the k-space form of the paper's Hamiltonian
+// (Eq. hlm2) has photon energy sum_a 1/2 p_a^2 + 1/2 (omega_a q_a - D_a)^2 with
+// D_a = lambda_a sum_n u_a(R_n) M_n, the gather of the paper's Step 2 done as a reduction over
+// cells. The step is H_2(dt/2) - drift(dt) - H_2(dt/2), where H_2 = V + H_ph is solved exactly at
+// frozen nuclei: each mode turns about its displaced centre D_a / omega_a by omega_a tau (the
+// rotation of Eq. qknk) and every nucleus j of cell n receives the time-integrated force
+//     dp_j = tau F_j + E_n b_j,  E_n = sum_a u_a(R_n) W_a,
+//     W_a = lambda_a [y_a sin(omega_a tau) + p_a (1 - cos(omega_a tau)) / omega_a],  y_a = q_a - D_a/omega_a,
+// the k-space form of the nuclear coupling force of Eq. dpj integrated over the half step (the
+// scatter of the paper's Step 4).
+//
+// k_photon: one block per mode; the deterministic block reduction forms D_a from the cell
+//           dipoles, then one thread applies the half-flows of that mode and records its energy.
+// k_field:  each block owns 32 cells; its 8 warps split the mode sum, a fixed-order reduction
+//           combines them, then one thread per cell applies the kicks (and the drift). The last
+//           block to finish sums the per-block energy partials in block order (deterministic)
+//           and appends the energies of the synchronised state to the history ring.
+#include "cavmd_internal.cuh"
+
+namespace {
+
+constexpr int PH_THREADS = 256;
+constexpr int FLD_CELLS = 32;
+constexpr int FLD_SLICES = 8;
+
+__global__ void k_mode_functions(const double *__restrict__ k, const double *__restrict__ phi,
+                                 const double *__restrict__ R, int M, int N, double *__restrict__ U) {
+    const long long total = (long long)M * N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int a = (int)(t / N), n = (int)(t - (long long)a * N);
+        const double arg = k[3 * a] * R[3 * n] + k[3 * a + 1] * R[3 * n + 1] + k[3 * a + 2] * R[3 * n + 2] + phi[a];
+        U[t] = cos(arg);
+    }
+}
+
+__device__ __forceinline__ double block_sum_ordered(double v, double *red) {
+    // fixed-order tree: warp shuffles (xor pattern is the same on every launch), then warp sums
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CAVMD_FULL_MASK, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    return s;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {
+    __shared__ double red[PH_THREADS / 32];
+    const int al = blockIdx.x;
+    double D = 0.0;
+    if (flags & PH_FORWARD) {
+        const double *u = a.U + (size_t)al * a.N;
+        double s = 0.0;
+        for (int n = threadIdx.x; n < a.N; n += PH_THREADS) s = fma(u[n], a.M_cell[n], s);
+        s = block_sum_ordered(s, red);
+        if (threadIdx.x == 0) {
+            D = a.lam[al] * s;
+            a.D[al] = D;
+        }
+    } else if (threadIdx.x == 0) {
+        D = a.D[al];
+    }
+    if (threadIdx.x != 0) return;
+    const double w = a.omega[al], iw = a.inv_omega[al], lam = a.lam[al];
+    const double c = a.cos_h[al], s = a.sin_h[al], omc = a.omc_h[al];
+    const double cen = D * iw;
+    double qs, ps;
+    if (flags & PH_INIT_RELAXED) {
+        qs = cen;
+        ps = 0.0;
+    } else if (flags & PH_INIT_ZERO) {
+        qs = 0.0;
+        ps = 0.0;
+    } else if (flags & PH_SECOND) {
+        const double q = a.q[al], p = a.pq[al];
+        const double y = q - cen;
+        a.W2[al] = lam * fma(y, s, p * omc);
+        qs = cen + fma(y, c, p * s * iw);
+        ps = fma(p, c, -w * y * s);
+    } else {
+        qs = a.q_sync[al];
+        ps = a.pq_sync[al];
+    }
+    a.q_sync[al] = qs;
+    a.pq_sync[al] = ps;
+    if (flags & PH_ENERGY) {
+        const double x = fma(w, qs, -D);
+        double *e = a.e_mode + 4 * al;
+        e[0] = 0.5 * fma(ps, ps, x * x);
+        e[1] = -w * qs * D;
+        e[2] = 0.5 * D * D;
+        e[3] = 0.5 * fma(ps, ps, (w * qs) * (w * qs));
+    }
+    if (flags & PH_FIRST) {
+        const double y = qs - cen;
+        a.W1[al] = lam * fma(y, s, ps * omc);
+        a.q[al] = cen + fma(y, c, ps * s * iw);
+        a.pq[al] = fma(ps, c, -w * y * s);
+    } else {
+        a.q[al] = qs;
+        a.pq[al] = ps;
+    }
+}
+
+__global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs a, const int flags) {
+    __shared__ double red2[FLD_SLICES][FLD_CELLS];
+    __shared__ double red1[FLD_SLICES][FLD_CELLS];
+    __shared__ double ek[FLD_CELLS], ed[FLD_CELLS];
+    __shared__ bool last;
+    const int cl = threadIdx.x & (FLD_CELLS - 1);
+    const int sl = threadIdx.x / FLD_CELLS;
+    const int n = blockIdx.x * FLD_CELLS + cl;
+    double e2 = 0.0, e1 = 0.0;
+    if (n < a.N && (flags & (FLD_SECOND | FLD_FIRST))) {
+        const bool two = flags & FLD_SECOND, one = flags & FLD_FIRST;
+        for (int al = sl; al < a.M; al += FLD_SLICES) {
+            const double u = a.U[(size_t)al * a.N + n];
+            if (two) e2 = fma(u, __ldg(a.W2 + al), e2);
+            if (one) e1 = fma(u, __ldg(a.W1 + al), e1);
+        }
+    }
+    red2[sl][cl] = e2;
+    red1[sl][cl] = e1;
+    __syncthreads();
+    if (sl == 0) {
+        double kin = 0.0, edf = 0.0;
+        if (n < a.N) {
+            for (int s = 1; s < FLD_SLICES; ++s) {
+                e2 += red2[s][cl];
+                e1 += red1[s][cl];
+            }
+            const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
+            for (int j = j0; j < j1; ++j) {
+                const double im = a.inv_mass[j];
+                double pj[3];
+                for (int k = 0; k < 3; ++k) {
+                    pj[k] = a.p[3 * j + k];
+                    const double f = a.F[3 * j + k], bb = a.b[3 * j + k];
+                    if (flags & FLD_SECOND) pj[k] = fma(a.tau, f, fma(e2, bb, pj[k]));
+                    kin = fma(0.5 * im * pj[k], pj[k], kin);
+                    if (flags & FLD_FIRST) {
+                        pj[k] = fma(a.tau, f, fma(e1, bb, pj[k]));
+                        a.r[3 * j + k] = fma(a.dt * im, pj[k], a.r[3 * j + k]);
+                    }
+                    a.p[3 * j + k] = pj[k];
+                }
+            }
+            edf = a.E_cell[n];
+        }
+        ek[cl] = kin;
+        ed[cl] = edf;
+    }
+    if (!(flags & FLD_ENERGY)) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double k = 0.0, d = 0.0;
+        for (int i = 0; i < FLD_CELLS; ++i) {
+            k += ek[i];
+            d += ed[i];
+        }
+        a.e_kin_part[blockIdx.x] = k;
+        a.e_dftb_part[blockIdx.x] = d;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.done_counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double kin = 0.0, edf = 0.0;
+    for (int i = 0; i < (int)gridDim.x; ++i) {
+        kin += *((volatile double *)a.e_kin_part + i);
+        edf += *((volatile double *)a.e_dftb_part + i);
+    }
+    double eph = 0.0, ecp = 0.0, edse = 0.0, efree = 0.0;
+    for (int al = 0; al < a.M; ++al) {
+        eph += a.e_mode[4 * al + 0];
+        ecp += a.e_mode[4 * al + 1];
+        edse += a.e_mode[4 * al + 2];
+        efree += a.e_mode[4 * al + 3];
+    }
+    long long step = *a.step_counter;
+    if (flags & FLD_SECOND) {
+        step += 1;
+        *a.step_counter = step;
+    }
+    double *h = a.hist + 8 * (size_t)(step % a.hist_cap);
+    h[0] = kin;
+    h[1] = edf;
+    h[2] = eph;
+    h[3] = ecp;
+    h[4] = edse;
+    h[5] = efree;
+    h[6] = kin + edf + eph;
+    h[7] = (double)step;
+    if (!(isfinite(kin) && isfinite(edf) && isfinite(eph))) atomicOr(a.status, (unsigned)ERRBIT_NONFINITE);
+    *a.done_counter = 0u;
+}
+
+__global__ void k_field_only(const double *__restrict__ U, const double *__restrict__ W, int M, int N,
+                             double *__restrict__ E) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double e = 0.0;
+    for (int al = 0; al < M; ++al) e = fma(U[(size_t)al * N + n], W[al], e);
+    E[n] = e;
+}
+
+}  // namespace
+
+cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
+                                  double *U, cudaStream_t st) {
+    const long long total = (long long)M * N;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_mode_functions<<<blocks, 256, 0, st>>>(k, phi, R, M, N, U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st) {
+    k_photon<<<a.M, PH_THREADS, 0, st>>>(a, flags);
+    return cudaGetLastError();
+}
+
+int field_blocks(int N) { return (N + FLD_CELLS - 1) / FLD_CELLS; }
+
+cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st) {
+    k_field<<<field_blocks(a.N), FLD_CELLS * FLD_SLICES, 0, st>>>(a, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_only(const double *U, const double *W, int M, int N, double *E,
+                              cudaStream_t st) {
+    k_field_only<<<(N + 127) / 128, 128, 0, st>>>(U, W, M, N, E);
+    return cudaGetLastError();
+}

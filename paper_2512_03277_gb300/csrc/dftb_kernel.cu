@@ -1,0 +1,700 @@
+// Batched second-order SCC-DFTB of small molecules, one group of NORB lanes per molecule.
+//
+// The paper evaluates -grad V_n, mu_n and the Mulliken charges of every cell on the fly with
+// SCC-DFTB (section "Computational details"; Eq. dpj needs -grad V_n). This kernel evaluates
+// many independent cells of one composition at once:
+//
+//   H0, S from Slater-Koster tables  ->  warm-started S-orthonormal basis C (Cholesky of C^T S C)
+//   -> SCC loop: shifts eps_A = sum_B gamma_AB dq_B, H = H0 + 1/2 S o (eps_A + eps_B),
+//      A = C^T H C, cyclic Jacobi on A (rotations applied to A and C), aufbau occupation,
+//      P = 2 C_occ C_occ^T, Mulliken populations, Anderson-accelerated mixing
+//   -> energy, analytic gradient (P dH0 + (P (eps_A+eps_B)/2 - W) dS + dgamma + dE_rep),
+//      dipole M_n = pol . sum_A Q_A r_A and the Mulliken dipole derivative b_A = Q_A pol.
+//
+// Layout: lane j of a group owns column j of every NORB x NORB matrix, stored column-major in
+// the group's shared-memory slot with an odd leading dimension. All groups of a warp advance in
+// lock step (__syncwarp); a group whose charges have converged idles until the slowest group
+// of its warp is done. The FP64 pipe bounds this kernel on GB300, so auxiliary quantities that
+// only steer the iteration (rotation angles, mixing coefficients, convergence tests) are formed
+// in FP32 or by integer comparisons, while every quantity that enters the result (rotations
+// themselves, matrices, populations, energies, forces) is computed in FP64.
+#include "cavmd_internal.cuh"
+
+namespace {
+
+constexpr int NHIST = 3;          // Anderson history (current + 2 previous iterates)
+constexpr int MAX_SWEEPS = 24;    // bound on Jacobi sweeps per SCC iteration
+constexpr double JACOBI_TOL = 1e-15;   // off-diagonal magnitude treated as converged (Hartree)
+constexpr double MIN_GAP = 1e-3;       // closed-shell HOMO-LUMO threshold (Hartree)
+
+template <int NAT, int NORB>
+struct MolShared {
+    static constexpr int LD = (NORB % 2 == 0) ? NORB + 1 : NORB;   // odd column stride
+    static constexpr int NPAIR = NAT * (NAT - 1) / 2;
+    double S[NORB * LD];
+    double H0[NORB * LD];
+    double A[NORB * LD];
+    double C[NORB * LD];
+    double Y[NORB * LD];
+    double P[NORB * LD];
+    double pos[NAT][3];
+    double gam[NAT][NAT];
+    double zv[NAT];
+    double q[NAT];
+    double qout[NAT];
+    double shift[NAT];
+    double hq[NHIST][NAT];
+    double hf[NHIST][NAT];
+    double red[NORB];
+    double cs[NORB / 2 + 1][2];
+    double invd[NORB];
+    double gpair[NPAIR > 0 ? NPAIR : 1][3];
+    double epair[NPAIR > 0 ? NPAIR : 1];
+    int occ_list[NORB];
+    int orb_atom[NORB];
+    int atom_off[NAT + 1];
+    int spec[NAT];
+    int pa[NPAIR > 0 ? NPAIR : 1];
+    int pb[NPAIR > 0 ? NPAIR : 1];
+    int flag;
+    int conv;
+    int iters;
+    int nocc;
+};
+
+__device__ __forceinline__ void radial(const double *par, double r, const DevSK &sk, double &v,
+                                       double &dv) {
+    const double a = par[0], b = par[1], c1 = par[2], c2 = par[3];
+    const double e = a * exp(-b * r);
+    const double poly = fma(fma(c2, r, c1), r, 1.0);
+    const double dpoly = fma(2.0 * c2, r, c1);
+    const double x = (r - (sk.r_cut - sk.taper)) * sk.inv_taper;
+    double f = 1.0, df = 0.0;
+    if (x > 0.0) {
+        if (x < 1.0) {
+            double sn, cn;
+            sincospi(x, &sn, &cn);
+            f = 0.5 * (1.0 + cn);
+            df = -0.5 * 3.141592653589793 * sk.inv_taper * sn;
+        } else {
+            f = 0.0;
+        }
+    }
+    v = e * poly * f;
+    dv = e * (fma(-b * poly, f, dpoly * f) + poly * df);
+}
+
+// Jacobi round-robin schedule for even n: in round r (0..n-2) index n-1 meets r and index j
+// meets (2r - j) mod (n-1). Returns the partner of j and the pair slot (0 = the pair with n-1).
+__device__ __forceinline__ int rr_partner(int j, int r, int n, int &slot) {
+    const int m = n - 1;
+    if (j == m) { slot = 0; return r; }
+    if (j == r) { slot = 0; return m; }
+    const int dlt = (j - r + m) % m;
+    slot = min(dlt, m - dlt);
+    return (r - dlt + m) % m;
+}
+
+__device__ __forceinline__ void rr_pair(int k, int r, int n, int &p, int &q) {
+    const int m = n - 1;
+    if (k == 0) { p = r; q = m; return; }
+    const int x = (r + k) % m, y = (r - k + m) % m;
+    p = min(x, y);
+    q = max(x, y);
+}
+
+// Rotation (c, s) that annihilates a_pq: tan(phi) = t from the FP32 quadratic, then (c, s) made
+// orthonormal in FP64 by two Newton steps on 1/sqrt(c^2 + s^2).
+__device__ __forceinline__ void jacobi_cs(double app, double aqq, double apq, double &c, double &s) {
+    const float d = (float)(aqq - app);
+    const float o = 2.0f * (float)apq;
+    float t = 0.0f;
+    if (o != 0.0f) t = o / (d + copysignf(sqrtf(fmaf(d, d, o * o)), d));
+    const float cf = rsqrtf(fmaf(t, t, 1.0f));
+    c = (double)cf;
+    s = (double)(t * cf);
+    for (int it = 0; it < 2; ++it) {
+        const double nrm = fma(c, c, s * s);
+        const double f = fma(-0.5, nrm, 1.5);
+        c *= f;
+        s *= f;
+    }
+}
+
+template <int NAT, int NORB>
+__global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a) {
+    const DevSK &sk = *skp;
+    using SM = MolShared<NAT, NORB>;
+    constexpr int LD = SM::LD;
+    constexpr int GPW = 32 / NORB;
+    constexpr int NPAIR = SM::NPAIR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int g = lane / NORB;
+    const int j = lane - g * NORB;
+    const bool act = g < GPW;
+    SM &m = reinterpret_cast<SM *>(smem_raw)[warp * GPW + (act ? g : 0)];
+    const int idx = (blockIdx.x * wpb + warp) * GPW + g;
+    const bool valid = act && idx < a.n_cells;
+    const int cidx = min(idx, a.n_cells - 1);
+    const int cell = a.cell_list ? a.cell_list[cidx] : cidx;
+    const int a0 = a.cell_offset[cell];
+
+    // ---------------------------------------------------------------- load geometry, layout
+    if (act && j < NAT) {
+        m.spec[j] = a.species[a0 + j];
+        m.pos[j][0] = a.r[3 * (a0 + j) + 0];
+        m.pos[j][1] = a.r[3 * (a0 + j) + 1];
+        m.pos[j][2] = a.r[3 * (a0 + j) + 2];
+    }
+    __syncwarp();
+    if (act && j == 0) {
+        int o = 0;
+        double nel = 0.0;
+        for (int at = 0; at < NAT; ++at) {
+            m.atom_off[at] = o;
+            const int no = sk.norb[m.spec[at]];
+            for (int k = 0; k < no; ++k) m.orb_atom[o + k] = at;
+            o += no;
+            m.zv[at] = sk.zval[m.spec[at]];
+            nel += m.zv[at];
+        }
+        m.atom_off[NAT] = o;
+        m.nocc = (int)(nel * 0.5f + 0.25f);
+        int pi = 0;
+        for (int x = 0; x < NAT; ++x)
+            for (int y = x + 1; y < NAT; ++y) { m.pa[pi] = x; m.pb[pi] = y; ++pi; }
+        m.flag = 0;
+        m.conv = 0;
+        m.iters = 0;
+    }
+    __syncwarp();
+
+    // ---------------------------------------------------------------- H0, S, gamma
+    if (act) {
+        const int at = m.orb_atom[j];
+        const int e = m.spec[at];
+        const double eps = (j == m.atom_off[at]) ? sk.onsite[e][0] : sk.onsite[e][1];
+        for (int i = 0; i < NORB; ++i) {
+            m.S[j * LD + i] = (i == j) ? 1.0 : 0.0;
+            m.H0[j * LD + i] = (i == j) ? eps : 0.0;
+        }
+    }
+    __syncwarp();
+    if (act) {
+        for (int pi = j; pi < NPAIR; pi += NORB) {
+            const int A = m.pa[pi], B = m.pb[pi];
+            const int eA = m.spec[A], eB = m.spec[B];
+            const int oA = m.atom_off[A], oB = m.atom_off[B];
+            const int na = sk.norb[eA], nb = sk.norb[eB];
+            const double dx = m.pos[B][0] - m.pos[A][0];
+            const double dy = m.pos[B][1] - m.pos[A][1];
+            const double dz = m.pos[B][2] - m.pos[A][2];
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const double ir = rsqrt_nr(r2);
+            const double r = r2 * ir;
+            const double ev[3] = {dx * ir, dy * ir, dz * ir};
+            for (int t = 0; t < 2; ++t) {
+                const double (*tab)[CAVMD_MAX_ELEM][4][4] = t == 0 ? sk.h0 : sk.s;
+                double *X = t == 0 ? m.H0 : m.S;
+                double v, dv;
+                radial(tab[eA][eB][CAVMD_SK_SS], r, sk, v, dv);
+                X[oB * LD + oA] = v;
+                X[oA * LD + oB] = v;
+                if (nb == 4) {
+                    radial(tab[eA][eB][CAVMD_SK_SP], r, sk, v, dv);
+                    for (int i = 0; i < 3; ++i) {
+                        X[(oB + 1 + i) * LD + oA] = ev[i] * v;
+                        X[oA * LD + oB + 1 + i] = ev[i] * v;
+                    }
+                }
+                if (na == 4) {
+                    radial(tab[eB][eA][CAVMD_SK_SP], r, sk, v, dv);
+                    for (int i = 0; i < 3; ++i) {
+                        X[oB * LD + oA + 1 + i] = -ev[i] * v;
+                        X[(oA + 1 + i) * LD + oB] = -ev[i] * v;
+                    }
+                }
+                if (na == 4 && nb == 4) {
+                    double vs, vp;
+                    radial(tab[eA][eB][CAVMD_SK_PPS], r, sk, vs, dv);
+                    radial(tab[eA][eB][CAVMD_SK_PPP], r, sk, vp, dv);
+                    const double dl = vs - vp;
+                    for (int i = 0; i < 3; ++i)
+                        for (int k = 0; k < 3; ++k) {
+                            const double val = fma(ev[i] * ev[k], dl, (i == k) ? vp : 0.0);
+                            X[(oB + 1 + k) * LD + oA + 1 + i] = val;
+                            X[(oA + 1 + i) * LD + oB + 1 + k] = val;
+                        }
+                }
+            }
+        }
+        if (j < NAT) {
+            for (int k = 0; k < NAT; ++k) {
+                const double Ua = sk.hubbard[m.spec[j]], Ub = sk.hubbard[m.spec[k]];
+                if (k == j) {
+                    m.gam[j][k] = Ua;
+                } else {
+                    const double dx = m.pos[k][0] - m.pos[j][0];
+                    const double dy = m.pos[k][1] - m.pos[j][1];
+                    const double dz = m.pos[k][2] - m.pos[j][2];
+                    const double cc = 2.0 / (Ua + Ub);
+                    m.gam[j][k] = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, cc * cc))));
+                }
+            }
+        }
+    }
+    __syncwarp();
+
+    // ---------------------------------------------------------------- warm-started S-orthonormal basis
+    if (act) {
+        if (a.have_warm) {
+            const double *cw = a.Cwarm + (size_t)cell * NORB * NORB;
+            for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = cw[j * NORB + i];
+            if (j < NAT) m.q[j] = a.qpop[a0 + j];
+        } else {
+            for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = (i == j) ? 1.0 : 0.0;
+            if (j < NAT) m.q[j] = m.zv[j];
+        }
+    }
+    __syncwarp();
+    // G = C^T S C  (in A)
+    if (act) {
+        if (a.have_warm) {
+            double y[NORB];
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) y[i] = 0.0;
+            for (int k = 0; k < NORB; ++k) {
+                const double ckj = m.C[j * LD + k];
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) y[i] = fma(m.S[k * LD + i], ckj, y[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) m.Y[j * LD + i] = y[i];
+        }
+    }
+    __syncwarp();
+    if (act) {
+        if (a.have_warm) {
+            for (int i = 0; i < NORB; ++i) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < NORB; ++k) s = fma(m.C[i * LD + k], m.Y[j * LD + k], s);
+                m.A[j * LD + i] = s;
+            }
+        } else {
+            for (int i = 0; i < NORB; ++i) m.A[j * LD + i] = m.S[j * LD + i];
+        }
+    }
+    __syncwarp();
+    // Cholesky G = L L^T, right-looking, lane = column (L in the lower triangle of A)
+    for (int k = 0; k < NORB; ++k) {
+        if (act && j == k) {
+            double d = m.A[k * LD + k];
+            if (!(d > 1e-300)) {
+                m.flag |= ERRBIT_S_NOT_PD;
+                d = 1.0;
+            }
+            const double y = rsqrt_nr(d);
+            m.invd[k] = y;
+            m.A[k * LD + k] = d * y;
+            for (int i = k + 1; i < NORB; ++i) m.A[k * LD + i] *= y;
+        }
+        __syncwarp();
+        if (act && j > k) {
+            const double ljk = m.A[k * LD + j];
+            for (int i = j; i < NORB; ++i) m.A[j * LD + i] = fma(-m.A[k * LD + i], ljk, m.A[j * LD + i]);
+        }
+        __syncwarp();
+    }
+    // C <- C L^-T (lane = row)
+    if (act) {
+        const int i = j;
+        for (int c = 0; c < NORB; ++c) {
+            double x = m.C[c * LD + i];
+            for (int k = 0; k < c; ++k) x = fma(-m.C[k * LD + i], m.A[k * LD + c], x);
+            m.C[c * LD + i] = x * m.invd[c];
+        }
+    }
+    __syncwarp();
+
+    // ---------------------------------------------------------------- SCC loop
+    int it = 0;
+    for (it = 1; it <= a.max_iter; ++it) {
+        const bool work = act && !m.conv;
+        if (work && j < NAT) {
+            double sh = 0.0;
+            for (int k = 0; k < NAT; ++k) sh = fma(m.gam[j][k], m.q[k] - m.zv[k], sh);
+            m.shift[j] = sh;
+        }
+        __syncwarp();
+        if (work) {   // H column j into A
+            const double shj = m.shift[m.orb_atom[j]];
+            for (int i = 0; i < NORB; ++i)
+                m.A[j * LD + i] = fma(0.5 * m.S[j * LD + i], m.shift[m.orb_atom[i]] + shj, m.H0[j * LD + i]);
+        }
+        __syncwarp();
+        if (work) {   // Y = H C
+            double y[NORB];
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) y[i] = 0.0;
+            for (int k = 0; k < NORB; ++k) {
+                const double ckj = m.C[j * LD + k];
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) y[i] = fma(m.A[k * LD + i], ckj, y[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) m.Y[j * LD + i] = y[i];
+        }
+        __syncwarp();
+        if (work) {   // A = C^T Y
+            double y[NORB];
+            for (int i = 0; i < NORB; ++i) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < NORB; ++k) s = fma(m.C[i * LD + k], m.Y[j * LD + k], s);
+                y[i] = s;
+            }
+            for (int i = 0; i < NORB; ++i) m.A[j * LD + i] = y[i];
+        }
+        __syncwarp();
+
+        // Jacobi sweeps on A, rotations accumulated into C
+        for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+            bool small = true;
+            if (work) {
+                for (int i = 0; i < NORB; ++i)
+                    if (i != j && !abs_lt(m.A[j * LD + i], JACOBI_TOL)) small = false;
+            }
+            if (__all_sync(CAVMD_FULL_MASK, small)) break;
+            if (sweep == MAX_SWEEPS - 1) {
+                if (work && !small) m.flag |= ERRBIT_TIMEOUT;
+                break;
+            }
+            for (int rd = 0; rd < NORB - 1; ++rd) {
+                int slot = 0;
+                const int pj = rr_partner(j, rd, NORB, slot);
+                const int p = min(j, pj), q = max(j, pj);
+                double c = 1.0, s = 0.0;
+                double na[NORB], nc[NORB];
+                if (work) {
+                    jacobi_cs(m.A[p * LD + p], m.A[q * LD + q], m.A[q * LD + p], c, s);
+                    const double cp = (j == p) ? c : s;       // new col j = cp * col p + cq * col q
+                    const double cq = (j == p) ? -s : c;
+#pragma unroll
+                    for (int i = 0; i < NORB; ++i) {
+                        na[i] = fma(cp, m.A[p * LD + i], cq * m.A[q * LD + i]);
+                        nc[i] = fma(cp, m.C[p * LD + i], cq * m.C[q * LD + i]);
+                    }
+                }
+                __syncwarp();
+                if (work) {
+#pragma unroll
+                    for (int i = 0; i < NORB; ++i) {
+                        m.A[j * LD + i] = na[i];
+                        m.C[j * LD + i] = nc[i];
+                    }
+                    if (j == p) {
+                        m.cs[slot][0] = c;
+                        m.cs[slot][1] = s;
+                    }
+                }
+                __syncwarp();
+                if (work) {
+#pragma unroll
+                    for (int k = 0; k < NORB / 2; ++k) {
+                        int pk, qk;
+                        rr_pair(k, rd, NORB, pk, qk);
+                        const double ck = m.cs[k][0], sk_ = m.cs[k][1];
+                        const double x = m.A[j * LD + pk], y = m.A[j * LD + qk];
+                        m.A[j * LD + pk] = fma(ck, x, -sk_ * y);
+                        m.A[j * LD + qk] = fma(sk_, x, ck * y);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+
+        // aufbau occupation: the nocc lowest eigenvalues
+        if (work) {
+            const long long kj = order_key(m.A[j * LD + j]);
+            int rank = 0;
+            for (int i = 0; i < NORB; ++i) {
+                const long long ki = order_key(m.A[i * LD + i]);
+                rank += (ki < kj) || (ki == kj && i < j);
+            }
+            if (rank < m.nocc) m.occ_list[rank] = j;
+        }
+        __syncwarp();
+        if (work) {   // P = 2 C_occ C_occ^T, column j, and (P S)_jj
+            double pc[NORB];
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) pc[i] = 0.0;
+            for (int o = 0; o < m.nocc; ++o) {
+                const int col = m.occ_list[o];
+                const double w = 2.0 * m.C[col * LD + j];
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) pc[i] = fma(w, m.C[col * LD + i], pc[i]);
+            }
+            double qo = 0.0;
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) {
+                m.P[j * LD + i] = pc[i];
+                qo = fma(pc[i], m.S[j * LD + i], qo);
+            }
+            m.red[j] = qo;
+        }
+        __syncwarp();
+        const int hs = (it - 1) % NHIST;
+        if (work && j < NAT) {
+            double qa = 0.0;
+            for (int o = m.atom_off[j]; o < m.atom_off[j + 1]; ++o) qa += m.red[o];
+            m.qout[j] = qa;
+            m.hq[hs][j] = m.q[j];
+            m.hf[hs][j] = qa - m.q[j];
+        }
+        __syncwarp();
+        if (work) {
+            // convergence test and Anderson coefficients (FP32: they only steer the iteration)
+            bool conv = true;
+            for (int at = 0; at < NAT; ++at)
+                if (!abs_lt(m.hf[hs][at], a.scc_tol)) conv = false;
+            float th1 = 0.0f, th2 = 0.0f;
+            const int h = min(it, NHIST);
+            if (!conv && h >= 2) {
+                const int h1 = (hs + NHIST - 1) % NHIST, h2 = (hs + NHIST - 2) % NHIST;
+                float a11 = 0.f, a12 = 0.f, a22 = 0.f, b1 = 0.f, b2 = 0.f;
+                for (int at = 0; at < NAT; ++at) {
+                    const float f0 = (float)m.hf[hs][at];
+                    const float d1 = (float)(m.hf[h1][at] - m.hf[hs][at]);
+                    const float d2 = h >= 3 ? (float)(m.hf[h2][at] - m.hf[hs][at]) : 0.f;
+                    a11 = fmaf(d1, d1, a11);
+                    a12 = fmaf(d1, d2, a12);
+                    a22 = fmaf(d2, d2, a22);
+                    b1 = fmaf(-d1, f0, b1);
+                    b2 = fmaf(-d2, f0, b2);
+                }
+                const float det = a11 * a22 - a12 * a12;
+                if (h >= 3 && det > 1e-6f * a11 * a22 && det > 0.f) {
+                    th1 = (b1 * a22 - b2 * a12) / det;
+                    th2 = (a11 * b2 - a12 * b1) / det;
+                } else if (a11 > 0.f) {
+                    th1 = b1 / a11;
+                }
+                if (!(fabsf(th1) < 50.f) || !(fabsf(th2) < 50.f)) { th1 = 0.f; th2 = 0.f; }
+            }
+            if (j < NAT) {
+                if (conv) {
+                    m.q[j] = m.qout[j];
+                } else {
+                    const int h1 = (hs + NHIST - 1) % NHIST, h2 = (hs + NHIST - 2) % NHIST;
+                    const double t1 = th1, t2 = th2;
+                    const double q0 = m.hq[hs][j], f0 = m.hf[hs][j];
+                    double qb = q0, fb = f0;
+                    if (h >= 2) { qb = fma(t1, m.hq[h1][j] - q0, qb); fb = fma(t1, m.hf[h1][j] - f0, fb); }
+                    if (h >= 3) { qb = fma(t2, m.hq[h2][j] - q0, qb); fb = fma(t2, m.hf[h2][j] - f0, fb); }
+                    m.q[j] = fma(a.beta, fb, qb);
+                }
+            }
+            if (j == 0 && conv) {
+                m.conv = 1;
+                m.iters = it;
+            }
+        }
+        __syncwarp();
+        if (__all_sync(CAVMD_FULL_MASK, !act || m.conv)) break;
+    }
+    if (act && j == 0 && !m.conv) {
+        m.flag |= ERRBIT_SCC_NOCONV;
+        m.iters = a.max_iter;
+    }
+    __syncwarp();
+
+    // ---------------------------------------------------------------- energy, forces, dipole
+    if (act && j < NAT) {
+        double sh = 0.0;
+        for (int k = 0; k < NAT; ++k) sh = fma(m.gam[j][k], m.q[k] - m.zv[k], sh);
+        m.shift[j] = sh;
+    }
+    __syncwarp();
+    if (act) {   // W (energy-weighted density) into Y, band energy partial, HOMO-LUMO gap
+        double wc[NORB];
+#pragma unroll
+        for (int i = 0; i < NORB; ++i) wc[i] = 0.0;
+        for (int o = 0; o < m.nocc; ++o) {
+            const int col = m.occ_list[o];
+            const double w = 2.0 * m.A[col * LD + col] * m.C[col * LD + j];
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) wc[i] = fma(w, m.C[col * LD + i], wc[i]);
+        }
+        double eb = 0.0;
+#pragma unroll
+        for (int i = 0; i < NORB; ++i) {
+            m.Y[j * LD + i] = wc[i];
+            eb = fma(m.P[j * LD + i], m.H0[j * LD + i], eb);
+        }
+        m.red[j] = eb;
+        if (j == 0 && m.nocc < NORB) {
+            double homo = -1e300, lumo = 1e300;
+            for (int i = 0; i < NORB; ++i) {
+                bool oc = false;
+                for (int o = 0; o < m.nocc; ++o) oc |= (m.occ_list[o] == i);
+                const double ei = m.A[i * LD + i];
+                if (oc) homo = fmax(homo, ei); else lumo = fmin(lumo, ei);
+            }
+            if (!(lumo - homo > MIN_GAP)) m.flag |= ERRBIT_ZERO_GAP;
+        }
+    }
+    __syncwarp();
+    if (act) {
+        for (int pi = j; pi < NPAIR; pi += NORB) {
+            const int A = m.pa[pi], B = m.pb[pi];
+            const int eA = m.spec[A], eB = m.spec[B];
+            const int oA = m.atom_off[A], oB = m.atom_off[B];
+            const int na = sk.norb[eA], nb = sk.norb[eB];
+            const double dx = m.pos[B][0] - m.pos[A][0];
+            const double dy = m.pos[B][1] - m.pos[A][1];
+            const double dz = m.pos[B][2] - m.pos[A][2];
+            const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            const double ir = rsqrt_nr(r2);
+            const double r = r2 * ir;
+            const double e[3] = {dx * ir, dy * ir, dz * ir};
+            const double hshift = 0.5 * (m.shift[A] + m.shift[B]);
+            double gk[3] = {0.0, 0.0, 0.0};
+            for (int t = 0; t < 2; ++t) {
+                const double (*tab)[CAVMD_MAX_ELEM][4][4] = t == 0 ? sk.h0 : sk.s;
+                // weights of the (A, B) block: P for H0, P (eps_A + eps_B)/2 - W for S
+                auto wt = [&](int mu, int nu) -> double {
+                    const double pv = m.P[nu * LD + mu];
+                    return t == 0 ? pv : fma(pv, hshift, -m.Y[nu * LD + mu]);
+                };
+                double v, dv;
+                radial(tab[eA][eB][CAVMD_SK_SS], r, sk, v, dv);
+                {
+                    const double w = wt(oA, oB) * dv;
+                    for (int k = 0; k < 3; ++k) gk[k] = fma(w, e[k], gk[k]);
+                }
+                if (nb == 4) {
+                    radial(tab[eA][eB][CAVMD_SK_SP], r, sk, v, dv);
+                    double w[3], we = 0.0;
+                    for (int i = 0; i < 3; ++i) { w[i] = wt(oA, oB + 1 + i); we = fma(w[i], e[i], we); }
+                    for (int k = 0; k < 3; ++k)
+                        gk[k] += fma(w[k] - we * e[k], v * ir, we * e[k] * dv);
+                }
+                if (na == 4) {
+                    radial(tab[eB][eA][CAVMD_SK_SP], r, sk, v, dv);
+                    double w[3], we = 0.0;
+                    for (int i = 0; i < 3; ++i) { w[i] = wt(oA + 1 + i, oB); we = fma(w[i], e[i], we); }
+                    for (int k = 0; k < 3; ++k)
+                        gk[k] -= fma(w[k] - we * e[k], v * ir, we * e[k] * dv);
+                }
+                if (na == 4 && nb == 4) {
+                    double vs, dvs, vp, dvp;
+                    radial(tab[eA][eB][CAVMD_SK_PPS], r, sk, vs, dvs);
+                    radial(tab[eA][eB][CAVMD_SK_PPP], r, sk, vp, dvp);
+                    double Wm[3][3], We[3] = {0, 0, 0}, WTe[3] = {0, 0, 0}, tr = 0.0;
+                    for (int i = 0; i < 3; ++i)
+                        for (int k = 0; k < 3; ++k) Wm[i][k] = wt(oA + 1 + i, oB + 1 + k);
+                    for (int i = 0; i < 3; ++i) {
+                        tr += Wm[i][i];
+                        for (int k = 0; k < 3; ++k) {
+                            We[i] = fma(Wm[i][k], e[k], We[i]);
+                            WTe[k] = fma(Wm[i][k], e[i], WTe[k]);
+                        }
+                    }
+                    double eWe = 0.0;
+                    for (int i = 0; i < 3; ++i) eWe = fma(e[i], We[i], eWe);
+                    const double dl = vs - vp, ddl = dvs - dvp;
+                    for (int k = 0; k < 3; ++k)
+                        gk[k] += (We[k] + WTe[k] - 2.0 * eWe * e[k]) * dl * ir + eWe * e[k] * ddl +
+                                 tr * e[k] * dvp;
+                }
+            }
+            for (int k = 0; k < 3; ++k) gk[k] *= 2.0;
+            // second-order charge term and pair repulsion
+            const double Ua = sk.hubbard[eA], Ub = sk.hubbard[eB];
+            const double cc = 2.0 / (Ua + Ub);
+            const double gi = rsqrt_nr(fma(r, r, cc * cc));
+            const double dgam = -r * gi * gi * gi;
+            const double qq = (m.q[A] - m.zv[A]) * (m.q[B] - m.zv[B]) * dgam;
+            const double arep = sk.rep[eA][eB][0], brep = sk.rep[eA][eB][1];
+            double erep = 0.0, derep = 0.0;
+            if (arep != 0.0) {
+                const double vr = arep * exp(-brep * r);
+                const double x = (r - (sk.r_cut - sk.taper)) * sk.inv_taper;
+                double f = 1.0, df = 0.0;
+                if (x > 0.0) {
+                    if (x < 1.0) {
+                        double sn, cn;
+                        sincospi(x, &sn, &cn);
+                        f = 0.5 * (1.0 + cn);
+                        df = -0.5 * 3.141592653589793 * sk.inv_taper * sn;
+                    } else {
+                        f = 0.0;
+                    }
+                }
+                erep = vr * f;
+                derep = vr * (df - brep * f);
+            }
+            for (int k = 0; k < 3; ++k) m.gpair[pi][k] = gk[k] + (qq + derep) * e[k];
+            m.epair[pi] = erep;
+        }
+    }
+    __syncwarp();
+    if (valid && j < NAT) {
+        double f[3] = {0.0, 0.0, 0.0};
+        for (int pi = 0; pi < NPAIR; ++pi) {
+            const double sg = (m.pb[pi] == j) ? -1.0 : ((m.pa[pi] == j) ? 1.0 : 0.0);
+            for (int k = 0; k < 3; ++k) f[k] = fma(sg, m.gpair[pi][k], f[k]);
+        }
+        const int at = a0 + j;
+        for (int k = 0; k < 3; ++k) a.F[3 * at + k] = f[k];
+        a.qpop[at] = m.q[j];
+        if (a.write_b) {
+            const double Q = m.zv[j] - m.q[j];
+            a.b[3 * at + 0] = Q * a.pol0;
+            a.b[3 * at + 1] = Q * a.pol1;
+            a.b[3 * at + 2] = Q * a.pol2;
+        }
+    }
+    if (valid) {
+        double *cw = a.Cwarm + (size_t)cell * NORB * NORB;
+        for (int i = 0; i < NORB; ++i) cw[j * NORB + i] = m.C[j * LD + i];
+    }
+    if (valid && j == 0) {
+        double E = 0.0;
+        for (int i = 0; i < NORB; ++i) E += m.red[i];
+        double e2 = 0.0;
+        for (int x = 0; x < NAT; ++x)
+            for (int y = 0; y < NAT; ++y)
+                e2 = fma(m.gam[x][y] * (m.q[x] - m.zv[x]), m.q[y] - m.zv[y], e2);
+        E = fma(0.5, e2, E);
+        for (int pi = 0; pi < NPAIR; ++pi) E += m.epair[pi];
+        double mu[3] = {0.0, 0.0, 0.0};
+        for (int at = 0; at < NAT; ++at) {
+            const double Q = m.zv[at] - m.q[at];
+            for (int k = 0; k < 3; ++k) mu[k] = fma(Q, m.pos[at][k] - m.pos[0][k], mu[k]);
+        }
+        a.E_cell[cell] = E;
+        a.M_cell[cell] = fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
+        a.iters[cell] = m.iters;
+        if (m.flag) atomicOr(a.status, (unsigned)m.flag);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_dftb_water(const DevSK *sk, const DftbArgs &a, cudaStream_t st) {
+    constexpr int NAT = 3, NORB = 6;
+    using SM = MolShared<NAT, NORB>;
+    const int threads = 64;
+    const int per_block = (threads / 32) * (32 / NORB);
+    const int blocks = (a.n_cells + per_block - 1) / per_block;
+    const size_t smem = sizeof(SM) * (threads / 32) * (32 / NORB);
+    if (a.n_cells <= 0) return cudaSuccess;
+    dftb_kernel<NAT, NORB><<<blocks, threads, smem, st>>>(sk, a);
+    return cudaGetLastError();
+}

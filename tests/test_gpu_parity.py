@@ -1,0 +1,165 @@
+"""GPU (C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP64 mode): forces 1e-9 relative to the largest force, Mulliken populations and
+dipoles 1e-10 absolute, cell energies 1e-10 absolute. Both sides converge the charges to a
+residual below 1e-12, which bounds the difference of the converged fixed points well inside
+these limits; the remaining differences are rounding in 6x6 FP64 linear algebra.
+"""
+import numpy as np
+import pytest
+
+import cavmd_synth as cs
+from oracle import cavity as OC
+
+pytestmark = pytest.mark.gpu
+
+F_REL, Q_ABS, E_ABS = 1e-9, 1e-10, 1e-10
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2512_03277_gb300 import build
+    build.build()
+    import paper_2512_03277_gb300 as P
+    P.load_library()
+    return P
+
+
+def _oracle(w, **kw):
+    sy, mo, pa = w["system"], w["modes"], w["params"]
+    mat = OC.DFTBMatter(pa, sy, **kw)
+    md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
+    return mat, md
+
+
+def _ctx(P, w, **opt):
+    o = P.default_options()
+    for k, v in opt.items():
+        setattr(o, k, v)
+    return P.Context(w["system"], w["params"], w["modes"], o)
+
+
+def _check_eval(ev, mat, md):
+    ref = md.out
+    fs = np.abs(ref["F"]).max()
+    np.testing.assert_allclose(ev["F_dftb"], ref["F"], rtol=0, atol=F_REL * fs)
+    np.testing.assert_allclose(ev["q_pop"], mat.q, rtol=0, atol=Q_ABS)
+    np.testing.assert_allclose(ev["M"], ref["M"], rtol=0, atol=Q_ABS)
+    np.testing.assert_allclose(ev["b"], ref["b"], rtol=0, atol=Q_ABS)
+    np.testing.assert_allclose(ev["E_cell"], ref["E"], rtol=0, atol=E_ABS)
+
+
+@pytest.mark.parametrize("name,n", [("c1", None), ("c2", 53), ("c2", 1)])
+def test_initial_evaluation(P, name, n):
+    w = cs.make_workload(name, n_cells=n)
+    ctx = _ctx(P, w)
+    mat, md = _oracle(w)
+    ev = ctx.cavmd_get_eval()
+    _check_eval(ev, mat, md)
+    # instantaneous total force including the cavity field
+    fs = np.abs(md.F).max()
+    np.testing.assert_allclose(ev["F_total"], md.F, rtol=0, atol=F_REL * fs)
+    obs = ctx.cavmd_observables()
+    np.testing.assert_allclose(obs["D"], md.D, rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(obs["q"], md.q, rtol=1e-11, atol=1e-14)
+    e = md.energies()
+    for k in ("kinetic", "dftb", "photon", "coupling", "dse"):
+        key = {"kinetic": "e_kin", "dftb": "e_dftb", "photon": "e_photon", "coupling": "e_coupling",
+               "dse": "e_dse"}[k]
+        np.testing.assert_allclose(obs[key], e[k], rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,n,steps", [("c1", None, 20), ("c2", 37, 5)])
+def test_trajectory(P, name, n, steps):
+    w = cs.make_workload(name, n_cells=n)
+    ctx = _ctx(P, w, graph_chunk=0)
+    mat, md = _oracle(w)
+    x0 = w["system"].r.copy()
+    for s in range(steps):
+        ctx.cavmd_step(1)
+        md.step()
+        st = ctx.cavmd_get_state()
+        dr = md.r - x0
+        tol = 1e-9 * (1 + s)
+        np.testing.assert_allclose(st["r"] - x0, dr, rtol=0, atol=tol * np.abs(dr).max())
+        np.testing.assert_allclose(st["p"], md.p, rtol=0, atol=tol * np.abs(md.p).max())
+        np.testing.assert_allclose(st["q"], md.q, rtol=0, atol=tol * np.abs(md.q).max())
+        np.testing.assert_allclose(st["pq"], md.pq, rtol=0, atol=tol * np.abs(md.pq).max() + 1e-15)
+        obs = ctx.cavmd_observables()
+        e = md.energies()
+        np.testing.assert_allclose(obs["e_total"], e["total"], rtol=1e-11)
+    _check_eval(ctx.cavmd_get_eval(), mat, md)
+
+
+def test_graph_replay_is_bitwise_identical_to_direct_launches(P):
+    w = cs.make_workload("c2", n_cells=40, n_modes=64)
+    a = _ctx(P, w, graph_chunk=0)
+    b = _ctx(P, w, graph_chunk=4)
+    a.cavmd_step(9)
+    b.cavmd_step(9)
+    sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        assert np.array_equal(sa[k], sb[k]), k
+    c = _ctx(P, w, graph_chunk=0)
+    c.cavmd_step(9)
+    assert np.array_equal(c.cavmd_get_state()["p"], sa["p"])     # run to run deterministic
+
+
+def test_energy_history_and_conservation(P):
+    w = cs.make_workload("c1")
+    ctx = _ctx(P, w)
+    ctx.cavmd_step(400)
+    h = ctx.cavmd_energy_history(401)
+    assert h.shape == (401, 8)
+    assert np.array_equal(h[:, 7], np.arange(401))
+    nat = w["system"].n_atoms
+    e = h[:, 6] - h[0, 6]
+    assert np.abs(e).max() / nat < 2e-5
+    drift = np.polyfit(np.arange(len(e)), e, 1)[0] * len(e) / nat
+    assert abs(drift) < 1e-6
+
+
+def test_state_round_trip_and_resume(P):
+    w = cs.make_workload("c1", n_cells=4)
+    ctx = _ctx(P, w)
+    ctx.cavmd_step(3)
+    st = ctx.cavmd_get_state()
+    ctx.cavmd_step(4)
+    ref = ctx.cavmd_get_state()
+    ctx.cavmd_set_state(st)
+    assert ctx.cavmd_get_state()["step"] == 3
+    ctx.cavmd_step(4)
+    got = ctx.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        np.testing.assert_allclose(got[k], ref[k], rtol=0, atol=1e-9 * np.abs(ref[k]).max() + 1e-15)
+
+
+def test_scc_iteration_limit_is_reported(P):
+    import paper_2512_03277_gb300 as PP
+    w = cs.make_workload("c1", n_cells=2)
+    with pytest.raises(PP.CavmdError) as ex:
+        _ctx(P, w, scc_max_iter=2)
+    assert ex.value.code == -3
+
+
+def test_full_size_c2_sampled(P):
+    """4096 waters x 512 modes, the benchmark workload: every cell's charges against the oracle
+    (cells are independent), D_a against the oracle contraction, and one step on sampled atoms."""
+    w = cs.make_workload("c2")
+    ctx = _ctx(P, w)
+    mat, md = _oracle(w)
+    ev = ctx.cavmd_get_eval()
+    _check_eval(ev, mat, md)
+    obs = ctx.cavmd_observables()
+    np.testing.assert_allclose(obs["D"], md.D, rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(ev["q_pop"].reshape(-1, 3).sum(1), 8.0, atol=1e-12)
+    ctx.cavmd_step(1)
+    md.step()
+    st = ctx.cavmd_get_state()
+    rng = np.random.default_rng(0)
+    idx = rng.choice(w["system"].n_atoms, 300, replace=False)
+    np.testing.assert_allclose(st["p"][idx], md.p[idx], rtol=0, atol=1e-9 * np.abs(md.p).max())
+    np.testing.assert_allclose(st["q"], md.q, rtol=0, atol=1e-9 * np.abs(md.q).max())
