@@ -32,7 +32,7 @@ struct cavmd_ctx {
     // device buffers
     DevSK *d_sk = nullptr;
     int *d_off = nullptr, *d_species = nullptr, *d_iters = nullptr;
-    double *d_r = nullptr, *d_p = nullptr, *d_F = nullptr, *d_b = nullptr, *d_qpop = nullptr;
+    double *d_r = nullptr, *d_p = nullptr, *d_F = nullptr, *d_b = nullptr, *d_qpop = nullptr, *d_qprev = nullptr;
     double *d_C = nullptr, *d_E = nullptr, *d_Mc = nullptr, *d_mass = nullptr, *d_imass = nullptr;
     double *d_U = nullptr, *d_k = nullptr, *d_phi = nullptr, *d_R = nullptr;
     double *d_omega = nullptr, *d_lam = nullptr, *d_iomega = nullptr;
@@ -338,7 +338,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     AL(c->d_sk, 1);
     AL(c->d_off, N + 1); AL(c->d_species, NA); AL(c->d_iters, N);
     AL(c->d_r, 3 * NA); AL(c->d_p, 3 * NA); AL(c->d_F, 3 * NA); AL(c->d_b, 3 * NA);
-    AL(c->d_qpop, NA); AL(c->d_C, (size_t)N * 36); AL(c->d_E, N); AL(c->d_Mc, N);
+    AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)N * 36); AL(c->d_E, N); AL(c->d_Mc, N);
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N);
     AL(c->d_U, (size_t)M * N); AL(c->d_k, 3 * M); AL(c->d_phi, M); AL(c->d_R, 3 * N);
     AL(c->d_omega, M); AL(c->d_lam, M); AL(c->d_iomega, M); AL(c->d_cos, M); AL(c->d_sin, M); AL(c->d_omc, M);
@@ -382,6 +382,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.F = c->d_F;
     d.b = c->d_b;
     d.qpop = c->d_qpop;
+    d.qprev = c->d_qprev;
     d.Cwarm = c->d_C;
     d.E_cell = c->d_E;
     d.M_cell = c->d_Mc;

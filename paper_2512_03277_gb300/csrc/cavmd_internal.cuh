@@ -40,6 +40,7 @@ struct DftbArgs {
     double *F;                 // [3 n_atoms] out: -dE/dr
     double *b;                 // [3 n_atoms] out: Mulliken b_j = Q_j pol (charge_model 0)
     double *qpop;              // [n_atoms] in/out: Mulliken populations (warm start)
+    double *qprev;             // [n_atoms] in/out: populations of the step before (predictor)
     double *Cwarm;             // [n_cells_total][NORB*NORB] in/out eigenvectors (column-major)
     double *E_cell;            // [N] out
     double *M_cell;            // [N] out

@@ -13,7 +13,7 @@
 //
 // k_photon: one block per mode; the deterministic block reduction forms D_a from the cell
 //           dipoles, then one thread applies the half-flows of that mode and records its energy.
-// k_field:  each block owns 32 cells; its 8 warps split the mode sum, a fixed-order reduction
+// k_field:  each block owns 32 cells; its 32 warps split the mode sum, a fixed-order reduction
 //           combines them, then one thread per cell applies the kicks (and the drift). The last
 //           block to finish sums the per-block energy partials in block order (deterministic)
 //           and appends the energies of the synchronised state to the history ring.
@@ -23,7 +23,7 @@ namespace {
 
 constexpr int PH_THREADS = 256;
 constexpr int FLD_CELLS = 32;
-constexpr int FLD_SLICES = 8;
+constexpr int FLD_SLICES = 32;   // warps per block; each warp sums every 32nd mode for 32 cells
 
 __global__ void k_mode_functions(const double *__restrict__ k, const double *__restrict__ phi,
                                  const double *__restrict__ R, int M, int N, double *__restrict__ U) {
@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
     if (flags & PH_FORWARD) {
         const double *u = a.U + (size_t)al * a.N;
         double s = 0.0;
+#pragma unroll 4
         for (int n = threadIdx.x; n < a.N; n += PH_THREADS) s = fma(u[n], a.M_cell[n], s);
         s = block_sum_ordered(s, red);
         if (threadIdx.x == 0) {
@@ -107,82 +108,104 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
     }
 }
 
+// Partial field sums over the modes a = sl, sl + FLD_SLICES, ... for cell n; the loads of u are
+// independent of the accumulation, so the unrolled loop keeps several of them in flight.
+template <bool TWO, bool ONE>
+__device__ __forceinline__ void field_partial(const StepArgs &a, int n, int sl, double &e2, double &e1) {
+    const double *u = a.U + n;
+#pragma unroll 8
+    for (int al = sl; al < a.M; al += FLD_SLICES) {
+        const double v = u[(size_t)al * a.N];
+        if (TWO) e2 = fma(v, __ldg(a.W2 + al), e2);
+        if (ONE) e1 = fma(v, __ldg(a.W1 + al), e1);
+    }
+}
+
 __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs a, const int flags) {
     __shared__ double red2[FLD_SLICES][FLD_CELLS];
     __shared__ double red1[FLD_SLICES][FLD_CELLS];
-    __shared__ double ek[FLD_CELLS], ed[FLD_CELLS];
     __shared__ bool last;
     const int cl = threadIdx.x & (FLD_CELLS - 1);
     const int sl = threadIdx.x / FLD_CELLS;
     const int n = blockIdx.x * FLD_CELLS + cl;
     double e2 = 0.0, e1 = 0.0;
-    if (n < a.N && (flags & (FLD_SECOND | FLD_FIRST))) {
+    if (n < a.N) {
         const bool two = flags & FLD_SECOND, one = flags & FLD_FIRST;
-        for (int al = sl; al < a.M; al += FLD_SLICES) {
-            const double u = a.U[(size_t)al * a.N + n];
-            if (two) e2 = fma(u, __ldg(a.W2 + al), e2);
-            if (one) e1 = fma(u, __ldg(a.W1 + al), e1);
-        }
+        if (two && one) field_partial<true, true>(a, n, sl, e2, e1);
+        else if (two) field_partial<true, false>(a, n, sl, e2, e1);
+        else if (one) field_partial<false, true>(a, n, sl, e2, e1);
     }
     red2[sl][cl] = e2;
     red1[sl][cl] = e1;
     __syncthreads();
-    if (sl == 0) {
-        double kin = 0.0, edf = 0.0;
-        if (n < a.N) {
-            for (int s = 1; s < FLD_SLICES; ++s) {
-                e2 += red2[s][cl];
-                e1 += red1[s][cl];
-            }
-            const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
-            for (int j = j0; j < j1; ++j) {
-                const double im = a.inv_mass[j];
-                double pj[3];
-                for (int k = 0; k < 3; ++k) {
-                    pj[k] = a.p[3 * j + k];
-                    const double f = a.F[3 * j + k], bb = a.b[3 * j + k];
-                    if (flags & FLD_SECOND) pj[k] = fma(a.tau, f, fma(e2, bb, pj[k]));
-                    kin = fma(0.5 * im * pj[k], pj[k], kin);
-                    if (flags & FLD_FIRST) {
-                        pj[k] = fma(a.tau, f, fma(e1, bb, pj[k]));
-                        a.r[3 * j + k] = fma(a.dt * im, pj[k], a.r[3 * j + k]);
-                    }
-                    a.p[3 * j + k] = pj[k];
-                }
-            }
-            edf = a.E_cell[n];
+    double kin = 0.0, edf = 0.0;
+    if (sl == 0 && n < a.N) {
+        for (int s = 1; s < FLD_SLICES; ++s) {
+            e2 += red2[s][cl];
+            e1 += red1[s][cl];
         }
-        ek[cl] = kin;
-        ed[cl] = edf;
+        const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
+        for (int j = j0; j < j1; ++j) {
+            const double im = a.inv_mass[j];
+            double pj[3];
+            for (int k = 0; k < 3; ++k) {
+                pj[k] = a.p[3 * j + k];
+                const double f = a.F[3 * j + k], bb = a.b[3 * j + k];
+                if (flags & FLD_SECOND) pj[k] = fma(a.tau, f, fma(e2, bb, pj[k]));
+                kin = fma(0.5 * im * pj[k], pj[k], kin);
+                if (flags & FLD_FIRST) {
+                    pj[k] = fma(a.tau, f, fma(e1, bb, pj[k]));
+                    a.r[3 * j + k] = fma(a.dt * im, pj[k], a.r[3 * j + k]);
+                }
+                a.p[3 * j + k] = pj[k];
+            }
+        }
+        edf = a.E_cell[n];
     }
     if (!(flags & FLD_ENERGY)) return;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double k = 0.0, d = 0.0;
-        for (int i = 0; i < FLD_CELLS; ++i) {
-            k += ek[i];
-            d += ed[i];
+    // per-block partials (warp 0, fixed shuffle tree), then the last block to arrive forms the
+    // totals with the whole block in a fixed order
+    if (sl == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
+            edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
         }
-        a.e_kin_part[blockIdx.x] = k;
-        a.e_dftb_part[blockIdx.x] = d;
-        __threadfence();
-        const unsigned ticket = atomicAdd(a.done_counter, 1u);
-        last = (ticket == gridDim.x - 1);
+        if (cl == 0) {
+            a.e_kin_part[blockIdx.x] = kin;
+            a.e_dftb_part[blockIdx.x] = edf;
+            __threadfence();
+            const unsigned ticket = atomicAdd(a.done_counter, 1u);
+            last = (ticket == gridDim.x - 1);
+        }
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last) return;
     __threadfence();
-    double kin = 0.0, edf = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) {
-        kin += *((volatile double *)a.e_kin_part + i);
-        edf += *((volatile double *)a.e_dftb_part + i);
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        v[0] += __ldcg(a.e_kin_part + i);
+        v[1] += __ldcg(a.e_dftb_part + i);
     }
-    double eph = 0.0, ecp = 0.0, edse = 0.0, efree = 0.0;
-    for (int al = 0; al < a.M; ++al) {
-        eph += a.e_mode[4 * al + 0];
-        ecp += a.e_mode[4 * al + 1];
-        edse += a.e_mode[4 * al + 2];
-        efree += a.e_mode[4 * al + 3];
+    for (int al = threadIdx.x; al < a.M; al += blockDim.x) {
+        const double *e = a.e_mode + 4 * al;
+        v[2] += e[0];
+        v[3] += e[1];
+        v[4] += e[2];
+        v[5] += e[3];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(CAVMD_FULL_MASK, v[k], o);
+        if (cl == 0) red2[k][sl] = v[k];      // slot reuse: red2 is free after the field sums
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double t[6];
+    for (int k = 0; k < 6; ++k) {
+        t[k] = 0.0;
+        for (int w = 0; w < FLD_SLICES; ++w) t[k] += red2[k][w];
     }
     long long step = *a.step_counter;
     if (flags & FLD_SECOND) {
@@ -190,15 +213,15 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
         *a.step_counter = step;
     }
     double *h = a.hist + 8 * (size_t)(step % a.hist_cap);
-    h[0] = kin;
-    h[1] = edf;
-    h[2] = eph;
-    h[3] = ecp;
-    h[4] = edse;
-    h[5] = efree;
-    h[6] = kin + edf + eph;
+    h[0] = t[0];
+    h[1] = t[1];
+    h[2] = t[2];
+    h[3] = t[3];
+    h[4] = t[4];
+    h[5] = t[5];
+    h[6] = t[0] + t[1] + t[2];
     h[7] = (double)step;
-    if (!(isfinite(kin) && isfinite(edf) && isfinite(eph))) atomicOr(a.status, (unsigned)ERRBIT_NONFINITE);
+    if (!(isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2]))) atomicOr(a.status, (unsigned)ERRBIT_NONFINITE);
     *a.done_counter = 0u;
 }
 

@@ -26,6 +26,8 @@ constexpr int NHIST = 3;          // Anderson history (current + 2 previous iter
 constexpr int MAX_SWEEPS = 24;    // bound on Jacobi sweeps per SCC iteration
 constexpr double JACOBI_TOL = 1e-15;   // off-diagonal magnitude treated as converged (Hartree)
 constexpr double MIN_GAP = 1e-3;       // closed-shell HOMO-LUMO threshold (Hartree)
+constexpr double EIG_TOL = 1e-10;      // occupied-virtual coupling treated as converged (Hartree)
+constexpr float KMAX_PERT = 1e-4f;     // largest generator entry for the second-order update
 
 template <int NAT, int NORB>
 struct MolShared {
@@ -45,12 +47,16 @@ struct MolShared {
     double shift[NAT];
     double hq[NHIST][NAT];
     double hf[NHIST][NAT];
+    double qstart[NAT];   // q(t) of the previous step, for the predictor
     double red[NORB];
     double cs[NORB / 2 + 1][2];
     double invd[NORB];
     double gpair[NPAIR > 0 ? NPAIR : 1][3];
     double epair[NPAIR > 0 ? NPAIR : 1];
+    double Hs[NORB * LD];   // H of the current SCC iteration
     int occ_list[NORB];
+    int occf[NORB];       // orbital column j is occupied
+    int eok[NORB];        // occupied-virtual couplings of column j were below EIG_TOL
     int orb_atom[NORB];
     int atom_off[NAT + 1];
     int spec[NAT];
@@ -254,7 +260,13 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         if (a.have_warm) {
             const double *cw = a.Cwarm + (size_t)cell * NORB * NORB;
             for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = cw[j * NORB + i];
-            if (j < NAT) m.q[j] = a.qpop[a0 + j];
+            // linear predictor 2 q(t) - q(t - dt) of the populations (q_prev equals q after a
+            // cold start, so the first warm step starts from q(t) itself)
+            if (j < NAT) {
+                const double qt = a.qpop[a0 + j];
+                m.qstart[j] = qt;
+                m.q[j] = fma(2.0, qt, -a.qprev[a0 + j]);
+            }
         } else {
             for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = (i == j) ? 1.0 : 0.0;
             if (j < NAT) m.q[j] = m.zv[j];
@@ -322,6 +334,17 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
     __syncwarp();
 
     // ---------------------------------------------------------------- SCC loop
+    // Each iteration builds H(q) and A = C^T H C in the current S-orthonormal basis C and moves C
+    // towards the eigenvectors of H. When the occupied-virtual couplings are small, C takes the
+    // second-order exponential V = I + K + K^2/2 of the first-order generator
+    // K_kj = A_kj / (A_jj - A_kk) over occupied-virtual pairs: V is orthogonal to O(K^4) and, like
+    // a Jacobi sweep, squares the remaining coupling, at a third of the cost. Otherwise (the first
+    // iteration after a geometry change, a cold start, a large charge change) C takes Jacobi
+    // sweeps: one per iteration when warm started, to full convergence in the first iteration of a
+    // cold start. Only occupied-virtual mixing changes P, so occupied-occupied couplings are left
+    // to the final energy-weighted density, which uses the whole occupied block. The charges count
+    // as converged once |q_out - q| < tol and every occupied-virtual coupling was below EIG_TOL
+    // before the update.
     int it = 0;
     for (it = 1; it <= a.max_iter; ++it) {
         const bool work = act && !m.conv;
@@ -331,10 +354,10 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
             m.shift[j] = sh;
         }
         __syncwarp();
-        if (work) {   // H column j into A
+        if (work) {   // H column j
             const double shj = m.shift[m.orb_atom[j]];
             for (int i = 0; i < NORB; ++i)
-                m.A[j * LD + i] = fma(0.5 * m.S[j * LD + i], m.shift[m.orb_atom[i]] + shj, m.H0[j * LD + i]);
+                m.Hs[j * LD + i] = fma(0.5 * m.S[j * LD + i], m.shift[m.orb_atom[i]] + shj, m.H0[j * LD + i]);
         }
         __syncwarp();
         if (work) {   // Y = H C
@@ -344,7 +367,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
             for (int k = 0; k < NORB; ++k) {
                 const double ckj = m.C[j * LD + k];
 #pragma unroll
-                for (int i = 0; i < NORB; ++i) y[i] = fma(m.A[k * LD + i], ckj, y[i]);
+                for (int i = 0; i < NORB; ++i) y[i] = fma(m.Hs[k * LD + i], ckj, y[i]);
             }
 #pragma unroll
             for (int i = 0; i < NORB; ++i) m.Y[j * LD + i] = y[i];
@@ -361,64 +384,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
             for (int i = 0; i < NORB; ++i) m.A[j * LD + i] = y[i];
         }
         __syncwarp();
-
-        // Jacobi sweeps on A, rotations accumulated into C
-        for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
-            bool small = true;
-            if (work) {
-                for (int i = 0; i < NORB; ++i)
-                    if (i != j && !abs_lt(m.A[j * LD + i], JACOBI_TOL)) small = false;
-            }
-            if (__all_sync(CAVMD_FULL_MASK, small)) break;
-            if (sweep == MAX_SWEEPS - 1) {
-                if (work && !small) m.flag |= ERRBIT_TIMEOUT;
-                break;
-            }
-            for (int rd = 0; rd < NORB - 1; ++rd) {
-                int slot = 0;
-                const int pj = rr_partner(j, rd, NORB, slot);
-                const int p = min(j, pj), q = max(j, pj);
-                double c = 1.0, s = 0.0;
-                double na[NORB], nc[NORB];
-                if (work) {
-                    jacobi_cs(m.A[p * LD + p], m.A[q * LD + q], m.A[q * LD + p], c, s);
-                    const double cp = (j == p) ? c : s;       // new col j = cp * col p + cq * col q
-                    const double cq = (j == p) ? -s : c;
-#pragma unroll
-                    for (int i = 0; i < NORB; ++i) {
-                        na[i] = fma(cp, m.A[p * LD + i], cq * m.A[q * LD + i]);
-                        nc[i] = fma(cp, m.C[p * LD + i], cq * m.C[q * LD + i]);
-                    }
-                }
-                __syncwarp();
-                if (work) {
-#pragma unroll
-                    for (int i = 0; i < NORB; ++i) {
-                        m.A[j * LD + i] = na[i];
-                        m.C[j * LD + i] = nc[i];
-                    }
-                    if (j == p) {
-                        m.cs[slot][0] = c;
-                        m.cs[slot][1] = s;
-                    }
-                }
-                __syncwarp();
-                if (work) {
-#pragma unroll
-                    for (int k = 0; k < NORB / 2; ++k) {
-                        int pk, qk;
-                        rr_pair(k, rd, NORB, pk, qk);
-                        const double ck = m.cs[k][0], sk_ = m.cs[k][1];
-                        const double x = m.A[j * LD + pk], y = m.A[j * LD + qk];
-                        m.A[j * LD + pk] = fma(ck, x, -sk_ * y);
-                        m.A[j * LD + qk] = fma(sk_, x, ck * y);
-                    }
-                }
-                __syncwarp();
-            }
-        }
-
-        // aufbau occupation: the nocc lowest eigenvalues
+        // aufbau occupation from the diagonal of A
         if (work) {
             const long long kj = order_key(m.A[j * LD + j]);
             int rank = 0;
@@ -426,9 +392,133 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
                 const long long ki = order_key(m.A[i * LD + i]);
                 rank += (ki < kj) || (ki == kj && i < j);
             }
+            m.occf[j] = rank < m.nocc;
             if (rank < m.nocc) m.occ_list[rank] = j;
         }
         __syncwarp();
+        // first-order occupied-virtual generator, column j, into Y (FP32: it only steers)
+        float kmax = 0.0f;
+        if (work) {
+            const int oj = m.occf[j];
+            const double ajj = m.A[j * LD + j];
+            bool small = true;
+            for (int k = 0; k < NORB; ++k) {
+                double kv = 0.0;
+                if (m.occf[k] != oj) {
+                    const double akj = m.A[j * LD + k];
+                    if (!abs_lt(akj, EIG_TOL)) small = false;
+                    float kf = (float)akj / (float)(ajj - m.A[k * LD + k]);
+                    if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
+                    kv = (double)kf;
+                    kmax = fmaxf(kmax, fabsf(kf));
+                }
+                m.Y[j * LD + k] = kv;
+            }
+            m.eok[j] = small;
+        }
+        const bool cold_first = !a.have_warm && it == 1;
+        const bool perturb = __all_sync(CAVMD_FULL_MASK, !work || (kmax < KMAX_PERT && !cold_first));
+        __syncwarp();
+        if (perturb) {
+            double cn[NORB];
+            if (work) {   // V column j = e_j + K e_j + K (K e_j) / 2, then C <- C V
+                double v[NORB];
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) v[i] = m.Y[j * LD + i];
+                double w[NORB];
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) w[i] = 0.0;
+                for (int mm = 0; mm < NORB; ++mm) {
+                    const double kmj = v[mm];
+#pragma unroll
+                    for (int i = 0; i < NORB; ++i) w[i] = fma(m.Y[mm * LD + i], kmj, w[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) v[i] = fma(0.5, w[i], v[i] + (i == j ? 1.0 : 0.0));
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) cn[i] = 0.0;
+                for (int k = 0; k < NORB; ++k) {
+                    const double vk = v[k];
+#pragma unroll
+                    for (int i = 0; i < NORB; ++i) cn[i] = fma(m.C[k * LD + i], vk, cn[i]);
+                }
+            }
+            __syncwarp();
+            if (work) {
+#pragma unroll
+                for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = cn[i];
+            }
+            __syncwarp();
+        } else {
+            const int sweeps_per_iter = cold_first ? MAX_SWEEPS : 1;
+            for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+                bool small = true;
+                if (work) {
+                    for (int i = 0; i < NORB; ++i)
+                        if (i != j && !abs_lt(m.A[j * LD + i], JACOBI_TOL)) small = false;
+                }
+                if (__all_sync(CAVMD_FULL_MASK, small)) break;
+                if (sweep >= sweeps_per_iter) break;
+                if (sweep == MAX_SWEEPS - 1) {
+                    if (work && !small) m.flag |= ERRBIT_TIMEOUT;
+                    break;
+                }
+                for (int rd = 0; rd < NORB - 1; ++rd) {
+                    int slot = 0;
+                    const int pj = rr_partner(j, rd, NORB, slot);
+                    const int p = min(j, pj), q = max(j, pj);
+                    double c = 1.0, s = 0.0;
+                    double na[NORB], nc[NORB];
+                    if (work) {
+                        jacobi_cs(m.A[p * LD + p], m.A[q * LD + q], m.A[q * LD + p], c, s);
+                        const double cp = (j == p) ? c : s;       // new col j = cp * col p + cq * col q
+                        const double cq = (j == p) ? -s : c;
+#pragma unroll
+                        for (int i = 0; i < NORB; ++i) {
+                            na[i] = fma(cp, m.A[p * LD + i], cq * m.A[q * LD + i]);
+                            nc[i] = fma(cp, m.C[p * LD + i], cq * m.C[q * LD + i]);
+                        }
+                    }
+                    __syncwarp();
+                    if (work) {
+#pragma unroll
+                        for (int i = 0; i < NORB; ++i) {
+                            m.A[j * LD + i] = na[i];
+                            m.C[j * LD + i] = nc[i];
+                        }
+                        if (j == p) {
+                            m.cs[slot][0] = c;
+                            m.cs[slot][1] = s;
+                        }
+                    }
+                    __syncwarp();
+                    if (work) {
+#pragma unroll
+                        for (int k = 0; k < NORB / 2; ++k) {
+                            int pk, qk;
+                            rr_pair(k, rd, NORB, pk, qk);
+                            const double ck = m.cs[k][0], sk_ = m.cs[k][1];
+                            const double x = m.A[j * LD + pk], y = m.A[j * LD + qk];
+                            m.A[j * LD + pk] = fma(ck, x, -sk_ * y);
+                            m.A[j * LD + qk] = fma(sk_, x, ck * y);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            if (work) {   // occupation after the sweeps
+                const long long kj = order_key(m.A[j * LD + j]);
+                int rank = 0;
+                for (int i = 0; i < NORB; ++i) {
+                    const long long ki = order_key(m.A[i * LD + i]);
+                    rank += (ki < kj) || (ki == kj && i < j);
+                }
+                m.occf[j] = rank < m.nocc;
+                if (rank < m.nocc) m.occ_list[rank] = j;
+            }
+            __syncwarp();
+        }
+
         if (work) {   // P = 2 C_occ C_occ^T, column j, and (P S)_jj
             double pc[NORB];
 #pragma unroll
@@ -462,6 +552,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
             bool conv = true;
             for (int at = 0; at < NAT; ++at)
                 if (!abs_lt(m.hf[hs][at], a.scc_tol)) conv = false;
+            for (int c = 0; c < NORB; ++c) conv = conv && m.eok[c];
             float th1 = 0.0f, th2 = 0.0f;
             const int h = min(it, NHIST);
             if (!conv && h >= 2) {
@@ -520,15 +611,51 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         m.shift[j] = sh;
     }
     __syncwarp();
-    if (act) {   // W (energy-weighted density) into Y, band energy partial, HOMO-LUMO gap
+    // energy-weighted density W = 2 C_o (C_o^T H C_o) C_o^T with the H of the last iteration and the
+    // whole occupied block (basis independent inside the occupied subspace)
+    if (act) {   // Y = H C
+        double y[NORB];
+#pragma unroll
+        for (int i = 0; i < NORB; ++i) y[i] = 0.0;
+        for (int k = 0; k < NORB; ++k) {
+            const double ckj = m.C[j * LD + k];
+#pragma unroll
+            for (int i = 0; i < NORB; ++i) y[i] = fma(m.Hs[k * LD + i], ckj, y[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < NORB; ++i) m.Y[j * LD + i] = y[i];
+    }
+    __syncwarp();
+    if (act) {   // A = C^T Y
+        double y[NORB];
+        for (int i = 0; i < NORB; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < NORB; ++k) s = fma(m.C[i * LD + k], m.Y[j * LD + k], s);
+            y[i] = s;
+        }
+        for (int i = 0; i < NORB; ++i) m.A[j * LD + i] = y[i];
+    }
+    __syncwarp();
+    if (act) {   // W column j, band energy partial, HOMO-LUMO gap
+        double t[NORB];
+        for (int o = 0; o < m.nocc; ++o) {
+            const int co = m.occ_list[o];
+            double x = 0.0;
+            for (int o2 = 0; o2 < m.nocc; ++o2) {
+                const int c2 = m.occ_list[o2];
+                x = fma(m.A[c2 * LD + co], m.C[c2 * LD + j], x);
+            }
+            t[o] = 2.0 * x;
+        }
         double wc[NORB];
 #pragma unroll
         for (int i = 0; i < NORB; ++i) wc[i] = 0.0;
         for (int o = 0; o < m.nocc; ++o) {
-            const int col = m.occ_list[o];
-            const double w = 2.0 * m.A[col * LD + col] * m.C[col * LD + j];
+            const int co = m.occ_list[o];
+            const double w = t[o];
 #pragma unroll
-            for (int i = 0; i < NORB; ++i) wc[i] = fma(w, m.C[col * LD + i], wc[i]);
+            for (int i = 0; i < NORB; ++i) wc[i] = fma(w, m.C[co * LD + i], wc[i]);
         }
         double eb = 0.0;
 #pragma unroll
@@ -540,10 +667,8 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         if (j == 0 && m.nocc < NORB) {
             double homo = -1e300, lumo = 1e300;
             for (int i = 0; i < NORB; ++i) {
-                bool oc = false;
-                for (int o = 0; o < m.nocc; ++o) oc |= (m.occ_list[o] == i);
                 const double ei = m.A[i * LD + i];
-                if (oc) homo = fmax(homo, ei); else lumo = fmin(lumo, ei);
+                if (m.occf[i]) homo = fmax(homo, ei); else lumo = fmin(lumo, ei);
             }
             if (!(lumo - homo > MIN_GAP)) m.flag |= ERRBIT_ZERO_GAP;
         }
@@ -652,6 +777,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         }
         const int at = a0 + j;
         for (int k = 0; k < 3; ++k) a.F[3 * at + k] = f[k];
+        a.qprev[at] = a.have_warm ? m.qstart[j] : m.q[j];
         a.qpop[at] = m.q[j];
         if (a.write_b) {
             const double Q = m.zv[j] - m.q[j];
