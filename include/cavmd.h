@@ -210,12 +210,41 @@ int cavmd_get_eval(cavmd_ctx *ctx, cavmd_eval *out);
 int cavmd_phase_times(cavmd_ctx *ctx, int32_t enable, double *ms_out, int64_t *counts,
                       int32_t reset);
 
-/* Message of the last failure on ctx (or of the last failed cavmd_init when ctx is NULL).
+/* Message of the last failure on ctx (or, when ctx is NULL, of the last failed cavmd_init or
+ * context-free call on this thread).
  * The string stays valid until the next call on the same context. */
 const char *cavmd_last_error(const cavmd_ctx *ctx);
 
 /* Frees every device buffer and the context itself. NULL is allowed. */
 void cavmd_destroy(cavmd_ctx *ctx);
+
+/* Allocation-free field and kick (no counterpart in the paper; an addition for embedding).
+ *
+ * For callers that cannot allocate device memory while they run: a framework that owns all of
+ * the GPU's memory through its own pool, a latency-critical loop where cudaMalloc / cudaFree
+ * would synchronise the device, or a plug-in whose host code may not allocate. The call performs
+ * one half-step kick of the time step without any allocation, on caller-owned DEVICE arrays:
+ *   E_n = sum_a U[a * n_cells + n] W[a]                  (field on cell n; U row-major [n_modes][n_cells])
+ *   p_j += tau F_j + E_n b_j   for every atom j of cell n (cell_offset as in cavmd_system)
+ *   *e_kin_out = sum_j |p_j|^2 inv_mass[j] / 2             (after the kick, summed in a fixed order)
+ * E_out [n_cells] receives E_n and may be NULL. p is updated in place. All pointers are device
+ * pointers; stream is a cudaStream_t (NULL = the legacy default stream); the work is queued and
+ * the call returns without waiting.
+ *
+ * Scratch: the per-block energy partials and a counter live in one file-scope device array of
+ * fixed size inside the library (about 256 KB, held by every GPU that loads the library until the
+ * process exits). Hence the limit 1 <= n_cells <= CAVMD_NOALLOC_MAX_CELLS; larger sizes return
+ * CAVMD_ERR_INVALID_ARG with a message from cavmd_last_error(NULL). The call never allocates and
+ * never calls cudaMalloc or cudaFree. Its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. Every call clears the counter it needs, but all calls share the one array, which keeps
+ * the last call's contents: calls that may overlap on the GPU (other streams, other host threads)
+ * race and give wrong totals; serialise them. */
+#define CAVMD_NOALLOC_MAX_CELLS 1048576
+int cavmd_field_kick_noalloc(int32_t n_cells, int32_t n_modes, const int32_t *cell_offset,
+                             const double *U, const double *W, const double *F, const double *b,
+                             const double *inv_mass, double tau, double *p, double *E_out,
+                             double *e_kin_out, void *stream);
 
 /* Size of one of the library's structs, for bindings that lay them out by hand. */
 size_t cavmd_struct_size(int32_t which); /* 0 system, 1 sk_tables, 2 modes, 3 options,

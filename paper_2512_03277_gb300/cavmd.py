@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.cavmd_last_error.restype = C.c_char_p
     lib.cavmd_destroy.argtypes = [C.c_void_p]
     lib.cavmd_destroy.restype = None
+    lib.cavmd_field_kick_noalloc.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 6 + [C.c_double] + \
+        [C.c_void_p] * 4
     lib.cavmd_struct_size.argtypes = [C.c_int32]
     lib.cavmd_struct_size.restype = C.c_size_t
     for i, st in enumerate(STRUCTS):
@@ -158,6 +160,19 @@ def default_options() -> cavmd_options:
     o = cavmd_options()
     load_library().cavmd_default_options(C.byref(o))
     return o
+
+
+NOALLOC_MAX_CELLS = 1048576
+
+
+def cavmd_field_kick_noalloc(n_cells, n_modes, cell_offset, U, W, F, b, inv_mass, tau, p, E_out, e_kin_out,
+                             stream=0):
+    """The allocation-free field and kick of cavmd.h. Array arguments are device addresses (ints,
+    e.g. torch tensor data_ptr()); E_out may be 0. Raises CavmdError on a nonzero status."""
+    lib = load_library()
+    rc = lib.cavmd_field_kick_noalloc(int(n_cells), int(n_modes), cell_offset, U, W, F, b, inv_mass, float(tau),
+                                      p, E_out or None, e_kin_out, stream or None)
+    _check(rc, None)
 
 
 class Context:

@@ -21,6 +21,8 @@ namespace {
 thread_local std::string g_init_error;
 }
 
+void cavmd_set_global_error(const std::string &msg) { g_init_error = msg; }
+
 struct cavmd_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -105,6 +105,10 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
     return y;
 }
 
+#include <string>
+// Records the message returned by cavmd_last_error(NULL) (calls without a context).
+void cavmd_set_global_error(const std::string &msg);
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st);
 cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
