@@ -33,6 +33,9 @@ FP64_FLOPS_PER_CLK_SM = 4.0      # 2 FP64 FMA per clock per SM (1.25 TFLOP/s nom
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one dftb_kernel<3,6> launch on this workload, from one ncu capture
+# (profiles/dftb_kernel_c2_4096x512.md); None once the kernel has changed since that capture.
+DFTB_DRAM_BYTES_PER_LAUNCH = 1.883e6 + 768
 
 
 def _dist():
@@ -175,6 +178,7 @@ def main():
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixing", type=float, default=None, help="charge mixing (default: the library's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -200,6 +204,8 @@ def main():
         w["system"].p = cs.mb_momenta(np.random.default_rng(1000 + rank), w["system"])
     opt = P.default_options()
     opt.device = local
+    if args.mixing is not None:
+        opt.mixing = args.mixing
     ctx = P.Context(w["system"], w["params"], w["modes"], opt)
     stream = ctx.stream
     N = w["system"].n_cells
@@ -275,7 +281,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(args.workload, w),
         "roofline": {"bound": "alu", "kernel": "dftb_kernel<3,6>", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": DFTB_DRAM_BYTES_PER_LAUNCH if args.workload == "c2" else None,
                      "flops_per_launch": flops, "avg_launch_ms": dftb_ms,
                      "mean_scc_iters": float(np.mean(ev["scc_iters"])),
                      "peak_note": "FP64 ALU: 152 SMs x 4 FP64 flop/clk x 2070 MHz (derived, 1.26 TFLOP/s)"},

@@ -167,7 +167,7 @@ typedef struct {
 typedef struct cavmd_ctx cavmd_ctx;
 
 /* Fills *opt with the defaults: dt = 0.5 fs, FP64, Mulliken, born_interval 3, fd_step 1e-3,
- * scc_tol 1e-12, scc_max_iter 200, mixing 0.5, PHOTON_EXACT, relaxed photons, graph_chunk 50,
+ * scc_tol 1e-12, scc_max_iter 200, mixing 0.7, PHOTON_EXACT, relaxed photons, graph_chunk 50,
  * device 0, library stream, cudaMalloc, energy_history 1024. */
 void cavmd_default_options(cavmd_options *opt);
 

@@ -426,7 +426,7 @@ void cavmd_default_options(cavmd_options *o) {
     o->fd_step = 1e-3;
     o->scc_tol = 1e-12;
     o->scc_max_iter = 200;
-    o->mixing = 0.5;
+    o->mixing = 0.7;
     o->splitting = CAVMD_SPLIT_PHOTON_EXACT;
     o->photon_init = CAVMD_PHOTON_RELAXED;
     o->graph_chunk = 50;
