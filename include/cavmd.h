@@ -53,6 +53,12 @@ extern "C" {
 
 #define CAVMD_MAX_ELEM 4           /* element ids 0..3                                    */
 #define CAVMD_MAX_ATOMS_PER_CELL 3 /* cells with more atoms return CAVMD_ERR_UNSUPPORTED  */
+/* Dipole derivative b_j = dM_n/dr_j used by the coupling force:
+ *   MULLIKEN     b_j = Q_j pol (the paper's cheap replacement; not conservative);
+ *   BORN_FD      forward differences [M(r + h e) - M(r)] / h, the paper's choice, from 3 N_at
+ *                displaced SCC solves per cell (warm started from the cell's solution);
+ *   BORN_CENTRAL central differences from 6 N_at displaced solves (for tests and conservation);
+ *   BORN_MLP     a per-atom network (needs a loaded network).                                */
 
 /* Integral kinds of a Slater-Koster table entry [eA][eB][kind]: SP means an s
  * orbital on the first element and a p orbital on the second. */
@@ -115,7 +121,9 @@ typedef struct {
     double dt;                  /* time step, a.u.                                            */
     int32_t precision;          /* CAVMD_PREC_*                                               */
     int32_t charge_model;       /* CAVMD_CHARGE_*                                             */
-    int32_t born_interval;      /* refresh finite-difference Born charges every this many steps */
+    int32_t born_interval;      /* refresh finite-difference Born charges on every evaluation whose
+                                   index (0 = the initial one, then the step number) is a multiple
+                                   of this; the paper refreshes every 3 steps. Stale in between.  */
     double fd_step;             /* finite-difference displacement, bohr                      */
     double scc_tol;             /* max |q_out - q_in| per atom at convergence                */
     int32_t scc_max_iter;
@@ -206,7 +214,7 @@ int cavmd_get_eval(cavmd_ctx *ctx, cavmd_eval *out);
  * receives the summed durations and counts[CAVMD_N_PHASES] the launches since the last
  * reset (reset = 1 clears both after reading). Either output may be NULL. */
 #define CAVMD_N_PHASES 4        /* 0: SCC-DFTB, 1: forward contraction + photons,
-                                   2: field + kicks + drift, 3: other                    */
+                                   2: field + kicks + drift, 3: finite-difference Born rows */
 int cavmd_phase_times(cavmd_ctx *ctx, int32_t enable, double *ms_out, int64_t *counts,
                       int32_t reset);
 

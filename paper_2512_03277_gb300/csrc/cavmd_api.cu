@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -41,7 +42,7 @@ struct cavmd_ctx {
     double *d_cos = nullptr, *d_sin = nullptr, *d_omc = nullptr;
     double *d_q = nullptr, *d_pq = nullptr, *d_qs = nullptr, *d_pqs = nullptr, *d_D = nullptr;
     double *d_W1 = nullptr, *d_W2 = nullptr, *d_emode = nullptr, *d_Einst = nullptr;
-    double *d_ekp = nullptr, *d_edp = nullptr, *d_hist = nullptr;
+    double *d_ekp = nullptr, *d_edp = nullptr, *d_hist = nullptr, *d_Mdisp = nullptr;
     unsigned *d_done = nullptr, *d_status = nullptr;
     long long *d_step = nullptr;
     std::vector<void *> allocs;
@@ -49,8 +50,9 @@ struct cavmd_ctx {
     unsigned *h_status = nullptr;   // pinned
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
-    cudaGraphExec_t graph = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;   // keyed by the Born refresh phase of the first step
     int graph_steps = 0;
+    int n_disp = 0;                          // finite-difference rows per cell (0: Mulliken)
     int64_t step = 0;
     std::string err;
     // phase timers
@@ -182,6 +184,25 @@ cudaError_t run_dftb(cavmd_ctx *c, int have_warm) {
     return launch_dftb_water(c->d_sk, c->da, c->stream);
 }
 
+// Finite-difference dipole derivatives at the current positions (after the cell evaluation).
+cudaError_t run_born(cavmd_ctx *c) {
+    PhaseScope ps(c, 3);
+    DftbArgs d = c->da;
+    d.have_warm = 1;
+    d.n_disp = c->n_disp;
+    d.fd_central = c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL;
+    d.fd_h = c->opt.fd_step;
+    d.M_disp = c->d_Mdisp;
+    cudaError_t e = launch_dftb_water(c->d_sk, d, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_born_assemble(c->N, c->d_off, c->d_Mc, c->d_Mdisp, c->n_disp, d.fd_central, d.fd_h, c->d_b,
+                                c->stream);
+}
+
+bool born_refresh(const cavmd_ctx *c, int64_t eval_index) {
+    return c->n_disp > 0 && (eval_index % c->opt.born_interval) == 0;
+}
+
 cudaError_t run_photon(cavmd_ctx *c, int flags) {
     PhaseScope ps(c, 1);
     return launch_photon(c->sa, flags, c->stream);
@@ -192,14 +213,16 @@ cudaError_t run_field(cavmd_ctx *c, int flags) {
     return launch_field(c->sa, flags, c->stream);
 }
 
-// Queues n >= 1 steps starting and ending at a synchronised state.
-cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n) {
+// Queues n >= 1 steps starting and ending at a synchronised state; the first queued step is
+// step number first_step (evaluation index = step number, init being evaluation 0).
+cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     cudaError_t e;
     if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
     if ((e = run_field(c, FLD_FIRST)) != cudaSuccess) return e;
     for (int64_t s = 0; s < n; ++s) {
         const bool last = (s == n - 1);
         if ((e = run_dftb(c, 1)) != cudaSuccess) return e;
+        if (born_refresh(c, first_step + s) && (e = run_born(c)) != cudaSuccess) return e;
         if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
         if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
     }
@@ -208,6 +231,7 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n) {
 
 int initial_evaluation(cavmd_ctx *c, bool init_photons) {
     CK(run_dftb(c, 0));
+    if (c->n_disp > 0) CK(run_born(c));
     if (init_photons) {
         const int pf = (c->opt.photon_init == CAVMD_PHOTON_ZERO) ? PH_INIT_ZERO : PH_INIT_RELAXED;
         CK(run_photon(c, PH_FORWARD | pf | PH_ENERGY));
@@ -273,7 +297,11 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if (!(o->scc_tol > 0.0) || o->scc_max_iter < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad SCC tolerance or iteration limit");
     if (!(o->mixing > 0.0 && o->mixing <= 1.0)) return fail(c, CAVMD_ERR_INVALID_ARG, "mixing must be in (0, 1]");
     if (o->precision != CAVMD_PREC_FP64) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_PREC_FP64 in this build");
-    if (o->charge_model != CAVMD_CHARGE_MULLIKEN) return fail(c, CAVMD_ERR_UNSUPPORTED, "only Mulliken charges in this build");
+    if (o->charge_model == CAVMD_CHARGE_BORN_MLP) return fail(c, CAVMD_ERR_UNSUPPORTED, "CAVMD_CHARGE_BORN_MLP needs a loaded network");
+    if (o->charge_model < CAVMD_CHARGE_MULLIKEN || o->charge_model > CAVMD_CHARGE_BORN_MLP)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "bad charge_model");
+    if (o->charge_model != CAVMD_CHARGE_MULLIKEN && (o->born_interval < 1 || !(o->fd_step > 0.0)))
+        return fail(c, CAVMD_ERR_INVALID_ARG, "Born charges need born_interval >= 1 and fd_step > 0");
     if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_SPLIT_PHOTON_EXACT in this build");
     if (o->photon_init != CAVMD_PHOTON_RELAXED && o->photon_init != CAVMD_PHOTON_ZERO)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
@@ -285,7 +313,7 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
 void release(cavmd_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     for (auto &pd : c->pending) { cudaEventDestroy(pd.a); cudaEventDestroy(pd.b); }
     for (auto e : c->ev_free) cudaEventDestroy(e);
     for (void *p : c->allocs) {
@@ -349,6 +377,9 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     const int fb = field_blocks(N);
     AL(c->d_ekp, fb); AL(c->d_edp, fb); AL(c->d_hist, 8 * (size_t)c->opt.energy_history);
     AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1);
+    if (c->opt.charge_model == CAVMD_CHARGE_BORN_FD) c->n_disp = 3 * 3;
+    if (c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL) c->n_disp = 6 * 3;
+    if (c->n_disp) AL(c->d_Mdisp, (size_t)N * c->n_disp);
 
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(c->d_sk, &hsk, sizeof(DevSK), cudaMemcpyHostToDevice, st));
@@ -397,7 +428,11 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.beta = c->opt.mixing;
     d.max_iter = c->opt.scc_max_iter;
     d.have_warm = 0;
-    d.write_b = 1;
+    d.write_b = c->opt.charge_model == CAVMD_CHARGE_MULLIKEN;
+    d.n_disp = 0;
+    d.fd_central = 0;
+    d.fd_h = c->opt.fd_step;
+    d.M_disp = nullptr;
 
     StepArgs &s = c->sa;
     s.N = N; s.M = M; s.n_atoms = NA;
@@ -476,26 +511,33 @@ int cavmd_step(cavmd_ctx *c, int64_t nsteps) {
     if (nsteps == 0) return rc;
     CK(cudaSetDevice(c->device));
     int64_t left = nsteps;
-    const int G = c->opt.graph_chunk;
+    int64_t next = c->step + 1;                      // step number of the next queued step
+    int G = c->opt.graph_chunk;
+    if (c->n_disp > 0 && G > 0) G = ((G + c->opt.born_interval - 1) / c->opt.born_interval) * c->opt.born_interval;
     if (G > 0 && !c->timing && left >= G) {
-        if (!c->graph) {
+        const int phase = c->n_disp > 0 ? (int)(next % c->opt.born_interval) : 0;
+        auto it = c->graphs.find(phase);
+        if (it == c->graphs.end()) {
             cudaGraph_t g;
+            cudaGraphExec_t ge;
             CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t e = enqueue_steps(c, G);
+            cudaError_t e = enqueue_steps(c, G, next);
             cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
             if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch during graph capture");
             if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-            CK(cudaGraphInstantiate(&c->graph, g, 0));
+            CK(cudaGraphInstantiate(&ge, g, 0));
             cudaGraphDestroy(g);
+            it = c->graphs.emplace(phase, ge).first;
             c->graph_steps = G;
         }
-        while (left >= c->graph_steps) {
-            CK(cudaGraphLaunch(c->graph, c->stream));
-            left -= c->graph_steps;
+        while (left >= G) {   // G is a multiple of born_interval: every chunk starts at this phase
+            CK(cudaGraphLaunch(it->second, c->stream));
+            left -= G;
+            next += G;
         }
     }
     if (left > 0) {
-        cudaError_t e = enqueue_steps(c, left);
+        cudaError_t e = enqueue_steps(c, left, next);
         if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
     }
     c->step += nsteps;
@@ -572,7 +614,7 @@ int cavmd_set_state(cavmd_ctx *c, const cavmd_state *s) {
     long long stp = s->step;
     CK(cudaMemcpy(c->d_step, &stp, sizeof(long long), cudaMemcpyHostToDevice));
     c->step = s->step;
-    return initial_evaluation(c, false);
+    return initial_evaluation(c, false);   // Born charges, if any, are refreshed here as well
 }
 
 int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {

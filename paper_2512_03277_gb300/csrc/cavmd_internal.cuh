@@ -52,6 +52,12 @@ struct DftbArgs {
     int max_iter;
     int have_warm;             // 1: Cwarm and qpop hold a previous solution
     int write_b;               // 1: write Mulliken b
+    // finite-difference rows: n_disp > 0 turns every cell into n_disp displaced copies that only
+    // compute their dipole (3 NAT forward rows, or 6 NAT central rows in +h, -h pairs)
+    int n_disp;
+    int fd_central;
+    double fd_h;
+    double *M_disp;            // [n_cells][n_disp] out
 };
 
 // Arguments of the coupling / integrator kernels.
@@ -111,6 +117,10 @@ void cavmd_set_global_error(const std::string &msg);
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st);
+// b_j = dM/dr_j from the displaced dipoles (forward or central differences)
+cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const double *M_cell,
+                                 const double *M_disp, int n_disp, int central, double h, double *b,
+                                 cudaStream_t st);
 cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
                                   double *U, cudaStream_t st);
 // forward contraction of M_cell into D plus the photon half-flows (flags below)

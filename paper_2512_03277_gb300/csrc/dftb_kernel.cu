@@ -143,9 +143,12 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
     const int j = lane - g * NORB;
     const bool act = g < GPW;
     SM &m = reinterpret_cast<SM *>(smem_raw)[warp * GPW + (act ? g : 0)];
+    const bool disp = a.n_disp > 0;                       // finite-difference rows
+    const int n_rows = disp ? a.n_cells * a.n_disp : a.n_cells;
     const int idx = (blockIdx.x * wpb + warp) * GPW + g;
-    const bool valid = act && idx < a.n_cells;
-    const int cidx = min(idx, a.n_cells - 1);
+    const bool valid = act && idx < n_rows;
+    const int ridx = min(idx, n_rows - 1);
+    const int cidx = disp ? ridx / a.n_disp : ridx;
     const int cell = a.cell_list ? a.cell_list[cidx] : cidx;
     const int a0 = a.cell_offset[cell];
 
@@ -155,6 +158,13 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         m.pos[j][0] = a.r[3 * (a0 + j) + 0];
         m.pos[j][1] = a.r[3 * (a0 + j) + 1];
         m.pos[j][2] = a.r[3 * (a0 + j) + 2];
+        if (disp) {   // displaced copy: atom da, component dc, by +h (forward) or +-h (central)
+            const int k = ridx - cidx * a.n_disp;
+            const int kk = a.fd_central ? k >> 1 : k;
+            const int da = kk / 3, dc = kk - 3 * (kk / 3);
+            const double sg = (a.fd_central && (k & 1)) ? -1.0 : 1.0;
+            if (j == da) m.pos[j][dc] += sg * a.fd_h;
+        }
     }
     __syncwarp();
     if (act && j == 0) {
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
             if (j < NAT) {
                 const double qt = a.qpop[a0 + j];
                 m.qstart[j] = qt;
-                m.q[j] = fma(2.0, qt, -a.qprev[a0 + j]);
+                m.q[j] = disp ? qt : fma(2.0, qt, -a.qprev[a0 + j]);   // displaced rows start at q(r)
             }
         } else {
             for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = (i == j) ? 1.0 : 0.0;
@@ -604,6 +614,18 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
     }
     __syncwarp();
 
+    if (disp) {   // finite-difference row: only the dipole of the converged charges
+        if (valid && j == 0) {
+            double mu[3] = {0.0, 0.0, 0.0};
+            for (int at = 0; at < NAT; ++at) {
+                const double Q = m.zv[at] - m.q[at];
+                for (int k = 0; k < 3; ++k) mu[k] = fma(Q, m.pos[at][k] - m.pos[0][k], mu[k]);
+            }
+            a.M_disp[ridx] = fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
+            if (m.flag) atomicOr(a.status, (unsigned)m.flag);
+        }
+        return;
+    }
     // ---------------------------------------------------------------- energy, forces, dipole
     if (act && j < NAT) {
         double sh = 0.0;
@@ -811,14 +833,39 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
     }
 }
 
+__global__ void k_born_assemble(int n_cells, const int *__restrict__ off, const double *__restrict__ M0,
+                                const double *__restrict__ Md, int nd, int central, double h,
+                                double *__restrict__ b) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= n_cells) return;
+    const double ih = 1.0 / h;
+    const double *md = Md + (size_t)n * nd;
+    for (int j = off[n]; j < off[n + 1]; ++j) {
+        const int jl = j - off[n];
+        for (int k = 0; k < 3; ++k) {
+            const int r = 3 * jl + k;
+            b[3 * j + k] = central ? (md[2 * r] - md[2 * r + 1]) * (0.5 * ih) : (md[r] - M0[n]) * ih;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const double *M_cell,
+                                 const double *M_disp, int n_disp, int central, double h, double *b,
+                                 cudaStream_t st) {
+    k_born_assemble<<<(n_cells + 127) / 128, 128, 0, st>>>(n_cells, cell_offset, M_cell, M_disp, n_disp,
+                                                           central, h, b);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dftb_water(const DevSK *sk, const DftbArgs &a, cudaStream_t st) {
     constexpr int NAT = 3, NORB = 6;
     using SM = MolShared<NAT, NORB>;
     const int threads = 64;
     const int per_block = (threads / 32) * (32 / NORB);
-    const int blocks = (a.n_cells + per_block - 1) / per_block;
+    const long long rows = (long long)a.n_cells * (a.n_disp > 0 ? a.n_disp : 1);
+    const int blocks = (int)((rows + per_block - 1) / per_block);
     const size_t smem = sizeof(SM) * (threads / 32) * (32 / NORB);
     if (a.n_cells <= 0) return cudaSuccess;
     dftb_kernel<NAT, NORB><<<blocks, threads, smem, st>>>(sk, a);

@@ -14,6 +14,7 @@ from oracle import cavity as OC
 pytestmark = pytest.mark.gpu
 
 F_REL, Q_ABS, E_ABS = 1e-9, 1e-10, 1e-10
+B_ABS = 5e-8          # finite-difference Born charges at h = 1e-3 bohr (see the Born test)
 
 
 @pytest.fixture(scope="module")
@@ -173,3 +174,51 @@ def test_full_size_c2_sampled(P):
     idx = rng.choice(w["system"].n_atoms, 300, replace=False)
     np.testing.assert_allclose(st["p"][idx], md.p[idx], rtol=0, atol=1e-9 * np.abs(md.p).max())
     np.testing.assert_allclose(st["q"], md.q, rtol=0, atol=1e-9 * np.abs(md.q).max())
+
+
+@pytest.mark.parametrize("model,code", [("born_fd", 1), ("born_central", 2)])
+def test_born_charges_match_oracle(P, model, code):
+    """Finite-difference dipole derivatives (extra displaced rows on the GPU) against the oracle's
+    born_fd with the same step h = 1e-3 bohr. Each side's converged populations lie within about
+    2e-12 of the fixed point (residual below 1e-12, contraction rate about 0.4), the dipole lever
+    is about 3 atoms x 2 bohr, so each dipole differs by up to about 1e-11 and b by up to
+    2e-11 / h = 2e-8; the test allows 5e-8."""
+    w = cs.make_workload("c1")
+    ctx = _ctx(P, w, charge_model=code, born_interval=3, fd_step=1e-3)
+    mat, md = _oracle(w, charge_model=model, born_interval=3, fd_step=1e-3)
+    ev = ctx.cavmd_get_eval()
+    np.testing.assert_allclose(ev["b"], md.out["b"], rtol=0, atol=B_ABS)
+    _check_eval_forces(ev, mat, md)
+    # refresh schedule: steps 1, 2 keep b, step 3 recomputes it
+    b0 = ev["b"].copy()
+    for s in range(1, 5):
+        ctx.cavmd_step(1)
+        md.step()
+        evs = ctx.cavmd_get_eval()
+        np.testing.assert_allclose(evs["b"], md.out["b"], rtol=0, atol=B_ABS)
+        if s % 3:
+            assert np.array_equal(evs["b"], b0 if s < 3 else b3)
+        else:
+            b3 = evs["b"].copy()
+            assert not np.array_equal(b3, b0)
+        st = ctx.cavmd_get_state()
+        np.testing.assert_allclose(st["p"], md.p, rtol=0, atol=1e-9 * (1 + s) * np.abs(md.p).max())
+
+
+def _check_eval_forces(ev, mat, md):
+    fs = np.abs(md.out["F"]).max()
+    np.testing.assert_allclose(ev["F_dftb"], md.out["F"], rtol=0, atol=F_REL * fs)
+    np.testing.assert_allclose(ev["q_pop"], mat.q, rtol=0, atol=Q_ABS)
+
+
+def test_born_graph_chunks_follow_the_refresh_schedule(P):
+    """Graph chunks start at any refresh phase: results equal direct launches bit for bit."""
+    w = cs.make_workload("c2", n_cells=12, n_modes=32)
+    a = _ctx(P, w, charge_model=1, born_interval=3, graph_chunk=0)
+    b = _ctx(P, w, charge_model=1, born_interval=3, graph_chunk=2)
+    for n in (1, 7, 5):
+        a.cavmd_step(n)
+        b.cavmd_step(n)
+    sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        assert np.array_equal(sa[k], sb[k]), k
