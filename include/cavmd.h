@@ -58,7 +58,7 @@ extern "C" {
  *   BORN_FD      forward differences [M(r + h e) - M(r)] / h, the paper's choice, from 3 N_at
  *                displaced SCC solves per cell (warm started from the cell's solution);
  *   BORN_CENTRAL central differences from 6 N_at displaced solves (for tests and conservation);
- *   BORN_MLP     a per-atom network (needs a loaded network).                                */
+ *   BORN_MLP     the per-atom network of cavmd_load_born_mlp (below).                        */
 
 /* Integral kinds of a Slater-Koster table entry [eA][eB][kind]: SP means an s
  * orbital on the first element and a p orbital on the second. */
@@ -225,6 +225,50 @@ const char *cavmd_last_error(const cavmd_ctx *ctx);
 
 /* Frees every device buffer and the context itself. NULL is allowed. */
 void cavmd_destroy(cavmd_ctx *ctx);
+
+/* ------------------------------------------------------------------------------------------
+ * Born-charge network (CAVMD_CHARGE_BORN_MLP).
+ *
+ * Stands in for the finite-difference Born charges the paper calls its computational bottleneck
+ * (Results), against which it is trained. Per atom j of a cell: 32 invariant features of the
+ * other atoms of its cell within 8 bohr (11 Gaussian radial terms per neighbour element, 8
+ * angular terms, the element one-hot; elements 0 and 1 only), a local frame R_j (nearest
+ * neighbour, second-nearest orthogonalised, their cross product), and a 32-128-128-9 network
+ * with SiLU activations and bfloat16 weights evaluated in FP32. Its 9 outputs T_j, read as a
+ * 3 x 3 tensor in the local frame, give the Born tensor
+ *     Z_j = Q_j I + R_j^T T_j R_j - (mean over the cell of R^T T R),
+ * Q_j the Mulliken net charge, so sum_j Z_j = Q_cell I exactly and the zero network is the
+ * Mulliken model; b_j = pol^T Z_j. Parameters are one float array of CAVMD_MLP_NPARAMS values,
+ * in order W1[128][32], b1[128], W2[128][128], b2[128], W3[9][128], b3[9] (row-major); they are
+ * rounded to bfloat16 (nearest even) when loaded.
+ * Training minimises sum_j |Z_j - Z_ref_j|^2 / (9 n_atoms) with AdamW (beta 0.9, 0.999, eps
+ * 1e-8) on FP32 master weights, on the GPU. Data: water cells (O, H, H); all arrays host. */
+#define CAVMD_MLP_NFEAT 32
+#define CAVMD_MLP_HIDDEN 128
+#define CAVMD_MLP_NPARAMS 21897
+typedef struct cavmd_mlp cavmd_mlp;
+/* Creates a network with the given parameters on `device` (its own stream and memory). */
+int cavmd_mlp_create(cavmd_mlp **mlp, const float *params, int32_t n_params, int32_t device);
+/* Loads n_cells water cells: species [3 n_cells], positions r [9 n_cells] (bohr), Mulliken net
+ * charges Q [3 n_cells] and, for training, reference Born tensors Z_ref [27 n_cells]
+ * (Z_ref[9 j + 3 alpha + beta] = d mu_alpha / d r_j,beta), or NULL. Computes the features. */
+int cavmd_mlp_set_data(cavmd_mlp *mlp, int32_t n_cells, const int32_t *species, const double *r,
+                       const double *Q, const double *Z_ref);
+/* Loss and its gradient (FP32, [CAVMD_MLP_NPARAMS], may be NULL) over all loaded cells at the
+ * current bfloat16 weights. */
+int cavmd_mlp_loss_grad(cavmd_mlp *mlp, double *loss, float *grad);
+/* AdamW over `epochs` passes of shuffled mini-batches of batch_cells cells (shuffle seeded by
+ * seed); epoch_loss [epochs] (may be NULL) receives the mean batch loss of every epoch. */
+int cavmd_mlp_train(cavmd_mlp *mlp, int32_t epochs, int32_t batch_cells, float lr, float weight_decay,
+                    uint64_t seed, double *epoch_loss);
+/* Predicted Born tensors [27 n_cells] of the loaded cells. */
+int cavmd_mlp_predict(cavmd_mlp *mlp, double *Z_out);
+/* Current parameters (the bfloat16 values, as floats). */
+int cavmd_mlp_get_params(cavmd_mlp *mlp, float *params);
+void cavmd_mlp_destroy(cavmd_mlp *mlp);
+/* Loads network parameters into a context created with CAVMD_CHARGE_BORN_MLP and recomputes b
+ * at the current positions (before a load the network is zero, i.e. Mulliken charges). */
+int cavmd_load_born_mlp(cavmd_ctx *ctx, const float *params, int32_t n_params);
 
 /* Allocation-free field and kick (no counterpart in the paper; an addition for embedding).
  *

@@ -104,6 +104,16 @@ def load_library(path: str = LIB_PATH):
     lib.cavmd_destroy.restype = None
     lib.cavmd_field_kick_noalloc.argtypes = [C.c_int32, C.c_int32] + [C.c_void_p] * 6 + [C.c_double] + \
         [C.c_void_p] * 4
+    _fp = C.POINTER(C.c_float)
+    lib.cavmd_mlp_create.argtypes = [C.POINTER(C.c_void_p), _fp, C.c_int32, C.c_int32]
+    lib.cavmd_mlp_set_data.argtypes = [C.c_void_p, C.c_int32, _ip, _dp, _dp, _dp]
+    lib.cavmd_mlp_loss_grad.argtypes = [C.c_void_p, _dp, _fp]
+    lib.cavmd_mlp_train.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_uint64, _dp]
+    lib.cavmd_mlp_predict.argtypes = [C.c_void_p, _dp]
+    lib.cavmd_mlp_get_params.argtypes = [C.c_void_p, _fp]
+    lib.cavmd_mlp_destroy.argtypes = [C.c_void_p]
+    lib.cavmd_mlp_destroy.restype = None
+    lib.cavmd_load_born_mlp.argtypes = [C.c_void_p, _fp, C.c_int32]
     lib.cavmd_struct_size.argtypes = [C.c_int32]
     lib.cavmd_struct_size.restype = C.c_size_t
     for i, st in enumerate(STRUCTS):
@@ -173,6 +183,65 @@ def cavmd_field_kick_noalloc(n_cells, n_modes, cell_offset, U, W, F, b, inv_mass
     rc = lib.cavmd_field_kick_noalloc(int(n_cells), int(n_modes), cell_offset, U, W, F, b, inv_mass, float(tau),
                                       p, E_out or None, e_kin_out, stream or None)
     _check(rc, None)
+
+
+MLP_NPARAMS = 21897
+
+
+class BornMLP:
+    """The library's Born-charge network (cavmd_mlp_* in cavmd.h): trained and evaluated on the
+    GPU by the library's kernels. Arrays are host NumPy arrays."""
+
+    def __init__(self, params, device=0):
+        self.lib = load_library()
+        p = np.ascontiguousarray(params, np.float32)
+        if p.size != MLP_NPARAMS:
+            raise ValueError("need MLP_NPARAMS parameters")
+        self.handle = C.c_void_p()
+        _check(self.lib.cavmd_mlp_create(C.byref(self.handle), _ptr(p, C.c_float), p.size, int(device)), None)
+        self.n_cells = 0
+
+    def cavmd_mlp_set_data(self, species, r, Q, Z_ref=None):
+        sp = np.ascontiguousarray(species, np.int32).ravel()
+        self.n_cells = sp.size // 3
+        self._data = (sp, np.ascontiguousarray(r, np.float64).ravel(), np.ascontiguousarray(Q, np.float64).ravel(),
+                      None if Z_ref is None else np.ascontiguousarray(Z_ref, np.float64).ravel())
+        sp_, r_, Q_, Z_ = self._data
+        _check(self.lib.cavmd_mlp_set_data(self.handle, self.n_cells, _ptr(sp_, C.c_int32), _ptr(r_), _ptr(Q_),
+                                           None if Z_ is None else _ptr(Z_)), None)
+
+    def cavmd_mlp_loss_grad(self):
+        loss = C.c_double()
+        g = np.empty(MLP_NPARAMS, np.float32)
+        _check(self.lib.cavmd_mlp_loss_grad(self.handle, C.byref(loss), _ptr(g, C.c_float)), None)
+        return loss.value, g
+
+    def cavmd_mlp_train(self, epochs, batch_cells, lr, weight_decay=0.0, seed=0):
+        el = np.empty(epochs)
+        _check(self.lib.cavmd_mlp_train(self.handle, int(epochs), int(batch_cells), float(lr), float(weight_decay),
+                                        int(seed), _ptr(el)), None)
+        return el
+
+    def cavmd_mlp_predict(self):
+        Z = np.empty((3 * self.n_cells, 3, 3))
+        _check(self.lib.cavmd_mlp_predict(self.handle, _ptr(Z)), None)
+        return Z
+
+    def cavmd_mlp_get_params(self):
+        p = np.empty(MLP_NPARAMS, np.float32)
+        _check(self.lib.cavmd_mlp_get_params(self.handle, _ptr(p, C.c_float)), None)
+        return p
+
+    def cavmd_mlp_destroy(self):
+        if self.handle:
+            self.lib.cavmd_mlp_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.cavmd_mlp_destroy()
+        except Exception:
+            pass
 
 
 class Context:
@@ -296,6 +365,10 @@ class Context:
         _check(self.lib.cavmd_phase_times(self.handle, int(enable), _ptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)),
                                           int(reset)), self.handle)
         return ms, cnt
+
+    def cavmd_load_born_mlp(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        _check(self.lib.cavmd_load_born_mlp(self.handle, _ptr(p, C.c_float), p.size), self.handle)
 
     def cavmd_last_error(self) -> str:
         return self.lib.cavmd_last_error(self.handle).decode()

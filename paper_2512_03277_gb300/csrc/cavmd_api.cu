@@ -42,7 +42,9 @@ struct cavmd_ctx {
     double *d_cos = nullptr, *d_sin = nullptr, *d_omc = nullptr;
     double *d_q = nullptr, *d_pq = nullptr, *d_qs = nullptr, *d_pqs = nullptr, *d_D = nullptr;
     double *d_W1 = nullptr, *d_W2 = nullptr, *d_emode = nullptr, *d_Einst = nullptr;
-    double *d_ekp = nullptr, *d_edp = nullptr, *d_hist = nullptr, *d_Mdisp = nullptr;
+    double *d_ekp = nullptr, *d_edp = nullptr, *d_hist = nullptr, *d_Mdisp = nullptr, *d_Q = nullptr;
+    float *d_mlpX = nullptr, *d_mlpR = nullptr, *d_mlpZl = nullptr, *d_mlpf = nullptr;
+    void *d_mlpw = nullptr;                  // bfloat16 network parameters
     unsigned *d_done = nullptr, *d_status = nullptr;
     long long *d_step = nullptr;
     std::vector<void *> allocs;
@@ -199,6 +201,18 @@ cudaError_t run_born(cavmd_ctx *c) {
                                 c->stream);
 }
 
+// Network dipole derivatives at the current positions (after the cell evaluation).
+cudaError_t run_mlp(cavmd_ctx *c) {
+    PhaseScope ps(c, 3);
+    cudaError_t e = launch_mlp_features(c->N, c->d_off, c->d_species, c->d_r, c->d_mlpX, c->d_mlpR, c->d_status,
+                                        c->stream);
+    if (e == cudaSuccess) e = launch_mlp_forward(c->n_atoms, c->d_mlpX, c->d_mlpR, c->d_mlpw, c->d_mlpZl, c->stream);
+    if (e == cudaSuccess)
+        e = launch_mlp_born(c->N, c->d_off, c->d_mlpZl, c->d_mlpR, c->d_Q, c->pol[0], c->pol[1], c->pol[2], c->d_b,
+                            c->stream);
+    return e;
+}
+
 bool born_refresh(const cavmd_ctx *c, int64_t eval_index) {
     return c->n_disp > 0 && (eval_index % c->opt.born_interval) == 0;
 }
@@ -223,6 +237,7 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
         const bool last = (s == n - 1);
         if ((e = run_dftb(c, 1)) != cudaSuccess) return e;
         if (born_refresh(c, first_step + s) && (e = run_born(c)) != cudaSuccess) return e;
+        if (c->d_mlpw && (e = run_mlp(c)) != cudaSuccess) return e;
         if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
         if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
     }
@@ -232,6 +247,7 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
 int initial_evaluation(cavmd_ctx *c, bool init_photons) {
     CK(run_dftb(c, 0));
     if (c->n_disp > 0) CK(run_born(c));
+    if (c->d_mlpw) CK(run_mlp(c));
     if (init_photons) {
         const int pf = (c->opt.photon_init == CAVMD_PHOTON_ZERO) ? PH_INIT_ZERO : PH_INIT_RELAXED;
         CK(run_photon(c, PH_FORWARD | pf | PH_ENERGY));
@@ -297,7 +313,6 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if (!(o->scc_tol > 0.0) || o->scc_max_iter < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad SCC tolerance or iteration limit");
     if (!(o->mixing > 0.0 && o->mixing <= 1.0)) return fail(c, CAVMD_ERR_INVALID_ARG, "mixing must be in (0, 1]");
     if (o->precision != CAVMD_PREC_FP64) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_PREC_FP64 in this build");
-    if (o->charge_model == CAVMD_CHARGE_BORN_MLP) return fail(c, CAVMD_ERR_UNSUPPORTED, "CAVMD_CHARGE_BORN_MLP needs a loaded network");
     if (o->charge_model < CAVMD_CHARGE_MULLIKEN || o->charge_model > CAVMD_CHARGE_BORN_MLP)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad charge_model");
     if (o->charge_model != CAVMD_CHARGE_MULLIKEN && (o->born_interval < 1 || !(o->fd_step > 0.0)))
@@ -380,6 +395,18 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     if (c->opt.charge_model == CAVMD_CHARGE_BORN_FD) c->n_disp = 3 * 3;
     if (c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL) c->n_disp = 6 * 3;
     if (c->n_disp) AL(c->d_Mdisp, (size_t)N * c->n_disp);
+    if (c->opt.charge_model == CAVMD_CHARGE_BORN_MLP) {
+        AL(c->d_Q, NA);
+        AL(c->d_mlpX, (size_t)NA * CAVMD_MLP_NFEAT);
+        AL(c->d_mlpR, (size_t)NA * 9);
+        AL(c->d_mlpZl, (size_t)NA * 9);
+        AL(c->d_mlpf, CAVMD_MLP_NPARAMS);
+        void *w = nullptr;
+        int rc = dalloc(c, &w, (size_t)CAVMD_MLP_NPARAMS * 2);
+        if (rc) return rc;
+        c->d_mlpw = w;
+        CK(cudaMemsetAsync(c->d_mlpw, 0, (size_t)CAVMD_MLP_NPARAMS * 2, c->stream));   // zero network
+    }
 
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(c->d_sk, &hsk, sizeof(DevSK), cudaMemcpyHostToDevice, st));
@@ -433,6 +460,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.fd_central = 0;
     d.fd_h = c->opt.fd_step;
     d.M_disp = nullptr;
+    d.Qout = c->d_Q;
 
     StepArgs &s = c->sa;
     s.N = N; s.M = M; s.n_atoms = NA;
@@ -647,6 +675,20 @@ int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
                 for (int k = 0; k < 3; ++k) o->F_total[3 * i + k] = F[3 * i + k] + E[n] * b[3 * i + k];
     }
     return rc;
+}
+
+int cavmd_load_born_mlp(cavmd_ctx *c, const float *params, int32_t n_params) {
+    if (!c) return fail(nullptr, CAVMD_ERR_INVALID_ARG, "NULL context");
+    if (!params || n_params != CAVMD_MLP_NPARAMS) return fail(c, CAVMD_ERR_INVALID_ARG, "need CAVMD_MLP_NPARAMS parameters");
+    if (!c->d_mlpw) return fail(c, CAVMD_ERR_INVALID_ARG, "context was not created with CAVMD_CHARGE_BORN_MLP");
+    int rc = sync_status(c);
+    if (rc) return rc;
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) return fail(c, CAVMD_ERR_INVALID_ARG, "non-finite network parameter");
+    CK(cudaMemcpy(c->d_mlpf, params, sizeof(float) * n_params, cudaMemcpyHostToDevice));
+    CK(launch_to_bf16(c->d_mlpf, c->d_mlpw, n_params, c->stream));
+    CK(run_mlp(c));
+    return sync_status(c);
 }
 
 int cavmd_phase_times(cavmd_ctx *c, int32_t enable, double *ms, int64_t *cnt, int32_t reset) {

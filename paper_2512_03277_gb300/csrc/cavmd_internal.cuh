@@ -58,6 +58,7 @@ struct DftbArgs {
     int fd_central;
     double fd_h;
     double *M_disp;            // [n_cells][n_disp] out
+    double *Qout;              // [n_atoms] out: Mulliken net charges (may be NULL)
 };
 
 // Arguments of the coupling / integrator kernels.
@@ -121,6 +122,14 @@ cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream
 cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const double *M_cell,
                                  const double *M_disp, int n_disp, int central, double h, double *b,
                                  cudaStream_t st);
+// Born-charge network pieces used by a time step
+cudaError_t launch_mlp_features(int n_cells, const int *off, const int *species, const double *r, float *X,
+                                float *R, unsigned *status, cudaStream_t st);
+cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, const void *w_bf16, float *Zl,
+                               cudaStream_t st);
+cudaError_t launch_mlp_born(int n_cells, const int *off, const float *Zl, const float *R, const double *Q,
+                            double pol0, double pol1, double pol2, double *b, cudaStream_t st);
+cudaError_t launch_to_bf16(const float *src, void *dst, int n, cudaStream_t st);
 cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
                                   double *U, cudaStream_t st);
 // forward contraction of M_cell into D plus the photon half-flows (flags below)

@@ -801,6 +801,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         for (int k = 0; k < 3; ++k) a.F[3 * at + k] = f[k];
         a.qprev[at] = a.have_warm ? m.qstart[j] : m.q[j];
         a.qpop[at] = m.q[j];
+        if (a.Qout) a.Qout[at] = m.zv[j] - m.q[j];
         if (a.write_b) {
             const double Q = m.zv[j] - m.q[j];
             a.b[3 * at + 0] = Q * a.pol0;
