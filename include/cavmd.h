@@ -298,6 +298,12 @@ int cavmd_field_kick_noalloc(int32_t n_cells, int32_t n_modes, const int32_t *ce
                              const double *inv_mass, double tau, double *p, double *E_out,
                              double *e_kin_out, void *stream);
 
+/* Diagnostic of the tensor-core building block used by the mixed-precision coupling (no paper
+ * counterpart): C[128][N] = A[128][K] B[N][K]^T with A, B bfloat16 bit patterns (host, row-major,
+ * K contiguous) multiplied on the fifth-generation tensor cores with FP32 accumulation; C host,
+ * row-major. K a positive multiple of 64, N = 128 or 256. Allocates its own device buffers. */
+int cavmd_tc_selftest(const uint16_t *A, const uint16_t *B, int32_t K, int32_t N, float *C);
+
 /* Size of one of the library's structs, for bindings that lay them out by hand. */
 size_t cavmd_struct_size(int32_t which); /* 0 system, 1 sk_tables, 2 modes, 3 options,
                                             4 obs, 5 state, 6 eval */
