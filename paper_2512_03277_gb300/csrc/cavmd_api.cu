@@ -9,6 +9,7 @@
 // A call of cavmd_step(n) opens with the first half-flow (photon + field kernels without the
 // forward contraction) and closes with a second half-flow only, so the state between calls is
 // synchronised. Chunks of graph_chunk steps are captured once as a CUDA graph and replayed.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -45,6 +46,10 @@ struct cavmd_ctx {
     double *d_ekp = nullptr, *d_edp = nullptr, *d_hist = nullptr, *d_Mdisp = nullptr, *d_Q = nullptr;
     float *d_mlpX = nullptr, *d_mlpR = nullptr, *d_mlpZl = nullptr, *d_mlpf = nullptr;
     void *d_mlpw = nullptr;                  // bfloat16 network parameters
+    bool mixed = false;                      // tensor-core coupling (modes on a grid)
+    TcPlan tc{};
+    double *d_G = nullptr, *d_E2 = nullptr, *d_E1 = nullptr;
+    float *d_Wt2 = nullptr, *d_Wt1 = nullptr;
     unsigned *d_done = nullptr, *d_status = nullptr;
     long long *d_step = nullptr;
     std::vector<void *> allocs;
@@ -217,6 +222,21 @@ bool born_refresh(const cavmd_ctx *c, int64_t eval_index) {
     return c->n_disp > 0 && (eval_index % c->opt.born_interval) == 0;
 }
 
+cudaError_t run_tc_forward(cavmd_ctx *c) {
+    PhaseScope ps(c, 1);
+    return launch_tc_forward(c->tc, c->d_Mc, c->d_G, c->d_status, c->stream);
+}
+
+// Back product for the second half-flow (Wt2 -> E2) and, when `first`, the next first half-flow
+// (Wt1 -> E1); with second = false only Wt1 -> E1.
+cudaError_t run_tc_back(cavmd_ctx *c, bool second, bool first) {
+    PhaseScope ps(c, 2);
+    if (second)
+        return launch_tc_back(c->tc, c->d_Wt2, first ? c->d_Wt1 : nullptr, c->d_E2, first ? c->d_E1 : nullptr,
+                              c->d_status, c->stream);
+    return launch_tc_back(c->tc, c->d_Wt1, nullptr, c->d_E1, nullptr, c->d_status, c->stream);
+}
+
 cudaError_t run_photon(cavmd_ctx *c, int flags) {
     PhaseScope ps(c, 1);
     return launch_photon(c->sa, flags, c->stream);
@@ -231,13 +251,23 @@ cudaError_t run_field(cavmd_ctx *c, int flags) {
 // step number first_step (evaluation index = step number, init being evaluation 0).
 cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     cudaError_t e;
+    const int given = c->mixed ? FLD_E_GIVEN : 0;
     if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
-    if ((e = run_field(c, FLD_FIRST)) != cudaSuccess) return e;
+    if (c->mixed && (e = run_tc_back(c, false, true)) != cudaSuccess) return e;
+    if ((e = run_field(c, FLD_FIRST | given)) != cudaSuccess) return e;
     for (int64_t s = 0; s < n; ++s) {
         const bool last = (s == n - 1);
         if ((e = run_dftb(c, 1)) != cudaSuccess) return e;
         if (born_refresh(c, first_step + s) && (e = run_born(c)) != cudaSuccess) return e;
         if (c->d_mlpw && (e = run_mlp(c)) != cudaSuccess) return e;
+        if (c->mixed) {
+            if ((e = run_tc_forward(c)) != cudaSuccess) return e;
+            if ((e = run_photon(c, PH_FORWARD_G | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
+            if ((e = run_tc_back(c, true, !last)) != cudaSuccess) return e;
+            if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | FLD_E_GIVEN | (last ? 0 : FLD_FIRST))) != cudaSuccess)
+                return e;
+            continue;
+        }
         if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
         if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
     }
@@ -248,11 +278,16 @@ int initial_evaluation(cavmd_ctx *c, bool init_photons) {
     CK(run_dftb(c, 0));
     if (c->n_disp > 0) CK(run_born(c));
     if (c->d_mlpw) CK(run_mlp(c));
+    int fwd = PH_FORWARD;
+    if (c->mixed) {
+        CK(run_tc_forward(c));
+        fwd = PH_FORWARD_G;
+    }
     if (init_photons) {
         const int pf = (c->opt.photon_init == CAVMD_PHOTON_ZERO) ? PH_INIT_ZERO : PH_INIT_RELAXED;
-        CK(run_photon(c, PH_FORWARD | pf | PH_ENERGY));
+        CK(run_photon(c, fwd | pf | PH_ENERGY));
     } else {
-        CK(run_photon(c, PH_FORWARD | PH_ENERGY));   // keeps q_sync / pq_sync
+        CK(run_photon(c, fwd | PH_ENERGY));   // keeps q_sync / pq_sync
     }
     CK(run_field(c, FLD_ENERGY));
     return sync_status(c);
@@ -273,6 +308,53 @@ void fill_devsk(const cavmd_sk_tables *t, DevSK *d) {
     d->r_cut = t->r_cut;
     d->taper = t->taper;
     d->inv_taper = 1.0 / t->taper;
+}
+
+// Modes on a uniform in-plane grid in the order a = s + 2 (jy + Ky2 jx), k = (jx dkx, jy dky, 0),
+// phase 0 (s = 0) or -pi/2 (s = 1): the structure the tensor-core contraction factorises.
+bool detect_grid(const cavmd_modes *md, int &Kx, int &Ky2, double &dkx, double &dky, std::string &why) {
+    const int M = md->n_modes;
+    dkx = 0.0;
+    dky = 0.0;
+    for (int a = 0; a < M; ++a) {
+        const double kx = md->k[3 * a], ky = md->k[3 * a + 1], kz = md->k[3 * a + 2];
+        if (kz != 0.0 || kx < 0.0 || ky < 0.0) { why = "modes need k_z = 0 and k_x, k_y >= 0"; return false; }
+        if (kx > 0.0 && (dkx == 0.0 || kx < dkx)) dkx = kx;
+        if (ky > 0.0 && (dky == 0.0 || ky < dky)) dky = ky;
+    }
+    int mx = 0, my = 0;
+    std::vector<int> jxs(M), jys(M);
+    for (int a = 0; a < M; ++a) {
+        const double kx = md->k[3 * a], ky = md->k[3 * a + 1];
+        const long jx = dkx > 0.0 ? std::lround(kx / dkx) : 0, jy = dky > 0.0 ? std::lround(ky / dky) : 0;
+        if (std::fabs(kx - jx * dkx) > 1e-9 * dkx || std::fabs(ky - jy * dky) > 1e-9 * dky) {
+            why = "mode wave vectors are not on a uniform grid";
+            return false;
+        }
+        jxs[a] = (int)jx;
+        jys[a] = (int)jy;
+        mx = std::max(mx, (int)jx);
+        my = std::max(my, (int)jy);
+    }
+    Kx = mx + 1;
+    Ky2 = my + 1;
+    if (M != 2 * Kx * Ky2) { why = "mode count is not 2 Kx Ky2"; return false; }
+    for (int a = 0; a < M; ++a) {
+        const int s = a & 1, rem = a >> 1;
+        if (jxs[a] != rem / Ky2 || jys[a] != rem % Ky2) { why = "modes are not ordered a = s + 2 (jy + Ky2 jx)"; return false; }
+        const double ph = s == 0 ? 0.0 : -1.5707963267948966;
+        if (std::fabs(md->phi[a] - ph) > 1e-12) { why = "mode phases must be 0 (cos) and -pi/2 (sin)"; return false; }
+    }
+    if (2 * Kx > 128) { why = "2 Kx must not exceed 128"; return false; }
+    return true;
+}
+
+int padded_ky(int Ky2) {
+    const int need = 2 * Ky2;
+    const int sizes[] = {16, 32, 48, 64, 96, 128};
+    for (int v : sizes)
+        if (v >= need) return v;
+    return 0;
 }
 
 int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_modes *md,
@@ -312,7 +394,10 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if (!(o->dt > 0.0) || !std::isfinite(o->dt)) return fail(c, CAVMD_ERR_INVALID_ARG, "dt must be positive");
     if (!(o->scc_tol > 0.0) || o->scc_max_iter < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad SCC tolerance or iteration limit");
     if (!(o->mixing > 0.0 && o->mixing <= 1.0)) return fail(c, CAVMD_ERR_INVALID_ARG, "mixing must be in (0, 1]");
-    if (o->precision != CAVMD_PREC_FP64) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_PREC_FP64 in this build");
+    if (o->precision == CAVMD_PREC_MIXED_TF32)
+        return fail(c, CAVMD_ERR_UNSUPPORTED, "CAVMD_PREC_MIXED_TF32 is not built; use CAVMD_PREC_MIXED_BF16X3");
+    if (o->precision != CAVMD_PREC_FP64 && o->precision != CAVMD_PREC_MIXED_BF16X3)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "bad precision");
     if (o->charge_model < CAVMD_CHARGE_MULLIKEN || o->charge_model > CAVMD_CHARGE_BORN_MLP)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad charge_model");
     if (o->charge_model != CAVMD_CHARGE_MULLIKEN && (o->born_interval < 1 || !(o->fd_step > 0.0)))
@@ -322,6 +407,14 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
     if (o->graph_chunk < 0 || o->energy_history < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad graph_chunk or energy_history");
     if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return fail(c, CAVMD_ERR_INVALID_ARG, "dev_alloc and dev_free go together");
+    if (o->precision == CAVMD_PREC_MIXED_BF16X3) {
+        int Kx, Ky2;
+        double dkx, dky;
+        std::string why;
+        if (!detect_grid(md, Kx, Ky2, dkx, dky, why))
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "mixed-precision coupling needs modes on a grid: " + why);
+        if (!padded_ky(Ky2)) return fail(c, CAVMD_ERR_UNSUPPORTED, "2 Ky2 must not exceed 128");
+    }
     return CAVMD_OK;
 }
 
@@ -385,7 +478,9 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     AL(c->d_r, 3 * NA); AL(c->d_p, 3 * NA); AL(c->d_F, 3 * NA); AL(c->d_b, 3 * NA);
     AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)N * 36); AL(c->d_E, N); AL(c->d_Mc, N);
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N);
-    AL(c->d_U, (size_t)M * N); AL(c->d_k, 3 * M); AL(c->d_phi, M); AL(c->d_R, 3 * N);
+    c->mixed = c->opt.precision == CAVMD_PREC_MIXED_BF16X3;
+    if (!c->mixed) AL(c->d_U, (size_t)M * N);
+    AL(c->d_k, 3 * M); AL(c->d_phi, M); AL(c->d_R, 3 * N);
     AL(c->d_omega, M); AL(c->d_lam, M); AL(c->d_iomega, M); AL(c->d_cos, M); AL(c->d_sin, M); AL(c->d_omc, M);
     AL(c->d_q, M); AL(c->d_pq, M); AL(c->d_qs, M); AL(c->d_pqs, M); AL(c->d_D, M);
     AL(c->d_W1, M); AL(c->d_W2, M); AL(c->d_emode, 4 * M);
@@ -431,7 +526,27 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 8 * c->opt.energy_history, st));
     CK(cudaMemsetAsync(c->d_q, 0, sizeof(double) * M, st));
     CK(cudaMemsetAsync(c->d_pq, 0, sizeof(double) * M, st));
-    CK(launch_mode_functions(c->d_k, c->d_phi, c->d_R, M, N, c->d_U, st));
+    if (!c->mixed) {
+        CK(launch_mode_functions(c->d_k, c->d_phi, c->d_R, M, N, c->d_U, st));
+    } else {
+        TcPlan &p = c->tc;
+        std::string why;
+        detect_grid(md, p.Kx, p.Ky2, p.dkx, p.dky, why);
+        p.KY = padded_ky(p.Ky2);
+        p.N = N;
+        p.Npad = ((N + 127) / 128) * 128;
+        p.n_fwd_cta = std::min(p.Npad / 64, 152);
+        const size_t np = (size_t)p.Npad;
+        AL(p.Ahi, 128 * np); AL(p.Alo, 128 * np); AL(p.Af, 128 * np); AL(p.Bsrc, (size_t)p.KY * np);
+        AL(p.Yhi, (size_t)p.KY * np); AL(p.Ylo, (size_t)p.KY * np);
+        AL(p.partial, (size_t)p.n_fwd_cta * 128 * p.KY);
+        AL(c->d_G, 128 * (size_t)p.KY); AL(c->d_Wt2, 128 * (size_t)p.KY); AL(c->d_Wt1, 128 * (size_t)p.KY);
+        AL(c->d_E2, N); AL(c->d_E1, N);
+        CK(cudaMemsetAsync(c->d_Wt2, 0, sizeof(float) * 128 * p.KY, st));
+        CK(cudaMemsetAsync(c->d_Wt1, 0, sizeof(float) * 128 * p.KY, st));
+        CK(tc_prepare(p.KY));
+        CK(launch_tc_panels(p, c->d_R, st));
+    }
 
     DftbArgs &d = c->da;
     d.n_cells = N;
@@ -472,6 +587,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.W1 = c->d_W1; s.W2 = c->d_W2; s.e_mode = c->d_emode; s.e_kin_part = c->d_ekp; s.e_dftb_part = c->d_edp;
     s.done_counter = c->d_done; s.hist = c->d_hist; s.hist_cap = c->opt.energy_history;
     s.step_counter = c->d_step; s.status = c->d_status; s.dt = c->opt.dt; s.tau = tau;
+    s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->d_E2; s.E1in = c->d_E1;
+    s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     return CAVMD_OK;
 }
 
@@ -663,8 +780,25 @@ int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
         CK(cudaMemcpy(w.data(), c->d_omega, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(lam.data(), c->d_lam, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
         for (int a = 0; a < c->M; ++a) W[a] = lam[a] * (w[a] * q[a] - D[a]);
-        CK(cudaMemcpy(c->d_W1, W.data(), sizeof(double) * c->M, cudaMemcpyHostToDevice));
-        CK(launch_field_only(c->d_U, c->d_W1, c->M, c->N, c->d_Einst, c->stream));
+        if (c->mixed) {   // same arrangement of the weights as the photon kernel writes
+            const TcPlan &p = c->tc;
+            std::vector<float> Wt((size_t)128 * p.KY, 0.0f);
+            for (int a = 0; a < c->M; ++a) {
+                const int jx = a / (2 * p.Ky2), rem = a - jx * 2 * p.Ky2, jy = rem >> 1, sm = rem & 1;
+                if (sm == 0) {
+                    Wt[jx * p.KY + jy] = (float)W[a];
+                    Wt[(p.Kx + jx) * p.KY + p.Ky2 + jy] = (float)(-W[a]);
+                } else {
+                    Wt[jx * p.KY + p.Ky2 + jy] = (float)W[a];
+                    Wt[(p.Kx + jx) * p.KY + jy] = (float)W[a];
+                }
+            }
+            CK(cudaMemcpy(c->d_Wt1, Wt.data(), sizeof(float) * Wt.size(), cudaMemcpyHostToDevice));
+            CK(launch_tc_back(p, c->d_Wt1, nullptr, c->d_Einst, nullptr, c->d_status, c->stream));
+        } else {
+            CK(cudaMemcpy(c->d_W1, W.data(), sizeof(double) * c->M, cudaMemcpyHostToDevice));
+            CK(launch_field_only(c->d_U, c->d_W1, c->M, c->N, c->d_Einst, c->stream));
+        }
         CK(cudaStreamSynchronize(c->stream));
         std::vector<double> E(N), F(3 * NA), b(3 * NA);
         CK(cudaMemcpy(E.data(), c->d_Einst, sizeof(double) * N, cudaMemcpyDeviceToHost));

@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/cavmd.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,7 +90,27 @@ struct StepArgs {
     long long *step_counter;   // device step counter
     unsigned *status;
     double dt, tau;
+    // mixed-precision coupling (modes on a grid): Gram matrix in, weight matrices and fields out
+    const double *G;           // [128][KY] forward Gram matrix (PH_FORWARD_G)
+    float *Wt2, *Wt1;          // [128][KY] back-product weights written by the photon kernel
+    const double *E2in, *E1in; // [N] fields from the back product (FLD_E_GIVEN)
+    int Kx, Ky2, KY;
 };
+
+// Plan of the tensor-core coupling contraction for modes on a uniform in-plane grid.
+struct TcPlan {
+    int N, Npad, Kx, Ky2, KY, n_fwd_cta;
+    double dkx, dky;
+    __nv_bfloat16 *Ahi, *Alo, *Yhi, *Ylo;   // phase panels (bfloat16 hi / lo, core-matrix order)
+    float *Af, *Bsrc, *partial;             // FP32 panels and split-K partial Gram matrices
+};
+size_t tc_fwd_smem(int KY);
+size_t tc_back_smem(int KY);
+cudaError_t tc_prepare(int KY);   // kernel attributes (shared-memory size), once per plan
+cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st);
+cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsigned *status, cudaStream_t st);
+cudaError_t launch_tc_back(const TcPlan &p, const float *Wt2, const float *Wt1, double *E2, double *E1,
+                           unsigned *status, cudaStream_t st);
 
 // |x| < y for finite doubles and y > 0, by the ordering of the IEEE bit patterns: an integer
 // comparison that leaves the FP64 pipe free.
@@ -134,11 +155,11 @@ cudaError_t launch_mode_functions(const double *k, const double *phi, const doub
                                   double *U, cudaStream_t st);
 // forward contraction of M_cell into D plus the photon half-flows (flags below)
 enum { PH_FORWARD = 1, PH_SECOND = 2, PH_FIRST = 4, PH_INIT_RELAXED = 8, PH_INIT_ZERO = 16,
-       PH_ENERGY = 32 };
+       PH_ENERGY = 32, PH_FORWARD_G = 64 };
 cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st);
 // field on the cells with weights W2 (second half-flow kick) and/or W1 (first half-flow kick +
 // drift); always records the energies of the synchronised state when FLD_ENERGY is set
-enum { FLD_SECOND = 1, FLD_FIRST = 2, FLD_ENERGY = 4 };
+enum { FLD_SECOND = 1, FLD_FIRST = 2, FLD_ENERGY = 4, FLD_E_GIVEN = 8 };
 cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st);
 int field_blocks(int N);
 // instantaneous field E_n = sum_a u_a(R_n) W_a for a caller-supplied weight vector

@@ -49,6 +49,20 @@ __device__ __forceinline__ double block_sum_ordered(double v, double *red) {
     return s;   // valid in thread 0
 }
 
+// Weight W of mode (jx, jy, s) into the back-product matrix Wt (rows cos|sin of jx, columns
+// cos|sin of jy): cos modes at (jx, jy) and -(Kx + jx, Ky2 + jy), sin modes at (jx, Ky2 + jy) and
+// (Kx + jx, jy).
+__device__ __forceinline__ void put_weight(const StepArgs &a, float *Wt, int al, double W) {
+    const int jx = al / (2 * a.Ky2), rem = al - jx * 2 * a.Ky2, jy = rem >> 1, sm = rem & 1;
+    if (sm == 0) {
+        Wt[jx * a.KY + jy] = (float)W;
+        Wt[(a.Kx + jx) * a.KY + a.Ky2 + jy] = (float)(-W);
+    } else {
+        Wt[jx * a.KY + a.Ky2 + jy] = (float)W;
+        Wt[(a.Kx + jx) * a.KY + jy] = (float)W;
+    }
+}
+
 __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {
     __shared__ double red[PH_THREADS / 32];
     const int al = blockIdx.x;
@@ -61,6 +75,15 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         s = block_sum_ordered(s, red);
         if (threadIdx.x == 0) {
             D = a.lam[al] * s;
+            a.D[al] = D;
+        }
+    } else if (flags & PH_FORWARD_G) {
+        if (threadIdx.x == 0) {   // mode (jx, jy, s) from the factorised Gram matrix
+            const int jx = al / (2 * a.Ky2), rem = al - jx * 2 * a.Ky2, jy = rem >> 1, sm = rem & 1;
+            const double *g = a.G;
+            const double v = sm == 0 ? g[jx * a.KY + jy] - g[(a.Kx + jx) * a.KY + a.Ky2 + jy]
+                                     : g[(a.Kx + jx) * a.KY + jy] + g[jx * a.KY + a.Ky2 + jy];
+            D = a.lam[al] * v;
             a.D[al] = D;
         }
     } else if (threadIdx.x == 0) {
@@ -81,6 +104,7 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         const double q = a.q[al], p = a.pq[al];
         const double y = q - cen;
         a.W2[al] = lam * fma(y, s, p * omc);
+        if (a.Wt2) put_weight(a, a.Wt2, al, a.W2[al]);
         qs = cen + fma(y, c, p * s * iw);
         ps = fma(p, c, -w * y * s);
     } else {
@@ -100,6 +124,7 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
     if (flags & PH_FIRST) {
         const double y = qs - cen;
         a.W1[al] = lam * fma(y, s, ps * omc);
+        if (a.Wt1) put_weight(a, a.Wt1, al, a.W1[al]);
         a.q[al] = cen + fma(y, c, ps * s * iw);
         a.pq[al] = fma(ps, c, -w * y * s);
     } else {
@@ -129,7 +154,8 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
     const int sl = threadIdx.x / FLD_CELLS;
     const int n = blockIdx.x * FLD_CELLS + cl;
     double e2 = 0.0, e1 = 0.0;
-    if (n < a.N) {
+    const bool given = flags & FLD_E_GIVEN;
+    if (n < a.N && !given) {
         const bool two = flags & FLD_SECOND, one = flags & FLD_FIRST;
         if (two && one) field_partial<true, true>(a, n, sl, e2, e1);
         else if (two) field_partial<true, false>(a, n, sl, e2, e1);
@@ -140,9 +166,14 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
     __syncthreads();
     double kin = 0.0, edf = 0.0;
     if (sl == 0 && n < a.N) {
-        for (int s = 1; s < FLD_SLICES; ++s) {
-            e2 += red2[s][cl];
-            e1 += red1[s][cl];
+        if (given) {
+            if (flags & FLD_SECOND) e2 = a.E2in[n];
+            if (flags & FLD_FIRST) e1 = a.E1in[n];
+        } else {
+            for (int s = 1; s < FLD_SLICES; ++s) {
+                e2 += red2[s][cl];
+                e1 += red1[s][cl];
+            }
         }
         const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
         for (int j = j0; j < j1; ++j) {

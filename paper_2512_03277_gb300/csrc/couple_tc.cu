@@ -1,0 +1,347 @@
+// Mixed-precision coupling contraction on the fifth-generation tensor cores (modes on a uniform
+// in-plane grid).
+//
+// Modes a = (jx, jy, s), k_a = (jx dkx, jy dky, 0), u_a(R) = cos(k_a.R) (s = 0) or sin(k_a.R)
+// (s = 1), index a = s + 2 (jy + Ky2 jx). With thx_n = dkx X_n, thy_n = dky Y_n the phases
+// factorise (cos(a + b) = cos a cos b - sin a sin b, sin(a + b) = sin a cos b + cos a sin b), so
+//   forward:  G = A B^T,  A[i][n] = cos(jx thx_n) (i = jx) | sin(jx thx_n) (i = Kx + jx),
+//             B[j][n] = M_n cos(jy thy_n) (j = jy) | M_n sin(jy thy_n) (j = Ky2 + jy),
+//             D_cos = lambda (G[jx][jy] - G[Kx+jx][Ky2+jy]),  D_sin = lambda (G[Kx+jx][jy] + G[jx][Ky2+jy]);
+//   back:     E_n = sum_i A[i][n] T[i][n],  T = Wt Y^T,  Y[n][j] = cos|sin(jy thy_n),
+//             Wt[jx][jy] = Wc, Wt[jx][Ky2+jy] = Ws, Wt[Kx+jx][jy] = Ws, Wt[Kx+jx][Ky2+jy] = -Wc,
+// the exact contraction of the k-space form of the coupling (no N x M phase matrix is stored).
+// Operands are split x = hi + lo into bfloat16 pairs and multiplied as hi hi + hi lo + lo hi
+// with FP32 accumulation in TMEM (BF16x3). The forward product is split over cells across CTAs
+// and the partial Gram matrices are summed in a fixed order in FP64.
+#include <cuda_bf16.h>
+
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int KXP = 128;          // MMA M: 2 Kx rows padded to 128
+constexpr int FWD_CELLS = 64;     // cells (K) per forward stage
+constexpr int BACK_CELLS = 128;   // cells (N) per back tile
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// Init: phase panels. Forward A (hi, lo) and back-epilogue A (FP32) from the x phases; forward B
+// source panel (FP32) and back Y (hi, lo) from the y phases. Tile-major core-matrix order.
+__global__ void k_tc_panels(int N, int Npad, int Kx, int Ky2, int KY, double dkx, double dky,
+                            const double *__restrict__ R, __nv_bfloat16 *__restrict__ Ahi,
+                            __nv_bfloat16 *__restrict__ Alo, float *__restrict__ Af, float *__restrict__ Bsrc,
+                            __nv_bfloat16 *__restrict__ Yhi, __nv_bfloat16 *__restrict__ Ylo) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Npad) return;
+    const bool real = n < N;
+    const double tx = real ? dkx * R[3 * n] : 0.0, ty = real ? dky * R[3 * n + 1] : 0.0;
+    // forward A: tile t = n / 64, row i, k = n % 64 (LBO = 16 row groups x 128 B)
+    const int t = n / FWD_CELLS, kk = n - t * FWD_CELLS;
+    for (int i = 0; i < KXP; ++i) {
+        double v = 0.0;
+        if (real && i < 2 * Kx) v = (i < Kx) ? cos(i * tx) : sin((i - Kx) * tx);
+        __nv_bfloat16 hi, lo;
+        split_bf16((float)v, hi, lo);
+        const size_t e = (size_t)t * KXP * FWD_CELLS + tc::core_offset(i, kk, (KXP / 8) * 128) / 2;
+        Ahi[e] = hi;
+        Alo[e] = lo;
+        Af[(size_t)i * Npad + n] = (float)v;
+    }
+    for (int j = 0; j < KY; ++j) {
+        double v = 0.0;
+        if (real && j < 2 * Ky2) v = (j < Ky2) ? cos(j * ty) : sin((j - Ky2) * ty);
+        const size_t e = (size_t)t * KY * FWD_CELLS + tc::core_offset(j, kk, (KY / 8) * 128) / 2;
+        Bsrc[e] = (float)v;
+        // back Y: tile tb = n / 128, row = n % 128, k = j (LBO = 16 row groups x 128 B)
+        const int tb = n / BACK_CELLS, rb = n - tb * BACK_CELLS;
+        const size_t eb = (size_t)tb * BACK_CELLS * KY + tc::core_offset(rb, j, (BACK_CELLS / 8) * 128) / 2;
+        __nv_bfloat16 hi, lo;
+        split_bf16((float)v, hi, lo);
+        Yhi[eb] = hi;
+        Ylo[eb] = lo;
+    }
+}
+
+// Forward Gram product, split over cells: partial[cta][i][j] = sum over the CTA's cells of A B^T.
+template <int KY>
+__global__ void __launch_bounds__(128) k_tc_forward(int nblk_total, int blk_per_cta, const __nv_bfloat16 *__restrict__ Ahi,
+                                                    const __nv_bfloat16 *__restrict__ Alo, const float *__restrict__ Bsrc,
+                                                    const double *__restrict__ Mc, int N, float *__restrict__ partial,
+                                                    unsigned *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr uint32_t A_BYTES = KXP * FWD_CELLS * 2, B_BYTES = KY * FWD_CELLS * 2;
+    constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr uint32_t LBO_A = (KXP / 8) * 128, LBO_B = (KY / 8) * 128;
+    constexpr uint32_t TCOLS = KY <= 32 ? 32 : (KY <= 64 ? 64 : 128);   // power of two >= KY
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 2 * STAGE + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b0 = blockIdx.x * blk_per_cta;
+    const int b1 = min(nblk_total, b0 + blk_per_cta);
+    if (warp == 0) tc::tmem_alloc(slot, TCOLS);
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t idesc = tc::idesc_bf16(KXP, KY);
+    uint32_t parity[2] = {0u, 0u};
+    int issued[2] = {0, 0};
+    bool ok = true;
+    int it = 0;
+    for (int b = b0; b < b1; ++b, ++it) {
+        const int s = it & 1;
+        uint8_t *st = smem + s * STAGE;
+        if (issued[s]) {   // the MMAs that read this stage must have finished
+            const bool got = tc::mbar_wait(&bar[s], parity[s]);
+            parity[s] ^= 1u;
+            issued[s] = 0;
+            if (!__syncthreads_and(got)) { ok = false; break; }
+        }
+        // A: contiguous copies of the pre-arranged tile
+        const uint4 *ah = reinterpret_cast<const uint4 *>(Ahi + (size_t)b * KXP * FWD_CELLS);
+        const uint4 *al = reinterpret_cast<const uint4 *>(Alo + (size_t)b * KXP * FWD_CELLS);
+        for (int e = tid; e < (int)(A_BYTES / 16); e += 128) {
+            reinterpret_cast<uint4 *>(st)[e] = ah[e];
+            reinterpret_cast<uint4 *>(st + A_BYTES)[e] = al[e];
+        }
+        // B: 8 consecutive cells of one row per chunk, scaled by M_n and split
+        const float *bs = Bsrc + (size_t)b * KY * FWD_CELLS;
+        for (int c = tid; c < KY * FWD_CELLS / 8; c += 128) {
+            const int kgrp = c / KY, row = c - kgrp * KY;    // chunk order follows the core layout
+            const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_B);
+            const float4 v0 = *reinterpret_cast<const float4 *>(bs + off / 2);
+            const float4 v1 = *reinterpret_cast<const float4 *>(bs + off / 2 + 4);
+            const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
+            for (int q = 0; q < 8; ++q) {
+                const int n = b * FWD_CELLS + 8 * kgrp + q;
+                const float m = n < N ? (float)Mc[n] : 0.0f;
+                split_bf16(vv[q] * m, hi[q], lo[q]);
+            }
+            *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + off) = *reinterpret_cast<const uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + B_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_u32(st), sb = sa + 2 * A_BYTES;
+            for (int k = 0; k < FWD_CELLS / 16; ++k) {
+                const uint32_t oa = k * 2 * LBO_A, ob = k * 2 * LBO_B;
+                const uint64_t ahd = tc::make_desc(sa + oa, LBO_A, 128), ald = tc::make_desc(sa + A_BYTES + oa, LBO_A, 128);
+                const uint64_t bhd = tc::make_desc(sb + ob, LBO_B, 128), bld = tc::make_desc(sb + B_BYTES + ob, LBO_B, 128);
+                const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
+                tc::mma_bf16(tmem, ahd, bhd, idesc, acc);
+                tc::mma_bf16(tmem, ahd, bld, idesc, 1u);
+                tc::mma_bf16(tmem, ald, bhd, idesc, 1u);
+            }
+            tc::mma_commit(&bar[s]);
+        }
+        issued[s] = 1;
+    }
+    for (int s = 0; s < 2; ++s) {
+        if (issued[s]) {
+            const bool got = tc::mbar_wait(&bar[s], parity[s]);
+            if (!__syncthreads_and(got)) ok = false;
+        }
+    }
+    if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    tc::fence_after_sync();
+    float *P = partial + (size_t)blockIdx.x * KXP * KY;
+    if (ok && b1 > b0) {
+        for (int c0 = 0; c0 < KY; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            const int row = 32 * warp + lane;
+            for (int q = 0; q < 32 && c0 + q < KY; ++q) P[row * KY + c0 + q] = v[q];
+        }
+    } else {
+        for (int e = tid; e < KXP * KY; e += 128) P[e] = 0.0f;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+}
+
+__global__ void k_tc_reduce(int n_part, int size, const float *__restrict__ partial, double *__restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= size) return;
+    double s = 0.0;
+    for (int p = 0; p < n_part; ++p) s += partial[(size_t)p * size + e];
+    G[e] = s;
+}
+
+// Back product for a tile of 128 cells: E_n = sum_i A[i][n] (Wt Y^T)[i][n] for one or two weight
+// matrices (Wt2 -> E2, Wt1 -> E1).
+template <int KY>
+__global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, const float *__restrict__ Wt2, const float *__restrict__ Wt1,
+                                                 const __nv_bfloat16 *__restrict__ Yhi, const __nv_bfloat16 *__restrict__ Ylo,
+                                                 const float *__restrict__ Af, double *__restrict__ E2, double *__restrict__ E1,
+                                                 unsigned *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    constexpr uint32_t W_BYTES = KXP * KY * 2, Y_BYTES = BACK_CELLS * KY * 2;
+    constexpr uint32_t LBO_W = (KXP / 8) * 128, LBO_Y = (BACK_CELLS / 8) * 128;
+    uint8_t *sw = smem;                       // [Wt2 hi][Wt2 lo][Wt1 hi][Wt1 lo]
+    uint8_t *sy = smem + 4 * W_BYTES;         // [Y hi][Y lo]
+    float *red = reinterpret_cast<float *>(sy + 2 * Y_BYTES);     // [4 warps][128 cells]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(red + 4 * BACK_CELLS);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * BACK_CELLS;
+    const int nacc = Wt1 ? 2 : 1;
+    if (warp == 0) tc::tmem_alloc(slot, 256);
+    if (tid == 0) tc::mbar_init(&bar[0], 1);
+    // weights: 8 consecutive K (j) of one row i per chunk, split into hi / lo
+    for (int w = 0; w < nacc; ++w) {
+        const float *Wt = w == 0 ? Wt2 : Wt1;
+        for (int c = tid; c < KXP * KY / 8; c += 128) {
+            const int kgrp = c / KXP, row = c - kgrp * KXP;
+            const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_W);
+            __align__(16) __nv_bfloat16 hi[8], lo[8];
+            for (int q = 0; q < 8; ++q) split_bf16(Wt[row * KY + 8 * kgrp + q], hi[q], lo[q]);
+            *reinterpret_cast<uint4 *>(sw + (2 * w) * W_BYTES + off) = *reinterpret_cast<const uint4 *>(hi);
+            *reinterpret_cast<uint4 *>(sw + (2 * w + 1) * W_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
+        }
+    }
+    {
+        const uint4 *yh = reinterpret_cast<const uint4 *>(Yhi + (size_t)blockIdx.x * BACK_CELLS * KY);
+        const uint4 *yl = reinterpret_cast<const uint4 *>(Ylo + (size_t)blockIdx.x * BACK_CELLS * KY);
+        for (int e = tid; e < (int)(Y_BYTES / 16); e += 128) {
+            reinterpret_cast<uint4 *>(sy)[e] = yh[e];
+            reinterpret_cast<uint4 *>(sy + Y_BYTES)[e] = yl[e];
+        }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t idesc = tc::idesc_bf16(KXP, BACK_CELLS);
+    if (tid == 0) {
+        const uint32_t sws = tc::smem_u32(sw), sys = tc::smem_u32(sy);
+        for (int w = 0; w < nacc; ++w) {
+            const uint32_t d = tmem + (uint32_t)(w * BACK_CELLS);
+            for (int k = 0; k < KY / 16; ++k) {
+                const uint32_t ow = k * 2 * LBO_W, oy = k * 2 * LBO_Y;
+                const uint64_t whd = tc::make_desc(sws + (2 * w) * W_BYTES + ow, LBO_W, 128);
+                const uint64_t wld = tc::make_desc(sws + (2 * w + 1) * W_BYTES + ow, LBO_W, 128);
+                const uint64_t yhd = tc::make_desc(sys + oy, LBO_Y, 128), yld = tc::make_desc(sys + Y_BYTES + oy, LBO_Y, 128);
+                tc::mma_bf16(d, whd, yhd, idesc, k > 0 ? 1u : 0u);
+                tc::mma_bf16(d, whd, yld, idesc, 1u);
+                tc::mma_bf16(d, wld, yhd, idesc, 1u);
+            }
+        }
+        tc::mma_commit(&bar[0]);
+    }
+    const bool got = tc::mbar_wait(&bar[0], 0u);
+    const bool ok = __syncthreads_and(got) != 0;
+    if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    tc::fence_after_sync();
+    const int i = 32 * warp + lane;           // this thread's row (TMEM lane)
+    for (int w = 0; w < nacc && ok; ++w) {
+        double *E = w == 0 ? E2 : E1;
+        for (int c0 = 0; c0 < BACK_CELLS; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w * BACK_CELLS + c0), v);
+            const float *arow = Af + (size_t)i * Npad + n0 + c0;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                float x = v[q] * arow[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(CAVMD_FULL_MASK, x, o);
+                if (lane == 0) red[warp * BACK_CELLS + c0 + q] = x;
+            }
+        }
+        __syncthreads();
+        if (tid < BACK_CELLS && n0 + tid < N) {
+            double s = 0.0;
+            for (int ww = 0; ww < 4; ++ww) s += (double)red[ww * BACK_CELLS + tid];
+            E[n0 + tid] = s;
+        }
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+template <typename F>
+cudaError_t set_smem(F f, size_t bytes) {
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------- host
+
+size_t tc_fwd_smem(int KY) { return 2 * (2 * KXP * FWD_CELLS * 2 + 2 * (size_t)KY * FWD_CELLS * 2) + 64; }
+size_t tc_back_smem(int KY) {
+    return 4 * (size_t)KXP * KY * 2 + 2 * (size_t)BACK_CELLS * KY * 2 + 4 * BACK_CELLS * 4 + 64;
+}
+
+cudaError_t tc_prepare(int KY) {
+    const size_t f = tc_fwd_smem(KY), b = tc_back_smem(KY);
+    cudaError_t e = cudaErrorInvalidValue;
+#define PREP_CASE(KYV)                                                        \
+    case KYV:                                                                 \
+        e = set_smem(k_tc_forward<KYV>, f);                                   \
+        if (e == cudaSuccess) e = set_smem(k_tc_back<KYV>, b);                \
+        break;
+    switch (KY) { PREP_CASE(16) PREP_CASE(32) PREP_CASE(48) PREP_CASE(64) PREP_CASE(96) PREP_CASE(128) }
+#undef PREP_CASE
+    return e;
+}
+
+cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st) {
+    k_tc_panels<<<(p.Npad + 127) / 128, 128, 0, st>>>(p.N, p.Npad, p.Kx, p.Ky2, p.KY, p.dkx, p.dky, R, p.Ahi, p.Alo,
+                                                      p.Af, p.Bsrc, p.Yhi, p.Ylo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsigned *status, cudaStream_t st) {
+    const int nblk = p.Npad / FWD_CELLS;
+    const int per = (nblk + p.n_fwd_cta - 1) / p.n_fwd_cta;
+    const size_t sm = tc_fwd_smem(p.KY);
+    cudaError_t e = cudaSuccess;
+#define FWD_CASE(KYV)                                                                                     \
+    case KYV:                                                                                             \
+            k_tc_forward<KYV><<<p.n_fwd_cta, 128, sm, st>>>(nblk, per, p.Ahi, p.Alo, p.Bsrc, Mc, p.N,    \
+                                                            p.partial, status);                           \
+        break;
+    switch (p.KY) {
+        FWD_CASE(16) FWD_CASE(32) FWD_CASE(48) FWD_CASE(64) FWD_CASE(96) FWD_CASE(128)
+        default: return cudaErrorInvalidValue;
+    }
+#undef FWD_CASE
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int size = KXP * p.KY;
+    k_tc_reduce<<<(size + 255) / 256, 256, 0, st>>>(p.n_fwd_cta, size, p.partial, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_back(const TcPlan &p, const float *Wt2, const float *Wt1, double *E2, double *E1,
+                           unsigned *status, cudaStream_t st) {
+    const size_t sm = tc_back_smem(p.KY);
+    const int grid = p.Npad / BACK_CELLS;
+    cudaError_t e = cudaSuccess;
+#define BACK_CASE(KYV)                                                                                    \
+    case KYV:                                                                                             \
+            k_tc_back<KYV><<<grid, 128, sm, st>>>(p.N, p.Npad, Wt2, Wt1, p.Yhi, p.Ylo, p.Af, E2, E1, status); \
+        break;
+    switch (p.KY) {
+        BACK_CASE(16) BACK_CASE(32) BACK_CASE(48) BACK_CASE(64) BACK_CASE(96) BACK_CASE(128)
+        default: return cudaErrorInvalidValue;
+    }
+#undef BACK_CASE
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
