@@ -161,12 +161,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _config(workload, w, charge_model="mulliken"):
+def _config(workload, w, charge_model="mulliken", precision="fp64"):
     sy, mo = w["system"], w["modes"]
     cm = {"mulliken": "Mulliken", "born_fd": "forward-FD Born every 3 steps",
-          "born_central": "central-FD Born every 3 steps"}[charge_model]
-    return {"workload": f"{workload}: {sy.n_cells} water x {mo.n_modes} modes, FP64 SCC-DFTB, {cm}, dt 0.5 fs",
-            "n_cells": sy.n_cells, "n_atoms": sy.n_atoms, "n_modes": mo.n_modes, "precision": "fp64",
+          "born_central": "central-FD Born every 3 steps", "born_mlp": "network Born charges"}[charge_model]
+    cp = "FP64 coupling" if precision == "fp64" else "BF16x3 tensor-core coupling"
+    return {"workload": f"{workload}: {sy.n_cells} water x {mo.n_modes} modes, FP64 SCC-DFTB, {cm}, {cp}, dt 0.5 fs",
+            "n_cells": sy.n_cells, "n_atoms": sy.n_atoms, "n_modes": mo.n_modes, "precision": precision,
             "charge_model": charge_model, "l2": "256 MB buffer rewritten between timed steps (L2 flush)",
             "parallelism": "replicas"}
 
@@ -181,8 +182,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixing", type=float, default=None, help="charge mixing (default: the library's)")
-    ap.add_argument("--charge-model", default="mulliken", choices=["mulliken", "born_fd", "born_central"],
-                    help="dipole derivative (default: the workload's Mulliken charges)")
+    ap.add_argument("--charge-model", default="mulliken", choices=["mulliken", "born_fd", "born_central", "born_mlp"],
+                    help="dipole derivative (default: Mulliken charges)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="coupling contraction: FP64, or BF16x3 on the tensor cores (grid modes)")
+    ap.add_argument("--n-cells", type=int, default=None, help="trim the workload to this many cells")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -203,15 +207,22 @@ def main():
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     build.build()
-    w = cs.make_workload(args.workload)
+    w = cs.make_workload(args.workload, n_cells=args.n_cells)
     if rank > 0:   # independent replica: its own Maxwell-Boltzmann velocities
         w["system"].p = cs.mb_momenta(np.random.default_rng(1000 + rank), w["system"])
     opt = P.default_options()
     opt.device = local
     if args.mixing is not None:
         opt.mixing = args.mixing
-    opt.charge_model = {"mulliken": 0, "born_fd": 1, "born_central": 2}[args.charge_model]
+    opt.charge_model = {"mulliken": 0, "born_fd": 1, "born_central": 2, "born_mlp": 3}[args.charge_model]
+    opt.precision = {"fp64": 0, "mixed": 2}[args.precision]
     ctx = P.Context(w["system"], w["params"], w["modes"], opt)
+    if args.charge_model == "born_mlp":
+        # a seeded network: the cost of a time step does not depend on the weight values
+        rng = np.random.default_rng(4)
+        sizes = [(128, 32), (128,), (128, 128), (128,), (9, 128), (9,)]
+        params = np.concatenate([rng.uniform(-1, 1, s_).ravel() / np.sqrt(s_[-1]) * (len(s_) == 2) for s_ in sizes])
+        ctx.cavmd_load_born_mlp(params.astype(np.float32))
     stream = ctx.stream
     N = w["system"].n_cells
     for _ in range(args.warmup):
@@ -284,7 +295,7 @@ def main():
         "metric": "molecule-steps/s", "value": value, "unit": "molecule-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(args.workload, w, args.charge_model),
+        "data": "synthetic", "config": _config(args.workload, w, args.charge_model, args.precision),
         "roofline": {"bound": "alu", "kernel": "dftb_kernel<3,6>", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": DFTB_DRAM_BYTES_PER_LAUNCH if args.workload == "c2" else None,
@@ -293,13 +304,16 @@ def main():
                      "peak_note": "FP64 ALU: 152 SMs x 4 FP64 flop/clk x 2070 MHz (derived, 1.26 TFLOP/s)"},
         "phase_share": shares,
         "e2e": e2e,
-        "gpu_launches": int(phase_cnt.sum()) + (int(phase_cnt[3]) if args.charge_model != "mulliken" else 0),
+        "gpu_launches": int(phase_cnt.sum()) + (int(phase_cnt[3]) if args.charge_model in ("born_fd", "born_central") else 0)
+                        + 2 * (int(phase_cnt[3]) if args.charge_model == "born_mlp" else 0)
+                        + (int(phase_cnt[0]) if args.precision == "mixed" else 0),
         "clocks": clk,
         "wall_s_timed_region": t_wall,
         "energy_total": obs["e_total"], "temperature_K": obs["temperature"],
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        n_sample = None if w["system"].n_cells <= 4096 else 4096
+        line["cpu_baseline"] = cpu_baseline(args.workload, n_sample=n_sample)
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.cavmd_destroy()
