@@ -5,9 +5,15 @@ Recipes (all lengths in bohr, seeds: geometry 1, velocities 2, clusters 3):
 * water: the textbook water geometry (r_OH = 1.809 bohr, 104.52 deg),
   centre of mass at the cell centre, a uniform random rotation, then
   N(0, 0.02 bohr) noise on every coordinate;
-* clusters (H2O)_n: n waters whose centres of mass are uniform in a sphere of
-  radius (3n / (4 pi rho))^(1/3) at liquid density rho, with a minimum
-  centre distance, each water built as above;
+* clusters (H2O)_n: n waters placed one by one, each a rotated, noisy water
+  as above whose centre of mass is uniform in a sphere of radius
+  (3n / (4 pi rho))^(1/3) at liquid density rho, kept only when its centre is
+  at least 4.8 bohr from every placed centre and each of its atoms at least
+  3.0 bohr from every atom of the other waters (liquid water's closest
+  intermolecular contact, the O...H hydrogen bond, is about 3.4 bohr); after
+  200 rejected candidates for one water the cluster restarts in a sphere 5%
+  larger (candidates are drawn 16 at a time). The synthetic overlap integrals are not a Gram matrix at any
+  distance: closer contacts (about 1.4 bohr H...H) make S indefinite;
 * momenta: Maxwell-Boltzmann at 300 K, centre-of-mass velocity removed per
   cell;
 * modes: real cavity modes u_a(R) = cos(k_a . R + phi_a) with frequency
@@ -100,27 +106,43 @@ def _water_system(pos: np.ndarray, centres: np.ndarray) -> System:
 
 
 def cluster_batch(rng: np.random.Generator, sizes, centres, noise: float = 0.02,
-                  density: float = WATER_DENSITY, d_min: float = 4.8, ref=None) -> System:
-    """(H2O)_n clusters; cluster i holds sizes[i] waters around centres[i]."""
+                  density: float = WATER_DENSITY, d_min: float = 4.8, d_atom: float = 3.0,
+                  ref=None) -> System:
+    """(H2O)_n clusters; cluster i holds sizes[i] waters around centres[i]. Candidates for each
+    water are drawn 16 at a time and the first acceptable one is kept."""
     sizes = np.asarray(sizes, int)
     centres = np.asarray(centres, float)
     g = _centred_water(ref)
     species, pos, off = [], [], [0]
     for n, c in zip(sizes, centres):
         radius = (3.0 * n / (4.0 * np.pi * density)) ** (1.0 / 3.0)
-        coms = []
-        tries = 0
-        while len(coms) < n:
-            x = rng.uniform(-radius, radius, 3)
-            tries += 1
-            if x @ x > radius * radius:
-                continue
-            if all(np.linalg.norm(x - y) >= d_min for y in coms) or tries > 2000:
-                coms.append(x)
-        coms = np.array(coms)
-        rot = random_rotations(rng, n)
-        w = np.einsum("nij,aj->nai", rot, g) + rng.normal(0.0, noise, size=(n, 3, 3))
-        w += (coms + c)[:, None, :]
+        while True:
+            coms, waters = [], []
+            for _ in range(n):
+                found = None
+                for _batch in range(13):                     # about 200 candidates
+                    x = rng.uniform(-radius, radius, (16, 3))
+                    rot = random_rotations(rng, 16)
+                    wat = np.einsum("kij,aj->kai", rot, g) + rng.normal(0.0, noise, (16, 3, 3)) + x[:, None, :]
+                    good = (x * x).sum(1) <= radius * radius
+                    if coms:
+                        cm = np.array(coms)
+                        good &= np.linalg.norm(x[:, None, :] - cm[None], axis=2).min(1) >= d_min
+                        placed = np.concatenate(waters)
+                        da = np.linalg.norm(wat[:, :, None, :] - placed[None, None], axis=3).min(axis=(1, 2))
+                        good &= da >= d_atom
+                    k = np.flatnonzero(good)
+                    if len(k):
+                        found = k[0]
+                        break
+                if found is None:
+                    break
+                coms.append(x[found])
+                waters.append(wat[found])
+            if len(coms) == n:
+                break
+            radius *= 1.05
+        w = np.stack(waters) + c
         pos.append(w.reshape(-1, 3))
         species.append(np.tile(np.array([ELEM_O, ELEM_H, ELEM_H], np.int32), n))
         off.append(off[-1] + 3 * n)

@@ -52,7 +52,11 @@ extern "C" {
 #define CAVMD_ERR_NOMEM -9         /* device allocation failed                             */
 
 #define CAVMD_MAX_ELEM 4           /* element ids 0..3                                    */
-#define CAVMD_MAX_ATOMS_PER_CELL 3 /* cells with more atoms return CAVMD_ERR_UNSUPPORTED  */
+#define CAVMD_MAX_CELL_ORBITALS 64 /* orbitals per cell (an even count); more, or cells  */
+                                   /* whose on-chip storage exceeds 227 KB, return        */
+                                   /* CAVMD_ERR_UNSUPPORTED. Cells of 3 atoms and 6       */
+                                   /* orbitals take a lane-group kernel; any other mix of  */
+                                   /* cells takes the persistent cluster kernel.           */
 /* Dipole derivative b_j = dM_n/dr_j used by the coupling force:
  *   MULLIKEN     b_j = Q_j pol (the paper's cheap replacement; not conservative);
  *   BORN_FD      forward differences [M(r + h e) - M(r)] / h, the paper's choice, from 3 N_at

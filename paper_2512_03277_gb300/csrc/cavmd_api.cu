@@ -47,6 +47,9 @@ struct cavmd_ctx {
     float *d_mlpX = nullptr, *d_mlpR = nullptr, *d_mlpZl = nullptr, *d_mlpf = nullptr;
     void *d_mlpw = nullptr;                  // bfloat16 network parameters
     bool mixed = false;                      // tensor-core coupling (modes on a grid)
+    bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
+    GenericPlan gplan{};
+    long long *d_Coff = nullptr;             // eigenvector block of each cell (generic kernel)
     TcPlan tc{};
     double *d_G = nullptr, *d_E2 = nullptr, *d_E1 = nullptr;
     float *d_Wt2 = nullptr, *d_Wt1 = nullptr;
@@ -188,6 +191,7 @@ void collect_phase_times(cavmd_ctx *c) {
 cudaError_t run_dftb(cavmd_ctx *c, int have_warm) {
     PhaseScope ps(c, 0);
     c->da.have_warm = have_warm;
+    if (c->generic) return launch_dftb_generic(c->d_sk, c->da, c->gplan, c->stream);
     return launch_dftb_water(c->d_sk, c->da, c->stream);
 }
 
@@ -200,7 +204,8 @@ cudaError_t run_born(cavmd_ctx *c) {
     d.fd_central = c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL;
     d.fd_h = c->opt.fd_step;
     d.M_disp = c->d_Mdisp;
-    cudaError_t e = launch_dftb_water(c->d_sk, d, c->stream);
+    cudaError_t e = c->generic ? launch_dftb_generic(c->d_sk, d, c->gplan, c->stream)
+                               : launch_dftb_water(c->d_sk, d, c->stream);
     if (e != cudaSuccess) return e;
     return launch_born_assemble(c->N, c->d_off, c->d_Mc, c->d_Mdisp, c->n_disp, d.fd_central, d.fd_h, c->d_b,
                                 c->stream);
@@ -375,15 +380,24 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         if (!std::isfinite(sys->r[i]) || !std::isfinite(sys->p[i])) return fail(c, CAVMD_ERR_INVALID_ARG, "non-finite position or momentum");
     for (int n = 0; n < sys->n_cells; ++n) {
         const int a0 = sys->cell_offset[n], a1 = sys->cell_offset[n + 1];
-        if (a1 < a0) return fail(c, CAVMD_ERR_INVALID_ARG, "cell_offset not non-decreasing");
-        if (a1 - a0 != 3) return fail(c, CAVMD_ERR_UNSUPPORTED, "this build evaluates cells of exactly 3 atoms with 6 orbitals");
+        if (a1 <= a0) return fail(c, CAVMD_ERR_INVALID_ARG, "every cell needs at least one atom");
         int norb = 0;
         double nel = 0;
         for (int i = a0; i < a1; ++i) { norb += sk->norb[sys->species[i]]; nel += sk->zval[sys->species[i]]; }
-        if (norb != 6) return fail(c, CAVMD_ERR_UNSUPPORTED, "this build evaluates cells of exactly 3 atoms with 6 orbitals");
         const long ne = std::lround(nel);
         if (std::fabs(nel - ne) > 1e-12 || (ne & 1) || ne <= 0 || ne > 2 * norb)
             return fail(c, CAVMD_ERR_INVALID_ARG, "cells must be neutral and closed shell");
+        if (norb > CAVMD_MAX_CELL_ORBITALS || (norb & 1))
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "cells need an even number of orbitals, at most 64");
+    }
+    {   // shared memory of the persistent kernel for the largest cells
+        std::vector<int> norb_e(sk->norb, sk->norb + sk->n_elem);
+        GenericPlan gp{};
+        std::vector<int2> it, dit;
+        plan_dftb_generic(sys->cell_offset, sys->species, norb_e.data(), sys->n_cells, 0, gp, it, dit);
+        if (gp.smem > 227 * 1024 - 256)   // the opt-in limit per block, less the kernel's static bytes
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "cells too large for on-chip storage (" +
+                        std::to_string(gp.smem) + " bytes of shared memory per block)");
     }
     if (md->n_modes < 1 || !md->k || !md->omega || !md->lambda || !md->phi)
         return fail(c, CAVMD_ERR_INVALID_ARG, "need n_modes >= 1 and all mode arrays");
@@ -476,7 +490,17 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     AL(c->d_sk, 1);
     AL(c->d_off, N + 1); AL(c->d_species, NA); AL(c->d_iters, N);
     AL(c->d_r, 3 * NA); AL(c->d_p, 3 * NA); AL(c->d_F, 3 * NA); AL(c->d_b, 3 * NA);
-    AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)N * 36); AL(c->d_E, N); AL(c->d_Mc, N);
+    // eigenvector blocks: n_c^2 per cell; the water kernel takes every cell when all are 3-atom,
+    // 6-orbital cells, the persistent generic kernel otherwise
+    std::vector<long long> coff(N + 1, 0);
+    c->generic = false;
+    for (int n = 0; n < N; ++n) {
+        int no = 0;
+        for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) no += sk->norb[sys->species[i]];
+        if (no != 6 || sys->cell_offset[n + 1] - sys->cell_offset[n] != 3) c->generic = true;
+        coff[n + 1] = coff[n] + (long long)no * no;
+    }
+    AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)coff[N]); AL(c->d_E, N); AL(c->d_Mc, N);
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N);
     c->mixed = c->opt.precision == CAVMD_PREC_MIXED_BF16X3;
     if (!c->mixed) AL(c->d_U, (size_t)M * N);
@@ -487,9 +511,13 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     const int fb = field_blocks(N);
     AL(c->d_ekp, fb); AL(c->d_edp, fb); AL(c->d_hist, 8 * (size_t)c->opt.energy_history);
     AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1);
-    if (c->opt.charge_model == CAVMD_CHARGE_BORN_FD) c->n_disp = 3 * 3;
-    if (c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL) c->n_disp = 6 * 3;
-    if (c->n_disp) AL(c->d_Mdisp, (size_t)N * c->n_disp);
+    // finite-difference copies: 3 per atom (forward) or 6 (central); n_disp counts them per water
+    // cell for the water kernel, the generic kernel walks its own item list
+    int disp_per_atom = 0;
+    if (c->opt.charge_model == CAVMD_CHARGE_BORN_FD) disp_per_atom = 3;
+    if (c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL) disp_per_atom = 6;
+    c->n_disp = 3 * disp_per_atom;
+    if (c->n_disp) AL(c->d_Mdisp, (size_t)disp_per_atom * NA);
     if (c->opt.charge_model == CAVMD_CHARGE_BORN_MLP) {
         AL(c->d_Q, NA);
         AL(c->d_mlpX, (size_t)NA * CAVMD_MLP_NFEAT);
@@ -548,6 +576,26 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         CK(launch_tc_panels(p, c->d_R, st));
     }
 
+    if (c->generic) {
+        GenericPlan &g = c->gplan;
+        std::vector<int> norb_e(sk->norb, sk->norb + sk->n_elem);
+        std::vector<int2> items, disp_items;
+        plan_dftb_generic(sys->cell_offset, sys->species, norb_e.data(), N, disp_per_atom, g, items, disp_items);
+        AL(g.items, items.size());
+        AL(g.queue, 2);
+        CK(cudaMemcpyAsync(g.items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st));
+        if (!disp_items.empty()) {
+            AL(g.disp_items, disp_items.size());
+            CK(cudaMemcpyAsync(g.disp_items, disp_items.data(), sizeof(int2) * disp_items.size(),
+                               cudaMemcpyHostToDevice, st));
+        }
+        AL(c->d_Coff, N);
+        CK(cudaMemcpyAsync(c->d_Coff, coff.data(), sizeof(long long) * N, cudaMemcpyHostToDevice, st));
+        CK(prepare_dftb_generic(g));
+        // the host vectors must outlive the copies
+        CK(cudaStreamSynchronize(st));
+    }
+
     DftbArgs &d = c->da;
     d.n_cells = N;
     d.cell_list = nullptr;
@@ -559,6 +607,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.qpop = c->d_qpop;
     d.qprev = c->d_qprev;
     d.Cwarm = c->d_C;
+    d.Cwarm_off = c->d_Coff;
     d.E_cell = c->d_E;
     d.M_cell = c->d_Mc;
     d.iters = c->d_iters;

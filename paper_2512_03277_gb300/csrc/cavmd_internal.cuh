@@ -42,7 +42,8 @@ struct DftbArgs {
     double *b;                 // [3 n_atoms] out: Mulliken b_j = Q_j pol (charge_model 0)
     double *qpop;              // [n_atoms] in/out: Mulliken populations (warm start)
     double *qprev;             // [n_atoms] in/out: populations of the step before (predictor)
-    double *Cwarm;             // [n_cells_total][NORB*NORB] in/out eigenvectors (column-major)
+    double *Cwarm;             // in/out eigenvectors of every cell (column-major, n_c x n_c each)
+    const long long *Cwarm_off;   // [N] first element of each cell's block in Cwarm (NULL: 36 per cell)
     double *E_cell;            // [N] out
     double *M_cell;            // [N] out
     int *iters;                // [N] out
@@ -53,12 +54,12 @@ struct DftbArgs {
     int max_iter;
     int have_warm;             // 1: Cwarm and qpop hold a previous solution
     int write_b;               // 1: write Mulliken b
-    // finite-difference rows: n_disp > 0 turns every cell into n_disp displaced copies that only
-    // compute their dipole (3 NAT forward rows, or 6 NAT central rows in +h, -h pairs)
+    // finite-difference rows: n_disp > 0 turns every cell into displaced copies that only compute
+    // their dipole (3 per atom forward, or 6 per atom central in +h, -h pairs)
     int n_disp;
     int fd_central;
     double fd_h;
-    double *M_disp;            // [n_cells][n_disp] out
+    double *M_disp;            // [3 or 6 per atom] out: row k of the cell starting at atom a0 at 3 a0 + k (6 a0 + k)
     double *Qout;              // [n_atoms] out: Mulliken net charges (may be NULL)
 };
 
@@ -134,11 +135,28 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 }
 
 #include <string>
+#include <vector>
 // Records the message returned by cavmd_last_error(NULL) (calls without a context).
 void cavmd_set_global_error(const std::string &msg);
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st);
+
+// Plan of the persistent SCC-DFTB launch over cells of any composition (up to 64 orbitals).
+struct GenericPlan {
+    int nmax_b, amax_b, nmax_s, amax_s;          // largest cell of the large (> 32 orbitals) and small classes
+    int n_big, n_small, n_disp_big, n_disp_small;
+    int n_sm, blocks_per_sm;
+    size_t smem;                                 // dynamic shared memory per block
+    int2 *items, *disp_items;                    // device: (cell, -1) and (cell, displacement), largest first
+    unsigned *queue;                             // device: [2] work counters
+};
+// Host: item lists (largest first) and shared-memory size from the cell sizes.
+void plan_dftb_generic(const int *cell_offset, const int *species, const int *norb_of_elem, int n_cells,
+                       int n_disp_per_atom, GenericPlan &p, std::vector<int2> &items,
+                       std::vector<int2> &disp_items);
+cudaError_t prepare_dftb_generic(GenericPlan &p);   // kernel attribute and occupancy, once per plan
+cudaError_t launch_dftb_generic(const DevSK *sk_dev, const DftbArgs &a, const GenericPlan &p, cudaStream_t st);
 // b_j = dM/dr_j from the displaced dipoles (forward or central differences)
 cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const double *M_cell,
                                  const double *M_disp, int n_disp, int central, double h, double *b,

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
     // ---------------------------------------------------------------- warm-started S-orthonormal basis
     if (act) {
         if (a.have_warm) {
-            const double *cw = a.Cwarm + (size_t)cell * NORB * NORB;
+            const double *cw = a.Cwarm + (a.Cwarm_off ? a.Cwarm_off[cell] : (long long)cell * NORB * NORB);
             for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = cw[j * NORB + i];
             // linear predictor 2 q(t) - q(t - dt) of the populations (q_prev equals q after a
             // cold start, so the first warm step starts from q(t) itself)
@@ -621,7 +621,8 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
                 const double Q = m.zv[at] - m.q[at];
                 for (int k = 0; k < 3; ++k) mu[k] = fma(Q, m.pos[at][k] - m.pos[0][k], mu[k]);
             }
-            a.M_disp[ridx] = fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
+            a.M_disp[(long long)(a.fd_central ? 6 : 3) * a0 + (ridx - cidx * a.n_disp)] =
+                fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
             if (m.flag) atomicOr(a.status, (unsigned)m.flag);
         }
         return;
@@ -810,7 +811,7 @@ __global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp,
         }
     }
     if (valid) {
-        double *cw = a.Cwarm + (size_t)cell * NORB * NORB;
+        double *cw = a.Cwarm + (a.Cwarm_off ? a.Cwarm_off[cell] : (long long)cell * NORB * NORB);
         for (int i = 0; i < NORB; ++i) cw[j * NORB + i] = m.C[j * LD + i];
     }
     if (valid && j == 0) {
@@ -840,7 +841,7 @@ __global__ void k_born_assemble(int n_cells, const int *__restrict__ off, const 
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= n_cells) return;
     const double ih = 1.0 / h;
-    const double *md = Md + (size_t)n * nd;
+    const double *md = Md + (size_t)(central ? 6 : 3) * off[n];
     for (int j = off[n]; j < off[n + 1]; ++j) {
         const int jl = j - off[n];
         for (int k = 0; k < 3; ++k) {

@@ -109,10 +109,20 @@ def test_rejects_nonfinite_positions(lib, small):
 
 
 def test_rejects_unsupported_composition(lib, small):
+    """Clusters up to 64 orbitals are evaluated; (H2O)_11 has 66 and is refused before any device
+    work, as is a cell with an odd orbital count (here an s-only element carrying two electrons)."""
     rng = np.random.default_rng(0)
-    cl = cs.cluster_batch(rng, [2], np.zeros((1, 3)))
+    cl = cs.cluster_batch(rng, [11], np.zeros((1, 3)))
     cl.p = np.zeros_like(cl.r)
     rc, msg = _init_rc(lib, cl, small["params"], small["modes"])
+    assert rc == -8 and "64" in msg
+    pa = small["params"]
+    odd = cs.System(species=np.array([1], np.int32), cell_offset=np.array([0, 1], np.int32),
+                    r=np.zeros((1, 3)), p=np.zeros((1, 3)), R_ref=np.zeros((1, 3)))
+    zval = pa.zval.copy()
+    zval[1] = 2.0
+    from dataclasses import replace
+    rc, msg = _init_rc(lib, odd, replace(pa, zval=zval), small["modes"])
     assert rc == -8
 
 
