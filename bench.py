@@ -35,7 +35,7 @@ SM_MAX_MHZ = 2070.0
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one dftb_kernel<3,6> launch on this workload, from one ncu capture
 # (profiles/dftb_kernel_c2_4096x512.md); None once the kernel has changed since that capture.
-DFTB_DRAM_BYTES_PER_LAUNCH = 1.883e6 + 768
+DFTB_DRAM_BYTES_PER_LAUNCH = 1940736 + 3840
 
 
 def _dist():
@@ -197,6 +197,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="coupling contraction: FP64, or BF16x3 on the tensor cores (grid modes)")
     ap.add_argument("--n-cells", type=int, default=None, help="trim the workload to this many cells")
+    ap.add_argument("--acf-lags", type=int, default=None,
+                    help="on-device autocorrelation lags (default: 1024 for c5, whose configuration asks for "
+                         "it, else off)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -226,6 +229,9 @@ def main():
         opt.mixing = args.mixing
     opt.charge_model = {"mulliken": 0, "born_fd": 1, "born_central": 2, "born_mlp": 3}[args.charge_model]
     opt.precision = {"fp64": 0, "mixed": 2}[args.precision]
+    if args.acf_lags is None:
+        args.acf_lags = 1024 if args.workload == "c5" else 0
+    opt.acf_lags = args.acf_lags
     ctx = P.Context(w["system"], w["params"], w["modes"], opt)
     if args.charge_model == "born_mlp":
         # a seeded network: the cost of a time step does not depend on the weight values
@@ -319,6 +325,7 @@ def main():
         "gpu_launches": int(phase_cnt.sum()) + (int(phase_cnt[3]) if args.charge_model in ("born_fd", "born_central") else 0)
                         + 2 * (int(phase_cnt[3]) if args.charge_model == "born_mlp" else 0)
                         + (int(phase_cnt[0]) if args.precision == "mixed" else 0),
+        "acf_lags": args.acf_lags,
         "clocks": clk,
         "wall_s_timed_region": t_wall,
         "energy_total": obs["e_total"], "temperature_K": obs["temperature"],

@@ -141,6 +141,12 @@ typedef struct {
     cavmd_free_fn dev_free;     /* its matching free                                          */
     void *alloc_user;           /* passed back to dev_alloc / dev_free                        */
     int32_t energy_history;     /* steps of energy history kept on the device (>= 1)          */
+    int32_t acf_lags;           /* on-device autocorrelation of the photon coordinates and of the
+                                   total dipole, lags 0 .. acf_lags-1 (0 = off; see
+                                   cavmd_autocorrelation)                                        */
+    int32_t autotune;           /* 1: cavmd_init times candidate launch shapes of the SCC-DFTB
+                                   kernel on a trial step and keeps the fastest (all candidates
+                                   give bitwise identical results); 0: fixed defaults            */
 } cavmd_options;
 
 /* Observables at the current (synchronised) time. Optional arrays may be NULL. */
@@ -203,6 +209,19 @@ int cavmd_observables(cavmd_ctx *ctx, cavmd_obs *out);
  * (e_kin, e_dftb, e_photon, e_coupling, e_dse, e_photon_free, e_total, step), oldest first.
  * *n_out receives the number written. Waits for the queued work. */
 int cavmd_energy_history(cavmd_ctx *ctx, double *out, int32_t n, int32_t *n_out);
+
+/* Autocorrelation functions accumulated on the device (options.acf_lags > 0), the correlation
+ * functions behind the paper's molecular spectrum <mu_x(t) mu_x(0)> and angle-resolved photonic
+ * spectrum <q_k(t) q_k(0)> (Results). One sample per synchronised state: the state after
+ * cavmd_init (or cavmd_set_state, which restarts the accumulation) and the state after every
+ * step. Channels c = 0..M-1 are the photon coordinates q_c, channel M the total projected dipole
+ * sum_n M_n. out (HOST, (M + 1) * n_lags doubles, channel-major) receives the mean-removed
+ * unbiased estimator
+ *     C_c(l) = 1/(n - l) sum_{t=l}^{n-1} (x_t - xbar)(x_{t-l} - xbar),  xbar = mean of the n samples,
+ * for lag l (in steps) < n, and 0 for l >= n. *n_samples (may be NULL) receives n. reset != 0
+ * clears the accumulation after reading. Waits for the queued work. Errors: INVALID_ARG when the
+ * context was made with acf_lags = 0 or n_lags differs from it. */
+int cavmd_autocorrelation(cavmd_ctx *ctx, double *out, int32_t n_lags, int64_t *n_samples, int32_t reset);
 
 /* Waits, then copies the state into / out of the caller's host buffers. cavmd_set_state
  * re-evaluates every cell at the new positions (as cavmd_init does, without touching the

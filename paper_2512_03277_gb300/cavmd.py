@@ -55,7 +55,8 @@ class cavmd_options(C.Structure):
                 ("scc_max_iter", C.c_int32), ("mixing", C.c_double), ("splitting", C.c_int32),
                 ("photon_init", C.c_int32), ("graph_chunk", C.c_int32), ("device", C.c_int32),
                 ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p), ("energy_history", C.c_int32)]
+                ("alloc_user", C.c_void_p), ("energy_history", C.c_int32), ("acf_lags", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class cavmd_obs(C.Structure):
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH):
     lib.cavmd_step.argtypes = [C.c_void_p, C.c_int64]
     lib.cavmd_observables.argtypes = [C.c_void_p, C.POINTER(cavmd_obs)]
     lib.cavmd_energy_history.argtypes = [C.c_void_p, _dp, C.c_int32, _ip]
+    lib.cavmd_autocorrelation.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int64), C.c_int32]
     lib.cavmd_get_state.argtypes = [C.c_void_p, C.POINTER(cavmd_state)]
     lib.cavmd_set_state.argtypes = [C.c_void_p, C.POINTER(cavmd_state)]
     lib.cavmd_get_eval.argtypes = [C.c_void_p, C.POINTER(cavmd_eval)]
@@ -331,6 +333,15 @@ class Context:
         got = C.c_int32()
         _check(self.lib.cavmd_energy_history(self.handle, _ptr(buf), n, C.byref(got)), self.handle)
         return buf[:got.value]
+
+    def cavmd_autocorrelation(self, reset: bool = False):
+        """(acf [M + 1, L], n): the device-accumulated correlation functions of the photon
+        coordinates (rows 0..M-1) and the total dipole (row M), and the number of samples."""
+        L = self.opt.acf_lags
+        buf = np.empty((self.n_modes + 1, L))
+        n = C.c_int64()
+        _check(self.lib.cavmd_autocorrelation(self.handle, _ptr(buf), L, C.byref(n), int(reset)), self.handle)
+        return buf, n.value
 
     def cavmd_get_state(self):
         st = cavmd_state()

@@ -50,6 +50,8 @@ struct cavmd_ctx {
     bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
     GenericPlan gplan{};
     long long *d_Coff = nullptr;             // eigenvector block of each cell (generic kernel)
+    AcfArgs acf{};                           // on-device autocorrelation (acf.L > 0)
+    double *d_acf_out = nullptr;
     TcPlan tc{};
     double *d_G = nullptr, *d_E2 = nullptr, *d_E1 = nullptr;
     float *d_Wt2 = nullptr, *d_Wt1 = nullptr;
@@ -252,6 +254,25 @@ cudaError_t run_field(cavmd_ctx *c, int flags) {
     return launch_field(c->sa, flags, c->stream);
 }
 
+// One autocorrelation sample of the synchronised state (after the energy record).
+cudaError_t run_acf(cavmd_ctx *c) {
+    if (c->acf.L <= 0) return cudaSuccess;
+    PhaseScope ps(c, 2);
+    return launch_acf(c->acf, c->d_qs, c->d_Mc, c->N, c->stream);
+}
+
+cudaError_t reset_acf(cavmd_ctx *c) {
+    if (c->acf.L <= 0) return cudaSuccess;
+    const size_t cl = (size_t)c->acf.C * c->acf.L;
+    cudaError_t e = cudaMemsetAsync(c->acf.ring, 0, sizeof(double) * cl, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.head, 0, sizeof(double) * cl, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.acc, 0, sizeof(double) * cl, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.sum, 0, sizeof(double) * c->acf.C, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.n, 0, sizeof(long long), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.ticket, 0, sizeof(unsigned), c->stream);
+    return e;
+}
+
 // Queues n >= 1 steps starting and ending at a synchronised state; the first queued step is
 // step number first_step (evaluation index = step number, init being evaluation 0).
 cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
@@ -271,10 +292,11 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
             if ((e = run_tc_back(c, true, !last)) != cudaSuccess) return e;
             if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | FLD_E_GIVEN | (last ? 0 : FLD_FIRST))) != cudaSuccess)
                 return e;
-            continue;
+        } else {
+            if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
+            if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
         }
-        if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
-        if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
+        if ((e = run_acf(c)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -421,6 +443,8 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
     if (o->graph_chunk < 0 || o->energy_history < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad graph_chunk or energy_history");
     if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return fail(c, CAVMD_ERR_INVALID_ARG, "dev_alloc and dev_free go together");
+    if (o->acf_lags < 0 || (o->autotune != 0 && o->autotune != 1))
+        return fail(c, CAVMD_ERR_INVALID_ARG, "acf_lags must be >= 0 and autotune 0 or 1");
     if (o->precision == CAVMD_PREC_MIXED_BF16X3) {
         int Kx, Ky2;
         double dkx, dky;
@@ -576,6 +600,16 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         CK(launch_tc_panels(p, c->d_R, st));
     }
 
+    if (c->opt.acf_lags > 0) {
+        AcfArgs &a = c->acf;
+        a.M = M;
+        a.C = M + 1;
+        a.L = c->opt.acf_lags;
+        const size_t cl = (size_t)a.C * a.L;
+        AL(a.ring, cl); AL(a.head, cl); AL(a.acc, cl); AL(a.sum, a.C); AL(a.n, 1); AL(a.ticket, 1);
+        AL(c->d_acf_out, cl);
+        CK(reset_acf(c));
+    }
     if (c->generic) {
         GenericPlan &g = c->gplan;
         std::vector<int> norb_e(sk->norb, sk->norb + sk->n_elem);
@@ -680,6 +714,10 @@ int cavmd_init(cavmd_ctx **out, const cavmd_system *sys, const cavmd_sk_tables *
     for (int k = 0; k < 3; ++k) c->pol[k] = md->pol[k];
     rc = build_context(c, sys, sk, md);
     if (!rc) rc = initial_evaluation(c, true);
+    if (!rc) {
+        const cudaError_t e = run_acf(c);
+        if (e != cudaSuccess) rc = cuda_fail(c, e, "autocorrelation sample");
+    }
     if (rc) {
         g_init_error = c->err;
         release(c);
@@ -784,6 +822,22 @@ int cavmd_energy_history(cavmd_ctx *c, double *out, int32_t n, int32_t *n_out) {
     return rc;
 }
 
+int cavmd_autocorrelation(cavmd_ctx *c, double *out, int32_t n_lags, int64_t *n_samples, int32_t reset) {
+    if (!c || !out) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    if (c->acf.L <= 0) return fail(c, CAVMD_ERR_INVALID_ARG, "the context was made with acf_lags = 0");
+    if (n_lags != c->acf.L) return fail(c, CAVMD_ERR_INVALID_ARG, "n_lags differs from the context's acf_lags");
+    int rc = sync_status(c);
+    CK(launch_acf_finalize(c->acf, c->d_acf_out, c->stream));
+    long long n = 0;
+    CK(cudaMemcpyAsync(&n, c->acf.n, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out, c->d_acf_out, sizeof(double) * (size_t)c->acf.C * c->acf.L, cudaMemcpyDeviceToHost,
+                       c->stream));
+    if (reset) CK(reset_acf(c));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_samples) *n_samples = n;
+    return rc;
+}
+
 int cavmd_get_state(cavmd_ctx *c, cavmd_state *s) {
     if (!c || !s) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
     int rc = sync_status(c);
@@ -808,7 +862,11 @@ int cavmd_set_state(cavmd_ctx *c, const cavmd_state *s) {
     long long stp = s->step;
     CK(cudaMemcpy(c->d_step, &stp, sizeof(long long), cudaMemcpyHostToDevice));
     c->step = s->step;
-    return initial_evaluation(c, false);   // Born charges, if any, are refreshed here as well
+    rc = initial_evaluation(c, false);   // Born charges, if any, are refreshed here as well
+    if (rc) return rc;
+    CK(reset_acf(c));                      // a new trajectory segment: its own correlation functions
+    CK(run_acf(c));
+    return sync_status(c);
 }
 
 int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {

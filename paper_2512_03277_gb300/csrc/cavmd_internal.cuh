@@ -139,6 +139,17 @@ __device__ __forceinline__ double rsqrt_nr(double d) {
 // Records the message returned by cavmd_last_error(NULL) (calls without a context).
 void cavmd_set_global_error(const std::string &msg);
 
+// On-device autocorrelation accumulators (channels: M photon coordinates, then the total dipole).
+struct AcfArgs {
+    int M, C, L;                 // modes, channels (M + 1), lags
+    double *ring, *head, *acc;   // [C][L]: last L samples, first L samples, lag products
+    double *sum;                 // [C] running sums
+    long long *n;                // samples so far
+    unsigned *ticket;            // last-block counter
+};
+cudaError_t launch_acf(const AcfArgs &a, const double *q_sync, const double *M_cell, int N, cudaStream_t st);
+cudaError_t launch_acf_finalize(const AcfArgs &a, double *out, cudaStream_t st);
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st);
 

@@ -25,7 +25,13 @@ def autocorrelation(x: np.ndarray, max_lag: int | None = None) -> np.ndarray:
 
 def spectrum(x: np.ndarray, dt: float, max_lag: int | None = None, pad: int = 8):
     """(omega [Hartree], I(omega)) of a series sampled every dt (atomic units of time)."""
-    c = autocorrelation(x, max_lag)
+    return spectrum_from_acf(autocorrelation(x, max_lag), dt, pad)
+
+
+def spectrum_from_acf(c: np.ndarray, dt: float, pad: int = 8):
+    """(omega, I(omega)) from correlation functions c[lag, ...] sampled every dt, e.g. the
+    device-accumulated ones of cavmd_autocorrelation (transposed to lag-major)."""
+    c = np.asarray(c, float)
     n = len(c)
     w = 0.5 * (1.0 + np.cos(np.pi * np.arange(n) / n))          # Hann half-window
     c = c * w.reshape((-1,) + (1,) * (c.ndim - 1))
