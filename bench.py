@@ -197,6 +197,10 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="coupling contraction: FP64, or BF16x3 on the tensor cores (grid modes)")
     ap.add_argument("--n-cells", type=int, default=None, help="trim the workload to this many cells")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes instead of timing candidates at init")
+    ap.add_argument("--scc-history", type=int, default=None,
+                    help="Anderson history of the cluster kernel (default: the library's)")
     ap.add_argument("--acf-lags", type=int, default=None,
                     help="on-device autocorrelation lags (default: 1024 for c5, whose configuration asks for "
                          "it, else off)")
@@ -229,6 +233,9 @@ def main():
         opt.mixing = args.mixing
     opt.charge_model = {"mulliken": 0, "born_fd": 1, "born_central": 2, "born_mlp": 3}[args.charge_model]
     opt.precision = {"fp64": 0, "mixed": 2}[args.precision]
+    if args.scc_history is not None:
+        opt.scc_history = args.scc_history
+    opt.autotune = 0 if args.no_autotune else 1
     if args.acf_lags is None:
         args.acf_lags = 1024 if args.workload == "c5" else 0
     opt.acf_lags = args.acf_lags
@@ -327,6 +334,7 @@ def main():
                         + (int(phase_cnt[0]) if args.precision == "mixed" else 0),
         "acf_lags": args.acf_lags,
         "clocks": clk,
+        "tuning": ctx.cavmd_tuning(),
         "wall_s_timed_region": t_wall,
         "energy_total": obs["e_total"], "temperature_K": obs["temperature"],
     }

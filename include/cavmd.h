@@ -147,6 +147,9 @@ typedef struct {
     int32_t autotune;           /* 1: cavmd_init times candidate launch shapes of the SCC-DFTB
                                    kernel on a trial step and keeps the fastest (all candidates
                                    give bitwise identical results); 0: fixed defaults            */
+    int32_t scc_history;        /* Anderson mixing history of the cluster kernel: the current and
+                                   up to scc_history-1 previous iterates (1..6; 1 = linear mixing).
+                                   Cells of 3 atoms / 6 orbitals use a fixed history of 3.        */
 } cavmd_options;
 
 /* Observables at the current (synchronised) time. Optional arrays may be NULL. */
@@ -222,6 +225,11 @@ int cavmd_energy_history(cavmd_ctx *ctx, double *out, int32_t n, int32_t *n_out)
  * clears the accumulation after reading. Waits for the queued work. Errors: INVALID_ARG when the
  * context was made with acf_lags = 0 or n_lags differs from it. */
 int cavmd_autocorrelation(cavmd_ctx *ctx, double *out, int32_t n_lags, int64_t *n_samples, int32_t reset);
+
+/* A one-line report of the launch shapes in use: with options.autotune = 1, the candidates timed
+ * by cavmd_init on a trial step and the one kept. buf is a HOST buffer of len bytes; the report
+ * is truncated to fit and always NUL-terminated. */
+int cavmd_tuning(cavmd_ctx *ctx, char *buf, int32_t len);
 
 /* Waits, then copies the state into / out of the caller's host buffers. cavmd_set_state
  * re-evaluates every cell at the new positions (as cavmd_init does, without touching the

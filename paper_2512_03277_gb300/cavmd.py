@@ -56,7 +56,7 @@ class cavmd_options(C.Structure):
                 ("photon_init", C.c_int32), ("graph_chunk", C.c_int32), ("device", C.c_int32),
                 ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", C.c_void_p), ("energy_history", C.c_int32), ("acf_lags", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("scc_history", C.c_int32)]
 
 
 class cavmd_obs(C.Structure):
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.cavmd_observables.argtypes = [C.c_void_p, C.POINTER(cavmd_obs)]
     lib.cavmd_energy_history.argtypes = [C.c_void_p, _dp, C.c_int32, _ip]
     lib.cavmd_autocorrelation.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int64), C.c_int32]
+    lib.cavmd_tuning.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
     lib.cavmd_get_state.argtypes = [C.c_void_p, C.POINTER(cavmd_state)]
     lib.cavmd_set_state.argtypes = [C.c_void_p, C.POINTER(cavmd_state)]
     lib.cavmd_get_eval.argtypes = [C.c_void_p, C.POINTER(cavmd_eval)]
@@ -342,6 +343,11 @@ class Context:
         n = C.c_int64()
         _check(self.lib.cavmd_autocorrelation(self.handle, _ptr(buf), L, C.byref(n), int(reset)), self.handle)
         return buf, n.value
+
+    def cavmd_tuning(self) -> str:
+        buf = C.create_string_buffer(2048)
+        _check(self.lib.cavmd_tuning(self.handle, buf, len(buf)), self.handle)
+        return buf.value.decode()
 
     def cavmd_get_state(self):
         st = cavmd_state()

@@ -50,6 +50,9 @@ struct cavmd_ctx {
     bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
     GenericPlan gplan{};
     long long *d_Coff = nullptr;             // eigenvector block of each cell (generic kernel)
+    int water_warps = 2;                     // launch shape of the water kernel
+    long long n_cwarm = 0;                   // doubles in the warm-start eigenvector blocks
+    std::string tuning = "not tuned (options.autotune = 0): default launch shapes";
     AcfArgs acf{};                           // on-device autocorrelation (acf.L > 0)
     double *d_acf_out = nullptr;
     TcPlan tc{};
@@ -115,6 +118,15 @@ int dalloc(cavmd_ctx *c, void **p, size_t bytes) {
 template <typename T>
 int dalloc_n(cavmd_ctx *c, T **p, size_t n) {
     return dalloc(c, reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+// Frees a buffer of dalloc before the context ends (scratch of the tuner).
+void dfree(cavmd_ctx *c, void *p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_user);
+    else cudaFree(p);
 }
 
 #define AL(ptr, n)                                   \
@@ -194,7 +206,7 @@ cudaError_t run_dftb(cavmd_ctx *c, int have_warm) {
     PhaseScope ps(c, 0);
     c->da.have_warm = have_warm;
     if (c->generic) return launch_dftb_generic(c->d_sk, c->da, c->gplan, c->stream);
-    return launch_dftb_water(c->d_sk, c->da, c->stream);
+    return launch_dftb_water(c->d_sk, c->da, c->stream, c->water_warps);
 }
 
 // Finite-difference dipole derivatives at the current positions (after the cell evaluation).
@@ -207,7 +219,7 @@ cudaError_t run_born(cavmd_ctx *c) {
     d.fd_h = c->opt.fd_step;
     d.M_disp = c->d_Mdisp;
     cudaError_t e = c->generic ? launch_dftb_generic(c->d_sk, d, c->gplan, c->stream)
-                               : launch_dftb_water(c->d_sk, d, c->stream);
+                               : launch_dftb_water(c->d_sk, d, c->stream, c->water_warps);
     if (e != cudaSuccess) return e;
     return launch_born_assemble(c->N, c->d_off, c->d_Mc, c->d_Mdisp, c->n_disp, d.fd_central, d.fd_h, c->d_b,
                                 c->stream);
@@ -299,6 +311,95 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
         if ((e = run_acf(c)) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Launch-shape tuner. Candidates differ only in how work is mapped to threads and blocks, never in
+// arithmetic, so every candidate gives bitwise identical results:
+//   cluster kernel: product entries per thread per pass (2 or 4) x persistent blocks per SM;
+//   water kernel: warps per block (2, 4 or 8).
+// Each candidate evaluates a trial step (positions drifted by dt p / m, warm started from a copy of
+// the converged state) twice, timed with CUDA events on the context's stream; the fastest is kept.
+// The context's own state is not touched.
+int autotune(cavmd_ctx *c) {
+    const int NA = c->n_atoms, N = c->N;
+    cudaStream_t st = c->stream;
+    const long long ncw = c->n_cwarm;
+    double *r_t = nullptr, *F_t = nullptr, *b_t = nullptr, *qp_t = nullptr, *qv_t = nullptr, *C_t = nullptr;
+    double *E_t = nullptr, *M_t = nullptr, *Q_t = nullptr;
+    int *it_t = nullptr;
+    unsigned *st_t = nullptr;
+    AL(r_t, 3 * NA); AL(F_t, 3 * NA); AL(b_t, 3 * NA); AL(qp_t, NA); AL(qv_t, NA); AL(C_t, ncw);
+    AL(E_t, N); AL(M_t, N); AL(Q_t, NA); AL(it_t, N); AL(st_t, 1);
+    CK(launch_trial_positions(c->d_r, c->d_p, c->d_imass, c->opt.dt, NA, r_t, st));
+    DftbArgs t = c->da;
+    t.r = r_t; t.F = F_t; t.b = b_t; t.qpop = qp_t; t.qprev = qv_t; t.Cwarm = C_t; t.E_cell = E_t;
+    t.M_cell = M_t; t.iters = it_t; t.status = st_t; t.Qout = Q_t; t.have_warm = 1; t.n_disp = 0;
+    t.M_disp = nullptr;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct Cand { int a, b; float ms; };
+    std::vector<Cand> cands;
+    if (c->generic) {
+        for (int r : {2, 4})
+            for (int b = 1; b <= c->gplan.max_blocks_per_sm; ++b) cands.push_back({r, b, 0.f});
+    } else {
+        for (int w : {2, 4, 8}) cands.push_back({w, 0, 0.f});
+    }
+    for (auto &cd : cands) {
+        cd.ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            CK(cudaMemcpyAsync(qp_t, c->d_qpop, sizeof(double) * NA, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(qv_t, c->d_qprev, sizeof(double) * NA, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(C_t, c->d_C, sizeof(double) * ncw, cudaMemcpyDeviceToDevice, st));
+            CK(cudaEventRecord(e0, st));
+            if (c->generic) {
+                GenericPlan g = c->gplan;
+                g.r_entries = cd.a;
+                g.blocks_per_sm = cd.b;
+                CK(launch_dftb_generic(c->d_sk, t, g, st));
+            } else {
+                CK(launch_dftb_water(c->d_sk, t, st, cd.a));
+            }
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            cd.ms = std::min(cd.ms, ms);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const Cand *best = &cands[0];
+    for (auto &cd : cands)
+        if (cd.ms < best->ms) best = &cd;
+    char buf[160];
+    std::string rep;
+    if (c->generic) {
+        c->gplan.r_entries = best->a;
+        c->gplan.blocks_per_sm = best->b;
+        std::snprintf(buf, sizeof(buf), "k_dftb_generic: r_entries=%d blocks_per_sm=%d (%.3f ms); candidates:",
+                      best->a, best->b, best->ms);
+        rep = buf;
+        for (auto &cd : cands) {
+            std::snprintf(buf, sizeof(buf), " r%d/b%d %.3f ms", cd.a, cd.b, cd.ms);
+            rep += buf;
+        }
+    } else {
+        c->water_warps = best->a;
+        std::snprintf(buf, sizeof(buf), "dftb_kernel<3,6>: warps_per_block=%d (%.3f ms); candidates:", best->a,
+                      best->ms);
+        rep = buf;
+        for (auto &cd : cands) {
+            std::snprintf(buf, sizeof(buf), " w%d %.3f ms", cd.a, cd.ms);
+            rep += buf;
+        }
+    }
+    c->tuning = rep;
+    for (void *p : {(void *)r_t, (void *)F_t, (void *)b_t, (void *)qp_t, (void *)qv_t, (void *)C_t, (void *)E_t,
+                    (void *)M_t, (void *)Q_t, (void *)it_t, (void *)st_t})
+        dfree(c, p);
+    return CAVMD_OK;
 }
 
 int initial_evaluation(cavmd_ctx *c, bool init_photons) {
@@ -445,6 +546,7 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if ((o->dev_alloc == nullptr) != (o->dev_free == nullptr)) return fail(c, CAVMD_ERR_INVALID_ARG, "dev_alloc and dev_free go together");
     if (o->acf_lags < 0 || (o->autotune != 0 && o->autotune != 1))
         return fail(c, CAVMD_ERR_INVALID_ARG, "acf_lags must be >= 0 and autotune 0 or 1");
+    if (o->scc_history < 1 || o->scc_history > 6) return fail(c, CAVMD_ERR_INVALID_ARG, "scc_history must be 1..6");
     if (o->precision == CAVMD_PREC_MIXED_BF16X3) {
         int Kx, Ky2;
         double dkx, dky;
@@ -524,7 +626,9 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         if (no != 6 || sys->cell_offset[n + 1] - sys->cell_offset[n] != 3) c->generic = true;
         coff[n + 1] = coff[n] + (long long)no * no;
     }
+    c->n_cwarm = coff[N];
     AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)coff[N]); AL(c->d_E, N); AL(c->d_Mc, N);
+    if (!c->generic) CK(prepare_dftb_water(8));
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N);
     c->mixed = c->opt.precision == CAVMD_PREC_MIXED_BF16X3;
     if (!c->mixed) AL(c->d_U, (size_t)M * N);
@@ -652,6 +756,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.scc_tol = c->opt.scc_tol;
     d.beta = c->opt.mixing;
     d.max_iter = c->opt.scc_max_iter;
+    d.hist = c->opt.scc_history;
     d.have_warm = 0;
     d.write_b = c->opt.charge_model == CAVMD_CHARGE_MULLIKEN;
     d.n_disp = 0;
@@ -695,6 +800,7 @@ void cavmd_default_options(cavmd_options *o) {
     o->graph_chunk = 50;
     o->device = 0;
     o->energy_history = 1024;
+    o->scc_history = 3;
 }
 
 int cavmd_init(cavmd_ctx **out, const cavmd_system *sys, const cavmd_sk_tables *sk,
@@ -714,6 +820,7 @@ int cavmd_init(cavmd_ctx **out, const cavmd_system *sys, const cavmd_sk_tables *
     for (int k = 0; k < 3; ++k) c->pol[k] = md->pol[k];
     rc = build_context(c, sys, sk, md);
     if (!rc) rc = initial_evaluation(c, true);
+    if (!rc && c->opt.autotune) rc = autotune(c);
     if (!rc) {
         const cudaError_t e = run_acf(c);
         if (e != cudaSuccess) rc = cuda_fail(c, e, "autocorrelation sample");
@@ -836,6 +943,12 @@ int cavmd_autocorrelation(cavmd_ctx *c, double *out, int32_t n_lags, int64_t *n_
     CK(cudaStreamSynchronize(c->stream));
     if (n_samples) *n_samples = n;
     return rc;
+}
+
+int cavmd_tuning(cavmd_ctx *c, char *buf, int32_t len) {
+    if (!c || !buf || len < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad argument");
+    std::snprintf(buf, (size_t)len, "%s", c->tuning.c_str());
+    return CAVMD_OK;
 }
 
 int cavmd_get_state(cavmd_ctx *c, cavmd_state *s) {

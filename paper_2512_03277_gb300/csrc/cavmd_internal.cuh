@@ -52,6 +52,7 @@ struct DftbArgs {
     double scc_tol;
     double beta;
     int max_iter;
+    int hist;                  // Anderson history (cluster kernel): current + hist-1 previous iterates
     int have_warm;             // 1: Cwarm and qpop hold a previous solution
     int write_b;               // 1: write Mulliken b
     // finite-difference rows: n_disp > 0 turns every cell into displaced copies that only compute
@@ -151,13 +152,18 @@ cudaError_t launch_acf(const AcfArgs &a, const double *q_sync, const double *M_c
 cudaError_t launch_acf_finalize(const AcfArgs &a, double *out, cudaStream_t st);
 
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st);
+cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st, int warps = 2);
+cudaError_t prepare_dftb_water(int max_warps);   // shared-memory attribute for up to max_warps per block
+// r_trial = r + dt p / m: positions one drift ahead, for timing trial evaluations
+cudaError_t launch_trial_positions(const double *r, const double *p, const double *inv_mass, double dt, int n_atoms,
+                                   double *r_trial, cudaStream_t st);
 
 // Plan of the persistent SCC-DFTB launch over cells of any composition (up to 64 orbitals).
 struct GenericPlan {
     int nmax_b, amax_b, nmax_s, amax_s;          // largest cell of the large (> 32 orbitals) and small classes
     int n_big, n_small, n_disp_big, n_disp_small;
-    int n_sm, blocks_per_sm;
+    int n_sm, blocks_per_sm, max_blocks_per_sm;  // persistent grid: n_sm x blocks_per_sm blocks
+    int r_entries;                               // product entries per thread per pass (2 or 4)
     size_t smem;                                 // dynamic shared memory per block
     int2 *items, *disp_items;                    // device: (cell, -1) and (cell, displacement), largest first
     unsigned *queue;                             // device: [2] work counters

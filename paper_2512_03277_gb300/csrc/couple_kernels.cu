@@ -288,6 +288,19 @@ cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+static __global__ void k_trial_positions(const double *__restrict__ r, const double *__restrict__ p,
+                                  const double *__restrict__ inv_mass, double dt, int n, double *__restrict__ rt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    rt[i] = fma(dt * inv_mass[i / 3], p[i], r[i]);
+}
+
+cudaError_t launch_trial_positions(const double *r, const double *p, const double *inv_mass, double dt, int n_atoms,
+                                   double *r_trial, cudaStream_t st) {
+    k_trial_positions<<<(3 * n_atoms + 255) / 256, 256, 0, st>>>(r, p, inv_mass, dt, n_atoms, r_trial);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_field_only(const double *U, const double *W, int M, int N, double *E,
                               cudaStream_t st) {
     k_field_only<<<(N + 127) / 128, 128, 0, st>>>(U, W, M, N, E);

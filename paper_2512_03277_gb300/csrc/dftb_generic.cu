@@ -3,19 +3,23 @@
 //
 // The method is the one of the water kernel in dftb_kernel.cu (second-order SCC-DFTB, section
 // "Computational details"): warm-started S-orthonormal basis, SCC iterations with Jacobi sweeps or
-// the second-order occupied-virtual update, Anderson mixing, analytic forces. What differs is the
-// mapping to the machine, made for matrices too large for a lane group:
-//   * work items: a cell of more than 32 orbitals takes a whole 64-thread block (thread j owns
-//     orbital column j); smaller cells take one warp each, two per block. A persistent grid pulls
-//     items from a queue ordered by decreasing size, so large cells start first and small ones
-//     fill the tail (the item lists are built once on the host);
-//   * four n x n matrices per cell in shared memory, sized for the largest cell of each class:
-//     SH (the symmetric S in the strict lower triangle, the symmetric H0 in the upper triangle and
-//     on the diagonal, since S_ii = 1), C, A and Y. Every matrix product is a column product with
-//     eight independent row accumulators, one operand broadcast from shared memory;
-//   * the final stage reuses the four buffers for H, C_occ, C_occ^T H C_occ, P, W and the pair
-//     gradients, so the energy-weighted density needs no further storage. A (H2O)_8 cell (48
-//     orbitals) takes 87 KB, so two large cells share an SM.
+// the second-order occupied-virtual update, Anderson mixing, analytic forces. The mapping to the
+// machine is made for matrices too large for a lane group, on a GPU whose FP64 pipe (2 FMA per
+// clock per SM) is the only bottleneck, so what counts is the number of FP64 warp instructions:
+//   * work items: a cell of more than 32 orbitals takes a whole 128-thread block, smaller cells
+//     take 64 threads each, two per block. A persistent grid pulls items from a queue ordered by
+//     decreasing size, so large cells start first and small ones fill the tail;
+//   * every matrix product spreads its output entries evenly over the cell's threads (R entries
+//     per thread per pass, each summed over k in increasing order), so nearly every lane of
+//     every FP64 instruction does useful work whatever the orbital count; the results do not
+//     depend on R or on the grid size;
+//   * per SCC iteration only what the update needs is formed: H C, the diagonal and the
+//     occupied-virtual block of C^T H C, K^2 in its two diagonal blocks from the compact
+//     occupied-virtual generator, C V, and S C_occ for the Mulliken populations;
+//   * four n x n matrices per cell in shared memory: SH (the symmetric S in the strict lower
+//     triangle, the symmetric H0 in the upper triangle and on the diagonal, since S_ii = 1),
+//     C, A and Y, plus the compact generator. A (H2O)_8 cell (48 orbitals) takes about 92 KB, so
+//     two large cells share an SM.
 #include <algorithm>
 #include <vector>
 
@@ -23,19 +27,21 @@
 
 namespace {
 
-constexpr int GNHIST = 3;
+constexpr int GNHIST = 6;              // largest Anderson history (current + 5 previous iterates)
 constexpr int G_MAX_SWEEPS = 40;
 constexpr double G_JACOBI_TOL = 1e-15;
 constexpr double G_MIN_GAP = 1e-3;
 constexpr double G_EIG_TOL = 1e-10;
 constexpr float G_KMAX_PERT = 1e-4f;
-constexpr int CH = 8;       // rows per register block
-constexpr int GTPB = 64;    // threads per block
+constexpr int BT = 128;                // threads per block
+constexpr int TB = 128;                // threads per large cell
+constexpr int TS = 64;                 // threads per small cell (two per block)
 
 // Shared-memory layout of one cell (byte offsets) for cells of at most nmax orbitals, amax atoms.
 struct GLayout {
     int nmax, amax, pmax;
-    unsigned SH, C, A, Y, pos, gam, zv, q, qout, qst, shift, shl, hq, hf, red, diag, cs, invd, ints, total;
+    unsigned SH, C, A, Y, Kc, pos, gam, zv, q, qout, qst, shift, shl, hq, hf, red, diag, cs, invd, th, ints,
+        total;
 };
 
 __host__ __device__ inline GLayout g_layout(int nmax, int amax) {
@@ -43,14 +49,15 @@ __host__ __device__ inline GLayout g_layout(int nmax, int amax) {
     L.nmax = nmax;
     L.amax = amax;
     L.pmax = amax * (amax - 1) / 2 > 0 ? amax * (amax - 1) / 2 : 1;
-    const int ld = (nmax % 2 == 0) ? nmax + 1 : nmax;
+    const int ld = nmax + 1;
     const unsigned mat = (unsigned)(nmax * ld + 8) * 8;   // 8 doubles of slack for clamped reads
-    const unsigned ymat = mat > (unsigned)L.pmax * 32u ? mat : (unsigned)L.pmax * 32u;   // Y also holds pair gradients
+    const unsigned ymat = mat > (unsigned)L.pmax * 32u ? mat : (unsigned)L.pmax * 32u;   // pair gradients fit too
     unsigned o = 0;
     L.SH = o; o += mat;
-    L.C = o; o += mat;
+    L.C = o; o += ymat;   // C and Y swap roles: both can hold the pair gradients
     L.A = o; o += mat;
     L.Y = o; o += ymat;
+    L.Kc = o; o += (unsigned)((nmax / 2) * ((nmax + 1) / 2) + 8) * 8;   // n_occ x n_virt <= n^2 / 4
     L.pos = o; o += amax * 3 * 8;
     L.gam = o; o += amax * amax * 8;
     L.zv = o; o += amax * 8;
@@ -65,13 +72,38 @@ __host__ __device__ inline GLayout g_layout(int nmax, int amax) {
     L.diag = o; o += nmax * 8;
     L.cs = o; o += (nmax / 2 + 1) * 16;
     L.invd = o; o += nmax * 8;
+    L.th = o; o += GNHIST * 8;
     L.ints = o;
-    // ints: spec[amax], atom_off[amax+1], orb_atom[nmax], occ_list[nmax], occf[nmax], eok[nmax],
-    //       pa[pmax], pb[pmax], fl[8]
-    o += (unsigned)(2 * amax + 1 + 4 * nmax + 2 * L.pmax + 8) * 4;
+    // ints: spec[amax], atom_off[amax+1], orb_atom[nmax], occ_list[nmax], virt_list[nmax],
+    //       occf[nmax], pp[nmax/2+1], pq[nmax/2+1], pa[pmax], pb[pmax], fl[8]
+    o += (unsigned)(2 * amax + 1 + 4 * nmax + 2 * (nmax / 2 + 1) + 2 * L.pmax + 8) * 4;
     L.total = (o + 15u) & ~15u;
     return L;
 }
+
+// A group of T threads evaluating one cell: the whole block (T = BT), or one half of it
+// (T = 64, named barrier 1 or 2).
+template <int T>
+struct Grp {
+    int tid;
+    int bar;
+    int *vote;   // T/32 ints of shared scratch (halves only)
+    __device__ __forceinline__ void sync() const {
+        if (T == BT) __syncthreads();
+        else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory");
+    }
+    __device__ __forceinline__ bool all(bool p) const {
+        if (T == BT) return __syncthreads_and(p) != 0;
+        const bool w = __all_sync(CAVMD_FULL_MASK, p);
+        sync();   // earlier readers of vote are done
+        if ((tid & 31) == 0) vote[tid >> 5] = w;
+        sync();
+        bool r = true;
+#pragma unroll
+        for (int i = 0; i < T / 32; ++i) r = r && vote[i];
+        return r;
+    }
+};
 
 __device__ __forceinline__ void radial_g(const double *par, double r, const DevSK &sk, double &v, double &dv) {
     const double a = par[0], b = par[1], c1 = par[2], c2 = par[3];
@@ -94,16 +126,7 @@ __device__ __forceinline__ void radial_g(const double *par, double r, const DevS
     dv = e * (fma(-b * poly, f, dpoly * f) + poly * df);
 }
 
-// Round-robin Jacobi schedule for even n (rounds r = 0..n-2; index n-1 meets r).
-__device__ __forceinline__ int g_partner(int j, int r, int n, int &slot) {
-    const int m = n - 1;
-    if (j == m) { slot = 0; return r; }
-    if (j == r) { slot = 0; return m; }
-    const int dlt = (j - r + m) % m;
-    slot = min(dlt, m - dlt);
-    return (r - dlt + m) % m;
-}
-
+// Round-robin Jacobi schedule for even n: pair k of round r (0..n-2); index n-1 meets r.
 __device__ __forceinline__ void g_pair(int k, int r, int n, int &p, int &q) {
     const int m = n - 1;
     if (k == 0) { p = r; q = m; return; }
@@ -129,93 +152,60 @@ __device__ __forceinline__ void g_jacobi_cs(double app, double aqq, double apq, 
     }
 }
 
-template <int T>
-__device__ __forceinline__ void gsync() {
-    if (T == 32) __syncwarp(); else __syncthreads();
-}
-
-template <int T>
-__device__ __forceinline__ bool gall(bool p) {
-    if (T == 32) {
-        __syncwarp();
-        return __all_sync(CAVMD_FULL_MASK, p);
-    }
-    return __syncthreads_and(p) != 0;
-}
-
-// Column product: for rows i < n_out, epi(i, sum_{k < n_k} X(i, k) Z(k)), with
-//   X(i, k) = X[k * xs_k + i * xs_i] (a broadcast read: the same for every thread) and
-//   Z(k) = Z[k * zs] (this thread's operand). Rows are done CH at a time with independent
-// accumulators; rows past n_out read row n_out - 1 and are dropped.
-template <typename Epi>
-__device__ __forceinline__ void col_product(int n_out, int n_k, const double *X, int xs_i, int xs_k,
-                                            const double *Z, int zs, Epi epi) {
-    for (int i0 = 0; i0 < n_out; i0 += CH) {
-        int ro[CH];
+// Flattened dot products: for every entry e < n_out of this thread (e = tid, tid + T, ...),
+// epi(e, sum_{k < nk} xb(e)[k xs] zb(e)[k zs]), the sum taken in increasing k. R entries per pass
+// with independent accumulators; the last pass clamps its surplus entries to n_out - 1 and drops
+// them.
+template <int T, int R, typename XB, typename ZB, typename EPI>
+__device__ __forceinline__ void flat(int tid, int n_out, int nk, int xs, int zs, XB xb, ZB zb, EPI epi) {
+    for (int e0 = tid; e0 < n_out; e0 += T * R) {
+        const double *xp[R];
+        const double *zp[R];
+        double acc[R];
 #pragma unroll
-        for (int t = 0; t < CH; ++t) ro[t] = min(i0 + t, n_out - 1) * xs_i;
-        double acc[CH];
+        for (int r = 0; r < R; ++r) {
+            const int e = min(e0 + r * T, n_out - 1);
+            xp[r] = xb(e);
+            zp[r] = zb(e);
+            acc[r] = 0.0;
+        }
+        for (int k = 0; k < nk; ++k) {
 #pragma unroll
-        for (int t = 0; t < CH; ++t) acc[t] = 0.0;
-        for (int k = 0; k < n_k; ++k) {
-            const double z = Z[k * zs];
-            const double *xk = X + k * xs_k;
-#pragma unroll
-            for (int t = 0; t < CH; ++t) acc[t] = fma(xk[ro[t]], z, acc[t]);
+            for (int r = 0; r < R; ++r) acc[r] = fma(xp[r][k * xs], zp[r][k * zs], acc[r]);
         }
 #pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (i0 + t < n_out) epi(i0 + t, acc[t]);
-    }
-}
-
-// The same with the occupied columns of C as X and Z: for rows i < n_out,
-// epi(i, sum_o C(i, occ[o]) C(jz, occ[o])).
-template <typename Epi>
-__device__ __forceinline__ void col_product_occ(int n_out, int nocc, const double *C, int LD, const int *occ,
-                                                int jz, Epi epi) {
-    for (int i0 = 0; i0 < n_out; i0 += CH) {
-        int ro[CH];
-#pragma unroll
-        for (int t = 0; t < CH; ++t) ro[t] = min(i0 + t, n_out - 1);
-        double acc[CH];
-#pragma unroll
-        for (int t = 0; t < CH; ++t) acc[t] = 0.0;
-        for (int o = 0; o < nocc; ++o) {
-            const double *co = C + occ[o] * LD;
-            const double z = co[jz];
-#pragma unroll
-            for (int t = 0; t < CH; ++t) acc[t] = fma(co[ro[t]], z, acc[t]);
-        }
-#pragma unroll
-        for (int t = 0; t < CH; ++t)
-            if (i0 + t < n_out) epi(i0 + t, acc[t]);
+        for (int r = 0; r < R; ++r)
+            if (e0 + r * T < n_out) epi(e0 + r * T, acc[r]);
     }
 }
 
 // One cell (main evaluation, kd < 0) or one displaced copy of it (kd = displacement index),
-// evaluated by T threads; j = this thread's index among them.
-template <int T>
+// evaluated by the T threads of group g.
+template <int T, int R>
 __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L, unsigned char *sm, int cell,
-                           int kd, int j) {
+                           int kd, const Grp<T> &g) {
+    const int j = g.tid;
     const bool disp = kd >= 0;
     const int a0 = a.cell_offset[cell];
     const int nat = a.cell_offset[cell + 1] - a0;
-    double *SH = (double *)(sm + L.SH), *C = (double *)(sm + L.C);
-    double *A = (double *)(sm + L.A), *Y = (double *)(sm + L.Y);
+    double *SH = (double *)(sm + L.SH), *A = (double *)(sm + L.A), *Kc = (double *)(sm + L.Kc);
+    double *C = (double *)(sm + L.C), *Y = (double *)(sm + L.Y);   // swapped by the second-order update
     double(*pos)[3] = (double(*)[3])(sm + L.pos);
     double *gam = (double *)(sm + L.gam), *zv = (double *)(sm + L.zv), *q = (double *)(sm + L.q);
     double *qout = (double *)(sm + L.qout), *qst = (double *)(sm + L.qst);
     double *shift = (double *)(sm + L.shift), *shl = (double *)(sm + L.shl);
     double *hq = (double *)(sm + L.hq), *hf = (double *)(sm + L.hf), *red = (double *)(sm + L.red);
     double *diag = (double *)(sm + L.diag), *cs = (double *)(sm + L.cs), *invd = (double *)(sm + L.invd);
+    double *th = (double *)(sm + L.th);
     int *spec = (int *)(sm + L.ints);
     int *atom_off = spec + L.amax;
     int *orb_atom = atom_off + L.amax + 1;
     int *occ_list = orb_atom + L.nmax;
-    int *occf = occ_list + L.nmax;
-    int *eok = occf + L.nmax;
-    int *pa = eok + L.nmax;
+    int *virt_list = occ_list + L.nmax;
+    int *occf = virt_list + L.nmax;
+    int *pp = occf + L.nmax;
+    int *pq = pp + (L.nmax / 2 + 1);
+    int *pa = pq + (L.nmax / 2 + 1);
     int *pb = pa + L.pmax;
     int *fl = pb + L.pmax;   // 0 error bits, 2 iterations, 3 occupied orbitals, 4 orbitals, 5 pairs
     const int AM = L.amax;
@@ -230,7 +220,7 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             if (j == da) pos[j][dc] += sg * a.fd_h;
         }
     }
-    gsync<T>();
+    g.sync();
     if (j == 0) {
         int o = 0;
         double nel = 0.0;
@@ -252,28 +242,32 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             for (int y = x + 1; y < nat; ++y) { pa[pi] = x; pb[pi] = y; ++pi; }
         fl[5] = pi;
     }
-    gsync<T>();
+    g.sync();
     const int n = fl[4], nocc = fl[3], npair = fl[5];
+    const int nv = n - nocc;
     const int LD = n + 1;   // n is even (closed shell), so the stride is odd
-    const bool act = j < n;
-    // S(i, j) and H0(i, j) from the shared buffer: column j below the diagonal, row j above it
-    auto s_ij = [&](int i) -> double {
-        const double lo = SH[j * LD + i], up = SH[i * LD + j];
-        return i == j ? 1.0 : (i > j ? lo : up);
+    const int nn = n * n;
+    // S(i, k) and H0(i, k) from the shared buffer: column k below the diagonal, row k above it
+    auto s_at = [&](int i, int k) -> double {
+        const double lo = SH[k * LD + i], up = SH[i * LD + k];
+        return i == k ? 1.0 : (i > k ? lo : up);
     };
-    auto h0_ij = [&](int i) -> double {
-        const double lo = SH[j * LD + i], up = SH[i * LD + j];
-        return i <= j ? lo : up;
+    auto h0_at = [&](int i, int k) -> double {
+        const double lo = SH[k * LD + i], up = SH[i * LD + k];
+        return i <= k ? lo : up;
     };
 
     // ---------------------------------------------------------------- H0, S, gamma
-    if (act) {
-        const int at = orb_atom[j];
-        const int e = spec[at];
-        const double eps = (j == atom_off[at]) ? sk.onsite[e][0] : sk.onsite[e][1];
-        for (int i = 0; i < n; ++i) SH[j * LD + i] = (i == j) ? eps : 0.0;
+    for (int e = j; e < nn; e += T) {
+        const int c = e / n, i = e - c * n;
+        double v = 0.0;
+        if (i == c) {
+            const int at = orb_atom[c], el = spec[at];
+            v = (c == atom_off[at]) ? sk.onsite[el][0] : sk.onsite[el][1];
+        }
+        SH[c * LD + i] = v;
     }
-    gsync<T>();
+    g.sync();
     for (int pi = j; pi < npair; pi += T) {
         const int PA = pa[pi], PB = pb[pi];
         const int eA = spec[PA], eB = spec[PB];
@@ -326,13 +320,9 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
     // ---------------------------------------------------------------- warm-started S-orthonormal basis
     const long long coff = a.Cwarm_off ? a.Cwarm_off[cell] : (long long)cell * 36;
     const double *cw = a.Cwarm + coff;
-    if (a.have_warm) {
-        for (int e2 = j; e2 < n * n; e2 += T) {   // coalesced copy of the previous eigenvectors
-            const int c = e2 / n;
-            C[c * LD + (e2 - c * n)] = cw[e2];
-        }
-    } else if (act) {
-        for (int i = 0; i < n; ++i) C[j * LD + i] = (i == j) ? 1.0 : 0.0;
+    for (int e = j; e < nn; e += T) {   // coalesced copy of the previous eigenvectors
+        const int c = e / n, i = e - c * n;
+        C[c * LD + i] = a.have_warm ? cw[e] : (i == c ? 1.0 : 0.0);
     }
     if (j < nat) {
         if (a.have_warm) {   // predictor 2 q(t) - q(t - dt); displaced copies start from q(t)
@@ -343,18 +333,20 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             q[j] = zv[j];
         }
     }
-    gsync<T>();
-    if (act)   // S, full, into A
-        for (int i = 0; i < n; ++i) A[j * LD + i] = s_ij(i);
-    if (a.have_warm) {
-        gsync<T>();
-        if (act)   // Y = S C
-            col_product(n, n, A, 1, LD, C + j * LD, 1, [&](int i, double v) { Y[j * LD + i] = v; });
-        gsync<T>();
-        if (act)   // A = C^T Y
-            col_product(n, n, C, LD, 1, Y + j * LD, 1, [&](int i, double v) { A[j * LD + i] = v; });
+    g.sync();
+    for (int e = j; e < nn; e += T) {   // S, full, into A
+        const int c = e / n, i = e - c * n;
+        A[c * LD + i] = s_at(i, c);
     }
-    gsync<T>();
+    if (a.have_warm) {   // A = C^T S C
+        g.sync();
+        flat<T, R>(j, nn, n, LD, 1, [&](int e) { return A + (e % n); }, [&](int e) { return C + (e / n) * LD; },
+                   [&](int e, double v) { Y[(e / n) * LD + e % n] = v; });
+        g.sync();
+        flat<T, R>(j, nn, n, 1, 1, [&](int e) { return C + (e % n) * LD; }, [&](int e) { return Y + (e / n) * LD; },
+                   [&](int e, double v) { A[(e / n) * LD + e % n] = v; });
+    }
+    g.sync();
     for (int k = 0; k < n; ++k) {   // Cholesky A = L L^T, right-looking, thread = column
         if (j == k) {
             double d = A[k * LD + k];
@@ -364,14 +356,14 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             A[k * LD + k] = d * y;
             for (int i = k + 1; i < n; ++i) A[k * LD + i] *= y;
         }
-        gsync<T>();
-        if (act && j > k) {
+        g.sync();
+        if (j > k && j < n) {
             const double ljk = A[k * LD + j];
             for (int i = j; i < n; ++i) A[j * LD + i] = fma(-A[k * LD + i], ljk, A[j * LD + i]);
         }
-        gsync<T>();
+        g.sync();
     }
-    if (act) {   // C <- C L^-T, thread = row
+    if (j < n) {   // C <- C L^-T, thread = row
         const int i = j;
         for (int c = 0; c < n; ++c) {
             double x = C[c * LD + i];
@@ -379,9 +371,28 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             C[c * LD + i] = x * invd[c];
         }
     }
-    gsync<T>();
+    g.sync();
+
+    // aufbau occupation from diag[]: occupied and virtual index lists in order of rank
+    auto rank_occupation = [&]() {
+        if (j < n) {
+            const long long kj = order_key(diag[j]);
+            int rank = 0;
+            for (int i = 0; i < n; ++i) {
+                const long long ki = order_key(diag[i]);
+                rank += (ki < kj) || (ki == kj && i < j);
+            }
+            occf[j] = rank < nocc;
+            if (rank < nocc) occ_list[rank] = j; else virt_list[rank - nocc] = j;
+        }
+    };
 
     // ---------------------------------------------------------------- SCC loop
+    // Per iteration: H(q) into A; Y = H C; the diagonal of C^T Y, the occupation, the occupied-
+    // virtual block of C^T Y and the compact generator K(v, o) = A_vo / (A_oo - A_vv). When every
+    // generator entry is below KMAX the basis takes C <- C (I + K + K^2/2) (orthogonal to O(K^4));
+    // otherwise the rest of A = C^T H C is formed and Jacobi sweeps move C (one per iteration when
+    // warm started, to convergence on a cold start).
     int it;
     for (it = 1; it <= a.max_iter; ++it) {
         if (j < nat) {
@@ -389,147 +400,142 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             for (int k = 0; k < nat; ++k) sh = fma(gam[j * AM + k], q[k] - zv[k], sh);
             shift[j] = sh;
         }
-        gsync<T>();
-        if (act) {   // H column j into A
-            const double shj = shift[orb_atom[j]];
-            for (int i = 0; i < n; ++i) A[j * LD + i] = fma(0.5 * s_ij(i), shift[orb_atom[i]] + shj, h0_ij(i));
+        g.sync();
+        for (int e = j; e < nn; e += T) {   // H into A
+            const int c = e / n, i = e - c * n;
+            A[c * LD + i] = fma(0.5 * s_at(i, c), shift[orb_atom[i]] + shift[orb_atom[c]], h0_at(i, c));
         }
-        gsync<T>();
-        if (act)   // Y = H C
-            col_product(n, n, A, 1, LD, C + j * LD, 1, [&](int i, double v) { Y[j * LD + i] = v; });
-        gsync<T>();
-        if (act)   // A = C^T Y
-            col_product(n, n, C, LD, 1, Y + j * LD, 1, [&](int i, double v) { A[j * LD + i] = v; });
-        gsync<T>();
-        if (act) {   // aufbau occupation from the diagonal
-            const double ajj = A[j * LD + j];
-            diag[j] = ajj;
-            const long long kj = order_key(ajj);
-            int rank = 0;
-            for (int i = 0; i < n; ++i) {
-                const long long ki = order_key(A[i * LD + i]);
-                rank += (ki < kj) || (ki == kj && i < j);
-            }
-            occf[j] = rank < nocc;
-            if (rank < nocc) occ_list[rank] = j;
-        }
-        gsync<T>();
+        g.sync();
+        flat<T, R>(j, nn, n, LD, 1, [&](int e) { return A + (e % n); }, [&](int e) { return C + (e / n) * LD; },
+                   [&](int e, double v) { Y[(e / n) * LD + e % n] = v; });
+        g.sync();
+        flat<T, R>(j, n, n, 1, 1, [&](int e) { return C + e * LD; }, [&](int e) { return Y + e * LD; },
+                   [&](int e, double v) { diag[e] = v; });
+        g.sync();
+        rank_occupation();
+        g.sync();
+        // occupied-virtual block of C^T H C (entry e: virtual index e % nv, occupied e / nv)
+        bool small = true;
         float kmax = 0.0f;
-        if (act) {   // occupied-virtual generator, column j, into Y (FP32: it only steers)
-            const int oj = occf[j];
-            const double ajj = A[j * LD + j];
-            bool small = true;
-            for (int k = 0; k < n; ++k) {
-                double kv = 0.0;
-                if (occf[k] != oj) {
-                    const double akj = A[j * LD + k];
-                    if (!abs_lt(akj, G_EIG_TOL)) small = false;
-                    float kf = (float)akj / (float)(ajj - A[k * LD + k]);
-                    if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;
-                    kv = (double)kf;
-                    kmax = fmaxf(kmax, fabsf(kf));
-                }
-                Y[j * LD + k] = kv;
-            }
-            eok[j] = small;
-        }
+        flat<T, R>(j, nocc * nv, n, 1, 1, [&](int e) { return C + virt_list[e % nv] * LD; },
+                   [&](int e) { return Y + occ_list[e / nv] * LD; }, [&](int e, double v) {
+                       const int vi = virt_list[e % nv], oi = occ_list[e / nv];
+                       A[oi * LD + vi] = v;
+                       A[vi * LD + oi] = v;
+                       if (!abs_lt(v, G_EIG_TOL)) small = false;
+                       float kf = (float)v / (float)(diag[oi] - diag[vi]);
+                       if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
+                       kmax = fmaxf(kmax, fabsf(kf));
+                       Kc[e] = (double)kf;   // K(v, o) at [o][v]
+                   });
+        const bool eok = g.all(small);
         const bool cold_first = !a.have_warm && it == 1;
-        const bool perturb = gall<T>(!act || (kmax < G_KMAX_PERT && !cold_first));
+        const bool perturb = g.all(kmax < G_KMAX_PERT && !cold_first);
         if (perturb) {
-            if (act)   // V = I + K + K^2 / 2, column j, into A
-                col_product(n, n, Y, 1, LD, Y + j * LD, 1, [&](int i, double v) {
-                    A[j * LD + i] = fma(0.5, v, Y[j * LD + i] + (i == j ? 1.0 : 0.0));
-                });
-            gsync<T>();
-            if (act)   // C V into Y
-                col_product(n, n, C, 1, LD, A + j * LD, 1, [&](int i, double v) { Y[j * LD + i] = v; });
-            gsync<T>();
-            if (act)
-                for (int i = 0; i < n; ++i) C[j * LD + i] = Y[j * LD + i];
-            gsync<T>();
+            // V = I + K + K^2/2 into A: K(v, o) = Kc[o][v], K(o, v) = -Kc[o][v];
+            // (K^2)(o1, o2) = -sum_v Kc[o1][v] Kc[o2][v], (K^2)(v1, v2) = -sum_o Kc[o][v1] Kc[o][v2]
+            flat<T, R>(j, nocc * nocc, nv, 1, 1, [&](int e) { return Kc + (e % nocc) * nv; },
+                       [&](int e) { return Kc + (e / nocc) * nv; }, [&](int e, double v) {
+                           const int o1 = e % nocc, o2 = e / nocc;
+                           A[occ_list[o2] * LD + occ_list[o1]] = fma(-0.5, v, o1 == o2 ? 1.0 : 0.0);
+                       });
+            flat<T, R>(j, nv * nv, nocc, nv, nv, [&](int e) { return Kc + (e % nv); },
+                       [&](int e) { return Kc + (e / nv); }, [&](int e, double v) {
+                           const int v1 = e % nv, v2 = e / nv;
+                           A[virt_list[v2] * LD + virt_list[v1]] = fma(-0.5, v, v1 == v2 ? 1.0 : 0.0);
+                       });
+            for (int e = j; e < nocc * nv; e += T) {
+                const int vi = virt_list[e % nv], oi = occ_list[e / nv];
+                const double k = Kc[e];
+                A[oi * LD + vi] = k;    // V(v, o) = K(v, o)
+                A[vi * LD + oi] = -k;   // V(o, v) = K(o, v)
+            }
+            g.sync();
+            flat<T, R>(j, nn, n, LD, 1, [&](int e) { return C + (e % n); }, [&](int e) { return A + (e / n) * LD; },
+                       [&](int e, double v) { Y[(e / n) * LD + e % n] = v; });
+            g.sync();
+            double *t = C;
+            C = Y;
+            Y = t;
         } else {
+            // the rest of C^T H C: the occupied and virtual diagonal blocks
+            flat<T, R>(j, nocc * nocc, n, 1, 1, [&](int e) { return C + occ_list[e % nocc] * LD; },
+                       [&](int e) { return Y + occ_list[e / nocc] * LD; },
+                       [&](int e, double v) { A[occ_list[e / nocc] * LD + occ_list[e % nocc]] = v; });
+            flat<T, R>(j, nv * nv, n, 1, 1, [&](int e) { return C + virt_list[e % nv] * LD; },
+                       [&](int e) { return Y + virt_list[e / nv] * LD; },
+                       [&](int e, double v) { A[virt_list[e / nv] * LD + virt_list[e % nv]] = v; });
+            g.sync();
             const int sweeps = cold_first ? G_MAX_SWEEPS : 1;
             for (int sweep = 0; sweep < G_MAX_SWEEPS; ++sweep) {
-                bool small = true;
-                if (act)
-                    for (int i = 0; i < n; ++i)
-                        if (i != j && !abs_lt(A[j * LD + i], G_JACOBI_TOL)) small = false;
-                if (gall<T>(small)) break;
+                bool off_small = true;
+                for (int e = j; e < nn; e += T) {
+                    const int c = e / n, i = e - c * n;
+                    if (i != c && !abs_lt(A[c * LD + i], G_JACOBI_TOL)) off_small = false;
+                }
+                if (g.all(off_small)) break;
                 if (sweep >= sweeps) break;
                 if (sweep == G_MAX_SWEEPS - 1) {
-                    if (act && !small) atomicOr(&fl[0], ERRBIT_TIMEOUT);
+                    if (j == 0) atomicOr(&fl[0], ERRBIT_TIMEOUT);
                     break;
                 }
                 for (int rd = 0; rd < n - 1; ++rd) {
-                    int p = 0, qq = 0;
-                    double cp = 0.0, cq = 0.0;
-                    if (act) {
-                        int slot;
-                        const int pj = g_partner(j, rd, n, slot);
-                        p = min(j, pj);
-                        qq = max(j, pj);
+                    if (j < n / 2) {   // the rotations of this round
+                        int p, qq;
+                        g_pair(j, rd, n, p, qq);
                         double c, s;
                         g_jacobi_cs(A[p * LD + p], A[qq * LD + qq], A[qq * LD + p], c, s);
-                        cp = (j == p) ? c : s;     // new column j = cp col p + cq col q
-                        cq = (j == p) ? -s : c;
-                        if (j == p) { cs[2 * slot] = c; cs[2 * slot + 1] = s; }
+                        pp[j] = p;
+                        pq[j] = qq;
+                        cs[2 * j] = c;
+                        cs[2 * j + 1] = s;
                     }
-                    // columns in blocks of CH rows: read the pair's block, wait, write column j's
-                    for (int i0 = 0; i0 < n; i0 += CH) {
-                        double na[CH], nc[CH];
-                        if (act) {
-#pragma unroll
-                            for (int t = 0; t < CH; ++t) {
-                                const int i = min(i0 + t, n - 1);
-                                na[t] = fma(cp, A[p * LD + i], cq * A[qq * LD + i]);
-                                nc[t] = fma(cp, C[p * LD + i], cq * C[qq * LD + i]);
-                            }
-                        }
-                        gsync<T>();
-                        if (act) {
-#pragma unroll
-                            for (int t = 0; t < CH; ++t) {
-                                if (i0 + t < n) {
-                                    A[j * LD + i0 + t] = na[t];
-                                    C[j * LD + i0 + t] = nc[t];
-                                }
-                            }
-                        }
+                    g.sync();
+                    for (int e = j; e < n * (n / 2); e += T) {   // columns p, q of A and C, row i
+                        const int k = e / n, i = e - k * n;
+                        const int p = pp[k], qq = pq[k];
+                        const double c = cs[2 * k], s = cs[2 * k + 1];
+                        const double ap = A[p * LD + i], aq = A[qq * LD + i];
+                        A[p * LD + i] = fma(c, ap, -s * aq);
+                        A[qq * LD + i] = fma(s, ap, c * aq);
+                        const double cp = C[p * LD + i], cq = C[qq * LD + i];
+                        C[p * LD + i] = fma(c, cp, -s * cq);
+                        C[qq * LD + i] = fma(s, cp, c * cq);
                     }
-                    if (act) {   // rows of column j, for every pair of the round
-                        for (int k = 0; k < n / 2; ++k) {
-                            int pk, qk;
-                            g_pair(k, rd, n, pk, qk);
-                            const double ck = cs[2 * k], sk_ = cs[2 * k + 1];
-                            const double x = A[j * LD + pk], y = A[j * LD + qk];
-                            A[j * LD + pk] = fma(ck, x, -sk_ * y);
-                            A[j * LD + qk] = fma(sk_, x, ck * y);
-                        }
+                    g.sync();
+                    for (int e = j; e < n * (n / 2); e += T) {   // rows p, q of A, column c
+                        const int k = e / n, c = e - k * n;
+                        const int p = pp[k], qq = pq[k];
+                        const double ck = cs[2 * k], sk_ = cs[2 * k + 1];
+                        const double x = A[c * LD + p], y = A[c * LD + qq];
+                        A[c * LD + p] = fma(ck, x, -sk_ * y);
+                        A[c * LD + qq] = fma(sk_, x, ck * y);
                     }
-                    gsync<T>();
+                    g.sync();
                 }
             }
-            if (act) {
-                const double ajj = A[j * LD + j];
-                diag[j] = ajj;
-                const long long kj = order_key(ajj);
-                int rank = 0;
-                for (int i = 0; i < n; ++i) {
-                    const long long ki = order_key(A[i * LD + i]);
-                    rank += (ki < kj) || (ki == kj && i < j);
-                }
-                occf[j] = rank < nocc;
-                if (rank < nocc) occ_list[rank] = j;
-            }
-            gsync<T>();
+            if (j < n) diag[j] = A[j * LD + j];
+            g.sync();
+            rank_occupation();
+            g.sync();
         }
-        if (act) {   // Mulliken population of orbital j: (P S)_jj, P = 2 C_occ C_occ^T
+        // Mulliken populations: (P S)_ii = 2 sum_o C(i, o) (S C)(i, o); S C_occ into A
+        for (int e = j; e < n * nocc; e += T) {
+            const int o = e / n, i = e - o * n;
+            const double *co = C + occ_list[o] * LD;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc = fma(s_at(i, k), co[k], acc);
+            A[o * LD + i] = acc;
+        }
+        g.sync();
+        if (j < n) {
             double qo = 0.0;
-            col_product_occ(n, nocc, C, LD, occ_list, j, [&](int i, double v) { qo = fma(2.0 * v, s_ij(i), qo); });
-            red[j] = qo;
+            for (int o = 0; o < nocc; ++o) qo = fma(C[occ_list[o] * LD + j], A[o * LD + j], qo);
+            red[j] = 2.0 * qo;
         }
-        gsync<T>();
-        const int hs = (it - 1) % GNHIST;
+        g.sync();
+        const int NH = a.hist;   // ring of the last NH iterates
+        const int hs = (it - 1) % NH;
         if (j < nat) {
             double qa = 0.0;
             for (int o = atom_off[j]; o < atom_off[j + 1]; ++o) qa += red[o];
@@ -538,59 +544,90 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             hq[hs * AM + j] = q[j];
             hf[hs * AM + j] = qa - q[j];
         }
-        gsync<T>();
-        bool conv = true;
+        g.sync();
+        bool conv = eok;
         for (int at = 0; at < nat; ++at)
             if (!abs_lt(hf[hs * AM + at], a.scc_tol)) conv = false;
-        for (int c = 0; c < n; ++c) conv = conv && eok[c];
+        const int h = min(it, NH);
+        if (!conv && j == 0) {
+            // Anderson coefficients over the h - 1 previous iterates: normal equations in FP32 with
+            // a small diagonal shift, solved by Cholesky (they only steer the iteration)
+            float Mx[GNHIST - 1][GNHIST - 1], bv[GNHIST - 1], x[GNHIST - 1];
+            const int m = h - 1;
+            for (int u = 0; u < m; ++u) {
+                const int hu = (hs + NH - 1 - u) % NH;
+                float b = 0.f;
+                for (int w = 0; w <= u; ++w) {
+                    const int hw = (hs + NH - 1 - w) % NH;
+                    float s = 0.f;
+                    for (int at = 0; at < nat; ++at) {
+                        const float du = (float)(hf[hu * AM + at] - hf[hs * AM + at]);
+                        const float dw = (float)(hf[hw * AM + at] - hf[hs * AM + at]);
+                        s = fmaf(du, dw, s);
+                    }
+                    Mx[u][w] = s;
+                }
+                for (int at = 0; at < nat; ++at)
+                    b = fmaf(-(float)(hf[hu * AM + at] - hf[hs * AM + at]), (float)hf[hs * AM + at], b);
+                bv[u] = b;
+            }
+            float dmax = 0.f;
+            for (int u = 0; u < m; ++u) dmax = fmaxf(dmax, Mx[u][u]);
+            bool ok = m > 0 && dmax > 0.f;
+            for (int u = 0; u < m && ok; ++u) {   // lower Cholesky factor of M + 1e-6 max(diag) I, in place
+                for (int w = 0; w <= u && ok; ++w) {
+                    float s = Mx[u][w] + (u == w ? 1e-6f * dmax : 0.f);
+                    for (int l = 0; l < w; ++l) s -= Mx[u][l] * Mx[w][l];
+                    if (u == w) {
+                        if (!(s > 0.f)) ok = false; else Mx[u][u] = sqrtf(s);
+                    } else {
+                        Mx[u][w] = s / Mx[w][w];
+                    }
+                }
+            }
+            if (ok) {
+                for (int u = 0; u < m; ++u) {
+                    float s = bv[u];
+                    for (int l = 0; l < u; ++l) s -= Mx[u][l] * x[l];
+                    x[u] = s / Mx[u][u];
+                }
+                for (int u = m - 1; u >= 0; --u) {
+                    float s = x[u];
+                    for (int l = u + 1; l < m; ++l) s -= Mx[l][u] * x[l];
+                    x[u] = s / Mx[u][u];
+                }
+                for (int u = 0; u < m; ++u)
+                    if (!(fabsf(x[u]) < 50.f)) ok = false;
+            }
+            for (int u = 0; u < GNHIST - 1; ++u) th[u] = (ok && u < m) ? (double)x[u] : 0.0;
+        }
+        g.sync();
         if (j < nat) {
             if (conv) {
                 q[j] = qout[j];
-            } else {   // Anderson mixing over the last GNHIST iterates (coefficients in FP32)
-                float th1 = 0.0f, th2 = 0.0f;
-                const int h = min(it, GNHIST);
-                const int h1 = (hs + GNHIST - 1) % GNHIST, h2 = (hs + GNHIST - 2) % GNHIST;
-                if (h >= 2) {
-                    float a11 = 0.f, a12 = 0.f, a22 = 0.f, b1 = 0.f, b2 = 0.f;
-                    for (int at = 0; at < nat; ++at) {
-                        const float f0 = (float)hf[hs * AM + at];
-                        const float d1 = (float)(hf[h1 * AM + at] - hf[hs * AM + at]);
-                        const float d2 = h >= 3 ? (float)(hf[h2 * AM + at] - hf[hs * AM + at]) : 0.f;
-                        a11 = fmaf(d1, d1, a11);
-                        a12 = fmaf(d1, d2, a12);
-                        a22 = fmaf(d2, d2, a22);
-                        b1 = fmaf(-d1, f0, b1);
-                        b2 = fmaf(-d2, f0, b2);
-                    }
-                    const float det = a11 * a22 - a12 * a12;
-                    if (h >= 3 && det > 1e-6f * a11 * a22 && det > 0.f) {
-                        th1 = (b1 * a22 - b2 * a12) / det;
-                        th2 = (a11 * b2 - a12 * b1) / det;
-                    } else if (a11 > 0.f) {
-                        th1 = b1 / a11;
-                    }
-                    if (!(fabsf(th1) < 50.f) || !(fabsf(th2) < 50.f)) { th1 = 0.f; th2 = 0.f; }
-                }
-                const double t1 = th1, t2 = th2;
+            } else {
                 const double q0 = hq[hs * AM + j], f0 = hf[hs * AM + j];
                 double qb = q0, fb = f0;
-                if (h >= 2) { qb = fma(t1, hq[h1 * AM + j] - q0, qb); fb = fma(t1, hf[h1 * AM + j] - f0, fb); }
-                if (h >= 3) { qb = fma(t2, hq[h2 * AM + j] - q0, qb); fb = fma(t2, hf[h2 * AM + j] - f0, fb); }
+                for (int u = 0; u < h - 1; ++u) {
+                    const int hu = (hs + NH - 1 - u) % NH;
+                    qb = fma(th[u], hq[hu * AM + j] - q0, qb);
+                    fb = fma(th[u], hf[hu * AM + j] - f0, fb);
+                }
                 q[j] = fma(a.beta, fb, qb);
             }
         }
-        gsync<T>();   // the next iteration's shifts read every atom's charge
+        g.sync();   // the next iteration's shifts read every atom's charge
         if (conv) {   // the same value in every thread: all leave together
             if (j == 0) fl[2] = it;
             break;
         }
     }
-    gsync<T>();
+    g.sync();
     if (j == 0 && it > a.max_iter) {
         atomicOr(&fl[0], ERRBIT_SCC_NOCONV);
         fl[2] = a.max_iter;
     }
-    gsync<T>();
+    g.sync();
 
     if (disp) {   // displaced copy: only the dipole of the converged charges
         if (j == 0) {
@@ -602,16 +639,16 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             a.M_disp[(long long)(a.fd_central ? 6 : 3) * a0 + kd] = fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
             if (fl[0]) atomicOr(a.status, (unsigned)fl[0]);
         }
-        gsync<T>();
+        g.sync();
         return;
     }
 
     // ---------------------------------------------------------------- energy, forces, dipole
     {   // eigenvectors for the next warm start
         double *cwo = a.Cwarm + coff;
-        for (int e2 = j; e2 < n * n; e2 += T) {
-            const int c = e2 / n;
-            cwo[e2] = C[c * LD + (e2 - c * n)];
+        for (int e = j; e < nn; e += T) {
+            const int c = e / n;
+            cwo[e] = C[c * LD + (e - c * n)];
         }
     }
     if (j < nat) {
@@ -620,24 +657,27 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
         shift[j] = sh;
     }
     // W = 2 C_occ (C_occ^T H C_occ) C_occ^T with the H of the last iteration and the whole occupied
-    // block; buffers: A <- H; Y <- T = H C_occ; A <- C_occ; C <- Aoo = C_occ^T T;
-    // Y <- t = 2 Aoo C_occ^T; C <- P (band energy with H0); SH <- W = C_occ t; Y <- pair gradients
-    if (act) {
-        const double shj = shl[orb_atom[j]];
-        for (int i = 0; i < n; ++i) A[j * LD + i] = fma(0.5 * s_ij(i), shl[orb_atom[i]] + shj, h0_ij(i));
+    // block. Buffers: A <- H; Y <- T = H C_occ; A <- C_occ; C <- Aoo = C_occ^T T;
+    // Y <- t = 2 Aoo C_occ^T; C <- P; SH <- W = C_occ t; Y <- pair gradients
+    for (int e = j; e < nn; e += T) {
+        const int c = e / n, i = e - c * n;
+        A[c * LD + i] = fma(0.5 * s_at(i, c), shl[orb_atom[i]] + shl[orb_atom[c]], h0_at(i, c));
     }
-    gsync<T>();
-    if (j < nocc)
-        col_product(n, n, A, 1, LD, C + occ_list[j] * LD, 1, [&](int i, double v) { Y[j * LD + i] = v; });
-    gsync<T>();
-    if (j < nocc)
-        for (int i = 0; i < n; ++i) A[j * LD + i] = C[occ_list[j] * LD + i];
-    gsync<T>();
-    if (j < nocc)
-        col_product(nocc, n, A, LD, 1, Y + j * LD, 1, [&](int i, double v) { C[j * LD + i] = v; });
-    gsync<T>();
-    if (act)
-        col_product(nocc, nocc, C, 1, LD, A + j, LD, [&](int i, double v) { Y[j * LD + i] = 2.0 * v; });
+    g.sync();
+    flat<T, R>(j, n * nocc, n, LD, 1, [&](int e) { return A + (e % n); },
+               [&](int e) { return C + occ_list[e / n] * LD; }, [&](int e, double v) { Y[(e / n) * LD + e % n] = v; });
+    g.sync();
+    for (int e = j; e < n * nocc; e += T) {
+        const int o = e / n, i = e - o * n;
+        A[o * LD + i] = C[occ_list[o] * LD + i];
+    }
+    g.sync();
+    flat<T, R>(j, nocc * nocc, n, 1, 1, [&](int e) { return A + (e % nocc) * LD; },
+               [&](int e) { return Y + (e / nocc) * LD; }, [&](int e, double v) { C[(e / nocc) * LD + e % nocc] = v; });
+    g.sync();
+    // t(o, i) = 2 sum_o2 Aoo(o, o2) C_occ(i, o2) into Y[i * LD + o]
+    flat<T, R>(j, nocc * n, nocc, LD, LD, [&](int e) { return C + (e % nocc); }, [&](int e) { return A + (e / nocc); },
+               [&](int e, double v) { Y[(e / nocc) * LD + e % nocc] = 2.0 * v; });
     if (j == 0 && nocc < n) {   // HOMO-LUMO gap of the last iteration
         double homo = -1e300, lumo = 1e300;
         for (int c = 0; c < n; ++c) {
@@ -645,19 +685,21 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
         }
         if (!(lumo - homo > G_MIN_GAP)) atomicOr(&fl[0], ERRBIT_ZERO_GAP);
     }
-    gsync<T>();
-    if (act) {
+    g.sync();
+    // P = 2 C_occ C_occ^T into C
+    flat<T, R>(j, nn, nocc, LD, LD, [&](int e) { return A + (e % n); }, [&](int e) { return A + (e / n); },
+               [&](int e, double v) { C[(e / n) * LD + e % n] = 2.0 * v; });
+    g.sync();
+    if (j < n) {   // band energy, per column in a fixed order
         double eb = 0.0;
-        col_product(n, nocc, A, 1, LD, A + j, LD, [&](int i, double v) {
-            C[j * LD + i] = 2.0 * v;
-            eb = fma(2.0 * v, h0_ij(i), eb);
-        });
+        for (int i = 0; i < n; ++i) eb = fma(C[j * LD + i], h0_at(i, j), eb);
         red[j] = eb;
     }
-    gsync<T>();
-    if (act)
-        col_product(n, nocc, A, 1, LD, Y + j * LD, 1, [&](int i, double v) { SH[j * LD + i] = v; });
-    gsync<T>();
+    g.sync();
+    // W(i, c) = sum_o C_occ(i, o) t(o, c) into SH
+    flat<T, R>(j, nn, nocc, LD, 1, [&](int e) { return A + (e % n); }, [&](int e) { return Y + (e / n) * LD; },
+               [&](int e, double v) { SH[(e / n) * LD + e % n] = v; });
+    g.sync();
     const double *P = C, *W = SH;
     double *gp = Y, *ep = Y + 3 * L.pmax;
     for (int pi = j; pi < npair; pi += T) {
@@ -746,7 +788,7 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
         for (int k = 0; k < 3; ++k) gp[3 * pi + k] = gk[k] + (qq + derep) * e[k];
         ep[pi] = erep;
     }
-    gsync<T>();
+    g.sync();
     if (j < nat) {
         double f[3] = {0.0, 0.0, 0.0};
         for (int pi = 0; pi < npair; ++pi) {
@@ -784,22 +826,24 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
         a.iters[cell] = fl[2];
         if (fl[0]) atomicOr(a.status, (unsigned)fl[0]);
     }
-    gsync<T>();
+    g.sync();
 }
 
-// Persistent grid over a queue of work units: units [0, n_big) are one large item each (whole
-// block), the rest take two small items (one per warp).
-__global__ void __launch_bounds__(GTPB) k_dftb_generic(const DevSK *__restrict__ skp, const DftbArgs a,
-                                                       const int2 *__restrict__ items, int n_big, int n_small,
-                                                       unsigned *__restrict__ queue, int nmax_b, int amax_b,
-                                                       int nmax_s, int amax_s) {
+// Persistent grid over a queue of work units: units [0, n_big) are one large item each (the whole
+// block), the rest take two small items (one per half of the block).
+template <int R>
+__global__ void __launch_bounds__(BT, 2) k_dftb_generic(const DevSK *__restrict__ skp, const DftbArgs a,
+                                                     const int2 *__restrict__ items, int n_big, int n_small,
+                                                     unsigned *__restrict__ queue, int nmax_b, int amax_b,
+                                                     int nmax_s, int amax_s) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int next;
+    __shared__ int vote[2][2];
     const DevSK &sk = *skp;
     const GLayout Lb = g_layout(nmax_b, amax_b);
     const GLayout Ls = g_layout(nmax_s, amax_s);
     const int n_units = n_big + (n_small + 1) / 2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int half = threadIdx.x / TS;
     for (;;) {
         if (threadIdx.x == 0) next = (int)atomicAdd(queue, 1u);
         __syncthreads();
@@ -808,16 +852,25 @@ __global__ void __launch_bounds__(GTPB) k_dftb_generic(const DevSK *__restrict__
         if (w >= n_units) break;
         if (w < n_big) {
             const int2 it = items[w];
-            g_molecule<GTPB>(sk, a, Lb, smem, it.x, it.y, threadIdx.x);
+            const Grp<TB> g{(int)threadIdx.x, 0, nullptr};
+            g_molecule<TB, R>(sk, a, Lb, smem, it.x, it.y, g);
         } else {
-            const int s = 2 * (w - n_big) + warp;
+            const int s = 2 * (w - n_big) + half;
             if (s < n_small) {
                 const int2 it = items[n_big + s];
-                g_molecule<32>(sk, a, Ls, smem + warp * Ls.total, it.x, it.y, lane);
+                const Grp<TS> g{(int)threadIdx.x - half * TS, 1 + half, vote[half]};
+                g_molecule<TS, R>(sk, a, Ls, smem + half * Ls.total, it.x, it.y, g);
             }
         }
         __syncthreads();
     }
+}
+
+template <int R>
+cudaError_t set_attr(size_t smem, int &blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_dftb_generic<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_dftb_generic<R>, BT, smem);
+    return e;
 }
 
 }  // namespace
@@ -855,16 +908,19 @@ void plan_dftb_generic(const int *cell_offset, const int *species, const int *no
         for (int k = 0; k < n_disp_per_atom * nat; ++k) disp_items.push_back(make_int2(c, k));
     }
     p.smem = dftb_generic_smem(p.nmax_b, p.amax_b, p.nmax_s, p.amax_s);
+    p.r_entries = 4;
+    p.blocks_per_sm = 0;
 }
 
 cudaError_t prepare_dftb_generic(GenericPlan &p) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p.n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dftb_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p.blocks_per_sm, k_dftb_generic, GTPB, p.smem);
+    int b2 = 0, b4 = 0;
+    if (e == cudaSuccess) e = set_attr<2>(p.smem, b2);
+    if (e == cudaSuccess) e = set_attr<4>(p.smem, b4);
+    p.max_blocks_per_sm = std::max(1, std::min(b2, b4));
+    if (p.blocks_per_sm <= 0 || p.blocks_per_sm > p.max_blocks_per_sm) p.blocks_per_sm = p.max_blocks_per_sm;
     return e;
 }
 
@@ -879,7 +935,11 @@ cudaError_t launch_dftb_generic(const DevSK *sk, const DftbArgs &a, const Generi
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     const int grid = std::min(units, p.n_sm * std::max(p.blocks_per_sm, 1));
-    k_dftb_generic<<<grid, GTPB, p.smem, st>>>(sk, a, items, nb, ns, queue, p.nmax_b, p.amax_b, p.nmax_s,
-                                               p.amax_s);
+    if (p.r_entries == 2)
+        k_dftb_generic<2><<<grid, BT, p.smem, st>>>(sk, a, items, nb, ns, queue, p.nmax_b, p.amax_b, p.nmax_s,
+                                                   p.amax_s);
+    else
+        k_dftb_generic<4><<<grid, BT, p.smem, st>>>(sk, a, items, nb, ns, queue, p.nmax_b, p.amax_b, p.nmax_s,
+                                                   p.amax_s);
     return cudaGetLastError();
 }

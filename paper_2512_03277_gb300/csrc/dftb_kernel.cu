@@ -128,7 +128,7 @@ __device__ __forceinline__ void jacobi_cs(double app, double aqq, double apq, do
 }
 
 template <int NAT, int NORB>
-__global__ void __launch_bounds__(64) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a) {
+__global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a) {
     const DevSK &sk = *skp;
     using SM = MolShared<NAT, NORB>;
     constexpr int LD = SM::LD;
@@ -861,15 +861,22 @@ cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_dftb_water(const DevSK *sk, const DftbArgs &a, cudaStream_t st) {
+// warps per block: 2, 4 or 8 (5 waters per warp); every choice gives bitwise identical results.
+cudaError_t launch_dftb_water(const DevSK *sk, const DftbArgs &a, cudaStream_t st, int warps) {
     constexpr int NAT = 3, NORB = 6;
     using SM = MolShared<NAT, NORB>;
-    const int threads = 64;
-    const int per_block = (threads / 32) * (32 / NORB);
+    const int threads = 32 * warps;
+    const int per_block = warps * (32 / NORB);
     const long long rows = (long long)a.n_cells * (a.n_disp > 0 ? a.n_disp : 1);
     const int blocks = (int)((rows + per_block - 1) / per_block);
-    const size_t smem = sizeof(SM) * (threads / 32) * (32 / NORB);
+    const size_t smem = sizeof(SM) * per_block;
     if (a.n_cells <= 0) return cudaSuccess;
     dftb_kernel<NAT, NORB><<<blocks, threads, smem, st>>>(sk, a);
     return cudaGetLastError();
+}
+
+cudaError_t prepare_dftb_water(int max_warps) {
+    using SM = MolShared<3, 6>;
+    return cudaFuncSetAttribute(dftb_kernel<3, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(SM) * max_warps * 5));
 }
