@@ -647,6 +647,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     c->n_disp = 3 * disp_per_atom;
     if (c->n_disp) AL(c->d_Mdisp, (size_t)disp_per_atom * NA);
     if (c->opt.charge_model == CAVMD_CHARGE_BORN_MLP) {
+        CK(prepare_mlp_forward());
         AL(c->d_Q, NA);
         AL(c->d_mlpX, (size_t)NA * CAVMD_MLP_NFEAT);
         AL(c->d_mlpR, (size_t)NA * 9);

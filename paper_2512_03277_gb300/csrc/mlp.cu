@@ -187,6 +187,112 @@ __global__ void __launch_bounds__(NH) k_forward(int n, const float *__restrict__
     }
 }
 
+// Inference forward for the time step: the same arithmetic as k_forward (every output summed from
+// its bias over the inputs in increasing order, so the results are bitwise equal), mapped for
+// throughput. A persistent block keeps the BF16 weights in shared memory (transposed, input-major),
+// takes tiles of TA = 32 atoms, and every thread computes a 4-atom x 4-unit register tile per layer:
+// per input it loads one float4 of activations (feature-major layout) and four BF16 weights, and
+// issues 16 FMAs. Weights widen to FP32 by a 16-bit shift.
+constexpr int TA = 32;
+constexpr int FT = 256;
+constexpr size_t FWD_SMEM = (size_t)NF * NH * 2 + (size_t)NH * NH * 2 + (size_t)NO * NH * 4 + (2 * NH + 16) * 4 +
+                            (size_t)NF * TA * 4 + 2 * (size_t)NH * TA * 4 + (size_t)TA * NO * 4;
+
+__device__ __forceinline__ void bf16x4(const unsigned short *p, float w[4]) {
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    w[0] = __uint_as_float(v.x << 16);
+    w[1] = __uint_as_float(v.x & 0xffff0000u);
+    w[2] = __uint_as_float(v.y << 16);
+    w[3] = __uint_as_float(v.y & 0xffff0000u);
+}
+
+// one dense layer of the tile: out[u][a] = silu(b[u] + sum_k W[u][k] in[k][a]) for 128 units u
+template <int K>
+__device__ __forceinline__ void tile_layer(const unsigned short *WT, const float *b, const float *in, float *out) {
+    const int ag = threadIdx.x & 7, hg = threadIdx.x >> 3;
+    float acc[4][4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const float bb = b[4 * hg + h];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][h] = bb;
+    }
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) {
+        const float4 x = *reinterpret_cast<const float4 *>(in + k * TA + 4 * ag);
+        float w[4];
+        bf16x4(WT + k * NH + 4 * hg, w);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            acc[0][h] = fmaf(w[h], x.x, acc[0][h]);
+            acc[1][h] = fmaf(w[h], x.y, acc[1][h]);
+            acc[2][h] = fmaf(w[h], x.z, acc[2][h]);
+            acc[3][h] = fmaf(w[h], x.w, acc[3][h]);
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+        *reinterpret_cast<float4 *>(out + (4 * hg + h) * TA + 4 * ag) =
+            make_float4(silu(acc[0][h]), silu(acc[1][h]), silu(acc[2][h]), silu(acc[3][h]));
+}
+
+__global__ void __launch_bounds__(FT, 2) k_forward_tiled(int n, const float *__restrict__ X,
+                                                         const float *__restrict__ R,
+                                                         const __nv_bfloat16 *__restrict__ w,
+                                                         float *__restrict__ Zl) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned short *W1T = reinterpret_cast<unsigned short *>(sm);          // [NF][NH]
+    unsigned short *W2T = W1T + NF * NH;                                    // [NH][NH]
+    float *W3 = reinterpret_cast<float *>(W2T + NH * NH);                   // [NO][NH]
+    float *b1 = W3 + NO * NH, *b2 = b1 + NH, *b3 = b2 + NH;                 // b3: [16]
+    float *xT = b3 + 16;                                                    // [NF][TA]
+    float *h1T = xT + NF * TA, *h2T = h1T + NH * TA;                        // [NH][TA]
+    float *ys = h2T + NH * TA;                                              // [TA][NO]
+    const unsigned short *wr = reinterpret_cast<const unsigned short *>(w);
+    const int t = threadIdx.x;
+    for (int e = t; e < NH * NF; e += FT) W1T[(e % NF) * NH + e / NF] = wr[OFF_W1 + e];
+    for (int e = t; e < NH * NH; e += FT) W2T[(e % NH) * NH + e / NH] = wr[OFF_W2 + e];
+    for (int e = t; e < NO * NH; e += FT) W3[e] = wv(w, OFF_W3 + e);
+    for (int e = t; e < NH; e += FT) {
+        b1[e] = wv(w, OFF_B1 + e);
+        b2[e] = wv(w, OFF_B2 + e);
+    }
+    if (t < 16) b3[t] = t < NO ? wv(w, OFF_B3 + t) : 0.0f;
+    const int n_tiles = (n + TA - 1) / TA;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int t0 = tile * TA;
+        __syncthreads();   // weights ready; the previous tile is done with xT and ys
+        for (int e = t; e < TA * NF; e += FT) {
+            const int a = e / NF, i = e - a * NF;
+            xT[i * TA + a] = (t0 + a < n) ? X[(size_t)(t0 + a) * NF + i] : 0.0f;
+        }
+        __syncthreads();
+        tile_layer<NF>(W1T, b1, xT, h1T);
+        __syncthreads();
+        tile_layer<NH>(W2T, b2, h1T, h2T);
+        __syncthreads();
+        for (int e = t; e < TA * NO; e += FT) {
+            const int a = e % TA, o = e / TA;
+            float y = b3[o];
+            for (int v = 0; v < NH; ++v) y = fmaf(W3[o * NH + v], h2T[v * TA + a], y);
+            ys[a * NO + o] = y;
+        }
+        __syncthreads();
+        if (t < TA && t0 + t < n) {
+            const float *Rj = R + (size_t)(t0 + t) * 9;
+            const float *yt = ys + t * NO;
+            // Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
+            for (int i = 0; i < 3; ++i)
+                for (int k = 0; k < 3; ++k) {
+                    float s = 0.0f;
+                    for (int aa = 0; aa < 3; ++aa)
+                        for (int bb = 0; bb < 3; ++bb) s = fmaf(Rj[3 * aa + i] * yt[3 * aa + bb], Rj[3 * bb + k], s);
+                    Zl[(size_t)(t0 + t) * 9 + 3 * i + k] = s;
+                }
+        }
+    }
+}
+
 // per cell: Z = Q I + Zl - mean; with Zref: squared-error partial and gy = R (gZ - mean gZ) R^T
 __global__ void k_cell_tensors(int n_cells, const int *__restrict__ off, const float *__restrict__ Zl,
                                const float *__restrict__ R, const double *__restrict__ Q,
@@ -399,10 +505,20 @@ cudaError_t launch_mlp_features(int n_cells, const int *off, const int *species,
     return cudaGetLastError();
 }
 
+cudaError_t prepare_mlp_forward() {
+    return cudaFuncSetAttribute(k_forward_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM);
+}
+
 cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, const void *w_bf16, float *Zl,
                                cudaStream_t st) {
-    k_forward<<<(n_atoms + TILE - 1) / TILE, NH, 0, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl,
-                                                          nullptr, nullptr, nullptr, nullptr);
+    if (n_atoms <= 0) return cudaSuccess;
+    int dev = 0, n_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int tiles = (n_atoms + TA - 1) / TA;
+    const int grid = std::min(tiles, 2 * n_sm);
+    k_forward_tiled<<<grid, FT, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl);
     return cudaGetLastError();
 }
 
@@ -514,6 +630,8 @@ int cavmd_mlp_create(cavmd_mlp **out, const float *params, int32_t n_params, int
     if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e)));
     e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, "cudaStreamCreate"));
+    e = prepare_mlp_forward();
+    if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, "cudaFuncSetAttribute (network forward)"));
     if ((rc = mlp_alloc(m, &m->master, NPAR)) || (rc = mlp_alloc(m, &m->m1, NPAR)) ||
         (rc = mlp_alloc(m, &m->m2, NPAR)) || (rc = mlp_alloc(m, &m->g, NPAR)) || (rc = mlp_alloc(m, &m->w, NPAR)) ||
         (rc = mlp_alloc(m, &m->loss, 1)) || (rc = mlp_alloc(m, &m->status, 1)))
