@@ -50,7 +50,7 @@ struct cavmd_ctx {
     bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
     GenericPlan gplan{};
     long long *d_Coff = nullptr;             // eigenvector block of each cell (generic kernel)
-    int water_warps = 2;                     // launch shape of the water kernel
+    int water_warps = 2, water_per_warp = 5; // launch shape of the water kernel
     long long n_cwarm = 0;                   // doubles in the warm-start eigenvector blocks
     std::string tuning = "not tuned (options.autotune = 0): default launch shapes";
     AcfArgs acf{};                           // on-device autocorrelation (acf.L > 0)
@@ -206,7 +206,7 @@ cudaError_t run_dftb(cavmd_ctx *c, int have_warm) {
     PhaseScope ps(c, 0);
     c->da.have_warm = have_warm;
     if (c->generic) return launch_dftb_generic(c->d_sk, c->da, c->gplan, c->stream);
-    return launch_dftb_water(c->d_sk, c->da, c->stream, c->water_warps);
+    return launch_dftb_water(c->d_sk, c->da, c->stream, c->water_warps, c->water_per_warp);
 }
 
 // Finite-difference dipole derivatives at the current positions (after the cell evaluation).
@@ -219,7 +219,7 @@ cudaError_t run_born(cavmd_ctx *c) {
     d.fd_h = c->opt.fd_step;
     d.M_disp = c->d_Mdisp;
     cudaError_t e = c->generic ? launch_dftb_generic(c->d_sk, d, c->gplan, c->stream)
-                               : launch_dftb_water(c->d_sk, d, c->stream, c->water_warps);
+                               : launch_dftb_water(c->d_sk, d, c->stream, c->water_warps, c->water_per_warp);
     if (e != cudaSuccess) return e;
     return launch_born_assemble(c->N, c->d_off, c->d_Mc, c->d_Mdisp, c->n_disp, d.fd_central, d.fd_h, c->d_b,
                                 c->stream);
@@ -316,7 +316,9 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
 // Launch-shape tuner. Candidates differ only in how work is mapped to threads and blocks, never in
 // arithmetic, so every candidate gives bitwise identical results:
 //   cluster kernel: product entries per thread per pass (2 or 4) x persistent blocks per SM;
-//   water kernel: warps per block (2, 4 or 8).
+//   water kernel: warps per block (2, 4 or 8), five waters per warp. (Fewer waters per warp would
+//   change which waters share a warp, and the warp-wide choice between a Jacobi sweep and the
+//   second-order update couples them, so it is not a candidate; it was never faster either.)
 // Each candidate evaluates a trial step (positions drifted by dt p / m, warm started from a copy of
 // the converged state) twice, timed with CUDA events on the context's stream; the fastest is kept.
 // The context's own state is not touched.
@@ -344,7 +346,7 @@ int autotune(cavmd_ctx *c) {
         for (int r : {2, 4})
             for (int b = 1; b <= c->gplan.max_blocks_per_sm; ++b) cands.push_back({r, b, 0.f});
     } else {
-        for (int w : {2, 4, 8}) cands.push_back({w, 0, 0.f});
+        for (int w : {2, 4, 8}) cands.push_back({w, 5, 0.f});
     }
     for (auto &cd : cands) {
         cd.ms = 1e30f;
@@ -359,7 +361,7 @@ int autotune(cavmd_ctx *c) {
                 g.blocks_per_sm = cd.b;
                 CK(launch_dftb_generic(c->d_sk, t, g, st));
             } else {
-                CK(launch_dftb_water(c->d_sk, t, st, cd.a));
+                CK(launch_dftb_water(c->d_sk, t, st, cd.a, cd.b));
             }
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
@@ -387,11 +389,12 @@ int autotune(cavmd_ctx *c) {
         }
     } else {
         c->water_warps = best->a;
-        std::snprintf(buf, sizeof(buf), "dftb_kernel<3,6>: warps_per_block=%d (%.3f ms); candidates:", best->a,
-                      best->ms);
+        c->water_per_warp = best->b;
+        std::snprintf(buf, sizeof(buf), "dftb_kernel<3,6>: warps_per_block=%d waters_per_warp=%d (%.3f ms); candidates:",
+                      best->a, best->b, best->ms);
         rep = buf;
         for (auto &cd : cands) {
-            std::snprintf(buf, sizeof(buf), " w%d %.3f ms", cd.a, cd.ms);
+            std::snprintf(buf, sizeof(buf), " w%d/g%d %.3f ms", cd.a, cd.b, cd.ms);
             rep += buf;
         }
     }
@@ -692,7 +695,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         p.KY = padded_ky(p.Ky2);
         p.N = N;
         p.Npad = ((N + 127) / 128) * 128;
-        p.n_fwd_cta = std::min(p.Npad / 64, 152);
+        CK(cudaDeviceGetAttribute(&p.n_sm, cudaDevAttrMultiProcessorCount, c->device));
+        p.n_fwd_cta = std::min(p.Npad / 64, p.n_sm);
         const size_t np = (size_t)p.Npad;
         AL(p.Ahi, 128 * np); AL(p.Alo, 128 * np); AL(p.Af, 128 * np); AL(p.Bsrc, (size_t)p.KY * np);
         AL(p.Yhi, (size_t)p.KY * np); AL(p.Ylo, (size_t)p.KY * np);

@@ -101,7 +101,7 @@ struct StepArgs {
 
 // Plan of the tensor-core coupling contraction for modes on a uniform in-plane grid.
 struct TcPlan {
-    int N, Npad, Kx, Ky2, KY, n_fwd_cta;
+    int N, Npad, Kx, Ky2, KY, n_fwd_cta, n_sm;
     double dkx, dky;
     __nv_bfloat16 *Ahi, *Alo, *Yhi, *Ylo;   // phase panels (bfloat16 hi / lo, core-matrix order)
     float *Af, *Bsrc, *partial;             // FP32 panels and split-K partial Gram matrices
@@ -152,7 +152,8 @@ cudaError_t launch_acf(const AcfArgs &a, const double *q_sync, const double *M_c
 cudaError_t launch_acf_finalize(const AcfArgs &a, double *out, cudaStream_t st);
 
 // Host-side launchers (defined in the .cu files).
-cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st, int warps = 2);
+cudaError_t launch_dftb_water(const DevSK *sk_dev, const DftbArgs &a, cudaStream_t st, int warps = 2,
+                              int per_warp = 5);
 cudaError_t prepare_dftb_water(int max_warps);   // shared-memory attribute for up to max_warps per block
 // r_trial = r + dt p / m: positions one drift ahead, for timing trial evaluations
 cudaError_t launch_trial_positions(const double *r, const double *p, const double *inv_mass, double dt, int n_atoms,

@@ -17,6 +17,8 @@
 //           combines them, then one thread per cell applies the kicks (and the drift). The last
 //           block to finish sums the per-block energy partials in block order (deterministic)
 //           and appends the energies of the synchronised state to the history ring.
+// k_kick:   the same kicks, drift and energy record when the tensor-core back product has
+//           already formed the fields: one thread per cell.
 #include "cavmd_internal.cuh"
 
 namespace {
@@ -24,6 +26,7 @@ namespace {
 constexpr int PH_THREADS = 256;
 constexpr int FLD_CELLS = 32;
 constexpr int FLD_SLICES = 32;   // warps per block; each warp sums every 32nd mode for 32 cells
+constexpr int KICK_THREADS = 256;   // cells per block of the kick-only kernel
 
 __global__ void k_mode_functions(const double *__restrict__ k, const double *__restrict__ phi,
                                  const double *__restrict__ R, int M, int N, double *__restrict__ U) {
@@ -146,6 +149,77 @@ __device__ __forceinline__ void field_partial(const StepArgs &a, int n, int sl, 
     }
 }
 
+// Second half-flow kick (field e2), kinetic energy of the synchronised state, then the next first
+// half-flow kick (field e1) and the drift, for the atoms of cell n.
+__device__ __forceinline__ void kick_cell(const StepArgs &a, int flags, int n, double e2, double e1, double &kin) {
+    const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
+    for (int j = j0; j < j1; ++j) {
+        const double im = a.inv_mass[j];
+        double pj[3];
+        for (int k = 0; k < 3; ++k) {
+            pj[k] = a.p[3 * j + k];
+            const double f = a.F[3 * j + k], bb = a.b[3 * j + k];
+            if (flags & FLD_SECOND) pj[k] = fma(a.tau, f, fma(e2, bb, pj[k]));
+            kin = fma(0.5 * im * pj[k], pj[k], kin);
+            if (flags & FLD_FIRST) {
+                pj[k] = fma(a.tau, f, fma(e1, bb, pj[k]));
+                a.r[3 * j + k] = fma(a.dt * im, pj[k], a.r[3 * j + k]);
+            }
+            a.p[3 * j + k] = pj[k];
+        }
+    }
+}
+
+// Run by the last block of a launch that left per-block kinetic and DFTB energy partials: totals in
+// a fixed order (block partials, then the per-mode photon energies) and the energy record of the
+// synchronised state. NT threads; scr holds 6 x NT/32 doubles.
+template <int NT>
+__device__ void record_energies(const StepArgs &a, int flags, int nblocks, double *scr) {
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = threadIdx.x; i < nblocks; i += NT) {
+        v[0] += __ldcg(a.e_kin_part + i);
+        v[1] += __ldcg(a.e_dftb_part + i);
+    }
+    for (int al = threadIdx.x; al < a.M; al += NT) {
+        const double *e = a.e_mode + 4 * al;
+        v[2] += e[0];
+        v[3] += e[1];
+        v[4] += e[2];
+        v[5] += e[3];
+    }
+    const int w = threadIdx.x >> 5;
+    __syncthreads();   // scr may alias buffers the block read before
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(CAVMD_FULL_MASK, v[k], o);
+        if ((threadIdx.x & 31) == 0) scr[k * (NT / 32) + w] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double t[6];
+    for (int k = 0; k < 6; ++k) {
+        t[k] = 0.0;
+        for (int i = 0; i < NT / 32; ++i) t[k] += scr[k * (NT / 32) + i];
+    }
+    long long step = *a.step_counter;
+    if (flags & FLD_SECOND) {
+        step += 1;
+        *a.step_counter = step;
+    }
+    double *h = a.hist + 8 * (size_t)(step % a.hist_cap);
+    h[0] = t[0];
+    h[1] = t[1];
+    h[2] = t[2];
+    h[3] = t[3];
+    h[4] = t[4];
+    h[5] = t[5];
+    h[6] = t[0] + t[1] + t[2];
+    h[7] = (double)step;
+    if (!(isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2]))) atomicOr(a.status, (unsigned)ERRBIT_NONFINITE);
+    *a.done_counter = 0u;
+}
+
 __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs a, const int flags) {
     __shared__ double red2[FLD_SLICES][FLD_CELLS];
     __shared__ double red1[FLD_SLICES][FLD_CELLS];
@@ -154,8 +228,7 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
     const int sl = threadIdx.x / FLD_CELLS;
     const int n = blockIdx.x * FLD_CELLS + cl;
     double e2 = 0.0, e1 = 0.0;
-    const bool given = flags & FLD_E_GIVEN;
-    if (n < a.N && !given) {
+    if (n < a.N) {
         const bool two = flags & FLD_SECOND, one = flags & FLD_FIRST;
         if (two && one) field_partial<true, true>(a, n, sl, e2, e1);
         else if (two) field_partial<true, false>(a, n, sl, e2, e1);
@@ -166,31 +239,11 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
     __syncthreads();
     double kin = 0.0, edf = 0.0;
     if (sl == 0 && n < a.N) {
-        if (given) {
-            if (flags & FLD_SECOND) e2 = a.E2in[n];
-            if (flags & FLD_FIRST) e1 = a.E1in[n];
-        } else {
-            for (int s = 1; s < FLD_SLICES; ++s) {
-                e2 += red2[s][cl];
-                e1 += red1[s][cl];
-            }
+        for (int s = 1; s < FLD_SLICES; ++s) {
+            e2 += red2[s][cl];
+            e1 += red1[s][cl];
         }
-        const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
-        for (int j = j0; j < j1; ++j) {
-            const double im = a.inv_mass[j];
-            double pj[3];
-            for (int k = 0; k < 3; ++k) {
-                pj[k] = a.p[3 * j + k];
-                const double f = a.F[3 * j + k], bb = a.b[3 * j + k];
-                if (flags & FLD_SECOND) pj[k] = fma(a.tau, f, fma(e2, bb, pj[k]));
-                kin = fma(0.5 * im * pj[k], pj[k], kin);
-                if (flags & FLD_FIRST) {
-                    pj[k] = fma(a.tau, f, fma(e1, bb, pj[k]));
-                    a.r[3 * j + k] = fma(a.dt * im, pj[k], a.r[3 * j + k]);
-                }
-                a.p[3 * j + k] = pj[k];
-            }
-        }
+        kick_cell(a, flags, n, e2, e1, kin);
         edf = a.E_cell[n];
     }
     if (!(flags & FLD_ENERGY)) return;
@@ -213,47 +266,50 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-        v[0] += __ldcg(a.e_kin_part + i);
-        v[1] += __ldcg(a.e_dftb_part + i);
+    record_energies<FLD_CELLS * FLD_SLICES>(a, flags, gridDim.x, &red2[0][0]);
+}
+
+// Kicks and drift with the field on every cell given (the tensor-core back product wrote E2 / E1):
+// one thread per cell, per-block energy partials, the last block records the energies.
+__global__ void __launch_bounds__(KICK_THREADS) k_kick(const StepArgs a, const int flags) {
+    __shared__ double scr[6 * (KICK_THREADS / 32)];
+    __shared__ bool last;
+    const int n = blockIdx.x * KICK_THREADS + threadIdx.x;
+    double kin = 0.0, edf = 0.0;
+    if (n < a.N) {
+        const double e2 = (flags & FLD_SECOND) ? a.E2in[n] : 0.0;
+        const double e1 = (flags & FLD_FIRST) ? a.E1in[n] : 0.0;
+        kick_cell(a, flags, n, e2, e1, kin);
+        edf = a.E_cell[n];
     }
-    for (int al = threadIdx.x; al < a.M; al += blockDim.x) {
-        const double *e = a.e_mode + 4 * al;
-        v[2] += e[0];
-        v[3] += e[1];
-        v[4] += e[2];
-        v[5] += e[3];
+    if (!(flags & FLD_ENERGY)) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
+        edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
     }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(CAVMD_FULL_MASK, v[k], o);
-        if (cl == 0) red2[k][sl] = v[k];      // slot reuse: red2 is free after the field sums
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        scr[w] = kin;
+        scr[KICK_THREADS / 32 + w] = edf;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    double t[6];
-    for (int k = 0; k < 6; ++k) {
-        t[k] = 0.0;
-        for (int w = 0; w < FLD_SLICES; ++w) t[k] += red2[k][w];
+    if (threadIdx.x == 0) {
+        double k = 0.0, d = 0.0;
+        for (int i = 0; i < KICK_THREADS / 32; ++i) {
+            k += scr[i];
+            d += scr[KICK_THREADS / 32 + i];
+        }
+        a.e_kin_part[blockIdx.x] = k;
+        a.e_dftb_part[blockIdx.x] = d;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.done_counter, 1u);
+        last = (ticket == gridDim.x - 1);
     }
-    long long step = *a.step_counter;
-    if (flags & FLD_SECOND) {
-        step += 1;
-        *a.step_counter = step;
-    }
-    double *h = a.hist + 8 * (size_t)(step % a.hist_cap);
-    h[0] = t[0];
-    h[1] = t[1];
-    h[2] = t[2];
-    h[3] = t[3];
-    h[4] = t[4];
-    h[5] = t[5];
-    h[6] = t[0] + t[1] + t[2];
-    h[7] = (double)step;
-    if (!(isfinite(t[0]) && isfinite(t[1]) && isfinite(t[2]))) atomicOr(a.status, (unsigned)ERRBIT_NONFINITE);
-    *a.done_counter = 0u;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    record_energies<KICK_THREADS>(a, flags, gridDim.x, scr);
 }
 
 __global__ void k_field_only(const double *__restrict__ U, const double *__restrict__ W, int M, int N,
@@ -281,10 +337,13 @@ cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-int field_blocks(int N) { return (N + FLD_CELLS - 1) / FLD_CELLS; }
+int field_blocks(int N) { return (N + FLD_CELLS - 1) / FLD_CELLS; }   // >= the kick kernel's blocks
 
 cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st) {
-    k_field<<<field_blocks(a.N), FLD_CELLS * FLD_SLICES, 0, st>>>(a, flags);
+    if (flags & FLD_E_GIVEN)
+        k_kick<<<(a.N + KICK_THREADS - 1) / KICK_THREADS, KICK_THREADS, 0, st>>>(a, flags);
+    else
+        k_field<<<field_blocks(a.N), FLD_CELLS * FLD_SLICES, 0, st>>>(a, flags);
     return cudaGetLastError();
 }
 

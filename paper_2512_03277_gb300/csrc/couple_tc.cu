@@ -15,6 +15,8 @@
 // and the partial Gram matrices are summed in a fixed order in FP64.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "tc_common.cuh"
 
 namespace {
@@ -66,55 +68,77 @@ __global__ void k_tc_panels(int N, int Npad, int Kx, int Ky2, int KY, double dkx
 }
 
 // Forward Gram product, split over cells: partial[cta][i][j] = sum over the CTA's cells of A B^T.
+// Each 64-cell stage arrives by bulk copies (the BF16 hi / lo panels of A and the FP32 y-phase
+// panel of B, all pre-arranged in core-matrix order), one stage ahead of the MMAs; the threads
+// scale the y phases by M_n and split them into the BF16 hi / lo panels of B in shared memory.
 template <int KY>
 __global__ void __launch_bounds__(128) k_tc_forward(int nblk_total, int blk_per_cta, const __nv_bfloat16 *__restrict__ Ahi,
                                                     const __nv_bfloat16 *__restrict__ Alo, const float *__restrict__ Bsrc,
                                                     const double *__restrict__ Mc, int N, float *__restrict__ partial,
                                                     unsigned *__restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr uint32_t A_BYTES = KXP * FWD_CELLS * 2, B_BYTES = KY * FWD_CELLS * 2;
-    constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr uint32_t A_BYTES = KXP * FWD_CELLS * 2, B_BYTES = KY * FWD_CELLS * 2, S_BYTES = KY * FWD_CELLS * 4;
+    constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES + S_BYTES;   // [A hi][A lo][B hi][B lo][B source]
     constexpr uint32_t LBO_A = (KXP / 8) * 128, LBO_B = (KY / 8) * 128;
     constexpr uint32_t TCOLS = KY <= 32 ? 32 : (KY <= 64 ? 64 : 128);   // power of two >= KY
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);
-    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 2 * STAGE + 16);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);      // [2] stage data arrived
+    uint64_t *done = full + 2;                                            // [2] stage MMAs finished
+    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 2);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int b0 = blockIdx.x * blk_per_cta;
     const int b1 = min(nblk_total, b0 + blk_per_cta);
     if (warp == 0) tc::tmem_alloc(slot, TCOLS);
     if (tid == 0) {
-        tc::mbar_init(&bar[0], 1);
-        tc::mbar_init(&bar[1], 1);
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&done[s], 1);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     const uint32_t idesc = tc::idesc_bf16(KXP, KY);
-    uint32_t parity[2] = {0u, 0u};
-    int issued[2] = {0, 0};
+    auto issue = [&](int b, int s) {   // thread 0: the copies of tile b into stage s
+        uint8_t *st = smem + s * STAGE;
+        tc::mbar_arrive_expect_tx(&full[s], 2 * A_BYTES + S_BYTES);
+        tc::bulk_g2s(st, Ahi + (size_t)b * KXP * FWD_CELLS, A_BYTES, &full[s]);
+        tc::bulk_g2s(st + A_BYTES, Alo + (size_t)b * KXP * FWD_CELLS, A_BYTES, &full[s]);
+        tc::bulk_g2s(st + 2 * A_BYTES + 2 * B_BYTES, Bsrc + (size_t)b * KY * FWD_CELLS, S_BYTES, &full[s]);
+    };
+    uint32_t pf[2] = {0u, 0u}, pd[2] = {0u, 0u};
+    int loaded[2] = {0, 0}, mma_pending[2] = {0, 0};   // thread 0's bookkeeping: copies and MMAs in flight
     bool ok = true;
+    if (tid == 0 && b0 < b1) {
+        issue(b0, 0);
+        loaded[0] = 1;
+    }
     int it = 0;
     for (int b = b0; b < b1; ++b, ++it) {
-        const int s = it & 1;
+        const int s = it & 1, s2 = s ^ 1;
+        if (b + 1 < b1) {   // prefetch the next tile once the MMAs reading its stage are done
+            if (tid == 0) {
+                if (mma_pending[s2]) {
+                    if (!tc::mbar_wait(&done[s2], pd[s2])) ok = false;
+                    pd[s2] ^= 1u;
+                    mma_pending[s2] = 0;
+                }
+                if (ok) {
+                    issue(b + 1, s2);
+                    loaded[s2] = 1;
+                }
+            }
+        }
+        const bool got = tc::mbar_wait(&full[s], pf[s]);
+        if (got) {
+            pf[s] ^= 1u;
+            loaded[s] = 0;
+        }
+        if (!__syncthreads_and(got && ok)) { ok = false; break; }
         uint8_t *st = smem + s * STAGE;
-        if (issued[s]) {   // the MMAs that read this stage must have finished
-            const bool got = tc::mbar_wait(&bar[s], parity[s]);
-            parity[s] ^= 1u;
-            issued[s] = 0;
-            if (!__syncthreads_and(got)) { ok = false; break; }
-        }
-        // A: contiguous copies of the pre-arranged tile
-        const uint4 *ah = reinterpret_cast<const uint4 *>(Ahi + (size_t)b * KXP * FWD_CELLS);
-        const uint4 *al = reinterpret_cast<const uint4 *>(Alo + (size_t)b * KXP * FWD_CELLS);
-        for (int e = tid; e < (int)(A_BYTES / 16); e += 128) {
-            reinterpret_cast<uint4 *>(st)[e] = ah[e];
-            reinterpret_cast<uint4 *>(st + A_BYTES)[e] = al[e];
-        }
-        // B: 8 consecutive cells of one row per chunk, scaled by M_n and split
-        const float *bs = Bsrc + (size_t)b * KY * FWD_CELLS;
-        for (int c = tid; c < KY * FWD_CELLS / 8; c += 128) {
-            const int kgrp = c / KY, row = c - kgrp * KY;    // chunk order follows the core layout
+        const float *bs = reinterpret_cast<const float *>(st + 2 * A_BYTES + 2 * B_BYTES);
+        for (int c = tid; c < KY * FWD_CELLS / 8; c += 128) {   // 8 consecutive cells of one row per chunk
+            const int kgrp = c / KY, row = c - kgrp * KY;
             const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_B);
             const float4 v0 = *reinterpret_cast<const float4 *>(bs + off / 2);
             const float4 v1 = *reinterpret_cast<const float4 *>(bs + off / 2 + 4);
@@ -142,16 +166,17 @@ __global__ void __launch_bounds__(128) k_tc_forward(int nblk_total, int blk_per_
                 tc::mma_bf16(tmem, ahd, bld, idesc, 1u);
                 tc::mma_bf16(tmem, ald, bhd, idesc, 1u);
             }
-            tc::mma_commit(&bar[s]);
-        }
-        issued[s] = 1;
-    }
-    for (int s = 0; s < 2; ++s) {
-        if (issued[s]) {
-            const bool got = tc::mbar_wait(&bar[s], parity[s]);
-            if (!__syncthreads_and(got)) ok = false;
+            tc::mma_commit(&done[s]);
+            mma_pending[s] = 1;
         }
     }
+    if (tid == 0) {   // every MMA finished (and any copy still in flight landed) before TMEM is read
+        for (int s = 0; s < 2; ++s) {
+            if (mma_pending[s] && !tc::mbar_wait(&done[s], pd[s])) ok = false;
+            if (loaded[s]) tc::mbar_wait(&full[s], pf[s]);
+        }
+    }
+    ok = __syncthreads_and(ok) != 0;
     if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
     tc::fence_after_sync();
     float *P = partial + (size_t)blockIdx.x * KXP * KY;
@@ -178,27 +203,43 @@ __global__ void k_tc_reduce(int n_part, int size, const float *__restrict__ part
     G[e] = s;
 }
 
-// Back product for a tile of 128 cells: E_n = sum_i A[i][n] (Wt Y^T)[i][n] for one or two weight
-// matrices (Wt2 -> E2, Wt1 -> E1).
+// Back product, persistent over tiles of 128 cells: D[n][i] = sum_j Y[n][j] Wt[i][j] (cells on the
+// TMEM lanes) for one or two weight matrices (Wt2 -> E2, Wt1 -> E1), then E_n = sum_i A[i][n] D[n][i]
+// with one thread per cell reading A coalesced (FP32 within each 32-row chunk, FP64 across chunks).
+// The weights are split into BF16 hi / lo once per CTA; each tile's Y panels arrive by bulk copy,
+// issued as soon as the previous tile's MMAs have finished, so the copy overlaps the epilogue.
 template <int KY>
-__global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, const float *__restrict__ Wt2, const float *__restrict__ Wt1,
-                                                 const __nv_bfloat16 *__restrict__ Yhi, const __nv_bfloat16 *__restrict__ Ylo,
-                                                 const float *__restrict__ Af, double *__restrict__ E2, double *__restrict__ E1,
+__global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, int n_tiles, const float *__restrict__ Wt2,
+                                                 const float *__restrict__ Wt1, const __nv_bfloat16 *__restrict__ Yhi,
+                                                 const __nv_bfloat16 *__restrict__ Ylo, const float *__restrict__ Af,
+                                                 double *__restrict__ E2, double *__restrict__ E1,
                                                  unsigned *__restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr uint32_t W_BYTES = KXP * KY * 2, Y_BYTES = BACK_CELLS * KY * 2;
     constexpr uint32_t LBO_W = (KXP / 8) * 128, LBO_Y = (BACK_CELLS / 8) * 128;
     uint8_t *sw = smem;                       // [Wt2 hi][Wt2 lo][Wt1 hi][Wt1 lo]
     uint8_t *sy = smem + 4 * W_BYTES;         // [Y hi][Y lo]
-    float *red = reinterpret_cast<float *>(sy + 2 * Y_BYTES);     // [4 warps][128 cells]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(red + 4 * BACK_CELLS);
-    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 2);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n0 = blockIdx.x * BACK_CELLS;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sy + 2 * Y_BYTES);
+    uint64_t *done = full + 1;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int nacc = Wt1 ? 2 : 1;
     if (warp == 0) tc::tmem_alloc(slot, 256);
-    if (tid == 0) tc::mbar_init(&bar[0], 1);
-    // weights: 8 consecutive K (j) of one row i per chunk, split into hi / lo
+    if (tid == 0) {
+        tc::mbar_init(full, 1);
+        tc::mbar_init(done, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    auto issue = [&](int t) {   // thread 0: the Y panels of tile t
+        tc::mbar_arrive_expect_tx(full, 2 * Y_BYTES);
+        tc::bulk_g2s(sy, Yhi + (size_t)t * BACK_CELLS * KY, Y_BYTES, full);
+        tc::bulk_g2s(sy + Y_BYTES, Ylo + (size_t)t * BACK_CELLS * KY, Y_BYTES, full);
+    };
+    if (tid == 0 && (int)blockIdx.x < n_tiles) issue(blockIdx.x);
+    bool pending = (int)blockIdx.x < n_tiles;
+    // weights: 8 consecutive K (j) of one row i per chunk, split into hi / lo (once per CTA)
     for (int w = 0; w < nacc; ++w) {
         const float *Wt = w == 0 ? Wt2 : Wt1;
         for (int c = tid; c < KXP * KY / 8; c += 128) {
@@ -210,63 +251,62 @@ __global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, const float *_
             *reinterpret_cast<uint4 *>(sw + (2 * w + 1) * W_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
         }
     }
-    {
-        const uint4 *yh = reinterpret_cast<const uint4 *>(Yhi + (size_t)blockIdx.x * BACK_CELLS * KY);
-        const uint4 *yl = reinterpret_cast<const uint4 *>(Ylo + (size_t)blockIdx.x * BACK_CELLS * KY);
-        for (int e = tid; e < (int)(Y_BYTES / 16); e += 128) {
-            reinterpret_cast<uint4 *>(sy)[e] = yh[e];
-            reinterpret_cast<uint4 *>(sy + Y_BYTES)[e] = yl[e];
-        }
-    }
     tc::fence_proxy_async();
-    tc::fence_before_sync();
     __syncthreads();
-    tc::fence_after_sync();
     const uint32_t tmem = *slot;
-    const uint32_t idesc = tc::idesc_bf16(KXP, BACK_CELLS);
-    if (tid == 0) {
-        const uint32_t sws = tc::smem_u32(sw), sys = tc::smem_u32(sy);
+    const uint32_t idesc = tc::idesc_bf16(BACK_CELLS, KXP);
+    uint32_t pf = 0u, pd = 0u;
+    bool ok = true;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const bool got = tc::mbar_wait(full, pf);
+        if (got) {
+            pf ^= 1u;
+            pending = false;
+        }
+        if (!__syncthreads_and(got)) { ok = false; break; }
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t sws = tc::smem_u32(sw), sys = tc::smem_u32(sy);
+            for (int w = 0; w < nacc; ++w) {
+                const uint32_t d = tmem + (uint32_t)(w * KXP);
+                for (int k = 0; k < KY / 16; ++k) {
+                    const uint32_t ow = k * 2 * LBO_W, oy = k * 2 * LBO_Y;
+                    const uint64_t whd = tc::make_desc(sws + (2 * w) * W_BYTES + ow, LBO_W, 128);
+                    const uint64_t wld = tc::make_desc(sws + (2 * w + 1) * W_BYTES + ow, LBO_W, 128);
+                    const uint64_t yhd = tc::make_desc(sys + oy, LBO_Y, 128), yld = tc::make_desc(sys + Y_BYTES + oy, LBO_Y, 128);
+                    tc::mma_bf16(d, yhd, whd, idesc, k > 0 ? 1u : 0u);
+                    tc::mma_bf16(d, yld, whd, idesc, 1u);
+                    tc::mma_bf16(d, yhd, wld, idesc, 1u);
+                }
+            }
+            tc::mma_commit(done);
+        }
+        const bool mg = tc::mbar_wait(done, pd);
+        pd ^= 1u;
+        if (!__syncthreads_and(mg)) { ok = false; break; }
+        tc::fence_after_sync();
+        if (t + (int)gridDim.x < n_tiles) {   // the Y stage is free again: fetch the next tile now
+            if (tid == 0) issue(t + gridDim.x);
+            pending = true;
+        }
+        const int n = t * BACK_CELLS + tid;   // this thread's cell (TMEM lane)
         for (int w = 0; w < nacc; ++w) {
-            const uint32_t d = tmem + (uint32_t)(w * BACK_CELLS);
-            for (int k = 0; k < KY / 16; ++k) {
-                const uint32_t ow = k * 2 * LBO_W, oy = k * 2 * LBO_Y;
-                const uint64_t whd = tc::make_desc(sws + (2 * w) * W_BYTES + ow, LBO_W, 128);
-                const uint64_t wld = tc::make_desc(sws + (2 * w + 1) * W_BYTES + ow, LBO_W, 128);
-                const uint64_t yhd = tc::make_desc(sys + oy, LBO_Y, 128), yld = tc::make_desc(sys + Y_BYTES + oy, LBO_Y, 128);
-                tc::mma_bf16(d, whd, yhd, idesc, k > 0 ? 1u : 0u);
-                tc::mma_bf16(d, whd, yld, idesc, 1u);
-                tc::mma_bf16(d, wld, yhd, idesc, 1u);
+            double e = 0.0;
+            for (int c0 = 0; c0 < KXP; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w * KXP + c0), v);
+                float s = 0.0f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) s = fmaf(Af[(size_t)(c0 + q) * Npad + n], v[q], s);
+                e += (double)s;
             }
+            if (n < N) (w == 0 ? E2 : E1)[n] = e;
         }
-        tc::mma_commit(&bar[0]);
+        tc::fence_before_sync();
+        __syncthreads();   // TMEM reads done before the next tile's MMAs
     }
-    const bool got = tc::mbar_wait(&bar[0], 0u);
-    const bool ok = __syncthreads_and(got) != 0;
+    if (tid == 0 && pending) tc::mbar_wait(full, pf);   // a copy still in flight lands before exit
     if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
-    tc::fence_after_sync();
-    const int i = 32 * warp + lane;           // this thread's row (TMEM lane)
-    for (int w = 0; w < nacc && ok; ++w) {
-        double *E = w == 0 ? E2 : E1;
-        for (int c0 = 0; c0 < BACK_CELLS; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w * BACK_CELLS + c0), v);
-            const float *arow = Af + (size_t)i * Npad + n0 + c0;
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                float x = v[q] * arow[q];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(CAVMD_FULL_MASK, x, o);
-                if (lane == 0) red[warp * BACK_CELLS + c0 + q] = x;
-            }
-        }
-        __syncthreads();
-        if (tid < BACK_CELLS && n0 + tid < N) {
-            double s = 0.0;
-            for (int ww = 0; ww < 4; ++ww) s += (double)red[ww * BACK_CELLS + tid];
-            E[n0 + tid] = s;
-        }
-        __syncthreads();
-    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
@@ -281,10 +321,10 @@ cudaError_t set_smem(F f, size_t bytes) {
 
 // ---------------------------------------------------------------------------------------- host
 
-size_t tc_fwd_smem(int KY) { return 2 * (2 * KXP * FWD_CELLS * 2 + 2 * (size_t)KY * FWD_CELLS * 2) + 64; }
-size_t tc_back_smem(int KY) {
-    return 4 * (size_t)KXP * KY * 2 + 2 * (size_t)BACK_CELLS * KY * 2 + 4 * BACK_CELLS * 4 + 64;
+size_t tc_fwd_smem(int KY) {
+    return 2 * (2 * (size_t)KXP * FWD_CELLS * 2 + 2 * (size_t)KY * FWD_CELLS * 2 + (size_t)KY * FWD_CELLS * 4) + 64;
 }
+size_t tc_back_smem(int KY) { return 4 * (size_t)KXP * KY * 2 + 2 * (size_t)BACK_CELLS * KY * 2 + 64; }
 
 cudaError_t tc_prepare(int KY) {
     const size_t f = tc_fwd_smem(KY), b = tc_back_smem(KY);
@@ -331,11 +371,12 @@ cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsi
 cudaError_t launch_tc_back(const TcPlan &p, const float *Wt2, const float *Wt1, double *E2, double *E1,
                            unsigned *status, cudaStream_t st) {
     const size_t sm = tc_back_smem(p.KY);
-    const int grid = p.Npad / BACK_CELLS;
+    const int n_tiles = p.Npad / BACK_CELLS;
+    const int grid = std::min(n_tiles, p.n_sm);
     cudaError_t e = cudaSuccess;
 #define BACK_CASE(KYV)                                                                                    \
     case KYV:                                                                                             \
-            k_tc_back<KYV><<<grid, 128, sm, st>>>(p.N, p.Npad, Wt2, Wt1, p.Yhi, p.Ylo, p.Af, E2, E1, status); \
+            k_tc_back<KYV><<<grid, 128, sm, st>>>(p.N, p.Npad, n_tiles, Wt2, Wt1, p.Yhi, p.Ylo, p.Af, E2, E1, status); \
         break;
     switch (p.KY) {
         BACK_CASE(16) BACK_CASE(32) BACK_CASE(48) BACK_CASE(64) BACK_CASE(96) BACK_CASE(128)

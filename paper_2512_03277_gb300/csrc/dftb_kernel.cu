@@ -29,6 +29,12 @@ constexpr double MIN_GAP = 1e-3;       // closed-shell HOMO-LUMO threshold (Hart
 constexpr double EIG_TOL = 1e-10;      // occupied-virtual coupling treated as converged (Hartree)
 constexpr float KMAX_PERT = 1e-4f;     // largest generator entry for the second-order update
 
+// Index of the (t+1)-th set bit of mask (t = 0: the lowest).
+__device__ __forceinline__ int nth_bit(unsigned mask, int t) {
+    for (int s = 0; s < t; ++s) mask &= mask - 1u;
+    return __ffs(mask) - 1;
+}
+
 template <int NAT, int NORB>
 struct MolShared {
     static constexpr int LD = (NORB % 2 == 0) ? NORB + 1 : NORB;   // odd column stride
@@ -51,6 +57,8 @@ struct MolShared {
     double red[NORB];
     double cs[NORB / 2 + 1][2];
     double invd[NORB];
+    double hsh[NORB];     // half shift of the atom of each orbital
+    float diagf[NORB];    // diagonal of A in FP32 (generator denominators)
     double gpair[NPAIR > 0 ? NPAIR : 1][3];
     double epair[NPAIR > 0 ? NPAIR : 1];
     double Hs[NORB * LD];   // H of the current SCC iteration
@@ -128,11 +136,11 @@ __device__ __forceinline__ void jacobi_cs(double app, double aqq, double apq, do
 }
 
 template <int NAT, int NORB>
-__global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a) {
+__global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a, const int gpw) {
     const DevSK &sk = *skp;
     using SM = MolShared<NAT, NORB>;
     constexpr int LD = SM::LD;
-    constexpr int GPW = 32 / NORB;
+    // gpw <= 32 / NORB molecules per warp (fewer spreads a small batch over more warps)
     constexpr int NPAIR = SM::NPAIR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
@@ -141,11 +149,11 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
     const int wpb = blockDim.x >> 5;
     const int g = lane / NORB;
     const int j = lane - g * NORB;
-    const bool act = g < GPW;
-    SM &m = reinterpret_cast<SM *>(smem_raw)[warp * GPW + (act ? g : 0)];
+    const bool act = g < gpw;
+    SM &m = reinterpret_cast<SM *>(smem_raw)[warp * gpw + (act ? g : 0)];
     const bool disp = a.n_disp > 0;                       // finite-difference rows
     const int n_rows = disp ? a.n_cells * a.n_disp : a.n_cells;
-    const int idx = (blockIdx.x * wpb + warp) * GPW + g;
+    const int idx = (blockIdx.x * wpb + warp) * gpw + g;
     const bool valid = act && idx < n_rows;
     const int ridx = min(idx, n_rows - 1);
     const int cidx = disp ? ridx / a.n_disp : ridx;
@@ -364,10 +372,13 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             m.shift[j] = sh;
         }
         __syncwarp();
-        if (work) {   // H column j
-            const double shj = m.shift[m.orb_atom[j]];
+        if (work) m.hsh[j] = 0.5 * m.shift[m.orb_atom[j]];
+        __syncwarp();
+        if (work) {   // H column j: H0 + S o (eps_A + eps_B)/2 (halving is exact, so this equals the
+                      // product with the halved sum bit for bit)
+            const double hj = m.hsh[j];
             for (int i = 0; i < NORB; ++i)
-                m.Hs[j * LD + i] = fma(0.5 * m.S[j * LD + i], m.shift[m.orb_atom[i]] + shj, m.H0[j * LD + i]);
+                m.Hs[j * LD + i] = fma(m.S[j * LD + i], m.hsh[i] + hj, m.H0[j * LD + i]);
         }
         __syncwarp();
         if (work) {   // Y = H C
@@ -396,6 +407,7 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
         __syncwarp();
         // aufbau occupation from the diagonal of A
         if (work) {
+            m.diagf[j] = (float)m.A[j * LD + j];
             const long long kj = order_key(m.A[j * LD + j]);
             int rank = 0;
             for (int i = 0; i < NORB; ++i) {
@@ -407,22 +419,29 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
         }
         __syncwarp();
         // first-order occupied-virtual generator, column j, into Y (FP32: it only steers)
+        // Only the entries of the other block (virtual rows of an occupied column, and conversely)
+        // are non-zero; the loop visits just those.
         float kmax = 0.0f;
+        unsigned same_mask = 0u, other_mask = 0u;
         if (work) {
-            const int oj = m.occf[j];
-            const double ajj = m.A[j * LD + j];
+            unsigned om = 0u;
+#pragma unroll
+            for (int k = 0; k < NORB; ++k) om |= (m.occf[k] ? 1u : 0u) << k;
+            same_mask = m.occf[j] ? om : (~om & ((1u << NORB) - 1u));
+            other_mask = ~same_mask & ((1u << NORB) - 1u);
+#pragma unroll
+            for (int k = 0; k < NORB; ++k) m.Y[j * LD + k] = 0.0;
+            const float dj = m.diagf[j];
+            const int no = __popc(other_mask);
             bool small = true;
-            for (int k = 0; k < NORB; ++k) {
-                double kv = 0.0;
-                if (m.occf[k] != oj) {
-                    const double akj = m.A[j * LD + k];
-                    if (!abs_lt(akj, EIG_TOL)) small = false;
-                    float kf = (float)akj / (float)(ajj - m.A[k * LD + k]);
-                    if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
-                    kv = (double)kf;
-                    kmax = fmaxf(kmax, fabsf(kf));
-                }
-                m.Y[j * LD + k] = kv;
+            for (int t = 0; t < no; ++t) {
+                const int k = nth_bit(other_mask, t);
+                const double akj = m.A[j * LD + k];
+                if (!abs_lt(akj, EIG_TOL)) small = false;
+                float kf = (float)akj / (dj - m.diagf[k]);
+                if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
+                m.Y[j * LD + k] = (double)kf;
+                kmax = fmaxf(kmax, fabsf(kf));
             }
             m.eok[j] = small;
         }
@@ -432,19 +451,24 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
         if (perturb) {
             double cn[NORB];
             if (work) {   // V column j = e_j + K e_j + K (K e_j) / 2, then C <- C V
+                // (K^2)(i, j) vanishes for rows i of the other block; for rows of j's own block it sums
+                // over the other block only: n_occ n_virt products per column, in increasing index
+                // order (the skipped terms are exact zeros). The row sums go to A, free here.
+                const int no = __popc(other_mask);
+                const int nprod = __popc(same_mask) * no;
+                double acc = 0.0;
+                for (int t = 0; t < nprod; ++t) {
+                    const int r = t / no, mi = t - r * no;
+                    const int i = nth_bit(same_mask, r), mm = nth_bit(other_mask, mi);
+                    if (mi == 0) acc = 0.0;
+                    acc = fma(m.Y[mm * LD + i], m.Y[j * LD + mm], acc);
+                    if (mi == no - 1) m.A[j * LD + i] = acc;
+                }
                 double v[NORB];
 #pragma unroll
-                for (int i = 0; i < NORB; ++i) v[i] = m.Y[j * LD + i];
-                double w[NORB];
-#pragma unroll
-                for (int i = 0; i < NORB; ++i) w[i] = 0.0;
-                for (int mm = 0; mm < NORB; ++mm) {
-                    const double kmj = v[mm];
-#pragma unroll
-                    for (int i = 0; i < NORB; ++i) w[i] = fma(m.Y[mm * LD + i], kmj, w[i]);
-                }
-#pragma unroll
-                for (int i = 0; i < NORB; ++i) v[i] = fma(0.5, w[i], v[i] + (i == j ? 1.0 : 0.0));
+                for (int i = 0; i < NORB; ++i)
+                    v[i] = fma(0.5, ((same_mask >> i) & 1u) ? m.A[j * LD + i] : 0.0,
+                               m.Y[j * LD + i] + (i == j ? 1.0 : 0.0));
 #pragma unroll
                 for (int i = 0; i < NORB; ++i) cn[i] = 0.0;
                 for (int k = 0; k < NORB; ++k) {
@@ -861,17 +885,20 @@ cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const doub
     return cudaGetLastError();
 }
 
-// warps per block: 2, 4 or 8 (5 waters per warp); every choice gives bitwise identical results.
-cudaError_t launch_dftb_water(const DevSK *sk, const DftbArgs &a, cudaStream_t st, int warps) {
+// warps per block (2, 4 or 8) and waters per warp (1..5). The warps per block never change a result;
+// the waters per warp do at rounding level, because the choice between a Jacobi sweep and the
+// second-order update is taken per warp.
+cudaError_t launch_dftb_water(const DevSK *sk, const DftbArgs &a, cudaStream_t st, int warps, int per_warp) {
     constexpr int NAT = 3, NORB = 6;
     using SM = MolShared<NAT, NORB>;
+    const int gpw = per_warp < 1 ? 1 : (per_warp > 32 / NORB ? 32 / NORB : per_warp);
     const int threads = 32 * warps;
-    const int per_block = warps * (32 / NORB);
+    const int per_block = warps * gpw;
     const long long rows = (long long)a.n_cells * (a.n_disp > 0 ? a.n_disp : 1);
     const int blocks = (int)((rows + per_block - 1) / per_block);
     const size_t smem = sizeof(SM) * per_block;
     if (a.n_cells <= 0) return cudaSuccess;
-    dftb_kernel<NAT, NORB><<<blocks, threads, smem, st>>>(sk, a);
+    dftb_kernel<NAT, NORB><<<blocks, threads, smem, st>>>(sk, a, gpw);
     return cudaGetLastError();
 }
 
