@@ -241,9 +241,11 @@ int cavmd_set_state(cavmd_ctx *ctx, const cavmd_state *st);
 int cavmd_get_eval(cavmd_ctx *ctx, cavmd_eval *out);
 
 /* Per-phase device timers. enable = 1 starts recording CUDA events around every kernel
- * phase of later steps (on the context's stream); enable = 0 stops. ms_out[CAVMD_N_PHASES]
- * receives the summed durations and counts[CAVMD_N_PHASES] the launches since the last
- * reset (reset = 1 clears both after reading). Either output may be NULL. */
+ * phase of later steps (on the context's stream); enable = 2 only around the SCC-DFTB launches
+ * (phase 0: two events per step, which barely perturb a step's timing); enable = 0 stops.
+ * Recording disables CUDA-graph replay. ms_out[CAVMD_N_PHASES] receives the summed durations and
+ * counts[CAVMD_N_PHASES] the launches since the last reset (reset = 1 clears both after
+ * reading). Either output may be NULL. */
 #define CAVMD_N_PHASES 4        /* 0: SCC-DFTB, 1: forward contraction + photons,
                                    2: field + kicks + drift, 3: finite-difference Born rows */
 int cavmd_phase_times(cavmd_ctx *ctx, int32_t enable, double *ms_out, int64_t *counts,

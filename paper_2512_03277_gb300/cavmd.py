@@ -376,7 +376,8 @@ class Context:
         _check(self.lib.cavmd_get_eval(self.handle, C.byref(ev)), self.handle)
         return out
 
-    def cavmd_phase_times(self, enable: bool, reset: bool = True):
+    def cavmd_phase_times(self, enable: int, reset: bool = True):
+        """enable: 0 off, 1 events around every launch, 2 around the SCC-DFTB launches only."""
         ms = np.zeros(N_PHASES)
         cnt = np.zeros(N_PHASES, np.int64)
         _check(self.lib.cavmd_phase_times(self.handle, int(enable), _ptr(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)),

@@ -72,6 +72,7 @@ struct cavmd_ctx {
     std::string err;
     // phase timers
     bool timing = false;
+    bool timing_all = true;                  // events around every phase (else only phase 0)
     struct Pending { cudaEvent_t a, b; int phase; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> ev_free;
@@ -173,7 +174,7 @@ struct PhaseScope {
     cavmd_ctx *c;
     cavmd_ctx::Pending pd{};
     bool on;
-    PhaseScope(cavmd_ctx *c_, int phase) : c(c_), on(c_->timing) {
+    PhaseScope(cavmd_ctx *c_, int phase) : c(c_), on(c_->timing && (c_->timing_all || phase == 0)) {
         if (on) {
             pd.a = get_event(c);
             pd.b = get_event(c);
@@ -289,10 +290,11 @@ cudaError_t reset_acf(cavmd_ctx *c) {
 // step number first_step (evaluation index = step number, init being evaluation 0).
 cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     cudaError_t e;
-    const int given = c->mixed ? FLD_E_GIVEN : 0;
+    // The opening first half-flow: its field E1 was formed at the end of the previous call (or by
+    // cavmd_init / cavmd_set_state) from the same synchronised state, so only the photon rotation
+    // and the kick and drift remain.
     if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
-    if (c->mixed && (e = run_tc_back(c, false, true)) != cudaSuccess) return e;
-    if ((e = run_field(c, FLD_FIRST | given)) != cudaSuccess) return e;
+    if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
     for (int64_t s = 0; s < n; ++s) {
         const bool last = (s == n - 1);
         if ((e = run_dftb(c, 1)) != cudaSuccess) return e;
@@ -300,13 +302,14 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
         if (c->d_mlpw && (e = run_mlp(c)) != cudaSuccess) return e;
         if (c->mixed) {
             if ((e = run_tc_forward(c)) != cudaSuccess) return e;
-            if ((e = run_photon(c, PH_FORWARD_G | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
-            if ((e = run_tc_back(c, true, !last)) != cudaSuccess) return e;
+            if ((e = run_photon(c, PH_FORWARD_G | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) != cudaSuccess)
+                return e;
+            if ((e = run_tc_back(c, true, true)) != cudaSuccess) return e;   // E1 also for the next call
             if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | FLD_E_GIVEN | (last ? 0 : FLD_FIRST))) != cudaSuccess)
                 return e;
         } else {
-            if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? 0 : PH_FIRST))) != cudaSuccess) return e;
-            if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? 0 : FLD_FIRST))) != cudaSuccess) return e;
+            if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) != cudaSuccess) return e;
+            if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? FLD_E1_STORE : FLD_FIRST))) != cudaSuccess) return e;
         }
         if ((e = run_acf(c)) != cudaSuccess) return e;
     }
@@ -414,13 +417,16 @@ int initial_evaluation(cavmd_ctx *c, bool init_photons) {
         CK(run_tc_forward(c));
         fwd = PH_FORWARD_G;
     }
+    // energies of the synchronised state, and the field of the next first half-flow (kept for the
+    // opening of the next cavmd_step call)
     if (init_photons) {
         const int pf = (c->opt.photon_init == CAVMD_PHOTON_ZERO) ? PH_INIT_ZERO : PH_INIT_RELAXED;
-        CK(run_photon(c, fwd | pf | PH_ENERGY));
+        CK(run_photon(c, fwd | pf | PH_ENERGY | PH_W1));
     } else {
-        CK(run_photon(c, fwd | PH_ENERGY));   // keeps q_sync / pq_sync
+        CK(run_photon(c, fwd | PH_ENERGY | PH_W1));   // keeps q_sync / pq_sync
     }
-    CK(run_field(c, FLD_ENERGY));
+    if (c->mixed) CK(run_tc_back(c, false, true));
+    CK(run_field(c, FLD_ENERGY | (c->mixed ? 0 : FLD_E1_STORE)));
     return sync_status(c);
 }
 
@@ -632,7 +638,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     c->n_cwarm = coff[N];
     AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)coff[N]); AL(c->d_E, N); AL(c->d_Mc, N);
     if (!c->generic) CK(prepare_dftb_water(8));
-    AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N);
+    AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N); AL(c->d_E1, N);
     c->mixed = c->opt.precision == CAVMD_PREC_MIXED_BF16X3;
     if (!c->mixed) AL(c->d_U, (size_t)M * N);
     AL(c->d_k, 3 * M); AL(c->d_phi, M); AL(c->d_R, 3 * N);
@@ -702,7 +708,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         AL(p.Yhi, (size_t)p.KY * np); AL(p.Ylo, (size_t)p.KY * np);
         AL(p.partial, (size_t)p.n_fwd_cta * 128 * p.KY);
         AL(c->d_G, 128 * (size_t)p.KY); AL(c->d_Wt2, 128 * (size_t)p.KY); AL(c->d_Wt1, 128 * (size_t)p.KY);
-        AL(c->d_E2, N); AL(c->d_E1, N);
+        AL(c->d_E2, N);
         CK(cudaMemsetAsync(c->d_Wt2, 0, sizeof(float) * 128 * p.KY, st));
         CK(cudaMemsetAsync(c->d_Wt1, 0, sizeof(float) * 128 * p.KY, st));
         CK(tc_prepare(p.KY));
@@ -780,7 +786,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.W1 = c->d_W1; s.W2 = c->d_W2; s.e_mode = c->d_emode; s.e_kin_part = c->d_ekp; s.e_dftb_part = c->d_edp;
     s.done_counter = c->d_done; s.hist = c->d_hist; s.hist_cap = c->opt.energy_history;
     s.step_counter = c->d_step; s.status = c->d_status; s.dt = c->opt.dt; s.tau = tau;
-    s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->d_E2; s.E1in = c->d_E1;
+    s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->d_E2; s.E1in = c->d_E1; s.E1store = c->d_E1;
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     return CAVMD_OK;
 }
@@ -1059,7 +1065,9 @@ int cavmd_phase_times(cavmd_ctx *c, int32_t enable, double *ms, int64_t *cnt, in
         if (cnt) cnt[i] = c->phase_cnt[i];
         if (reset) { c->phase_ms[i] = 0; c->phase_cnt[i] = 0; }
     }
+    if (enable < 0 || enable > 2) return fail(c, CAVMD_ERR_INVALID_ARG, "enable must be 0, 1 or 2");
     c->timing = enable != 0;
+    c->timing_all = enable != 2;
     return CAVMD_OK;
 }
 

@@ -96,6 +96,7 @@ struct StepArgs {
     const double *G;           // [128][KY] forward Gram matrix (PH_FORWARD_G)
     float *Wt2, *Wt1;          // [128][KY] back-product weights written by the photon kernel
     const double *E2in, *E1in; // [N] fields from the back product (FLD_E_GIVEN)
+    double *E1store;           // [N] the next first half-flow's field, kept for the next call (FLD_E1_STORE)
     int Kx, Ky2, KY;
 };
 
@@ -191,12 +192,14 @@ cudaError_t launch_to_bf16(const float *src, void *dst, int n, cudaStream_t st);
 cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
                                   double *U, cudaStream_t st);
 // forward contraction of M_cell into D plus the photon half-flows (flags below)
+// PH_W1: weights of the next first half-flow from the synchronised state, without rotating
 enum { PH_FORWARD = 1, PH_SECOND = 2, PH_FIRST = 4, PH_INIT_RELAXED = 8, PH_INIT_ZERO = 16,
-       PH_ENERGY = 32, PH_FORWARD_G = 64 };
+       PH_ENERGY = 32, PH_FORWARD_G = 64, PH_W1 = 128 };
 cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st);
 // field on the cells with weights W2 (second half-flow kick) and/or W1 (first half-flow kick +
 // drift); always records the energies of the synchronised state when FLD_ENERGY is set
-enum { FLD_SECOND = 1, FLD_FIRST = 2, FLD_ENERGY = 4, FLD_E_GIVEN = 8 };
+// FLD_E1_STORE: form the next first half-flow's field from W1 and store it, without that kick
+enum { FLD_SECOND = 1, FLD_FIRST = 2, FLD_ENERGY = 4, FLD_E_GIVEN = 8, FLD_E1_STORE = 16 };
 cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st);
 int field_blocks(int N);
 // instantaneous field E_n = sum_a u_a(R_n) W_a for a caller-supplied weight vector

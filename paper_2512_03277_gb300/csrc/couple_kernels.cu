@@ -26,7 +26,7 @@ namespace {
 constexpr int PH_THREADS = 256;
 constexpr int FLD_CELLS = 32;
 constexpr int FLD_SLICES = 32;   // warps per block; each warp sums every 32nd mode for 32 cells
-constexpr int KICK_THREADS = 256;   // cells per block of the kick-only kernel
+constexpr int KICK_THREADS = 64;    // cells per block of the kick-only kernel
 
 __global__ void k_mode_functions(const double *__restrict__ k, const double *__restrict__ phi,
                                  const double *__restrict__ R, int M, int N, double *__restrict__ U) {
@@ -124,10 +124,13 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         e[2] = 0.5 * D * D;
         e[3] = 0.5 * fma(ps, ps, (w * qs) * (w * qs));
     }
-    if (flags & PH_FIRST) {
+    if (flags & (PH_FIRST | PH_W1)) {
         const double y = qs - cen;
         a.W1[al] = lam * fma(y, s, ps * omc);
         if (a.Wt1) put_weight(a, a.Wt1, al, a.W1[al]);
+    }
+    if (flags & PH_FIRST) {
+        const double y = qs - cen;
         a.q[al] = cen + fma(y, c, ps * s * iw);
         a.pq[al] = fma(ps, c, -w * y * s);
     } else {
@@ -151,23 +154,40 @@ __device__ __forceinline__ void field_partial(const StepArgs &a, int n, int sl, 
 
 // Second half-flow kick (field e2), kinetic energy of the synchronised state, then the next first
 // half-flow kick (field e1) and the drift, for the atoms of cell n.
+// Atom j of a cell with fields e2, e1: kinetic energy returned. Every load of the atom is issued
+// before its stores (the arrays do not alias), so an atom costs one memory round trip.
+__device__ __forceinline__ double kick_atom(const StepArgs &a, int flags, int j, double e2, double e1) {
+    const double *__restrict__ F = a.F;
+    const double *__restrict__ b = a.b;
+    double *__restrict__ p = a.p;
+    double *__restrict__ r = a.r;
+    const double im = a.inv_mass[j];
+    double pj[3], f[3], bb[3], rj[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pj[k] = p[3 * j + k];
+        f[k] = F[3 * j + k];
+        bb[k] = b[3 * j + k];
+        rj[k] = (flags & FLD_FIRST) ? r[3 * j + k] : 0.0;
+    }
+    double kin = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (flags & FLD_SECOND) pj[k] = fma(a.tau, f[k], fma(e2, bb[k], pj[k]));
+        kin = fma(0.5 * im * pj[k], pj[k], kin);
+        if (flags & FLD_FIRST) {
+            pj[k] = fma(a.tau, f[k], fma(e1, bb[k], pj[k]));
+            r[3 * j + k] = fma(a.dt * im, pj[k], rj[k]);
+        }
+        p[3 * j + k] = pj[k];
+    }
+    return kin;
+}
+
+// All atoms of cell n (one thread).
 __device__ __forceinline__ void kick_cell(const StepArgs &a, int flags, int n, double e2, double e1, double &kin) {
     const int j0 = a.cell_offset[n], j1 = a.cell_offset[n + 1];
-    for (int j = j0; j < j1; ++j) {
-        const double im = a.inv_mass[j];
-        double pj[3];
-        for (int k = 0; k < 3; ++k) {
-            pj[k] = a.p[3 * j + k];
-            const double f = a.F[3 * j + k], bb = a.b[3 * j + k];
-            if (flags & FLD_SECOND) pj[k] = fma(a.tau, f, fma(e2, bb, pj[k]));
-            kin = fma(0.5 * im * pj[k], pj[k], kin);
-            if (flags & FLD_FIRST) {
-                pj[k] = fma(a.tau, f, fma(e1, bb, pj[k]));
-                a.r[3 * j + k] = fma(a.dt * im, pj[k], a.r[3 * j + k]);
-            }
-            a.p[3 * j + k] = pj[k];
-        }
-    }
+    for (int j = j0; j < j1; ++j) kin += kick_atom(a, flags, j, e2, e1);
 }
 
 // Run by the last block of a launch that left per-block kinetic and DFTB energy partials: totals in
@@ -223,13 +243,14 @@ __device__ void record_energies(const StepArgs &a, int flags, int nblocks, doubl
 __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs a, const int flags) {
     __shared__ double red2[FLD_SLICES][FLD_CELLS];
     __shared__ double red1[FLD_SLICES][FLD_CELLS];
+    __shared__ double es2[FLD_CELLS], es1[FLD_CELLS];
     __shared__ bool last;
     const int cl = threadIdx.x & (FLD_CELLS - 1);
     const int sl = threadIdx.x / FLD_CELLS;
     const int n = blockIdx.x * FLD_CELLS + cl;
     double e2 = 0.0, e1 = 0.0;
     if (n < a.N) {
-        const bool two = flags & FLD_SECOND, one = flags & FLD_FIRST;
+        const bool two = flags & FLD_SECOND, one = flags & (FLD_FIRST | FLD_E1_STORE);
         if (two && one) field_partial<true, true>(a, n, sl, e2, e1);
         else if (two) field_partial<true, false>(a, n, sl, e2, e1);
         else if (one) field_partial<false, true>(a, n, sl, e2, e1);
@@ -237,31 +258,47 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
     red2[sl][cl] = e2;
     red1[sl][cl] = e1;
     __syncthreads();
-    double kin = 0.0, edf = 0.0;
-    if (sl == 0 && n < a.N) {
+    if (sl == 0) {   // fixed-order slice sums of cell cl
         for (int s = 1; s < FLD_SLICES; ++s) {
             e2 += red2[s][cl];
             e1 += red1[s][cl];
         }
-        kick_cell(a, flags, n, e2, e1, kin);
-        edf = a.E_cell[n];
+        es2[cl] = e2;
+        es1[cl] = e1;
+        if ((flags & FLD_E1_STORE) && n < a.N) a.E1store[n] = e1;
+    }
+    __syncthreads();
+    // the atoms of cell cl are spread over the 32 slices
+    double kin = 0.0, edf = 0.0;
+    if (n < a.N) {
+        const int j1 = a.cell_offset[n + 1];
+        for (int j = a.cell_offset[n] + sl; j < j1; j += FLD_SLICES) kin += kick_atom(a, flags, j, es2[cl], es1[cl]);
+        if (sl == 0) edf = a.E_cell[n];
     }
     if (!(flags & FLD_ENERGY)) return;
-    // per-block partials (warp 0, fixed shuffle tree), then the last block to arrive forms the
-    // totals with the whole block in a fixed order
-    if (sl == 0) {
+    // per-block partials: fixed shuffle tree in every warp, then the 32 warp sums in order; the
+    // last block to arrive forms the totals with the whole block in a fixed order
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
-            edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
+        edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
+    }
+    if (cl == 0) {
+        red2[0][sl] = kin;   // red2 / red1 are free after the slice sums
+        red1[0][sl] = edf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double k = 0.0, d = 0.0;
+        for (int w = 0; w < FLD_SLICES; ++w) {
+            k += red2[0][w];
+            d += red1[0][w];
         }
-        if (cl == 0) {
-            a.e_kin_part[blockIdx.x] = kin;
-            a.e_dftb_part[blockIdx.x] = edf;
-            __threadfence();
-            const unsigned ticket = atomicAdd(a.done_counter, 1u);
-            last = (ticket == gridDim.x - 1);
-        }
+        a.e_kin_part[blockIdx.x] = k;
+        a.e_dftb_part[blockIdx.x] = d;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.done_counter, 1u);
+        last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
