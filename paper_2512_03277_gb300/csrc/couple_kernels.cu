@@ -13,8 +13,9 @@
 //
 // k_photon: one block per mode; the deterministic block reduction forms D_a from the cell
 //           dipoles, then one thread applies the half-flows of that mode and records its energy.
-// k_field:  each block owns 32 cells; its 32 warps split the mode sum, a fixed-order reduction
-//           combines them, then one thread per cell applies the kicks (and the drift). The last
+// k_field:  each block owns 16 cells and splits their mode sums over 16 slices; a fixed-order
+//           reduction combines the slices, then the cells' atoms are kicked (and drifted) by the
+//           slices in parallel. The last
 //           block to finish sums the per-block energy partials in block order (deterministic)
 //           and appends the energies of the synchronised state to the history ring.
 // k_kick:   the same kicks, drift and energy record when the tensor-core back product has
@@ -24,8 +25,8 @@
 namespace {
 
 constexpr int PH_THREADS = 256;
-constexpr int FLD_CELLS = 32;
-constexpr int FLD_SLICES = 32;   // warps per block; each warp sums every 32nd mode for 32 cells
+constexpr int FLD_CELLS = 16;    // cells per block (N / 16 blocks fill every SM for N >= 2432)
+constexpr int FLD_SLICES = 16;   // mode slices: thread (cell, slice) sums every 16th mode of its cell
 constexpr int KICK_THREADS = 64;    // cells per block of the kick-only kernel
 
 __global__ void k_mode_functions(const double *__restrict__ k, const double *__restrict__ phi,
@@ -283,14 +284,15 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field(const StepArgs 
         kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
         edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
     }
-    if (cl == 0) {
-        red2[0][sl] = kin;   // red2 / red1 are free after the slice sums
-        red1[0][sl] = edf;
+    constexpr int NW = FLD_CELLS * FLD_SLICES / 32;
+    if ((threadIdx.x & 31) == 0) {
+        red2[0][threadIdx.x >> 5] = kin;   // red2 / red1 are free after the slice sums
+        red1[0][threadIdx.x >> 5] = edf;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double k = 0.0, d = 0.0;
-        for (int w = 0; w < FLD_SLICES; ++w) {
+        for (int w = 0; w < NW; ++w) {
             k += red2[0][w];
             d += red1[0][w];
         }
