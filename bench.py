@@ -325,7 +325,7 @@ def main():
         ctx.cavmd_step(1)
         ctx.cavmd_observables_into(o)
     e2e_s = time.perf_counter() - t0
-    d2h = 8 * (N + 3 * ctx.n_modes) + 8 * 8 + 4 * N + 4
+    d2h = 8 * (16 + N + 3 * ctx.n_modes)   # one packed copy: energies, max SCC iterations, status, M, q, p, D
     e2e = {"value": n_mol * args.e2e_steps * ws / e2e_s, "unit": "molecule-steps/s", "h2d_bytes_per_step": 0,
            "d2h_bytes_per_step": d2h,
            "note": "cavmd_step(1) + cavmd_observables (energies, per-cell dipoles, photon q/p/D) every step; "

@@ -63,6 +63,7 @@ struct cavmd_ctx {
     std::vector<void *> allocs;
     // host-side bookkeeping
     unsigned *h_status = nullptr;   // pinned
+    double *d_obs = nullptr, *h_obs = nullptr;   // packed observables, device and pinned host
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
     std::map<int, cudaGraphExec_t> graphs;   // keyed by the Born refresh phase of the first step
@@ -579,6 +580,7 @@ void release(cavmd_ctx *c) {
     }
     if (c->status_ev) cudaEventDestroy(c->status_ev);
     if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->h_obs) cudaFreeHost(c->h_obs);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -593,6 +595,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         c->own_stream = true;
     }
     CK(cudaMallocHost(&c->h_status, sizeof(unsigned)));
+    CK(cudaMallocHost(&c->h_obs, sizeof(double) * (16 + (size_t)c->N + 3 * (size_t)c->M)));
     CK(cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming));
 
     // host-side derived arrays
@@ -648,6 +651,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     const int fb = field_blocks(N);
     AL(c->d_ekp, fb); AL(c->d_edp, fb); AL(c->d_hist, 8 * (size_t)c->opt.energy_history);
     AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1);
+    AL(c->d_obs, 16 + (size_t)N + 3 * (size_t)M);
     // finite-difference copies: 3 per atom (forward) or 6 (central); n_disp counts them per water
     // cell for the water kernel, the generic kernel walks its own item list
     int disp_per_atom = 0;
@@ -899,10 +903,22 @@ int cavmd_step(cavmd_ctx *c, int64_t nsteps) {
 
 int cavmd_observables(cavmd_ctx *c, cavmd_obs *o) {
     if (!c || !o) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
-    int rc = sync_status(c);
-    double h[8];
+    // one packing kernel, one copy into pinned memory, one wait
     const int slot = (int)(c->step % c->opt.energy_history);
-    CK(cudaMemcpy(h, c->d_hist + 8 * (size_t)slot, sizeof(h), cudaMemcpyDeviceToHost));
+    const bool arrays = o->M || o->q || o->p || o->D;
+    const size_t cnt = 16 + (arrays ? (size_t)c->N + 3 * (size_t)c->M : 0);
+    CK(launch_obs_pack(c->d_hist + 8 * (size_t)slot, c->d_iters, c->N, c->d_status, c->d_Mc, c->d_qs, c->d_pqs,
+                       c->d_D, c->M, arrays, c->d_obs, c->stream));
+    CK(cudaMemcpyAsync(c->h_obs, c->d_obs, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->status_pending = false;
+    int rc = CAVMD_OK;
+    const unsigned st = (unsigned)c->h_obs[9];
+    if (st) {
+        CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+        rc = status_to_code(c, st);
+    }
+    const double *h = c->h_obs;
     o->e_kin = h[0];
     o->e_dftb = h[1];
     o->e_photon = h[2];
@@ -912,15 +928,12 @@ int cavmd_observables(cavmd_ctx *c, cavmd_obs *o) {
     o->e_total = h[6];
     o->temperature = 2.0 * h[0] / (3.0 * c->n_atoms * 3.166811563e-6);
     o->step = c->step;
-    std::vector<int> it(c->N);
-    CK(cudaMemcpy(it.data(), c->d_iters, sizeof(int) * c->N, cudaMemcpyDeviceToHost));
-    int mx = 0;
-    for (int v : it) mx = v > mx ? v : mx;
-    o->scc_iter_max = mx;
-    if (o->M) CK(cudaMemcpy(o->M, c->d_Mc, sizeof(double) * c->N, cudaMemcpyDeviceToHost));
-    if (o->q) CK(cudaMemcpy(o->q, c->d_qs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
-    if (o->p) CK(cudaMemcpy(o->p, c->d_pqs, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
-    if (o->D) CK(cudaMemcpy(o->D, c->d_D, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
+    o->scc_iter_max = (int32_t)h[8];
+    const size_t N = c->N, M = c->M;
+    if (o->M) std::memcpy(o->M, h + 16, sizeof(double) * N);
+    if (o->q) std::memcpy(o->q, h + 16 + N, sizeof(double) * M);
+    if (o->p) std::memcpy(o->p, h + 16 + N + M, sizeof(double) * M);
+    if (o->D) std::memcpy(o->D, h + 16 + N + 2 * M, sizeof(double) * M);
     return rc;
 }
 

@@ -203,5 +203,9 @@ enum { FLD_SECOND = 1, FLD_FIRST = 2, FLD_ENERGY = 4, FLD_E_GIVEN = 8, FLD_E1_ST
 cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st);
 int field_blocks(int N);
 // instantaneous field E_n = sum_a u_a(R_n) W_a for a caller-supplied weight vector
+// the observables of the synchronised state packed into one buffer (see couple_kernels.cu)
+cudaError_t launch_obs_pack(const double *hist_slot, const int *iters, int N, const unsigned *status,
+                            const double *Mc, const double *q, const double *p, const double *D, int M,
+                            bool with_arrays, double *out, cudaStream_t st);
 cudaError_t launch_field_only(const double *U, const double *W, int M, int N, double *E,
                               cudaStream_t st);

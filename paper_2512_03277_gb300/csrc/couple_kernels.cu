@@ -399,6 +399,46 @@ cudaError_t launch_trial_positions(const double *r, const double *p, const doubl
     return cudaGetLastError();
 }
 
+// Observables of the synchronised state packed for one device-to-host copy:
+// out[0..7] the energy record, out[8] the largest SCC iteration count, out[9] the status word,
+// then M (N), q, p, D (M each) from out[16].
+static __global__ void k_obs_pack(const double *__restrict__ hist_slot, const int *__restrict__ iters, int N,
+                                  const unsigned *__restrict__ status, const double *__restrict__ Mc,
+                                  const double *__restrict__ q, const double *__restrict__ p,
+                                  const double *__restrict__ D, int M, int with_arrays,
+                                  double *__restrict__ out) {
+    __shared__ int mx[8];
+    const int t = threadIdx.x;
+    int m = 0;
+    for (int n = t; n < N; n += blockDim.x) m = max(m, iters[n]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(CAVMD_FULL_MASK, m, o));
+    if ((t & 31) == 0) mx[t >> 5] = m;
+    if (t < 8) out[t] = hist_slot[t];
+    if (with_arrays) {
+        for (int n = t; n < N; n += blockDim.x) out[16 + n] = Mc[n];
+        for (int a = t; a < M; a += blockDim.x) {
+            out[16 + N + a] = q[a];
+            out[16 + N + M + a] = p[a];
+            out[16 + N + 2 * M + a] = D[a];
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        int r = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, mx[w]);
+        out[8] = (double)r;
+        out[9] = (double)*status;
+    }
+}
+
+cudaError_t launch_obs_pack(const double *hist_slot, const int *iters, int N, const unsigned *status,
+                            const double *Mc, const double *q, const double *p, const double *D, int M,
+                            bool with_arrays, double *out, cudaStream_t st) {
+    k_obs_pack<<<1, 1024, 0, st>>>(hist_slot, iters, N, status, Mc, q, p, D, M, with_arrays ? 1 : 0, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_field_only(const double *U, const double *W, int M, int N, double *E,
                               cudaStream_t st) {
     k_field_only<<<(N + 127) / 128, 128, 0, st>>>(U, W, M, N, E);
