@@ -293,23 +293,35 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     cudaError_t e;
     // The opening first half-flow: its field E1 was formed at the end of the previous call (or by
     // cavmd_init / cavmd_set_state) from the same synchronised state, so only the photon rotation
-    // and the kick and drift remain.
-    if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
-    if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
+    // and the kick and drift remain. Water systems fold them into the first step's launches: the
+    // SCC-DFTB kernel kicks and drifts the atoms of its cells before reading their positions, and
+    // the photon kernel rotates the modes before their second half-flow. The cluster kernel takes
+    // two launches of their own.
+    const bool fold = !c->generic;
+    if (!fold) {
+        if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
+        if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
+    }
     for (int64_t s = 0; s < n; ++s) {
         const bool last = (s == n - 1);
-        if ((e = run_dftb(c, 1)) != cudaSuccess) return e;
+        const int open = (fold && s == 0) ? PH_OPEN : 0;
+        c->da.E_open = open ? c->d_E1 : nullptr;
+        e = run_dftb(c, 1);
+        c->da.E_open = nullptr;
+        if (e != cudaSuccess) return e;
         if (born_refresh(c, first_step + s) && (e = run_born(c)) != cudaSuccess) return e;
         if (c->d_mlpw && (e = run_mlp(c)) != cudaSuccess) return e;
         if (c->mixed) {
             if ((e = run_tc_forward(c)) != cudaSuccess) return e;
-            if ((e = run_photon(c, PH_FORWARD_G | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) != cudaSuccess)
+            if ((e = run_photon(c, open | PH_FORWARD_G | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) !=
+                cudaSuccess)
                 return e;
             if ((e = run_tc_back(c, true, true)) != cudaSuccess) return e;   // E1 also for the next call
             if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | FLD_E_GIVEN | (last ? 0 : FLD_FIRST))) != cudaSuccess)
                 return e;
         } else {
-            if ((e = run_photon(c, PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) != cudaSuccess) return e;
+            if ((e = run_photon(c, open | PH_FORWARD | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) != cudaSuccess)
+                return e;
             if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | (last ? FLD_E1_STORE : FLD_FIRST))) != cudaSuccess) return e;
         }
         if ((e = run_acf(c)) != cudaSuccess) return e;
@@ -792,6 +804,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.step_counter = c->d_step; s.status = c->d_status; s.dt = c->opt.dt; s.tau = tau;
     s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->d_E2; s.E1in = c->d_E1; s.E1store = c->d_E1;
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
+    d.E_open = nullptr;   // set for the first evaluation of a call (water kernel)
+    d.p_open = c->d_p; d.r_open = c->d_r; d.inv_mass = c->d_imass; d.tau = tau; d.dt = c->opt.dt;
     return CAVMD_OK;
 }
 

@@ -62,6 +62,14 @@ struct DftbArgs {
     double fd_h;
     double *M_disp;            // [3 or 6 per atom] out: row k of the cell starting at atom a0 at 3 a0 + k (6 a0 + k)
     double *Qout;              // [n_atoms] out: Mulliken net charges (may be NULL)
+    // Opening half-flow of a call's first step, applied by the water kernel to the atoms of its
+    // cells before it reads their positions: p += tau F + E_n b, then r += dt p / m (the same
+    // arithmetic as the kick kernel). E_open = NULL: none.
+    const double *E_open;      // [N] field of the opening half-flow
+    double *p_open;            // [3 n_atoms] momenta, kicked in place
+    double *r_open;            // [3 n_atoms] positions, drifted in place (the array r points to)
+    const double *inv_mass;    // [n_atoms]
+    double tau, dt;
 };
 
 // Arguments of the coupling / integrator kernels.
@@ -193,8 +201,10 @@ cudaError_t launch_mode_functions(const double *k, const double *phi, const doub
                                   double *U, cudaStream_t st);
 // forward contraction of M_cell into D plus the photon half-flows (flags below)
 // PH_W1: weights of the next first half-flow from the synchronised state, without rotating
+// PH_OPEN (with PH_SECOND): apply the opening first half-flow of a call from the synchronised
+// state before the second, instead of a PH_FIRST launch of its own
 enum { PH_FORWARD = 1, PH_SECOND = 2, PH_FIRST = 4, PH_INIT_RELAXED = 8, PH_INIT_ZERO = 16,
-       PH_ENERGY = 32, PH_FORWARD_G = 64, PH_W1 = 128 };
+       PH_ENERGY = 32, PH_FORWARD_G = 64, PH_W1 = 128, PH_OPEN = 256 };
 cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st);
 // field on the cells with weights W2 (second half-flow kick) and/or W1 (first half-flow kick +
 // drift); always records the energies of the synchronised state when FLD_ENERGY is set

@@ -67,10 +67,27 @@ __device__ __forceinline__ void put_weight(const StepArgs &a, float *Wt, int al,
     }
 }
 
+// Exact half-flow of one mode at frozen nuclei: rotation about the centre cen = D / omega by
+// omega tau (c = cos, s = sin), and the field weight lam [y sin + p (1 - cos) / omega] of the
+// same half-flow. Every rounding is explicit (no multiply-add contraction left to the compiler),
+// so the rotation applied at the end of a step and the one applied at the opening of the next
+// call give the same bits.
+__device__ __forceinline__ void mode_half_flow(double q, double p, double cen, double c, double s, double w,
+                                               double iw, double &qo, double &po) {
+    const double y = __dsub_rn(q, cen);
+    qo = __dadd_rn(cen, fma(y, c, __dmul_rn(__dmul_rn(p, s), iw)));
+    po = fma(p, c, __dmul_rn(__dmul_rn(-w, y), s));
+}
+__device__ __forceinline__ double mode_weight(double q, double p, double cen, double s, double omc, double lam) {
+    return __dmul_rn(lam, fma(__dsub_rn(q, cen), s, __dmul_rn(p, omc)));
+}
+
 __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {
     __shared__ double red[PH_THREADS / 32];
     const int al = blockIdx.x;
     double D = 0.0;
+    // PH_OPEN: the field of the synchronised state, read before the forward replaces it
+    const double D_sync = ((flags & PH_OPEN) && threadIdx.x == 0) ? a.D[al] : 0.0;
     if (flags & PH_FORWARD) {
         const double *u = a.U + (size_t)al * a.N;
         double s = 0.0;
@@ -96,7 +113,7 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
     if (threadIdx.x != 0) return;
     const double w = a.omega[al], iw = a.inv_omega[al], lam = a.lam[al];
     const double c = a.cos_h[al], s = a.sin_h[al], omc = a.omc_h[al];
-    const double cen = D * iw;
+    const double cen = __dmul_rn(D, iw);
     double qs, ps;
     if (flags & PH_INIT_RELAXED) {
         qs = cen;
@@ -105,12 +122,16 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         qs = 0.0;
         ps = 0.0;
     } else if (flags & PH_SECOND) {
-        const double q = a.q[al], p = a.pq[al];
-        const double y = q - cen;
-        a.W2[al] = lam * fma(y, s, p * omc);
+        double q, p;
+        if (flags & PH_OPEN)   // the opening first half-flow (as a PH_FIRST launch of its own)
+            mode_half_flow(a.q_sync[al], a.pq_sync[al], __dmul_rn(D_sync, iw), c, s, w, iw, q, p);
+        else {
+            q = a.q[al];
+            p = a.pq[al];
+        }
+        a.W2[al] = mode_weight(q, p, cen, s, omc, lam);
         if (a.Wt2) put_weight(a, a.Wt2, al, a.W2[al]);
-        qs = cen + fma(y, c, p * s * iw);
-        ps = fma(p, c, -w * y * s);
+        mode_half_flow(q, p, cen, c, s, w, iw, qs, ps);
     } else {
         qs = a.q_sync[al];
         ps = a.pq_sync[al];
@@ -126,14 +147,14 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         e[3] = 0.5 * fma(ps, ps, (w * qs) * (w * qs));
     }
     if (flags & (PH_FIRST | PH_W1)) {
-        const double y = qs - cen;
-        a.W1[al] = lam * fma(y, s, ps * omc);
+        a.W1[al] = mode_weight(qs, ps, cen, s, omc, lam);
         if (a.Wt1) put_weight(a, a.Wt1, al, a.W1[al]);
     }
     if (flags & PH_FIRST) {
-        const double y = qs - cen;
-        a.q[al] = cen + fma(y, c, ps * s * iw);
-        a.pq[al] = fma(ps, c, -w * y * s);
+        double q1, p1;
+        mode_half_flow(qs, ps, cen, c, s, w, iw, q1, p1);
+        a.q[al] = q1;
+        a.pq[al] = p1;
     } else {
         a.q[al] = qs;
         a.pq[al] = ps;

@@ -161,11 +161,23 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
     const int a0 = a.cell_offset[cell];
 
     // ---------------------------------------------------------------- load geometry, layout
+    const bool open = a.E_open != nullptr && !disp;
+    double p_new[3], r_new[3];
     if (act && j < NAT) {
         m.spec[j] = a.species[a0 + j];
         m.pos[j][0] = a.r[3 * (a0 + j) + 0];
         m.pos[j][1] = a.r[3 * (a0 + j) + 1];
         m.pos[j][2] = a.r[3 * (a0 + j) + 2];
+        if (open) {   // opening half-flow: kick by tau F + E_n b, then drift (stored after the warp sync)
+            const int at = a0 + j;
+            const double e1 = a.E_open[cell], im = a.inv_mass[at];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                p_new[k] = fma(a.tau, a.F[3 * at + k], fma(e1, a.b[3 * at + k], a.p_open[3 * at + k]));
+                r_new[k] = fma(a.dt * im, p_new[k], m.pos[j][k]);
+                m.pos[j][k] = r_new[k];
+            }
+        }
         if (disp) {   // displaced copy: atom da, component dc, by +h (forward) or +-h (central)
             const int k = ridx - cidx * a.n_disp;
             const int kk = a.fd_central ? k >> 1 : k;
@@ -174,7 +186,15 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             if (j == da) m.pos[j][dc] += sg * a.fd_h;
         }
     }
-    __syncwarp();
+    __syncwarp();   // every lane of the warp has read the state it kicks before any is stored
+    if (open && valid && j < NAT) {
+        const int at = a0 + j;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a.p_open[3 * at + k] = p_new[k];
+            a.r_open[3 * at + k] = r_new[k];
+        }
+    }
     if (act && j == 0) {
         int o = 0;
         double nel = 0.0;
