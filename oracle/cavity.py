@@ -49,6 +49,26 @@ def mode_functions(k, phi, R):
     return np.cos(np.asarray(k) @ np.asarray(R).T + np.asarray(phi)[:, None])
 
 
+def mode_function_sines(k, phi, R):
+    """s[a, n] = sin(k_a . R_n + phi_a): grad u_a(R) = -k_a s_a(R)."""
+    return np.sin(np.asarray(k) @ np.asarray(R).T + np.asarray(phi)[:, None])
+
+
+def cell_centres(r, mass, off):
+    """Centre of mass of every cell, shape (N, 3)."""
+    r = np.asarray(r, float)
+    out = np.zeros((len(off) - 1, 3))
+    for n in range(len(off) - 1):
+        m = mass[off[n]:off[n + 1]]
+        out[n] = (m[:, None] * r[off[n]:off[n + 1]]).sum(0) / m.sum()
+    return out
+
+
+def field_gradient_on_cells(S, lam, k, w):
+    """G_n = sum_a lambda_a w_a grad u_a(R_n) = -sum_a lambda_a w_a k_a s_a(R_n), shape (N, 3)."""
+    return -S.T @ ((lam * w)[:, None] * np.asarray(k))
+
+
 def forward(U, lam, M):
     """D_a = lambda_a sum_n u_a(R_n) M_n."""
     return lam * (U @ M)
@@ -157,16 +177,40 @@ class HarmonicMatter:
 # ---------------------------------------------------------------------------- dynamics
 
 class CavityMD:
-    """State and time step of the coupled nuclei + photon system."""
+    """State and time step of the coupled nuclei + photon system.
+
+    mode_positions: "fixed" evaluates u_a at the reference cell positions R_ref (the paper's
+    boxes sit at fixed positions R_n); "com" evaluates it at every cell's instantaneous centre
+    of mass R_n(r) = sum_j m_j r_j / m_n, regenerated after every drift. Then D_a depends on the
+    nuclear positions through u_a(R_n) as well, and -dH_ph/dr_j gains
+        (m_j / m_n) M_n sum_a lambda_a (omega_a q_a - D_a) grad u_a(R_n),  grad u_a = -k_a sin(k_a.R + phi_a).
+    R_n is frozen during the exact H_2 flow, so that flow stays exact and its time-integrated
+    force gains the same term with Y_a in place of (omega_a q_a - D_a). Only the photon_exact
+    splitting supports it."""
 
     def __init__(self, matter, r, p, modes_k, omega, lam, phi, R_ref, dt, splitting="photon_exact",
-                 photon_init="relaxed", U=None):
+                 photon_init="relaxed", U=None, mode_positions="fixed"):
         self.matter = matter
         self.r = np.array(r, float)
         self.p = np.array(p, float)
         self.omega = np.asarray(omega, float)
         self.lam = np.asarray(lam, float)
-        self.U = mode_functions(modes_k, phi, R_ref) if U is None else np.asarray(U, float)
+        self.k = np.asarray(modes_k, float)
+        self.phi = np.asarray(phi, float)
+        if mode_positions not in ("fixed", "com"):
+            raise ValueError(mode_positions)
+        if mode_positions == "com" and (splitting != "photon_exact" or U is not None):
+            raise ValueError("moving mode positions need the photon_exact splitting and no given U")
+        self.moving = mode_positions == "com"
+        self.off = np.concatenate([[0], np.cumsum(np.bincount(matter.cell_of_atom))]).astype(int)
+        self.w_atom = None
+        if self.moving:
+            m = matter.mass
+            mc = np.bincount(matter.cell_of_atom, m)
+            self.w_atom = m / mc[matter.cell_of_atom]          # m_j / m_n
+            self._mode_functions()
+        else:
+            self.U = mode_functions(modes_k, phi, R_ref) if U is None else np.asarray(U, float)
         self.dt = float(dt)
         self.splitting = splitting
         self.cell = matter.cell_of_atom
@@ -183,9 +227,23 @@ class CavityMD:
     def _evaluate_matter(self):
         self.out = self.matter(self.r)
 
+    def _mode_functions(self):
+        """u_a and sin(k_a.R + phi_a) at the current cell centres of mass (moving positions)."""
+        self.R = cell_centres(self.r, self.matter.mass, self.off)
+        self.U = mode_functions(self.k, self.phi, self.R)
+        self.S = mode_function_sines(self.k, self.phi, self.R)
+
+    def _position_term(self, w):
+        """Force (or time-integrated force) on every nucleus through u_a(R_n): with weights
+        w_a = omega_a q_a - D_a (or Y_a), (m_j / m_n) M_n sum_a lambda_a w_a grad u_a(R_n)."""
+        G = field_gradient_on_cells(self.S, self.lam, self.k, w)
+        return (self.w_atom * self.out["M"][self.cell])[:, None] * G[self.cell]
+
     def _coupling_force(self):
         self.E_field = field_on_cells(self.U, self.lam, self.omega, self.q, self.D)
         self.F = self.out["F"] + self.E_field[self.cell][:, None] * self.out["b"]
+        if self.moving:
+            self.F = self.F + self._position_term(self.omega * self.q - self.D)
 
     def _kick(self, h):
         self.p += h * self.F
@@ -201,6 +259,8 @@ class CavityMD:
         Y = y * sn + p0 * (1.0 - cs) / w
         self.E_field = field_on_cells(self.U, self.lam, np.ones_like(w), Y, np.zeros_like(w))
         self.p += tau * self.out["F"] + self.E_field[self.cell][:, None] * self.out["b"]
+        if self.moving:
+            self.p += self._position_term(Y)
         self.q = c + y * cs + p0 * sn / w
         self.pq = p0 * cs - w * y * sn
 
@@ -210,6 +270,8 @@ class CavityMD:
         if self.splitting == "photon_exact":
             self._h2_flow(h)
             self.r += self.dt * self.p / m
+            if self.moving:
+                self._mode_functions()
             self._evaluate_matter()
             self.D = forward(self.U, self.lam, self.out["M"])
             self._h2_flow(h)
