@@ -73,6 +73,14 @@ enum { CAVMD_CHARGE_MULLIKEN = 0, CAVMD_CHARGE_BORN_FD = 1, CAVMD_CHARGE_BORN_CE
        CAVMD_CHARGE_BORN_MLP = 3 };
 enum { CAVMD_SPLIT_PHOTON_EXACT = 0, CAVMD_SPLIT_STRANG = 1, CAVMD_SPLIT_PAPER = 2 };
 enum { CAVMD_PHOTON_RELAXED = 0, CAVMD_PHOTON_ZERO = 1 };
+/* Where the mode functions u_a are evaluated. FIXED: at the cells' reference positions R_n (the
+ * paper's boxes sit at fixed positions, Eq. hlm2). CENTRE_OF_MASS: at every cell's instantaneous
+ * centre of mass R_n(t) = sum_j m_j r_j / m_n, regenerated after every drift. Then D_a also
+ * depends on the positions through u_a(R_n), and each nucleus j of cell n feels the extra force
+ * (m_j / m_n) M_n sum_a lambda_a (omega_a q_a - D_a) grad u_a(R_n). This extends the paper,
+ * whose boxes do not move. FP64 coupling only: with CAVMD_PREC_MIXED_BF16X3, cavmd_init returns
+ * CAVMD_ERR_UNSUPPORTED. Each step regenerates M x N mode functions and their sines (FP64 sincos). */
+enum { CAVMD_MODES_FIXED = 0, CAVMD_MODES_CENTRE_OF_MASS = 1 };
 
 /* The cells. Cell c owns atoms cell_offset[c] .. cell_offset[c+1]-1. Cells are
  * neutral and closed shell (sum of valence charges even). */
@@ -150,6 +158,7 @@ typedef struct {
     int32_t scc_history;        /* Anderson mixing history of the cluster kernel: the current and
                                    up to scc_history-1 previous iterates (1..6; 1 = linear mixing).
                                    Cells of 3 atoms / 6 orbitals use a fixed history of 3.        */
+    int32_t mode_positions;     /* CAVMD_MODES_FIXED (default) or CAVMD_MODES_CENTRE_OF_MASS    */
 } cavmd_options;
 
 /* Observables at the current (synchronised) time. Optional arrays may be NULL. */

@@ -48,6 +48,10 @@ struct cavmd_ctx {
     void *d_mlpw = nullptr;                  // bfloat16 network parameters
     bool mixed = false;                      // tensor-core coupling (modes on a grid)
     bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
+    bool moving = false;                     // mode functions at the cells' centres of mass
+    double *d_Us = nullptr, *d_Wk2 = nullptr, *d_Wk1 = nullptr, *d_watom = nullptr;
+    double *d_G1 = nullptr, *d_Ginst = nullptr;
+    std::vector<double> h_watom;             // m_j / m_n
     GenericPlan gplan{};
     long long *d_Coff = nullptr;             // eigenvector block of each cell (generic kernel)
     int water_warps = 2, water_per_warp = 5; // launch shape of the water kernel
@@ -263,6 +267,13 @@ cudaError_t run_photon(cavmd_ctx *c, int flags) {
     return launch_photon(c->sa, flags, c->stream);
 }
 
+// Mode functions and their sines at the current cell centres of mass (moving mode positions).
+cudaError_t run_modes(cavmd_ctx *c) {
+    PhaseScope ps(c, 1);
+    return launch_mode_functions_com(c->d_k, c->d_phi, c->d_r, c->d_mass, c->d_off, c->M, c->N, c->d_U, c->d_Us,
+                                     c->stream);
+}
+
 cudaError_t run_field(cavmd_ctx *c, int flags) {
     PhaseScope ps(c, 2);
     return launch_field(c->sa, flags, c->stream);
@@ -297,7 +308,7 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     // SCC-DFTB kernel kicks and drifts the atoms of its cells before reading their positions, and
     // the photon kernel rotates the modes before their second half-flow. The cluster kernel takes
     // two launches of their own.
-    const bool fold = !c->generic;
+    const bool fold = !c->generic && !c->moving;
     if (!fold) {
         if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
         if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
@@ -309,6 +320,7 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
         e = run_dftb(c, 1);
         c->da.E_open = nullptr;
         if (e != cudaSuccess) return e;
+        if (c->moving && (e = run_modes(c)) != cudaSuccess) return e;   // positions of this step
         if (born_refresh(c, first_step + s) && (e = run_born(c)) != cudaSuccess) return e;
         if (c->d_mlpw && (e = run_mlp(c)) != cudaSuccess) return e;
         if (c->mixed) {
@@ -423,6 +435,7 @@ int autotune(cavmd_ctx *c) {
 
 int initial_evaluation(cavmd_ctx *c, bool init_photons) {
     CK(run_dftb(c, 0));
+    if (c->moving) CK(run_modes(c));
     if (c->n_disp > 0) CK(run_born(c));
     if (c->d_mlpw) CK(run_mlp(c));
     int fwd = PH_FORWARD;
@@ -569,6 +582,10 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if (o->acf_lags < 0 || (o->autotune != 0 && o->autotune != 1))
         return fail(c, CAVMD_ERR_INVALID_ARG, "acf_lags must be >= 0 and autotune 0 or 1");
     if (o->scc_history < 1 || o->scc_history > 6) return fail(c, CAVMD_ERR_INVALID_ARG, "scc_history must be 1..6");
+    if (o->mode_positions != CAVMD_MODES_FIXED && o->mode_positions != CAVMD_MODES_CENTRE_OF_MASS)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "bad mode_positions");
+    if (o->mode_positions == CAVMD_MODES_CENTRE_OF_MASS && o->precision != CAVMD_PREC_FP64)
+        return fail(c, CAVMD_ERR_UNSUPPORTED, "moving mode positions need the FP64 coupling");
     if (o->precision == CAVMD_PREC_MIXED_BF16X3) {
         int Kx, Ky2;
         double dkx, dky;
@@ -656,6 +673,17 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N); AL(c->d_E1, N);
     c->mixed = c->opt.precision == CAVMD_PREC_MIXED_BF16X3;
     if (!c->mixed) AL(c->d_U, (size_t)M * N);
+    c->moving = c->opt.mode_positions == CAVMD_MODES_CENTRE_OF_MASS;
+    if (c->moving) {
+        AL(c->d_Us, (size_t)M * N); AL(c->d_Wk2, 3 * M); AL(c->d_Wk1, 3 * M); AL(c->d_watom, NA);
+        AL(c->d_G1, 3 * N); AL(c->d_Ginst, 3 * N);
+        c->h_watom.assign(NA, 0.0);
+        for (int n = 0; n < N; ++n) {
+            double mt = 0.0;
+            for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) mt += mass[i];
+            for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) c->h_watom[i] = mass[i] / mt;
+        }
+    }
     AL(c->d_k, 3 * M); AL(c->d_phi, M); AL(c->d_R, 3 * N);
     AL(c->d_omega, M); AL(c->d_lam, M); AL(c->d_iomega, M); AL(c->d_cos, M); AL(c->d_sin, M); AL(c->d_omc, M);
     AL(c->d_q, M); AL(c->d_pq, M); AL(c->d_qs, M); AL(c->d_pqs, M); AL(c->d_D, M);
@@ -693,6 +721,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemcpyAsync(c->d_p, sys->p, sizeof(double) * 3 * NA, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_mass, mass.data(), sizeof(double) * NA, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_imass, imass.data(), sizeof(double) * NA, cudaMemcpyHostToDevice, st));
+    if (c->moving)
+        CK(cudaMemcpyAsync(c->d_watom, c->h_watom.data(), sizeof(double) * NA, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_R, R.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_k, md->k, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_phi, md->phi, sizeof(double) * M, cudaMemcpyHostToDevice, st));
@@ -804,6 +834,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.step_counter = c->d_step; s.status = c->d_status; s.dt = c->opt.dt; s.tau = tau;
     s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->d_E2; s.E1in = c->d_E1; s.E1store = c->d_E1;
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
+    s.Us = c->d_Us; s.kvec = c->d_k; s.Wk2 = c->d_Wk2; s.Wk1 = c->d_Wk1; s.w_atom = c->d_watom;
+    s.G1store = c->d_G1; s.G1in = c->d_G1;   // all NULL with fixed mode positions
     d.E_open = nullptr;   // set for the first evaluation of a call (water kernel)
     d.p_open = c->d_p; d.r_open = c->d_r; d.inv_mass = c->d_imass; d.tau = tau; d.dt = c->opt.dt;
     return CAVMD_OK;
@@ -1058,13 +1090,24 @@ int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
             CK(launch_field_only(c->d_U, c->d_W1, c->M, c->N, c->d_Einst, c->stream));
         }
         CK(cudaStreamSynchronize(c->stream));
-        std::vector<double> E(N), F(3 * NA), b(3 * NA);
+        std::vector<double> E(N), F(3 * NA), b(3 * NA), G, Mn;
+        if (c->moving) {   // position term: (m_j / m_n) M_n sum_a W_a grad u_a(R_n)
+            CK(launch_field_grad_only(c->d_Us, c->d_W1, c->d_k, c->M, c->N, c->d_Ginst, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            G.resize(3 * N);
+            Mn.resize(N);
+            CK(cudaMemcpy(G.data(), c->d_Ginst, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(Mn.data(), c->d_Mc, sizeof(double) * N, cudaMemcpyDeviceToHost));
+        }
         CK(cudaMemcpy(E.data(), c->d_Einst, sizeof(double) * N, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(F.data(), c->d_F, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(b.data(), c->d_b, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
         for (size_t n = 0; n < N; ++n)
             for (int i = c->h_off[n]; i < c->h_off[n + 1]; ++i)
-                for (int k = 0; k < 3; ++k) o->F_total[3 * i + k] = F[3 * i + k] + E[n] * b[3 * i + k];
+                for (int k = 0; k < 3; ++k) {
+                    o->F_total[3 * i + k] = F[3 * i + k] + E[n] * b[3 * i + k];
+                    if (c->moving) o->F_total[3 * i + k] += c->h_watom[i] * Mn[n] * G[3 * n + k];
+                }
     }
     return rc;
 }

@@ -106,6 +106,14 @@ struct StepArgs {
     const double *E2in, *E1in; // [N] fields from the back product (FLD_E_GIVEN)
     double *E1store;           // [N] the next first half-flow's field, kept for the next call (FLD_E1_STORE)
     int Kx, Ky2, KY;
+    // moving mode positions (Us != NULL): u_a at the cell centres of mass, their sines, and the
+    // position term of the kicks, (m_j / m_n) M_n G_n with G_n = sum_a Wk_a sin(k_a.R_n + phi_a)
+    const double *Us;          // [M][N] sin(k_a.R_n + phi_a), row-major
+    const double *kvec;        // [M][3] wave vectors
+    double *Wk2, *Wk1;         // [M][3] -W_a k_a of the second / first half-flow (written by k_photon)
+    const double *w_atom;      // [n_atoms] m_j / m_n
+    double *G1store;           // [N][3] G_n of the next first half-flow, kept for the next call
+    const double *G1in;        // [N][3] G_n of the opening first half-flow (FLD_E_GIVEN)
 };
 
 // Plan of the tensor-core coupling contraction for modes on a uniform in-plane grid.
@@ -199,6 +207,12 @@ cudaError_t launch_mlp_born(int n_cells, const int *off, const float *Zl, const 
 cudaError_t launch_to_bf16(const float *src, void *dst, int n, cudaStream_t st);
 cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
                                   double *U, cudaStream_t st);
+// u_a and sin(k_a.R + phi_a) at the centres of mass of the cells (moving mode positions)
+cudaError_t launch_mode_functions_com(const double *k, const double *phi, const double *r, const double *mass,
+                                      const int *cell_offset, int M, int N, double *U, double *Us, cudaStream_t st);
+// G_n = -sum_a W_a k_a Us[a][n] for a given W (evaluation read-back)
+cudaError_t launch_field_grad_only(const double *Us, const double *W, const double *k, int M, int N, double *G,
+                                   cudaStream_t st);
 // forward contraction of M_cell into D plus the photon half-flows (flags below)
 // PH_W1: weights of the next first half-flow from the synchronised state, without rotating
 // PH_OPEN (with PH_SECOND): apply the opening first half-flow of a call from the synchronised

@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         }
         a.W2[al] = mode_weight(q, p, cen, s, omc, lam);
         if (a.Wt2) put_weight(a, a.Wt2, al, a.W2[al]);
+        if (a.Wk2)
+            for (int k = 0; k < 3; ++k) a.Wk2[3 * al + k] = -a.W2[al] * a.kvec[3 * al + k];
         mode_half_flow(q, p, cen, c, s, w, iw, qs, ps);
     } else {
         qs = a.q_sync[al];
@@ -149,6 +151,8 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
     if (flags & (PH_FIRST | PH_W1)) {
         a.W1[al] = mode_weight(qs, ps, cen, s, omc, lam);
         if (a.Wt1) put_weight(a, a.Wt1, al, a.W1[al]);
+        if (a.Wk1)
+            for (int k = 0; k < 3; ++k) a.Wk1[3 * al + k] = -a.W1[al] * a.kvec[3 * al + k];
     }
     if (flags & PH_FIRST) {
         double q1, p1;
@@ -199,6 +203,37 @@ __device__ __forceinline__ double kick_atom(const StepArgs &a, int flags, int j,
         kin = fma(0.5 * im * pj[k], pj[k], kin);
         if (flags & FLD_FIRST) {
             pj[k] = fma(a.tau, f[k], fma(e1, bb[k], pj[k]));
+            r[3 * j + k] = fma(a.dt * im, pj[k], rj[k]);
+        }
+        p[3 * j + k] = pj[k];
+    }
+    return kin;
+}
+
+// kick_atom with the position term of moving mode positions: wm = (m_j / m_n) M_n times G_n of
+// each half-flow (g2, g1: 3 components; g2 unused without FLD_SECOND, g1 without FLD_FIRST).
+__device__ __forceinline__ double kick_atom_moving(const StepArgs &a, int flags, int j, double e2, double e1,
+                                                   const double *g2, const double *g1, double wm) {
+    const double *__restrict__ F = a.F;
+    const double *__restrict__ b = a.b;
+    double *__restrict__ p = a.p;
+    double *__restrict__ r = a.r;
+    const double im = a.inv_mass[j];
+    double pj[3], f[3], bb[3], rj[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pj[k] = p[3 * j + k];
+        f[k] = F[3 * j + k];
+        bb[k] = b[3 * j + k];
+        rj[k] = (flags & FLD_FIRST) ? r[3 * j + k] : 0.0;
+    }
+    double kin = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (flags & FLD_SECOND) pj[k] = fma(wm, g2[k], fma(a.tau, f[k], fma(e2, bb[k], pj[k])));
+        kin = fma(0.5 * im * pj[k], pj[k], kin);
+        if (flags & FLD_FIRST) {
+            pj[k] = fma(wm, g1[k], fma(a.tau, f[k], fma(e1, bb[k], pj[k])));
             r[3 * j + k] = fma(a.dt * im, pj[k], rj[k]);
         }
         p[3 * j + k] = pj[k];
@@ -339,7 +374,15 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(const StepArgs a, const i
     if (n < a.N) {
         const double e2 = (flags & FLD_SECOND) ? a.E2in[n] : 0.0;
         const double e1 = (flags & FLD_FIRST) ? a.E1in[n] : 0.0;
-        kick_cell(a, flags, n, e2, e1, kin);
+        if (a.G1in) {   // moving mode positions: the opening first half-flow only
+            const double g0[3] = {0.0, 0.0, 0.0};
+            const double g1[3] = {a.G1in[3 * n], a.G1in[3 * n + 1], a.G1in[3 * n + 2]};
+            const double Mn = a.M_cell[n];
+            for (int j = a.cell_offset[n]; j < a.cell_offset[n + 1]; ++j)
+                kin += kick_atom_moving(a, flags, j, e2, e1, g0, g1, a.w_atom[j] * Mn);
+        } else {
+            kick_cell(a, flags, n, e2, e1, kin);
+        }
         edf = a.E_cell[n];
     }
     if (!(flags & FLD_ENERGY)) return;
@@ -372,6 +415,138 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(const StepArgs a, const i
     record_energies<KICK_THREADS>(a, flags, gridDim.x, scr);
 }
 
+// k_field for moving mode positions: besides E_n of both half-flows, the position-term vectors
+// G_n = sum_a Us[a][n] Wk_a (Wk_a = -W_a k_a, written by k_photon), summed over the same 16 mode
+// slices and combined in the same fixed order; the kicks add (m_j / m_n) M_n G_n.
+__global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field_moving(const StepArgs a, const int flags) {
+    __shared__ double red[8][FLD_SLICES][FLD_CELLS];   // e2, e1, G2 (3), G1 (3)
+    __shared__ double es[8][FLD_CELLS];
+    __shared__ bool last;
+    const int cl = threadIdx.x & (FLD_CELLS - 1);
+    const int sl = threadIdx.x / FLD_CELLS;
+    const int n = blockIdx.x * FLD_CELLS + cl;
+    const bool two = flags & FLD_SECOND, one = flags & (FLD_FIRST | FLD_E1_STORE);
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    if (n < a.N) {
+        const double *u = a.U + n, *us = a.Us + n;
+#pragma unroll 4
+        for (int al = sl; al < a.M; al += FLD_SLICES) {
+            const double c = u[(size_t)al * a.N], sn = us[(size_t)al * a.N];
+            if (two) {
+                v[0] = fma(c, __ldg(a.W2 + al), v[0]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v[2 + k] = fma(sn, __ldg(a.Wk2 + 3 * al + k), v[2 + k]);
+            }
+            if (one) {
+                v[1] = fma(c, __ldg(a.W1 + al), v[1]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) v[5 + k] = fma(sn, __ldg(a.Wk1 + 3 * al + k), v[5 + k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) red[i][sl][cl] = v[i];
+    __syncthreads();
+    if (sl == 0) {   // fixed-order slice sums of cell cl
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            for (int q = 1; q < FLD_SLICES; ++q) v[i] += red[i][q][cl];
+            es[i][cl] = v[i];
+        }
+        if ((flags & FLD_E1_STORE) && n < a.N) {
+            a.E1store[n] = v[1];
+            for (int k = 0; k < 3; ++k) a.G1store[3 * n + k] = v[5 + k];
+        }
+    }
+    __syncthreads();
+    double kin = 0.0, edf = 0.0;
+    if (n < a.N) {
+        const int j1 = a.cell_offset[n + 1];
+        const double Mn = a.M_cell[n];
+        for (int j = a.cell_offset[n] + sl; j < j1; j += FLD_SLICES) {
+            const double g2[3] = {es[2][cl], es[3][cl], es[4][cl]};
+            const double g1[3] = {es[5][cl], es[6][cl], es[7][cl]};
+            kin += kick_atom_moving(a, flags, j, es[0][cl], es[1][cl], g2, g1, a.w_atom[j] * Mn);
+        }
+        if (sl == 0) edf = a.E_cell[n];
+    }
+    if (!(flags & FLD_ENERGY)) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
+        edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
+    }
+    constexpr int NW = FLD_CELLS * FLD_SLICES / 32;
+    double *scr = &red[0][0][0];   // free after the slice sums
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        scr[threadIdx.x >> 5] = kin;
+        scr[NW + (threadIdx.x >> 5)] = edf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double k = 0.0, d = 0.0;
+        for (int w = 0; w < NW; ++w) {
+            k += scr[w];
+            d += scr[NW + w];
+        }
+        a.e_kin_part[blockIdx.x] = k;
+        a.e_dftb_part[blockIdx.x] = d;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.done_counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    record_energies<FLD_CELLS * FLD_SLICES>(a, flags, gridDim.x, scr);
+}
+
+// u_a(R_n) = cos(k_a.R_n + phi_a) and sin(k_a.R_n + phi_a) at the centres of mass of the cells:
+// thread = cell (its centre summed over the cell's atoms in order), MF_MODES modes per thread.
+constexpr int MF_MODES = 16;
+__global__ void k_mode_functions_com(const double *__restrict__ k, const double *__restrict__ phi,
+                                     const double *__restrict__ r, const double *__restrict__ mass,
+                                     const int *__restrict__ off, int M, int N, double *__restrict__ U,
+                                     double *__restrict__ Us) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double mt = 0.0, x0 = 0.0, x1 = 0.0, x2 = 0.0;
+    for (int j = off[n]; j < off[n + 1]; ++j) {
+        const double m = mass[j];
+        mt += m;
+        x0 = fma(m, r[3 * j], x0);
+        x1 = fma(m, r[3 * j + 1], x1);
+        x2 = fma(m, r[3 * j + 2], x2);
+    }
+    const double R0 = x0 / mt, R1 = x1 / mt, R2 = x2 / mt;
+    const int a1 = min(M, (int)(blockIdx.y + 1) * MF_MODES);
+    for (int al = blockIdx.y * MF_MODES; al < a1; ++al) {
+        const double th = fma(k[3 * al], R0, fma(k[3 * al + 1], R1, fma(k[3 * al + 2], R2, phi[al])));
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        U[(size_t)al * N + n] = cs;
+        Us[(size_t)al * N + n] = sn;
+    }
+}
+
+// G_n = -sum_a W_a k_a Us[a][n] (thread per cell; evaluation read-back only).
+__global__ void k_field_grad_only(const double *__restrict__ Us, const double *__restrict__ W,
+                                  const double *__restrict__ k, int M, int N, double *__restrict__ G) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int al = 0; al < M; ++al) {
+        const double w = -W[al] * Us[(size_t)al * N + n];
+        g0 = fma(w, k[3 * al], g0);
+        g1 = fma(w, k[3 * al + 1], g1);
+        g2 = fma(w, k[3 * al + 2], g2);
+    }
+    G[3 * n] = g0;
+    G[3 * n + 1] = g1;
+    G[3 * n + 2] = g2;
+}
+
 __global__ void k_field_only(const double *__restrict__ U, const double *__restrict__ W, int M, int N,
                              double *__restrict__ E) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -392,6 +567,19 @@ cudaError_t launch_mode_functions(const double *k, const double *phi, const doub
     return cudaGetLastError();
 }
 
+cudaError_t launch_mode_functions_com(const double *k, const double *phi, const double *r, const double *mass,
+                                      const int *cell_offset, int M, int N, double *U, double *Us, cudaStream_t st) {
+    const dim3 grid((N + 127) / 128, (M + MF_MODES - 1) / MF_MODES);
+    k_mode_functions_com<<<grid, 128, 0, st>>>(k, phi, r, mass, cell_offset, M, N, U, Us);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_grad_only(const double *Us, const double *W, const double *k, int M, int N, double *G,
+                                   cudaStream_t st) {
+    k_field_grad_only<<<(N + 127) / 128, 128, 0, st>>>(Us, W, k, M, N, G);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st) {
     k_photon<<<a.M, PH_THREADS, 0, st>>>(a, flags);
     return cudaGetLastError();
@@ -402,6 +590,8 @@ int field_blocks(int N) { return (N + FLD_CELLS - 1) / FLD_CELLS; }   // >= the 
 cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st) {
     if (flags & FLD_E_GIVEN)
         k_kick<<<(a.N + KICK_THREADS - 1) / KICK_THREADS, KICK_THREADS, 0, st>>>(a, flags);
+    else if (a.Us)
+        k_field_moving<<<field_blocks(a.N), FLD_CELLS * FLD_SLICES, 0, st>>>(a, flags);
     else
         k_field<<<field_blocks(a.N), FLD_CELLS * FLD_SLICES, 0, st>>>(a, flags);
     return cudaGetLastError();

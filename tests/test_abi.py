@@ -134,3 +134,10 @@ def test_rejects_bad_options(lib, small):
     o = P.default_options()
     o.mixing = 1.5
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
+    o = P.default_options()
+    o.mode_positions = 2
+    assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
+    o = P.default_options()
+    o.mode_positions = 1
+    o.precision = 2      # moving mode positions need the FP64 coupling
+    assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -8
