@@ -168,7 +168,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def _config(workload, w, charge_model="mulliken", precision="fp64"):
+def _config(workload, w, charge_model="mulliken", precision="fp64", mode_positions="fixed"):
     sy, mo = w["system"], w["modes"]
     nw = sy.n_atoms // 3
     cells = (f"{nw} water" if nw == sy.n_cells else
@@ -176,7 +176,8 @@ def _config(workload, w, charge_model="mulliken", precision="fp64"):
     cm = {"mulliken": "Mulliken", "born_fd": "forward-FD Born every 3 steps",
           "born_central": "central-FD Born every 3 steps", "born_mlp": "network Born charges"}[charge_model]
     cp = "FP64 coupling" if precision == "fp64" else "BF16x3 tensor-core coupling"
-    return {"workload": f"{workload}: {cells} x {mo.n_modes} modes, FP64 SCC-DFTB, {cm}, {cp}, dt 0.5 fs",
+    mp = ", mode functions at the moving cell centres of mass" if mode_positions == "com" else ""
+    return {"workload": f"{workload}: {cells} x {mo.n_modes} modes, FP64 SCC-DFTB, {cm}, {cp}{mp}, dt 0.5 fs",
             "n_cells": sy.n_cells, "n_molecules": nw, "n_atoms": sy.n_atoms, "n_modes": mo.n_modes, "precision": precision,
             "charge_model": charge_model, "l2": "256 MB buffer rewritten between timed steps (L2 flush)",
             "parallelism": "replicas"}
@@ -205,6 +206,8 @@ def main():
                     help="keep the default launch shapes instead of timing candidates at init")
     ap.add_argument("--scc-history", type=int, default=None,
                     help="Anderson history of the cluster kernel (default: the library's)")
+    ap.add_argument("--mode-positions", default="fixed", choices=["fixed", "com"],
+                    help="mode functions at the reference cell positions, or at the moving cell centres of mass")
     ap.add_argument("--acf-lags", type=int, default=None,
                     help="on-device autocorrelation lags (default: 1024 for c5, whose configuration asks for "
                          "it, else off)")
@@ -240,6 +243,7 @@ def main():
     if args.scc_history is not None:
         opt.scc_history = args.scc_history
     opt.autotune = 0 if args.no_autotune else 1
+    opt.mode_positions = 1 if args.mode_positions == "com" else 0
     if args.acf_lags is None:
         args.acf_lags = 1024 if args.workload == "c5" else 0
     opt.acf_lags = args.acf_lags
@@ -335,7 +339,7 @@ def main():
         "metric": "molecule-steps/s", "value": value, "unit": "molecule-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(args.workload, w, args.charge_model, args.precision),
+        "data": "synthetic", "config": _config(args.workload, w, args.charge_model, args.precision, args.mode_positions),
         "roofline": {"bound": "alu", "kernel": "k_dftb_generic" if generic else "dftb_kernel<3,6>",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": DFTB_DRAM_BYTES_PER_LAUNCH if (args.workload == "c2" and args.n_cells is None) else None,
@@ -350,6 +354,7 @@ def main():
                         + 2 * (int(phase_cnt[3]) if args.charge_model == "born_mlp" else 0)
                         + (int(phase_cnt[0]) if args.precision == "mixed" else 0),
         "acf_lags": args.acf_lags,
+        "mode_positions": args.mode_positions,
         "clocks": clk,
         "tuning": ctx.cavmd_tuning(),
         "wall_s_timed_region": t_wall,

@@ -51,6 +51,7 @@ struct cavmd_ctx {
     bool moving = false;                     // mode functions at the cells' centres of mass
     double *d_Us = nullptr, *d_Wk2 = nullptr, *d_Wk1 = nullptr, *d_watom = nullptr;
     double *d_G1 = nullptr, *d_Ginst = nullptr;
+    double *d_U0 = nullptr, *d_Us0 = nullptr;   // mode functions and sines at the reference positions
     std::vector<double> h_watom;             // m_j / m_n
     GenericPlan gplan{};
     long long *d_Coff = nullptr;             // eigenvector block of each cell (generic kernel)
@@ -270,8 +271,8 @@ cudaError_t run_photon(cavmd_ctx *c, int flags) {
 // Mode functions and their sines at the current cell centres of mass (moving mode positions).
 cudaError_t run_modes(cavmd_ctx *c) {
     PhaseScope ps(c, 1);
-    return launch_mode_functions_com(c->d_k, c->d_phi, c->d_r, c->d_mass, c->d_off, c->M, c->N, c->d_U, c->d_Us,
-                                     c->stream);
+    return launch_mode_functions_com(c->d_k, c->d_R, c->d_U0, c->d_Us0, c->d_r, c->d_mass, c->d_off, c->M, c->N,
+                                     c->d_U, c->d_Us, c->stream);
 }
 
 cudaError_t run_field(cavmd_ctx *c, int flags) {
@@ -676,6 +677,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     c->moving = c->opt.mode_positions == CAVMD_MODES_CENTRE_OF_MASS;
     if (c->moving) {
         AL(c->d_Us, (size_t)M * N); AL(c->d_Wk2, 3 * M); AL(c->d_Wk1, 3 * M); AL(c->d_watom, NA);
+        AL(c->d_U0, (size_t)M * N); AL(c->d_Us0, (size_t)M * N);
         AL(c->d_G1, 3 * N); AL(c->d_Ginst, 3 * N);
         c->h_watom.assign(NA, 0.0);
         for (int n = 0; n < N; ++n) {
@@ -738,7 +740,10 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 8 * c->opt.energy_history, st));
     CK(cudaMemsetAsync(c->d_q, 0, sizeof(double) * M, st));
     CK(cudaMemsetAsync(c->d_pq, 0, sizeof(double) * M, st));
-    if (!c->mixed) {
+    if (c->moving) {
+        CK(launch_mode_functions_pair(c->d_k, c->d_phi, c->d_R, M, N, c->d_U0, c->d_Us0, st));
+        CK(cudaMemcpyAsync(c->d_U, c->d_U0, sizeof(double) * M * N, cudaMemcpyDeviceToDevice, st));
+    } else if (!c->mixed) {
         CK(launch_mode_functions(c->d_k, c->d_phi, c->d_R, M, N, c->d_U, st));
     } else {
         TcPlan &p = c->tc;

@@ -207,9 +207,14 @@ cudaError_t launch_mlp_born(int n_cells, const int *off, const float *Zl, const 
 cudaError_t launch_to_bf16(const float *src, void *dst, int n, cudaStream_t st);
 cudaError_t launch_mode_functions(const double *k, const double *phi, const double *R, int M, int N,
                                   double *U, cudaStream_t st);
-// u_a and sin(k_a.R + phi_a) at the centres of mass of the cells (moving mode positions)
-cudaError_t launch_mode_functions_com(const double *k, const double *phi, const double *r, const double *mass,
-                                      const int *cell_offset, int M, int N, double *U, double *Us, cudaStream_t st);
+// cos and sin of k_a.R_n + phi_a at given positions (moving mode positions: the reference functions)
+cudaError_t launch_mode_functions_pair(const double *k, const double *phi, const double *R, int M, int N, double *U,
+                                       double *Us, cudaStream_t st);
+// u_a and sin(k_a.R + phi_a) at the centres of mass of the cells, by angle addition from the
+// reference functions U0, Us0 at the positions R0 (moving mode positions)
+cudaError_t launch_mode_functions_com(const double *k, const double *R0, const double *U0, const double *Us0,
+                                      const double *r, const double *mass, const int *cell_offset, int M, int N,
+                                      double *U, double *Us, cudaStream_t st);
 // G_n = -sum_a W_a k_a Us[a][n] for a given W (evaluation read-back)
 cudaError_t launch_field_grad_only(const double *Us, const double *W, const double *k, int M, int N, double *G,
                                    cudaStream_t st);

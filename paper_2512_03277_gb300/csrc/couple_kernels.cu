@@ -502,10 +502,18 @@ __global__ void __launch_bounds__(FLD_CELLS *FLD_SLICES) k_field_moving(const St
     record_energies<FLD_CELLS * FLD_SLICES>(a, flags, gridDim.x, scr);
 }
 
-// u_a(R_n) = cos(k_a.R_n + phi_a) and sin(k_a.R_n + phi_a) at the centres of mass of the cells:
-// thread = cell (its centre summed over the cell's atoms in order), MF_MODES modes per thread.
+// u_a(R_n) = cos(k_a.R_n + phi_a) and sin(k_a.R_n + phi_a) at the centres of mass of the cells,
+// by angle addition from the same functions at the reference positions R0_n (U0, Us0, formed
+// once): with d = k_a.(R_n - R0_n), cos(t0 + d) = cos t0 cos d - sin t0 sin d and
+// sin(t0 + d) = sin t0 cos d + cos t0 sin d. A cell moves ~4e-3 bohr per step and optical wave
+// vectors are ~1e-4 / bohr, so d stays small: for |d| < 4e-3, cos d and sin d come from their
+// Taylor series to d^4 and d^5 (truncation below 1e-17), otherwise from sincos. d is measured
+// from the fixed reference every step, so nothing accumulates from step to step.
+// Thread = cell (its centre summed over the cell's atoms in order), MF_MODES modes per thread.
 constexpr int MF_MODES = 16;
-__global__ void k_mode_functions_com(const double *__restrict__ k, const double *__restrict__ phi,
+constexpr double MF_SERIES_MAX = 4e-3;
+__global__ void k_mode_functions_com(const double *__restrict__ k, const double *__restrict__ R0,
+                                     const double *__restrict__ U0, const double *__restrict__ Us0,
                                      const double *__restrict__ r, const double *__restrict__ mass,
                                      const int *__restrict__ off, int M, int N, double *__restrict__ U,
                                      double *__restrict__ Us) {
@@ -519,14 +527,37 @@ __global__ void k_mode_functions_com(const double *__restrict__ k, const double 
         x1 = fma(m, r[3 * j + 1], x1);
         x2 = fma(m, r[3 * j + 2], x2);
     }
-    const double R0 = x0 / mt, R1 = x1 / mt, R2 = x2 / mt;
+    const double d0 = x0 / mt - R0[3 * n], d1 = x1 / mt - R0[3 * n + 1], d2 = x2 / mt - R0[3 * n + 2];
     const int a1 = min(M, (int)(blockIdx.y + 1) * MF_MODES);
     for (int al = blockIdx.y * MF_MODES; al < a1; ++al) {
-        const double th = fma(k[3 * al], R0, fma(k[3 * al + 1], R1, fma(k[3 * al + 2], R2, phi[al])));
+        const double d = fma(k[3 * al], d0, fma(k[3 * al + 1], d1, k[3 * al + 2] * d2));
+        double sd, cd;
+        if (fabs(d) < MF_SERIES_MAX) {
+            const double d2s = d * d;
+            cd = fma(d2s, fma(d2s, 1.0 / 24.0, -0.5), 1.0);
+            sd = d * fma(d2s, fma(d2s, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+        } else {
+            sincos(d, &sd, &cd);
+        }
+        const size_t e = (size_t)al * N + n;
+        const double c0 = U0[e], s0 = Us0[e];
+        U[e] = fma(c0, cd, -s0 * sd);
+        Us[e] = fma(s0, cd, c0 * sd);
+    }
+}
+
+// cos and sin of k_a.R_n + phi_a at given positions (the reference functions, once).
+__global__ void k_mode_functions_pair(const double *__restrict__ k, const double *__restrict__ phi,
+                                      const double *__restrict__ R, int M, int N, double *__restrict__ U,
+                                      double *__restrict__ Us) {
+    const size_t total = (size_t)M * N;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int al = (int)(e / N), n = (int)(e - (size_t)al * N);
+        const double th = fma(k[3 * al], R[3 * n], fma(k[3 * al + 1], R[3 * n + 1], fma(k[3 * al + 2], R[3 * n + 2], phi[al])));
         double sn, cs;
         sincos(th, &sn, &cs);
-        U[(size_t)al * N + n] = cs;
-        Us[(size_t)al * N + n] = sn;
+        U[e] = cs;
+        Us[e] = sn;
     }
 }
 
@@ -567,10 +598,20 @@ cudaError_t launch_mode_functions(const double *k, const double *phi, const doub
     return cudaGetLastError();
 }
 
-cudaError_t launch_mode_functions_com(const double *k, const double *phi, const double *r, const double *mass,
-                                      const int *cell_offset, int M, int N, double *U, double *Us, cudaStream_t st) {
+cudaError_t launch_mode_functions_pair(const double *k, const double *phi, const double *R, int M, int N, double *U,
+                                       double *Us, cudaStream_t st) {
+    const long long total = (long long)M * N;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_mode_functions_pair<<<blocks, 256, 0, st>>>(k, phi, R, M, N, U, Us);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mode_functions_com(const double *k, const double *R0, const double *U0, const double *Us0,
+                                      const double *r, const double *mass, const int *cell_offset, int M, int N,
+                                      double *U, double *Us, cudaStream_t st) {
     const dim3 grid((N + 127) / 128, (M + MF_MODES - 1) / MF_MODES);
-    k_mode_functions_com<<<grid, 128, 0, st>>>(k, phi, r, mass, cell_offset, M, N, U, Us);
+    k_mode_functions_com<<<grid, 128, 0, st>>>(k, R0, U0, Us0, r, mass, cell_offset, M, N, U, Us);
     return cudaGetLastError();
 }
 

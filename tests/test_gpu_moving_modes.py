@@ -32,12 +32,12 @@ def P():
     return P
 
 
-def _workload(name="c2", n_cells=12, M=24, seed=7):
+def _workload(name="c2", n_cells=12, M=24, seed=7, kmin=0.1, kmax=0.3):
     w = cs.make_workload(name, n_cells=n_cells, n_modes=M)
     rng = np.random.default_rng(seed)
     mo = w["modes"]
     k = rng.normal(0.0, 1.0, (mo.n_modes, 3))
-    k *= rng.uniform(0.1, 0.3, (mo.n_modes, 1)) / np.linalg.norm(k, axis=1, keepdims=True)
+    k *= rng.uniform(kmin, kmax, (mo.n_modes, 1)) / np.linalg.norm(k, axis=1, keepdims=True)
     w = dict(w, modes=cs.Modes(k=k, omega=mo.omega, lam=4.0 * mo.lam, phi=rng.uniform(-np.pi, np.pi, mo.n_modes)))
     return w
 
@@ -93,6 +93,28 @@ def test_trajectory_matches_oracle(P, name, n, steps):
         np.testing.assert_allclose(st["pq"], md.pq, rtol=0, atol=tol * np.abs(md.pq).max() + 1e-15)
         np.testing.assert_allclose(ctx.cavmd_observables()["e_total"], md.energies()["total"], rtol=1e-11)
     assert np.abs(fixed.p - md.p).max() > 100 * tol * np.abs(md.p).max()   # 250x when written
+
+
+def test_small_phase_changes_take_the_series_path(P):
+    """Wave vectors of 0.01 to 0.03 / bohr: k.(R_n - R0_n) stays below 4e-3, so the mode functions
+    come from the Taylor series of the phase change (the optical case) rather than sincos."""
+    w = _workload(kmin=0.01, kmax=0.03)
+    ctx = _ctx(P, w, graph_chunk=0)
+    _, md = _oracle(w)
+    sy = w["system"]
+    x0 = sy.r.copy()
+    for s in range(6):
+        ctx.cavmd_step(1)
+        md.step()
+    R = OC.cell_centres(md.r, md.matter.mass, md.off)
+    assert np.abs((R - sy.R_ref) @ w["modes"].k.T).max() < 4e-3
+    st = ctx.cavmd_get_state()
+    tol = 6e-9
+    dr = md.r - x0
+    np.testing.assert_allclose(st["r"] - x0, dr, rtol=0, atol=tol * np.abs(dr).max())
+    np.testing.assert_allclose(st["p"], md.p, rtol=0, atol=tol * np.abs(md.p).max())
+    np.testing.assert_allclose(st["q"], md.q, rtol=0, atol=tol * np.abs(md.q).max())
+    np.testing.assert_allclose(ctx.cavmd_get_eval()["F_total"], md.F, rtol=0, atol=F_REL * np.abs(md.F).max())
 
 
 def test_graph_replay_is_bitwise_identical(P):
