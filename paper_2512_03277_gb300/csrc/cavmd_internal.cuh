@@ -200,7 +200,7 @@ cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const doub
 cudaError_t launch_mlp_features(int n_cells, const int *off, const int *species, const double *r, float *X,
                                 float *R, unsigned *status, cudaStream_t st);
 cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, const void *w_bf16, float *Zl,
-                               cudaStream_t st);
+                               unsigned *status, cudaStream_t st);
 cudaError_t prepare_mlp_forward();   // shared-memory attribute of the inference forward, once per process
 cudaError_t launch_mlp_born(int n_cells, const int *off, const float *Zl, const float *R, const double *Q,
                             double pol0, double pol1, double pol2, double *b, cudaStream_t st);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "cavmd_internal.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -187,110 +188,175 @@ __global__ void __launch_bounds__(NH) k_forward(int n, const float *__restrict__
     }
 }
 
-// Inference forward for the time step: the same arithmetic as k_forward (every output summed from
-// its bias over the inputs in increasing order, so the results are bitwise equal), mapped for
-// throughput. A persistent block keeps the BF16 weights in shared memory (transposed, input-major),
-// takes tiles of TA = 32 atoms, and every thread computes a 4-atom x 4-unit register tile per layer:
-// per input it loads one float4 of activations (feature-major layout) and four BF16 weights, and
-// issues 16 FMAs. Weights widen to FP32 by a 16-bit shift.
-constexpr int TA = 32;
-constexpr int FT = 256;
-constexpr size_t FWD_SMEM = (size_t)NF * NH * 2 + (size_t)NH * NH * 2 + (size_t)NO * NH * 4 + (2 * NH + 16) * 4 +
-                            (size_t)NF * TA * 4 + 2 * (size_t)NH * TA * 4 + (size_t)TA * NO * 4;
+// Inference forward for the time step on the fifth-generation tensor cores (tcgen05). A tile of
+// 128 atoms sits on the 128 TMEM lanes and each layer is one BF16 MMA chain D = A B^T with FP32
+// accumulation in TMEM:
+//   A = the layer input, 128 atoms x K, split into three BF16 parts: hi + mid + lo carries a
+//       float's 24-bit significand, so A B^T equals the FP32 products to accumulation rounding;
+//   B = the layer's BF16 weights (exact), N outputs x K, K-major core matrices.
+// L1: K = 32, N = 128 into TMEM columns 0..127; L2: K = 128, N = 128 into columns 128..255;
+// L3: K = 128, N = 16 (the 9 outputs, zero-padded) into columns 0..15, free again once L1's
+// epilogue has read them. The epilogues read TMEM (warp w: lanes 32 (w mod 4) .. + 31, columns
+// 64 (w div 4) .. + 63), add the bias, apply silu and write the next layer's split operand to
+// shared memory; the last forms Zl = R^T T R for its atom. One persistent CTA per SM loads the
+// weights once; every mbarrier wait is bounded (timeout: status bit, TMEM still released).
+constexpr int MT = 128;                              // atoms per tile = TMEM lanes
+constexpr int FWD_THREADS = 256;
+constexpr uint32_t LBO_A = (MT / 8) * 128;           // A operand: K-group stride (128 rows)
+constexpr uint32_t LBO_W = (NH / 8) * 128;           // W1, W2: 128 rows
+constexpr uint32_t LBO_W3 = (16 / 8) * 128;          // W3 padded to 16 rows
+constexpr uint32_t A_SPLIT = MT * NH * 2;            // one BF16 part of A, K up to 128
+constexpr uint32_t SW1 = NH * NF * 2, SW2 = NH * NH * 2, SW3 = 16 * NH * 2;
+constexpr size_t FWD_SMEM = SW1 + SW2 + SW3 + 3 * (size_t)A_SPLIT + (2 * NH + 16) * 4 + 64;
+static_assert(NF % 16 == 0 && NH % 16 == 0, "MMA K steps of 16");
 
-__device__ __forceinline__ void bf16x4(const unsigned short *p, float w[4]) {
-    const uint2 v = *reinterpret_cast<const uint2 *>(p);
-    w[0] = __uint_as_float(v.x << 16);
-    w[1] = __uint_as_float(v.x & 0xffff0000u);
-    w[2] = __uint_as_float(v.y << 16);
-    w[3] = __uint_as_float(v.y & 0xffff0000u);
+// 8 consecutive K of one row of A, split into hi / mid / lo BF16 parts (16 bytes each).
+__device__ __forceinline__ void split_store8(uint8_t *sa, uint32_t off, const float (&x)[8]) {
+    __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        h[q] = __float2bfloat16_rn(x[q]);
+        const float r = x[q] - __bfloat162float(h[q]);   // exact
+        m[q] = __float2bfloat16_rn(r);
+        l[q] = __float2bfloat16_rn(r - __bfloat162float(m[q]));
+    }
+    *reinterpret_cast<uint4 *>(sa + off) = *reinterpret_cast<const uint4 *>(h);
+    *reinterpret_cast<uint4 *>(sa + A_SPLIT + off) = *reinterpret_cast<const uint4 *>(m);
+    *reinterpret_cast<uint4 *>(sa + 2 * A_SPLIT + off) = *reinterpret_cast<const uint4 *>(l);
 }
 
-// one dense layer of the tile: out[u][a] = silu(b[u] + sum_k W[u][k] in[k][a]) for 128 units u
-template <int K>
-__device__ __forceinline__ void tile_layer(const unsigned short *WT, const float *b, const float *in, float *out) {
-    const int ag = threadIdx.x & 7, hg = threadIdx.x >> 3;
-    float acc[4][4];
+// BF16 weights [rows][K] (row-major in the parameter vector) into the K-major core-matrix layout;
+// rows >= nrows are zero.
+__device__ __forceinline__ void load_weights(uint8_t *dst, const uint16_t *src, int rows, int nrows, int K,
+                                             uint32_t lbo) {
+    for (int c = threadIdx.x; c < rows * (K / 8); c += blockDim.x) {
+        const int g = c / rows, row = c - g * rows;
+        __align__(16) uint16_t v[8];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const float bb = b[4 * hg + h];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) acc[a][h] = bb;
+        for (int q = 0; q < 8; ++q) v[q] = row < nrows ? src[row * K + 8 * g + q] : (uint16_t)0;
+        *reinterpret_cast<uint4 *>(dst + tc::core_offset(row, 8 * g, lbo)) = *reinterpret_cast<const uint4 *>(v);
     }
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-        const float4 x = *reinterpret_cast<const float4 *>(in + k * TA + 4 * ag);
-        float w[4];
-        bf16x4(WT + k * NH + 4 * hg, w);
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-            acc[0][h] = fmaf(w[h], x.x, acc[0][h]);
-            acc[1][h] = fmaf(w[h], x.y, acc[1][h]);
-            acc[2][h] = fmaf(w[h], x.z, acc[2][h]);
-            acc[3][h] = fmaf(w[h], x.w, acc[3][h]);
-        }
-    }
-#pragma unroll
-    for (int h = 0; h < 4; ++h)
-        *reinterpret_cast<float4 *>(out + (4 * hg + h) * TA + 4 * ag) =
-            make_float4(silu(acc[0][h]), silu(acc[1][h]), silu(acc[2][h]), silu(acc[3][h]));
 }
 
-__global__ void __launch_bounds__(FT, 2) k_forward_tiled(int n, const float *__restrict__ X,
-                                                         const float *__restrict__ R,
-                                                         const __nv_bfloat16 *__restrict__ w,
-                                                         float *__restrict__ Zl) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    unsigned short *W1T = reinterpret_cast<unsigned short *>(sm);          // [NF][NH]
-    unsigned short *W2T = W1T + NF * NH;                                    // [NH][NH]
-    float *W3 = reinterpret_cast<float *>(W2T + NH * NH);                   // [NO][NH]
-    float *b1 = W3 + NO * NH, *b2 = b1 + NH, *b3 = b2 + NH;                 // b3: [16]
-    float *xT = b3 + 16;                                                    // [NF][TA]
-    float *h1T = xT + NF * TA, *h2T = h1T + NH * TA;                        // [NH][TA]
-    float *ys = h2T + NH * TA;                                              // [TA][NO]
-    const unsigned short *wr = reinterpret_cast<const unsigned short *>(w);
-    const int t = threadIdx.x;
-    for (int e = t; e < NH * NF; e += FT) W1T[(e % NF) * NH + e / NF] = wr[OFF_W1 + e];
-    for (int e = t; e < NH * NH; e += FT) W2T[(e % NH) * NH + e / NH] = wr[OFF_W2 + e];
-    for (int e = t; e < NO * NH; e += FT) W3[e] = wv(w, OFF_W3 + e);
-    for (int e = t; e < NH; e += FT) {
-        b1[e] = wv(w, OFF_B1 + e);
-        b2[e] = wv(w, OFF_B2 + e);
+// One layer's MMA chain (thread 0): D (+)= sum over K steps and the three parts of A.
+__device__ __forceinline__ void layer_mma(uint32_t tmem_d, uint32_t sa, uint32_t sw, uint32_t lbo_w, int K,
+                                          uint32_t idesc) {
+    for (int k = 0; k < K / 16; ++k) {
+        const uint64_t bd = tc::make_desc(sw + (uint32_t)k * 2 * lbo_w, lbo_w, 128);
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+            tc::mma_bf16(tmem_d, tc::make_desc(sa + s * A_SPLIT + (uint32_t)k * 2 * LBO_A, LBO_A, 128), bd, idesc,
+                         (k > 0 || s > 0) ? 1u : 0u);
     }
-    if (t < 16) b3[t] = t < NO ? wv(w, OFF_B3 + t) : 0.0f;
-    const int n_tiles = (n + TA - 1) / TA;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int t0 = tile * TA;
-        __syncthreads();   // weights ready; the previous tile is done with xT and ys
-        for (int e = t; e < TA * NF; e += FT) {
-            const int a = e / NF, i = e - a * NF;
-            xT[i * TA + a] = (t0 + a < n) ? X[(size_t)(t0 + a) * NF + i] : 0.0f;
+}
+
+// Hidden-layer epilogue: 64 TMEM columns of this thread's atom -> silu(d + b) -> split A operand.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, int col0, const float *b, uint8_t *sa, int row) {
+#pragma unroll
+    for (int c = 0; c < 64; c += 32) {
+        float v[32];
+        tc::tmem_ld32(taddr + (uint32_t)c, v);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = silu(v[8 * g + q] + b[col0 + c + 8 * g + q]);
+            split_store8(sa, tc::core_offset(row, col0 + c + 8 * g, LBO_A), x);
         }
-        __syncthreads();
-        tile_layer<NF>(W1T, b1, xT, h1T);
-        __syncthreads();
-        tile_layer<NH>(W2T, b2, h1T, h2T);
-        __syncthreads();
-        for (int e = t; e < TA * NO; e += FT) {
-            const int a = e % TA, o = e / TA;
-            float y = b3[o];
-            for (int v = 0; v < NH; ++v) y = fmaf(W3[o * NH + v], h2T[v * TA + a], y);
-            ys[a * NO + o] = y;
+    }
+}
+
+__global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const float *__restrict__ X,
+                                                             const float *__restrict__ R,
+                                                             const __nv_bfloat16 *__restrict__ w,
+                                                             float *__restrict__ Zl, unsigned *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sw1 = smem, *sw2 = sw1 + SW1, *sw3 = sw2 + SW2, *sa = sw3 + SW3;   // sa: [hi][mid][lo]
+    float *bias = reinterpret_cast<float *>(sa + 3 * A_SPLIT);                  // b1 [128] b2 [128] b3 [16]
+    uint64_t *done = reinterpret_cast<uint64_t *>(bias + 2 * NH + 16);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(slot, 256);
+    if (tid == 0) tc::mbar_init(done, 1);
+    const uint16_t *wr = reinterpret_cast<const uint16_t *>(w);
+    load_weights(sw1, wr + OFF_W1, NH, NH, NF, LBO_W);
+    load_weights(sw2, wr + OFF_W2, NH, NH, NH, LBO_W);
+    load_weights(sw3, wr + OFF_W3, 16, NO, NH, LBO_W3);
+    for (int e = tid; e < 2 * NH + 16; e += FWD_THREADS)
+        bias[e] = e < 2 * NH ? wv(w, (e < NH ? OFF_B1 : OFF_B2 - NH) + e) : (e - 2 * NH < NO ? wv(w, OFF_B3 + e - 2 * NH) : 0.0f);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t sa_u = tc::smem_u32(sa), sw1_u = tc::smem_u32(sw1), sw2_u = tc::smem_u32(sw2),
+                   sw3_u = tc::smem_u32(sw3);
+    const uint32_t quad = warp & 3, half = warp >> 2;
+    const uint32_t lanes = tmem + ((32u * quad) << 16);   // this warp's TMEM lanes
+    const int row = 32 * quad + lane;                      // this thread's atom in the tile
+    const float *b1 = bias, *b2 = bias + NH, *b3 = bias + 2 * NH;
+    constexpr uint32_t ID128 = tc::idesc_bf16(MT, NH), ID16 = tc::idesc_bf16(MT, 16);
+    const int n_tiles = (n + MT - 1) / MT;
+    uint32_t pd = 0u;
+    bool ok = true;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int t0 = t * MT;
+        // input features -> A (K = 32)
+        for (int c = tid; c < MT * (NF / 8); c += FWD_THREADS) {
+            const int g = c / MT, r = c - g * MT;
+            float x[8];
+            if (t0 + r < n) {
+                const float4 u0 = *reinterpret_cast<const float4 *>(X + (size_t)(t0 + r) * NF + 8 * g);
+                const float4 u1 = *reinterpret_cast<const float4 *>(X + (size_t)(t0 + r) * NF + 8 * g + 4);
+                x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
+                x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) x[q] = 0.0f;
+            }
+            split_store8(sa, tc::core_offset(r, 8 * g, LBO_A), x);
         }
-        __syncthreads();
-        if (t < TA && t0 + t < n) {
-            const float *Rj = R + (size_t)(t0 + t) * 9;
-            const float *yt = ys + t * NO;
-            // Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
-            for (int i = 0; i < 3; ++i)
-                for (int k = 0; k < 3; ++k) {
-                    float s = 0.0f;
-                    for (int aa = 0; aa < 3; ++aa)
-                        for (int bb = 0; bb < 3; ++bb) s = fmaf(Rj[3 * aa + i] * yt[3 * aa + bb], Rj[3 * bb + k], s);
-                    Zl[(size_t)(t0 + t) * 9 + 3 * i + k] = s;
+        for (int layer = 0; layer < 3; ++layer) {
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();   // the operand is in shared memory; the previous TMEM reads are done
+            if (tid == 0) {
+                tc::fence_after_sync();
+                if (layer == 0) layer_mma(tmem, sa_u, sw1_u, LBO_W, NF, ID128);
+                else if (layer == 1) layer_mma(tmem + NH, sa_u, sw2_u, LBO_W, NH, ID128);
+                else layer_mma(tmem, sa_u, sw3_u, LBO_W3, NH, ID16);
+                tc::mma_commit(done);
+            }
+            const bool mg = tc::mbar_wait(done, pd);
+            pd ^= 1u;
+            if (!__syncthreads_and(mg)) { ok = false; break; }
+            tc::fence_after_sync();
+            if (layer == 0) hidden_epilogue(lanes + 64 * half, 64 * half, b1, sa, row);
+            else if (layer == 1) hidden_epilogue(lanes + NH + 64 * half, 64 * half, b2, sa, row);
+            else if (half == 0) {   // outputs: Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
+                float v[32];
+                tc::tmem_ld32(lanes, v);
+                if (t0 + row < n) {
+                    float y[NO];
+#pragma unroll
+                    for (int o = 0; o < NO; ++o) y[o] = v[o] + b3[o];
+                    const float *Rj = R + (size_t)(t0 + row) * 9;
+                    for (int i = 0; i < 3; ++i)
+                        for (int k = 0; k < 3; ++k) {
+                            float s = 0.0f;
+                            for (int aa = 0; aa < 3; ++aa)
+                                for (int bb = 0; bb < 3; ++bb) s = fmaf(Rj[3 * aa + i] * y[3 * aa + bb], Rj[3 * bb + k], s);
+                            Zl[(size_t)(t0 + row) * 9 + 3 * i + k] = s;
+                        }
                 }
+            }
         }
+        if (!ok) break;
     }
+    if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 // per cell: Z = Q I + Zl - mean; with Zref: squared-error partial and gy = R (gZ - mean gZ) R^T
@@ -506,19 +572,19 @@ cudaError_t launch_mlp_features(int n_cells, const int *off, const int *species,
 }
 
 cudaError_t prepare_mlp_forward() {
-    return cudaFuncSetAttribute(k_forward_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM);
+    return cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM);
 }
 
 cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, const void *w_bf16, float *Zl,
-                               cudaStream_t st) {
+                               unsigned *status, cudaStream_t st) {
     if (n_atoms <= 0) return cudaSuccess;
     int dev = 0, n_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int tiles = (n_atoms + TA - 1) / TA;
-    const int grid = std::min(tiles, 2 * n_sm);
-    k_forward_tiled<<<grid, FT, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl);
+    const int tiles = (n_atoms + MT - 1) / MT;
+    const int grid = std::min(tiles, n_sm);
+    k_forward_tc<<<grid, FWD_THREADS, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl, status);
     return cudaGetLastError();
 }
 
@@ -726,7 +792,7 @@ int cavmd_mlp_train(cavmd_mlp *m, int32_t epochs, int32_t batch_cells, float lr,
 int cavmd_mlp_predict(cavmd_mlp *m, double *Z_out) {
     if (!m || !m->n_cells || !Z_out) return mlp_fail(m, CAVMD_ERR_INVALID_ARG, "no data or NULL output");
     MCK(cudaSetDevice(m->device));
-    MCK(launch_mlp_forward(m->n_atoms, m->X, m->R, m->w, m->Zl, m->stream));
+    MCK(launch_mlp_forward(m->n_atoms, m->X, m->R, m->w, m->Zl, m->status, m->stream));
     k_cell_tensors<<<(m->n_cells + 127) / 128, 128, 0, m->stream>>>(m->n_cells, m->off, m->Zl, m->R, m->Q, nullptr,
                                                                     0.0, m->Zout, nullptr, nullptr, 0, 0, 0, nullptr);
     MCK(cudaGetLastError());
