@@ -196,12 +196,12 @@ __global__ void __launch_bounds__(NH) k_forward(int n, const float *__restrict__
 //   B = the layer's BF16 weights (exact), N outputs x K, K-major core matrices.
 // L1: K = 32, N = 128 into TMEM columns 0..127; L2: K = 128, N = 128 into columns 128..255;
 // L3: K = 128, N = 16 (the 9 outputs, zero-padded) into columns 0..15, free again once L1's
-// epilogue has read them. The epilogues read TMEM (warp w: lanes 32 (w mod 4) .. + 31, columns
-// 64 (w div 4) .. + 63), add the bias, apply silu and write the next layer's split operand to
+// epilogue has read them. The epilogues read TMEM (warp w of 16: lanes 32 (w mod 4) .. + 31,
+// columns 32 (w div 4) .. + 31), add the bias, apply silu and write the next layer's split operand to
 // shared memory; the last forms Zl = R^T T R for its atom. One persistent CTA per SM loads the
 // weights once; every mbarrier wait is bounded (timeout: status bit, TMEM still released).
 constexpr int MT = 128;                              // atoms per tile = TMEM lanes
-constexpr int FWD_THREADS = 256;
+constexpr int FWD_THREADS = 512;                     // 16 warps: four per TMEM lane quadrant
 constexpr uint32_t LBO_A = (MT / 8) * 128;           // A operand: K-group stride (128 rows)
 constexpr uint32_t LBO_W = (NH / 8) * 128;           // W1, W2: 128 rows
 constexpr uint32_t LBO_W3 = (16 / 8) * 128;          // W3 padded to 16 rows
@@ -210,20 +210,36 @@ constexpr uint32_t SW1 = NH * NF * 2, SW2 = NH * NH * 2, SW3 = 16 * NH * 2;
 constexpr size_t FWD_SMEM = SW1 + SW2 + SW3 + 3 * (size_t)A_SPLIT + (2 * NH + 16) * 4 + 64;
 static_assert(NF % 16 == 0 && NH % 16 == 0, "MMA K steps of 16");
 
+// Two floats -> two BF16 (round to nearest even, one packed conversion) and their exact remainders.
+__device__ __forceinline__ uint32_t bf16x2_split(float &a, float &b) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    const uint32_t u = *reinterpret_cast<const uint32_t *>(&p);
+    a -= __uint_as_float(u << 16);              // low half holds a
+    b -= __uint_as_float(u & 0xffff0000u);
+    return u;
+}
+
 // 8 consecutive K of one row of A, split into hi / mid / lo BF16 parts (16 bytes each).
 __device__ __forceinline__ void split_store8(uint8_t *sa, uint32_t off, const float (&x)[8]) {
-    __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+    float r[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        h[q] = __float2bfloat16_rn(x[q]);
-        const float r = x[q] - __bfloat162float(h[q]);   // exact
-        m[q] = __float2bfloat16_rn(r);
-        l[q] = __float2bfloat16_rn(r - __bfloat162float(m[q]));
+    for (int q = 0; q < 8; ++q) r[q] = x[q];
+    uint4 part[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        part[s].x = bf16x2_split(r[0], r[1]);
+        part[s].y = bf16x2_split(r[2], r[3]);
+        part[s].z = bf16x2_split(r[4], r[5]);
+        part[s].w = bf16x2_split(r[6], r[7]);
     }
-    *reinterpret_cast<uint4 *>(sa + off) = *reinterpret_cast<const uint4 *>(h);
-    *reinterpret_cast<uint4 *>(sa + A_SPLIT + off) = *reinterpret_cast<const uint4 *>(m);
-    *reinterpret_cast<uint4 *>(sa + 2 * A_SPLIT + off) = *reinterpret_cast<const uint4 *>(l);
+    *reinterpret_cast<uint4 *>(sa + off) = part[0];
+    *reinterpret_cast<uint4 *>(sa + A_SPLIT + off) = part[1];
+    *reinterpret_cast<uint4 *>(sa + 2 * A_SPLIT + off) = part[2];
 }
+
+// silu with the reciprocal of the special-function unit (the training kernels divide exactly; the
+// two differ by a few ulp)
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // BF16 weights [rows][K] (row-major in the parameter vector) into the K-major core-matrix layout;
 // rows >= nrows are zero.
@@ -250,19 +266,16 @@ __device__ __forceinline__ void layer_mma(uint32_t tmem_d, uint32_t sa, uint32_t
     }
 }
 
-// Hidden-layer epilogue: 64 TMEM columns of this thread's atom -> silu(d + b) -> split A operand.
+// Hidden-layer epilogue: 32 TMEM columns of this thread's atom -> silu(d + b) -> split A operand.
 __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, int col0, const float *b, uint8_t *sa, int row) {
+    float v[32];
+    tc::tmem_ld32(taddr, v);
 #pragma unroll
-    for (int c = 0; c < 64; c += 32) {
-        float v[32];
-        tc::tmem_ld32(taddr + (uint32_t)c, v);
+    for (int g = 0; g < 4; ++g) {
+        float x[8];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            float x[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) x[q] = silu(v[8 * g + q] + b[col0 + c + 8 * g + q]);
-            split_store8(sa, tc::core_offset(row, col0 + c + 8 * g, LBO_A), x);
-        }
+        for (int q = 0; q < 8; ++q) x[q] = silu_fast(v[8 * g + q] + b[col0 + 8 * g + q]);
+        split_store8(sa, tc::core_offset(row, col0 + 8 * g, LBO_A), x);
     }
 }
 
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const floa
     const uint32_t tmem = *slot;
     const uint32_t sa_u = tc::smem_u32(sa), sw1_u = tc::smem_u32(sw1), sw2_u = tc::smem_u32(sw2),
                    sw3_u = tc::smem_u32(sw3);
-    const uint32_t quad = warp & 3, half = warp >> 2;
+    const uint32_t quad = warp & 3, slice = warp >> 2;   // lane quadrant; 32-column slice
     const uint32_t lanes = tmem + ((32u * quad) << 16);   // this warp's TMEM lanes
     const int row = 32 * quad + lane;                      // this thread's atom in the tile
     const float *b1 = bias, *b2 = bias + NH, *b3 = bias + 2 * NH;
@@ -331,9 +344,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const floa
             pd ^= 1u;
             if (!__syncthreads_and(mg)) { ok = false; break; }
             tc::fence_after_sync();
-            if (layer == 0) hidden_epilogue(lanes + 64 * half, 64 * half, b1, sa, row);
-            else if (layer == 1) hidden_epilogue(lanes + NH + 64 * half, 64 * half, b2, sa, row);
-            else if (half == 0) {   // outputs: Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
+            if (layer == 0) hidden_epilogue(lanes + 32 * slice, 32 * slice, b1, sa, row);
+            else if (layer == 1) hidden_epilogue(lanes + NH + 32 * slice, 32 * slice, b2, sa, row);
+            else if (slice == 0) {   // outputs: Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
                 float v[32];
                 tc::tmem_ld32(lanes, v);
                 if (t0 + row < n) {
