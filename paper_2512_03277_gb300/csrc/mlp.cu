@@ -64,10 +64,14 @@ __global__ void k_features(int n_cells, const int *__restrict__ off, const int *
             const float rk = sqrtf(dx * dx + dy * dy + dz * dz);
             if (!(rk < RC)) continue;
             const float fc = fcut(rk);
-            const int e = species[k];
+            const int e = species[k];   // radial channels: O (0) and H (1); every index below is constant
+            const float w0 = e == 0 ? fc : 0.0f, w1 = e == 1 ? fc : 0.0f;
+#pragma unroll
             for (int a = 0; a < 11; ++a) {
                 const float t = rk - (0.8f + 0.7f * a);
-                x[11 * e + a] += __expf(-2.0f * t * t) * fc;
+                const float g = __expf(-2.0f * t * t);
+                x[a] = fmaf(g, w0, x[a]);
+                x[11 + a] = fmaf(g, w1, x[11 + a]);
             }
             if (rk < r1 || (rk == r1 && k < k1)) { r2 = r1; k2 = k1; r1 = rk; k1 = k; }
             else if (rk < r2 || (rk == r2 && k < k2)) { r2 = rk; k2 = k; }
@@ -79,16 +83,25 @@ __global__ void k_features(int n_cells, const int *__restrict__ off, const int *
                 if (!(rl < RC)) continue;
                 const float cs = (dx * ex + dy * ey + dz * ez) / (rk * rl);
                 const float rad = __expf(-0.05f * (rk * rk + rl * rl)) * fc * fcut(rl);
-                const float zs[4] = {1.0f, 2.0f, 4.0f, 8.0f};
+                // 2^(1-z) (1 +- cos)^z for z = 1, 2, 4, 8: powers by repeated squaring
+                const float pre[4] = {1.0f, 0.5f, 0.125f, 0.0078125f};   // 2^(1-z)
+                float pp = 1.0f + cs, pm = fmaxf(1.0f - cs, 0.0f);
+#pragma unroll
                 for (int zi = 0; zi < 4; ++zi) {
-                    const float pre = exp2f(1.0f - zs[zi]);
-                    x[22 + 2 * zi] += pre * powf(1.0f + cs, zs[zi]) * rad;
-                    x[22 + 2 * zi + 1] += pre * powf(fmaxf(1.0f - cs, 0.0f), zs[zi]) * rad;
+                    if (zi > 0) {
+                        pp *= pp;
+                        pm *= pm;
+                    }
+                    x[22 + 2 * zi] = fmaf(pre[zi] * pp, rad, x[22 + 2 * zi]);
+                    x[22 + 2 * zi + 1] = fmaf(pre[zi] * pm, rad, x[22 + 2 * zi + 1]);
                 }
             }
         }
-        x[30 + species[j]] = 1.0f;
-        for (int i = 0; i < NF; ++i) X[(size_t)j * NF + i] = x[i];
+        x[30] = species[j] == 0 ? 1.0f : 0.0f;
+        x[31] = species[j] == 1 ? 1.0f : 0.0f;
+        float4 *Xj = reinterpret_cast<float4 *>(X + (size_t)j * NF);
+#pragma unroll
+        for (int i = 0; i < NF / 4; ++i) Xj[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
         float fr[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
         if (k2 >= 0) {
             float e1[3], v[3];
@@ -381,6 +394,31 @@ __global__ void k_cell_tensors(int n_cells, const int *__restrict__ off, const f
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     const int a0 = off[c], a1 = off[c + 1];
+    if (b && !Zref && !Zout) {
+        // the time step's b only: the network part in FP32 (the precision of Zl), then the FP64
+        // charge term, b_j = sum_a pol_a (Zl_j - mean)[a][.] + pol Q_j
+        float mf[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int j = a0; j < a1; ++j)
+#pragma unroll
+            for (int q = 0; q < 9; ++q) mf[q] += Zl[(size_t)j * 9 + q];
+        const float ic = 1.0f / (float)(a1 - a0);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) mf[q] *= ic;
+        const float pf[3] = {(float)pol0, (float)pol1, (float)pol2};
+        const double pol[3] = {pol0, pol1, pol2};
+        for (int j = a0; j < a1; ++j) {
+            const float *z = Zl + (size_t)j * 9;
+            const double Qj = Q[j];
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+                float sv = 0.0f;
+#pragma unroll
+                for (int aa = 0; aa < 3; ++aa) sv = fmaf(pf[aa], z[3 * aa + be] - mf[3 * aa + be], sv);
+                b[3 * j + be] = fma(pol[be], Qj, (double)sv);
+            }
+        }
+        return;
+    }
     const double cnt = (double)(a1 - a0);
     double mean[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = a0; j < a1; ++j)
