@@ -71,6 +71,13 @@ enum { CAVMD_SK_SS = 0, CAVMD_SK_SP = 1, CAVMD_SK_PPS = 2, CAVMD_SK_PPP = 3 };
 enum { CAVMD_PREC_FP64 = 0, CAVMD_PREC_MIXED_TF32 = 1, CAVMD_PREC_MIXED_BF16X3 = 2 };
 enum { CAVMD_CHARGE_MULLIKEN = 0, CAVMD_CHARGE_BORN_FD = 1, CAVMD_CHARGE_BORN_CENTRAL = 2,
        CAVMD_CHARGE_BORN_MLP = 3 };
+/* Time step. PHOTON_EXACT: H_2(dt/2), drift(dt), H_2(dt/2), with H_2 = V + H_ph solved exactly at
+ * frozen nuclei (each mode turns about its displaced centre; the nuclei take the time-integrated
+ * force). PAPER: the paper's order, Eq. pj1 then Step 3: half-kick the nuclei and the photon
+ * momenta with the instantaneous force (p_a += dt/2 omega_a D_a), drift, evaluate, half-kick again,
+ * then turn every mode freely by omega_a dt (Eq. qknk). With cells on a line lattice, modes on its
+ * DFT grid and a flat dispersion, PAPER reproduces the paper's real-space / reciprocal-space
+ * Steps 1-4 exactly. STRANG is not built (CAVMD_ERR_UNSUPPORTED). */
 enum { CAVMD_SPLIT_PHOTON_EXACT = 0, CAVMD_SPLIT_STRANG = 1, CAVMD_SPLIT_PAPER = 2 };
 enum { CAVMD_PHOTON_RELAXED = 0, CAVMD_PHOTON_ZERO = 1 };
 /* Where the mode functions u_a are evaluated. FIXED: at the cells' reference positions R_n (the

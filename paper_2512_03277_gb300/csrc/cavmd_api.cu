@@ -575,7 +575,10 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad charge_model");
     if (o->charge_model != CAVMD_CHARGE_MULLIKEN && (o->born_interval < 1 || !(o->fd_step > 0.0)))
         return fail(c, CAVMD_ERR_INVALID_ARG, "Born charges need born_interval >= 1 and fd_step > 0");
-    if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT) return fail(c, CAVMD_ERR_UNSUPPORTED, "only CAVMD_SPLIT_PHOTON_EXACT in this build");
+    if (o->splitting == CAVMD_SPLIT_STRANG)
+        return fail(c, CAVMD_ERR_UNSUPPORTED, "CAVMD_SPLIT_STRANG is not built; use PHOTON_EXACT or PAPER");
+    if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT && o->splitting != CAVMD_SPLIT_PAPER)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "bad splitting");
     if (o->photon_init != CAVMD_PHOTON_RELAXED && o->photon_init != CAVMD_PHOTON_ZERO)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
     if (o->graph_chunk < 0 || o->energy_history < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad graph_chunk or energy_history");
@@ -841,6 +844,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     s.Us = c->d_Us; s.kvec = c->d_k; s.Wk2 = c->d_Wk2; s.Wk1 = c->d_Wk1; s.w_atom = c->d_watom;
     s.G1store = c->d_G1; s.G1in = c->d_G1;   // all NULL with fixed mode positions
+    s.paper = c->opt.splitting == CAVMD_SPLIT_PAPER;
     d.E_open = nullptr;   // set for the first evaluation of a call (water kernel)
     d.p_open = c->d_p; d.r_open = c->d_r; d.inv_mass = c->d_imass; d.tau = tau; d.dt = c->opt.dt;
     return CAVMD_OK;

@@ -82,6 +82,63 @@ __device__ __forceinline__ double mode_weight(double q, double p, double cen, do
     return __dmul_rn(lam, fma(__dsub_rn(q, cen), s, __dmul_rn(p, omc)));
 }
 
+// The paper's step order (CAVMD_SPLIT_PAPER; Eq. pj1, then the rotation of Eq. qknk, Step 3): the
+// nuclei and photon momenta take half-kicks with the instantaneous force, p_a += h omega_a D_a and
+// field weights W_a = h lambda_a (omega_a q_a - D_a), h = dt/2; after the second half-kick each
+// mode turns freely by omega_a dt. The synchronised state is the rotated one. The same weights
+// feed the field, tensor-core and position-term kernels as the exact half-flows' do.
+__device__ __forceinline__ double paper_weight(double q, double D, double w, double lam, double h) {
+    return __dmul_rn(h * lam, fma(w, q, -D));
+}
+__device__ __forceinline__ void put_weights(const StepArgs &a, int al, double W, double *Wv, float *Wt, double *Wk) {
+    Wv[al] = W;
+    if (Wt) put_weight(a, Wt, al, W);
+    if (Wk)
+        for (int k = 0; k < 3; ++k) Wk[3 * al + k] = -W * a.kvec[3 * al + k];
+}
+__device__ __forceinline__ void photon_paper_order(const StepArgs &a, int flags, int al, double D, double D_sync,
+                                                   double w, double iw, double lam, double c, double s, double cen) {
+    const double h = a.tau, hw = h * w;
+    double qs, ps;
+    if (flags & PH_INIT_RELAXED) {
+        qs = cen;
+        ps = 0.0;
+    } else if (flags & PH_INIT_ZERO) {
+        qs = 0.0;
+        ps = 0.0;
+    } else if (flags & PH_SECOND) {
+        double q, p;
+        if (flags & PH_OPEN) {   // the opening first half-kick, from the synchronised state
+            q = a.q_sync[al];
+            p = fma(hw, D_sync, a.pq_sync[al]);
+        } else {
+            q = a.q[al];
+            p = a.pq[al];
+        }
+        put_weights(a, al, paper_weight(q, D, w, lam, h), a.W2, a.Wt2, a.Wk2);
+        p = fma(hw, D, p);
+        const double cdt = fma(c, c, -s * s), sdt = 2.0 * s * c;   // cos, sin of omega dt
+        qs = fma(q, cdt, p * sdt * iw);
+        ps = fma(p, cdt, -w * q * sdt);
+    } else {
+        qs = a.q_sync[al];
+        ps = a.pq_sync[al];
+    }
+    a.q_sync[al] = qs;
+    a.pq_sync[al] = ps;
+    if (flags & PH_ENERGY) {
+        const double x = fma(w, qs, -D);
+        double *e = a.e_mode + 4 * al;
+        e[0] = 0.5 * fma(ps, ps, x * x);
+        e[1] = -w * qs * D;
+        e[2] = 0.5 * D * D;
+        e[3] = 0.5 * fma(ps, ps, (w * qs) * (w * qs));
+    }
+    if (flags & (PH_FIRST | PH_W1)) put_weights(a, al, paper_weight(qs, D, w, lam, h), a.W1, a.Wt1, a.Wk1);
+    a.q[al] = qs;
+    a.pq[al] = (flags & PH_FIRST) ? fma(hw, D, ps) : ps;
+}
+
 __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {
     __shared__ double red[PH_THREADS / 32];
     const int al = blockIdx.x;
@@ -114,6 +171,10 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
     const double w = a.omega[al], iw = a.inv_omega[al], lam = a.lam[al];
     const double c = a.cos_h[al], s = a.sin_h[al], omc = a.omc_h[al];
     const double cen = __dmul_rn(D, iw);
+    if (a.paper) {
+        photon_paper_order(a, flags, al, D, D_sync, w, iw, lam, c, s, cen);
+        return;
+    }
     double qs, ps;
     if (flags & PH_INIT_RELAXED) {
         qs = cen;

@@ -1,0 +1,138 @@
+"""The paper's step order (splitting = CAVMD_SPLIT_PAPER): half-kicks with the instantaneous
+coupling force (Eq. pj1), drift, evaluation, half-kick, then the free rotation of every mode by
+omega dt (Eq. qknk, Step 3), against the FP64 oracle on the same seeded inputs.
+
+Two references:
+  * the oracle's k-space integrator with the same order (oracle/cavity.py, splitting="paper"),
+    for general modes;
+  * the oracle's real-space / reciprocal-space Steps 1-4 (oracle/paper_scheme.py): real-space
+    photon coordinates q_n per box, the local coupling eta q_n mu_n + eta^2 mu_n^2 / (2 omega_0^2),
+    a DFT to k-space, the rotation, and the DFT back. With cells on a line lattice, modes on its
+    DFT grid and a flat dispersion the two are the same dynamics, so the GPU must reproduce the
+    paper's own scheme.
+Tolerances are those of the other trajectory tests: 1e-9 (times the step number) of the largest
+displacement, momentum and photon coordinate."""
+import numpy as np
+import pytest
+
+import cavmd_synth as cs
+from oracle import cavity as OC
+from oracle import paper_scheme as PS
+
+pytestmark = pytest.mark.gpu
+PAPER = 2
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2512_03277_gb300 import build
+    build.build()
+    import paper_2512_03277_gb300 as P
+    P.load_library()
+    return P
+
+
+def _ctx(P, w, **opt):
+    o = P.default_options()
+    o.splitting = PAPER
+    for k, v in opt.items():
+        setattr(o, k, v)
+    return P.Context(w["system"], w["params"], w["modes"], o)
+
+
+def _check(st, md, x0, s):
+    tol = 1e-9 * (1 + s)
+    dr = md.r - x0
+    np.testing.assert_allclose(st["r"] - x0, dr, rtol=0, atol=tol * np.abs(dr).max())
+    np.testing.assert_allclose(st["p"], md.p, rtol=0, atol=tol * np.abs(md.p).max())
+    np.testing.assert_allclose(st["q"], md.q, rtol=0, atol=tol * np.abs(md.q).max())
+    np.testing.assert_allclose(st["pq"], md.pq, rtol=0, atol=tol * np.abs(md.pq).max() + 1e-15)
+
+
+@pytest.mark.parametrize("name,n,steps", [("c1", None, 20), ("c2", 37, 6)])
+def test_trajectory_matches_oracle_paper_order(P, name, n, steps):
+    w = cs.make_workload(name, n_cells=n)
+    sy, mo, pa = w["system"], w["modes"], w["params"]
+    ctx = _ctx(P, w, graph_chunk=0)
+    md = OC.CavityMD(OC.DFTBMatter(pa, sy), sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref,
+                     w["options"]["dt"], splitting="paper")
+    x0 = sy.r.copy()
+    for s in range(steps):
+        ctx.cavmd_step(1)
+        md.step()
+        _check(ctx.cavmd_get_state(), md, x0, s)
+        np.testing.assert_allclose(ctx.cavmd_observables()["e_total"], md.energies()["total"], rtol=1e-11)
+    # the order matters: the exact half-flows give another trajectory
+    ex = OC.CavityMD(OC.DFTBMatter(pa, sy), sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
+    for _ in range(steps):
+        ex.step()
+    assert np.abs(ex.q - md.q).max() > 1e3 * 1e-9 * steps * np.abs(md.q).max()
+
+
+def test_reproduces_the_papers_real_space_steps(P):
+    """8 waters on a line lattice (a = 12 bohr), the 8 modes of its DFT grid with a flat
+    dispersion: the GPU's k-space steps against the oracle's real-space Steps 1-4."""
+    params = cs.load_water_params()
+    N, a, w0, g0 = 8, 12.0, 0.012, 0.002
+    cent = np.stack([np.arange(N) * a, np.zeros(N), np.zeros(N)], 1)
+    pos = cs.water_batch(np.random.default_rng(2), cent)
+    sy = cs.systems._water_system(pos, cent)
+    sy.p = cs.mb_momenta(np.random.default_rng(3), sy, 300.0)
+    ks, ph, lam = [], [], []
+    for j in range(N // 2 + 1):
+        for s in ((0,) if j in (0, N // 2) else (0, 1)):
+            ks.append(2 * np.pi * j / (N * a))
+            ph.append(0.0 if s == 0 else -np.pi / 2)
+            lam.append(np.sqrt(2) * g0 if j in (0, N // 2) else 2 * g0)
+    K = np.zeros((N, 3))
+    K[:, 0] = ks
+    modes = cs.Modes(k=K, omega=np.full(N, w0), lam=np.array(lam), phi=np.array(ph))
+    dt = 0.5 * 41.341373335
+    w = {"system": sy, "modes": modes, "params": params}
+    ctx = _ctx(P, w, dt=dt, graph_chunk=0)
+    ps = PS.PaperRealSpaceMD(OC.DFTBMatter(params, sy), sy.r, sy.p, cent[:, 0],
+                             2 * np.pi * np.arange(N) / (N * a), np.full(N, w0), g0, w0, dt)
+    x0 = sy.r.copy()
+    for s in range(6):
+        ctx.cavmd_step(1)
+        ps.step()
+        st = ctx.cavmd_get_state()
+        tol = 1e-9 * (1 + s)
+        dr = ps.r - x0
+        np.testing.assert_allclose(st["r"] - x0, dr, rtol=0, atol=tol * np.abs(dr).max())
+        np.testing.assert_allclose(st["p"], ps.p, rtol=0, atol=tol * np.abs(ps.p).max())
+        np.testing.assert_allclose(ctx.cavmd_observables()["e_total"], ps.energies()["total"], rtol=1e-11)
+
+
+def test_graph_replay_is_bitwise_identical(P):
+    w = cs.make_workload("c2", n_cells=24, n_modes=32)
+    a = _ctx(P, w, graph_chunk=0)
+    b = _ctx(P, w, graph_chunk=4)
+    a.cavmd_step(9)
+    b.cavmd_step(9)
+    sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_mixed_coupling_tracks_fp64(P):
+    """The BF16x3 tensor-core coupling in the paper's order: ten steps stay within the bounds of
+    the exact-half-flow mixed test (1e-6 of the largest momentum, 1e-4 of the largest photon
+    coordinate, 1e-9 relative in the total energy). The kick-then-rotate order is stable only for
+    omega dt below about 1, so the modes are an 8 x 8 grid near the cavity fundamental
+    (omega ~ 0.01 Hartree, omega dt ~ 0.2), not config 4's grid (omega dt up to 1830)."""
+    w = cs.make_workload("c4", n_cells=256)
+    L = np.pi * cs.units.C_LIGHT / 0.01
+    w = dict(w, modes=cs.grid_modes(8, 8, 5e-6, 5e-6, L, 0.002))
+    assert w["modes"].omega.max() * w["options"]["dt"] < 0.3
+    a = _ctx(P, w, precision=0)
+    b = _ctx(P, w, precision=2)
+    a.cavmd_step(10)
+    b.cavmd_step(10)
+    sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
+    np.testing.assert_allclose(sb["p"], sa["p"], rtol=0, atol=1e-6 * np.abs(sa["p"]).max())
+    np.testing.assert_allclose(sb["q"], sa["q"], rtol=0, atol=1e-4 * np.abs(sa["q"]).max())
+    np.testing.assert_allclose(b.cavmd_observables()["e_total"], a.cavmd_observables()["e_total"], rtol=1e-9)
