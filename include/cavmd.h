@@ -217,12 +217,26 @@ int cavmd_init(cavmd_ctx **ctx, const cavmd_system *sys, const cavmd_sk_tables *
                const cavmd_modes *modes, const cavmd_options *opt);
 
 /* Advances nsteps >= 0 time steps (Steps 1-4 of the paper's loop, in k-space form). The work is
- * queued on the context's stream; the call returns once it is queued, with the status of the
- * work queued by the previous call (a non-convergence or a non-finite value found there). */
+ * queued on the context's stream and the call returns once it is queued, without waiting for
+ * earlier work. It returns the status of earlier work that has already finished (a
+ * non-convergence or a non-finite value found there). An error in work still running stays in the
+ * device status word: a later cavmd_step, cavmd_observables or cavmd_observables_wait reports it. */
 int cavmd_step(cavmd_ctx *ctx, int64_t nsteps);
 
 /* Waits for the queued work and copies the observables of the current time into *out. */
 int cavmd_observables(cavmd_ctx *ctx, cavmd_obs *out);
+
+/* The same read-out in two halves, so that the host reads step t while the GPU runs step t + 1.
+ * cavmd_observables_async queues, behind every step queued so far, the packing of the current
+ * observables (with the arrays M, q, p, D when with_arrays != 0) and their copy into the
+ * context's pinned staging slot `slot` (0 or 1), and returns at once. cavmd_observables_wait
+ * waits for that copy and fills *out as cavmd_observables does (out->step is the step at which the
+ * read-out was queued; array pointers must be NULL if the slot was queued without arrays).
+ * Alternate the two slots: queue slot s % 2 after step s, then wait for slot (s - 1) % 2.
+ * cavmd_observables itself uses slot 0. Errors: CAVMD_ERR_INVALID_ARG for a bad slot, a wait
+ * with nothing queued in the slot, or arrays requested from a slot queued without them. */
+int cavmd_observables_async(cavmd_ctx *ctx, int32_t slot, int32_t with_arrays);
+int cavmd_observables_wait(cavmd_ctx *ctx, int32_t slot, cavmd_obs *out);
 
 /* Copies the energy history: up to n most recent steps, 8 doubles each
  * (e_kin, e_dftb, e_photon, e_coupling, e_dse, e_photon_free, e_total, step), oldest first.

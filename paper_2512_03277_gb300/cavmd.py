@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH):
                                C.POINTER(cavmd_modes), C.POINTER(cavmd_options)]
     lib.cavmd_step.argtypes = [C.c_void_p, C.c_int64]
     lib.cavmd_observables.argtypes = [C.c_void_p, C.POINTER(cavmd_obs)]
+    lib.cavmd_observables_async.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+    lib.cavmd_observables_wait.argtypes = [C.c_void_p, C.c_int32, C.POINTER(cavmd_obs)]
     lib.cavmd_energy_history.argtypes = [C.c_void_p, _dp, C.c_int32, _ip]
     lib.cavmd_autocorrelation.argtypes = [C.c_void_p, _dp, C.c_int32, C.POINTER(C.c_int64), C.c_int32]
     lib.cavmd_tuning.argtypes = [C.c_void_p, C.c_char_p, C.c_int32]
@@ -325,6 +327,30 @@ class Context:
                   "temperature", "step", "scc_iter_max"):
             out[k] = getattr(o, k)
         return out
+
+    def cavmd_observables_async(self, slot: int, want_arrays: bool = True):
+        """Queue the read-out of the current observables into staging slot 0 or 1 (no wait)."""
+        _check(self.lib.cavmd_observables_async(self.handle, int(slot), int(want_arrays)), self.handle)
+
+    def cavmd_observables_wait(self, slot: int, want_arrays: bool = True):
+        """Wait for the read-out queued in `slot` and return it like cavmd_observables."""
+        o = cavmd_obs()
+        out = {}
+        if want_arrays:
+            out["M"] = np.empty(self.n_cells)
+            out["q"] = np.empty(self.n_modes)
+            out["p"] = np.empty(self.n_modes)
+            out["D"] = np.empty(self.n_modes)
+            o.M, o.q, o.p, o.D = _ptr(out["M"]), _ptr(out["q"]), _ptr(out["p"]), _ptr(out["D"])
+        _check(self.lib.cavmd_observables_wait(self.handle, int(slot), C.byref(o)), self.handle)
+        for k in ("e_kin", "e_dftb", "e_photon", "e_coupling", "e_dse", "e_photon_free", "e_total",
+                  "temperature", "step", "scc_iter_max"):
+            out[k] = getattr(o, k)
+        return out
+
+    def cavmd_observables_wait_into(self, slot: int, obs: cavmd_obs):
+        """cavmd_observables_wait into a pre-built cavmd_obs whose arrays the caller owns."""
+        _check(self.lib.cavmd_observables_wait(self.handle, int(slot), C.byref(obs)), self.handle)
 
     def cavmd_observables_into(self, obs: cavmd_obs):
         """Fill a pre-built cavmd_obs whose arrays the caller owns (no Python allocation)."""

@@ -69,6 +69,13 @@ struct cavmd_ctx {
     // host-side bookkeeping
     unsigned *h_status = nullptr;   // pinned
     double *d_obs = nullptr, *h_obs = nullptr;   // packed observables, device and pinned host
+    // the second read-out slot and the state of both (cavmd_observables_async / _wait)
+    double *d_obs1 = nullptr, *h_obs1 = nullptr;
+    cudaEvent_t obs_ev[2] = {nullptr, nullptr};   // a slot's copy has landed
+    cudaEvent_t obs_packed[2] = {nullptr, nullptr};   // a slot's snapshot is packed on the device
+    cudaStream_t copy_stream = nullptr;             // device-to-host copies of the read-out
+    bool obs_queued[2] = {false, false}, obs_arrays[2] = {false, false};
+    int64_t obs_step[2] = {0, 0};
     cudaEvent_t status_ev = nullptr;
     bool status_pending = false;
     std::map<int, cudaGraphExec_t> graphs;   // keyed by the Born refresh phase of the first step
@@ -614,6 +621,15 @@ void release(cavmd_ctx *c) {
     if (c->status_ev) cudaEventDestroy(c->status_ev);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->h_obs) cudaFreeHost(c->h_obs);
+    if (c->h_obs1) cudaFreeHost(c->h_obs1);
+    for (auto e : c->obs_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : c->obs_packed)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -629,7 +645,11 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     }
     CK(cudaMallocHost(&c->h_status, sizeof(unsigned)));
     CK(cudaMallocHost(&c->h_obs, sizeof(double) * (16 + (size_t)c->N + 3 * (size_t)c->M)));
+    CK(cudaMallocHost(&c->h_obs1, sizeof(double) * (16 + (size_t)c->N + 3 * (size_t)c->M)));
     CK(cudaEventCreateWithFlags(&c->status_ev, cudaEventDisableTiming));
+    for (auto &e : c->obs_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto &e : c->obs_packed) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
 
     // host-side derived arrays
     std::vector<double> mass(NA), imass(NA), R(3 * N);
@@ -697,6 +717,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     AL(c->d_ekp, fb); AL(c->d_edp, fb); AL(c->d_hist, 8 * (size_t)c->opt.energy_history);
     AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1);
     AL(c->d_obs, 16 + (size_t)N + 3 * (size_t)M);
+    AL(c->d_obs1, 16 + (size_t)N + 3 * (size_t)M);
     // finite-difference copies: 3 per atom (forward) or 6 (central); n_disp counts them per water
     // cell for the water kernel, the generic kernel walks its own item list
     int disp_per_atom = 0;
@@ -908,13 +929,17 @@ int cavmd_step(cavmd_ctx *c, int64_t nsteps) {
     if (!c) return fail(nullptr, CAVMD_ERR_INVALID_ARG, "NULL context");
     if (nsteps < 0) return fail(c, CAVMD_ERR_INVALID_ARG, "nsteps < 0");
     int rc = CAVMD_OK;
-    if (c->status_pending) {
-        CK(cudaEventSynchronize(c->status_ev));
-        c->status_pending = false;
-        const unsigned st = *c->h_status;
-        if (st) {
-            CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
-            rc = status_to_code(c, st);
+    if (c->status_pending) {   // the status of earlier work, only if it has finished: no wait here
+        const cudaError_t q = cudaEventQuery(c->status_ev);
+        if (q == cudaSuccess) {
+            c->status_pending = false;
+            const unsigned st = *c->h_status;
+            if (st) {
+                CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
+                rc = status_to_code(c, st);
+            }
+        } else if (q != cudaErrorNotReady) {
+            return cuda_fail(c, q, "cudaEventQuery");
         }
     }
     if (nsteps == 0) return rc;
@@ -956,24 +981,43 @@ int cavmd_step(cavmd_ctx *c, int64_t nsteps) {
     return rc;
 }
 
-int cavmd_observables(cavmd_ctx *c, cavmd_obs *o) {
-    if (!c || !o) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
-    // one packing kernel, one copy into pinned memory, one wait
-    const int slot = (int)(c->step % c->opt.energy_history);
-    const bool arrays = o->M || o->q || o->p || o->D;
+int cavmd_observables_async(cavmd_ctx *c, int32_t slot, int32_t with_arrays) {
+    if (!c || slot < 0 || slot > 1) return fail(c, CAVMD_ERR_INVALID_ARG, "slot must be 0 or 1");
+    // one packing kernel and one copy into the slot's pinned buffer, both queued behind the steps
+    const int hs = (int)(c->step % c->opt.energy_history);
+    const bool arrays = with_arrays != 0;
     const size_t cnt = 16 + (arrays ? (size_t)c->N + 3 * (size_t)c->M : 0);
-    CK(launch_obs_pack(c->d_hist + 8 * (size_t)slot, c->d_iters, c->N, c->d_status, c->d_Mc, c->d_qs, c->d_pqs,
-                       c->d_D, c->M, arrays, c->d_obs, c->stream));
-    CK(cudaMemcpyAsync(c->h_obs, c->d_obs, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    c->status_pending = false;
+    double *d = slot ? c->d_obs1 : c->d_obs, *h = slot ? c->h_obs1 : c->h_obs;
+    // the snapshot is packed in stream order (the next step overwrites what it reads); its copy to
+    // the host runs on a side stream, overlapping the next step. The slot's previous copy must have
+    // left the device buffer before it is packed again.
+    CK(cudaStreamWaitEvent(c->stream, c->obs_ev[slot], 0));
+    CK(launch_obs_pack(c->d_hist + 8 * (size_t)hs, c->d_iters, c->N, c->d_status, c->d_Mc, c->d_qs, c->d_pqs,
+                       c->d_D, c->M, arrays, d, c->stream));
+    CK(cudaEventRecord(c->obs_packed[slot], c->stream));
+    CK(cudaStreamWaitEvent(c->copy_stream, c->obs_packed[slot], 0));
+    CK(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->copy_stream));
+    CK(cudaEventRecord(c->obs_ev[slot], c->copy_stream));
+    c->obs_queued[slot] = true;
+    c->obs_arrays[slot] = arrays;
+    c->obs_step[slot] = c->step;
+    return CAVMD_OK;
+}
+
+int cavmd_observables_wait(cavmd_ctx *c, int32_t slot, cavmd_obs *o) {
+    if (!c || !o || slot < 0 || slot > 1) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument or bad slot");
+    if (!c->obs_queued[slot]) return fail(c, CAVMD_ERR_INVALID_ARG, "no read-out queued in this slot");
+    if ((o->M || o->q || o->p || o->D) && !c->obs_arrays[slot])
+        return fail(c, CAVMD_ERR_INVALID_ARG, "the read-out of this slot was queued without arrays");
+    CK(cudaEventSynchronize(c->obs_ev[slot]));
+    c->obs_queued[slot] = false;
+    const double *h = slot ? c->h_obs1 : c->h_obs;
     int rc = CAVMD_OK;
-    const unsigned st = (unsigned)c->h_obs[9];
+    const unsigned st = (unsigned)h[9];
     if (st) {
         CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream));
         rc = status_to_code(c, st);
     }
-    const double *h = c->h_obs;
     o->e_kin = h[0];
     o->e_dftb = h[1];
     o->e_photon = h[2];
@@ -982,13 +1026,21 @@ int cavmd_observables(cavmd_ctx *c, cavmd_obs *o) {
     o->e_photon_free = h[5];
     o->e_total = h[6];
     o->temperature = 2.0 * h[0] / (3.0 * c->n_atoms * 3.166811563e-6);
-    o->step = c->step;
+    o->step = c->obs_step[slot];
     o->scc_iter_max = (int32_t)h[8];
     const size_t N = c->N, M = c->M;
     if (o->M) std::memcpy(o->M, h + 16, sizeof(double) * N);
     if (o->q) std::memcpy(o->q, h + 16 + N, sizeof(double) * M);
     if (o->p) std::memcpy(o->p, h + 16 + N + M, sizeof(double) * M);
     if (o->D) std::memcpy(o->D, h + 16 + N + 2 * M, sizeof(double) * M);
+    return rc;
+}
+
+int cavmd_observables(cavmd_ctx *c, cavmd_obs *o) {
+    if (!c || !o) return fail(c, CAVMD_ERR_INVALID_ARG, "NULL argument");
+    int rc = cavmd_observables_async(c, 0, (o->M || o->q || o->p || o->D) ? 1 : 0);
+    if (rc) return rc;
+    rc = cavmd_observables_wait(c, 0, o);
     return rc;
 }
 
