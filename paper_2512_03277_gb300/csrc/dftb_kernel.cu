@@ -29,12 +29,6 @@ constexpr double MIN_GAP = 1e-3;       // closed-shell HOMO-LUMO threshold (Hart
 constexpr double EIG_TOL = 1e-10;      // occupied-virtual coupling treated as converged (Hartree)
 constexpr float KMAX_PERT = 1e-4f;     // largest generator entry for the second-order update
 
-// Index of the (t+1)-th set bit of mask (t = 0: the lowest).
-__device__ __forceinline__ int nth_bit(unsigned mask, int t) {
-    for (int s = 0; s < t; ++s) mask &= mask - 1u;
-    return __ffs(mask) - 1;
-}
-
 template <int NAT, int NORB>
 struct MolShared {
     static constexpr int LD = (NORB % 2 == 0) ? NORB + 1 : NORB;   // odd column stride
@@ -452,10 +446,9 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
 #pragma unroll
             for (int k = 0; k < NORB; ++k) m.Y[j * LD + k] = 0.0;
             const float dj = m.diagf[j];
-            const int no = __popc(other_mask);
             bool small = true;
-            for (int t = 0; t < no; ++t) {
-                const int k = nth_bit(other_mask, t);
+            for (unsigned om = other_mask; om; om &= om - 1u) {
+                const int k = __ffs(om) - 1;
                 const double akj = m.A[j * LD + k];
                 if (!abs_lt(akj, EIG_TOL)) small = false;
                 float kf = (float)akj / (dj - m.diagf[k]);
@@ -474,15 +467,14 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
                 // (K^2)(i, j) vanishes for rows i of the other block; for rows of j's own block it sums
                 // over the other block only: n_occ n_virt products per column, in increasing index
                 // order (the skipped terms are exact zeros). The row sums go to A, free here.
-                const int no = __popc(other_mask);
-                const int nprod = __popc(same_mask) * no;
-                double acc = 0.0;
-                for (int t = 0; t < nprod; ++t) {
-                    const int r = t / no, mi = t - r * no;
-                    const int i = nth_bit(same_mask, r), mm = nth_bit(other_mask, mi);
-                    if (mi == 0) acc = 0.0;
-                    acc = fma(m.Y[mm * LD + i], m.Y[j * LD + mm], acc);
-                    if (mi == no - 1) m.A[j * LD + i] = acc;
+                for (unsigned sm = same_mask; sm; sm &= sm - 1u) {
+                    const int i = __ffs(sm) - 1;
+                    double acc = 0.0;
+                    for (unsigned om = other_mask; om; om &= om - 1u) {
+                        const int mm = __ffs(om) - 1;
+                        acc = fma(m.Y[mm * LD + i], m.Y[j * LD + mm], acc);
+                    }
+                    m.A[j * LD + i] = acc;
                 }
                 double v[NORB];
 #pragma unroll
