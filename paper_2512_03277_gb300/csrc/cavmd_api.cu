@@ -476,6 +476,12 @@ void fill_devsk(const cavmd_sk_tables *t, DevSK *d) {
     std::memcpy(d->h0, t->h0, sizeof(d->h0));
     std::memcpy(d->s, t->s, sizeof(d->s));
     std::memcpy(d->rep, t->rep, sizeof(d->rep));
+    for (int x = 0; x < CAVMD_MAX_ELEM; ++x)   // host IEEE division and product: the device's bits
+        for (int y = 0; y < CAVMD_MAX_ELEM; ++y) {
+            const double s2 = t->hubbard[x] + t->hubbard[y];
+            const double cc = s2 != 0.0 ? 2.0 / s2 : 0.0;
+            d->gamma_c2[x][y] = cc * cc;
+        }
     d->r_cut = t->r_cut;
     d->taper = t->taper;
     d->inv_taper = 1.0 / t->taper;

@@ -18,6 +18,7 @@ struct DevSK {
     double h0[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][4][4];
     double s[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][4][4];
     double rep[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM][2];
+    double gamma_c2[CAVMD_MAX_ELEM][CAVMD_MAX_ELEM];   // (2 / (U_A + U_B))^2 of the Klopman-Ohno gamma
     int norb[CAVMD_MAX_ELEM];
     double r_cut, taper, inv_taper;
 };

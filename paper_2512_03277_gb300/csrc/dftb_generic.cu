@@ -307,13 +307,11 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
     }
     for (int e2 = j; e2 < nat * nat; e2 += T) {
         const int x = e2 / nat, y = e2 - x * nat;
-        const double Ua = sk.hubbard[spec[x]], Ub = sk.hubbard[spec[y]];
         if (x == y) {
-            gam[x * AM + y] = Ua;
+            gam[x * AM + y] = sk.hubbard[spec[x]];
         } else {
             const double dx = pos[y][0] - pos[x][0], dy = pos[y][1] - pos[x][1], dz = pos[y][2] - pos[x][2];
-            const double cc = 2.0 / (Ua + Ub);
-            gam[x * AM + y] = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, cc * cc))));
+            gam[x * AM + y] = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, sk.gamma_c2[spec[x]][spec[y]]))));
         }
     }
 
@@ -761,9 +759,7 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
             }
         }
         for (int k = 0; k < 3; ++k) gk[k] *= 2.0;
-        const double Ua = sk.hubbard[eA], Ub = sk.hubbard[eB];
-        const double cc = 2.0 / (Ua + Ub);
-        const double gi = rsqrt_nr(fma(r, r, cc * cc));
+        const double gi = rsqrt_nr(fma(r, r, sk.gamma_c2[eA][eB]));
         const double dgam = -r * gi * gi * gi;
         const double qq = (q[PA] - zv[PA]) * (q[PB] - zv[PB]) * dgam;
         const double arep = sk.rep[eA][eB][0], brep = sk.rep[eA][eB][1];

@@ -272,15 +272,13 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
         }
         if (j < NAT) {
             for (int k = 0; k < NAT; ++k) {
-                const double Ua = sk.hubbard[m.spec[j]], Ub = sk.hubbard[m.spec[k]];
                 if (k == j) {
-                    m.gam[j][k] = Ua;
+                    m.gam[j][k] = sk.hubbard[m.spec[j]];
                 } else {
                     const double dx = m.pos[k][0] - m.pos[j][0];
                     const double dy = m.pos[k][1] - m.pos[j][1];
                     const double dz = m.pos[k][2] - m.pos[j][2];
-                    const double cc = 2.0 / (Ua + Ub);
-                    m.gam[j][k] = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, cc * cc))));
+                    m.gam[j][k] = rsqrt_nr(fma(dx, dx, fma(dy, dy, fma(dz, dz, sk.gamma_c2[m.spec[j]][m.spec[k]]))));
                 }
             }
         }
@@ -799,9 +797,7 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             }
             for (int k = 0; k < 3; ++k) gk[k] *= 2.0;
             // second-order charge term and pair repulsion
-            const double Ua = sk.hubbard[eA], Ub = sk.hubbard[eB];
-            const double cc = 2.0 / (Ua + Ub);
-            const double gi = rsqrt_nr(fma(r, r, cc * cc));
+            const double gi = rsqrt_nr(fma(r, r, sk.gamma_c2[eA][eB]));
             const double dgam = -r * gi * gi * gi;
             const double qq = (m.q[A] - m.zv[A]) * (m.q[B] - m.zv[B]) * dgam;
             const double arep = sk.rep[eA][eB][0], brep = sk.rep[eA][eB][1];
