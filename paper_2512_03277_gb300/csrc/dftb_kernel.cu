@@ -54,6 +54,7 @@ struct MolShared {
     double hsh[NORB];     // half shift of the atom of each orbital
     float diagf[NORB];    // diagonal of A in FP32 (generator denominators)
     double gpair[NPAIR > 0 ? NPAIR : 1][3];
+    double gpart[2][NPAIR > 0 ? NPAIR : 1][3];   // H0 and S parts of the pair gradients
     double epair[NPAIR > 0 ? NPAIR : 1];
     double Hs[NORB * LD];   // H of the current SCC iteration
     int occ_list[NORB];
@@ -223,7 +224,9 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
     }
     __syncwarp();
     if (act) {
-        for (int pi = j; pi < NPAIR; pi += NORB) {
+        // one (pair, table) task per lane: the H0 and the S integrals of a pair on two lanes
+        for (int task = j; task < 2 * NPAIR; task += NORB) {
+            const int pi = task % NPAIR, t = task / NPAIR;
             const int A = m.pa[pi], B = m.pb[pi];
             const int eA = m.spec[A], eB = m.spec[B];
             const int oA = m.atom_off[A], oB = m.atom_off[B];
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             const double ir = rsqrt_nr(r2);
             const double r = r2 * ir;
             const double ev[3] = {dx * ir, dy * ir, dz * ir};
-            for (int t = 0; t < 2; ++t) {
+            {
                 const double (*tab)[CAVMD_MAX_ELEM][4][4] = t == 0 ? sk.h0 : sk.s;
                 double *X = t == 0 ? m.H0 : m.S;
                 double v, dv;
@@ -732,7 +735,10 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
     }
     __syncwarp();
     if (act) {
-        for (int pi = j; pi < NPAIR; pi += NORB) {
+        // one (pair, table) task per lane: the H0 part of a pair's gradient on one lane, its S
+        // part (with the second-order and repulsion terms) on another; combined below
+        for (int task = j; task < 2 * NPAIR; task += NORB) {
+            const int pi = task % NPAIR, t = task / NPAIR;
             const int A = m.pa[pi], B = m.pb[pi];
             const int eA = m.spec[A], eB = m.spec[B];
             const int oA = m.atom_off[A], oB = m.atom_off[B];
@@ -746,7 +752,7 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             const double e[3] = {dx * ir, dy * ir, dz * ir};
             const double hshift = 0.5 * (m.shift[A] + m.shift[B]);
             double gk[3] = {0.0, 0.0, 0.0};
-            for (int t = 0; t < 2; ++t) {
+            {
                 const double (*tab)[CAVMD_MAX_ELEM][4][4] = t == 0 ? sk.h0 : sk.s;
                 // weights of the (A, B) block: P for H0, P (eps_A + eps_B)/2 - W for S
                 auto wt = [&](int mu, int nu) -> double {
@@ -795,34 +801,39 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
                                  tr * e[k] * dvp;
                 }
             }
-            for (int k = 0; k < 3; ++k) gk[k] *= 2.0;
-            // second-order charge term and pair repulsion
-            const double gi = rsqrt_nr(fma(r, r, sk.gamma_c2[eA][eB]));
-            const double dgam = -r * gi * gi * gi;
-            const double qq = (m.q[A] - m.zv[A]) * (m.q[B] - m.zv[B]) * dgam;
-            const double arep = sk.rep[eA][eB][0], brep = sk.rep[eA][eB][1];
-            double erep = 0.0, derep = 0.0;
-            if (arep != 0.0) {
-                const double vr = arep * exp(-brep * r);
-                const double x = (r - (sk.r_cut - sk.taper)) * sk.inv_taper;
-                double f = 1.0, df = 0.0;
-                if (x > 0.0) {
-                    if (x < 1.0) {
-                        double sn, cn;
-                        sincospi(x, &sn, &cn);
-                        f = 0.5 * (1.0 + cn);
-                        df = -0.5 * 3.141592653589793 * sk.inv_taper * sn;
-                    } else {
-                        f = 0.0;
+            for (int k = 0; k < 3; ++k) m.gpart[t][pi][k] = gk[k];
+            if (t == 1) {
+                // second-order charge term and pair repulsion
+                const double gi = rsqrt_nr(fma(r, r, sk.gamma_c2[eA][eB]));
+                const double dgam = -r * gi * gi * gi;
+                const double qq = (m.q[A] - m.zv[A]) * (m.q[B] - m.zv[B]) * dgam;
+                const double arep = sk.rep[eA][eB][0], brep = sk.rep[eA][eB][1];
+                double erep = 0.0, derep = 0.0;
+                if (arep != 0.0) {
+                    const double vr = arep * exp(-brep * r);
+                    const double x = (r - (sk.r_cut - sk.taper)) * sk.inv_taper;
+                    double f = 1.0, df = 0.0;
+                    if (x > 0.0) {
+                        if (x < 1.0) {
+                            double sn, cn;
+                            sincospi(x, &sn, &cn);
+                            f = 0.5 * (1.0 + cn);
+                            df = -0.5 * 3.141592653589793 * sk.inv_taper * sn;
+                        } else {
+                            f = 0.0;
+                        }
                     }
+                    erep = vr * f;
+                    derep = vr * (df - brep * f);
                 }
-                erep = vr * f;
-                derep = vr * (df - brep * f);
+                for (int k = 0; k < 3; ++k) m.gpair[pi][k] = (qq + derep) * e[k];
+                m.epair[pi] = erep;
             }
-            for (int k = 0; k < 3; ++k) m.gpair[pi][k] = gk[k] + (qq + derep) * e[k];
-            m.epair[pi] = erep;
         }
     }
+    __syncwarp();
+    if (act && j < NPAIR)
+        for (int k = 0; k < 3; ++k) m.gpair[j][k] = fma(2.0, m.gpart[0][j][k] + m.gpart[1][j][k], m.gpair[j][k]);
     __syncwarp();
     if (valid && j < NAT) {
         double f[3] = {0.0, 0.0, 0.0};
