@@ -147,3 +147,14 @@ def test_rejects_bad_options(lib, small):
     o = P.default_options()
     o.splitting = 3
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
+
+
+def test_rejects_empty_inputs(lib, small):
+    """No cells, or no modes: refused on the host before any device work."""
+    s = small["system"]
+    empty = cs.System(species=np.zeros(0, np.int32), cell_offset=np.zeros(1, np.int32),
+                      r=np.zeros((0, 3)), p=np.zeros((0, 3)), R_ref=np.zeros((0, 3)))
+    assert _init_rc(lib, empty, small["params"], small["modes"])[0] == -1
+    mo = small["modes"]
+    none = cs.Modes(k=np.zeros((0, 3)), omega=np.zeros(0), lam=np.zeros(0), phi=np.zeros(0))
+    assert _init_rc(lib, s, small["params"], none)[0] == -1
