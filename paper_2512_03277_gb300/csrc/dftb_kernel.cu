@@ -58,6 +58,7 @@ struct MolShared {
     double epair[NPAIR > 0 ? NPAIR : 1];
     double Hs[NORB * LD];   // H of the current SCC iteration
     int occ_list[NORB];
+    int virt_list[NORB];
     int occf[NORB];       // orbital column j is occupied
     int eok[NORB];        // occupied-virtual couplings of column j were below EIG_TOL
     int orb_atom[NORB];
@@ -131,7 +132,7 @@ __device__ __forceinline__ void jacobi_cs(double app, double aqq, double apq, do
 }
 
 template <int NAT, int NORB>
-__global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a, const int gpw) {
+__global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ skp, const DftbArgs a, const int gpw) {
     const DevSK &sk = *skp;
     using SM = MolShared<NAT, NORB>;
     constexpr int LD = SM::LD;
@@ -409,15 +410,15 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             for (int i = 0; i < NORB; ++i) m.Y[j * LD + i] = y[i];
         }
         __syncwarp();
-        if (work) {   // A = C^T Y
-            double y[NORB];
-            for (int i = 0; i < NORB; ++i) {
-                double s = 0.0;
+        // A = C^T H C = C^T Y is formed only where the iteration needs it: its diagonal (aufbau,
+        // denominators) and its occupied-virtual block (generator, convergence), the latter as
+        // (occupied, virtual) pair tasks spread over the lanes and stored symmetric. The Jacobi
+        // path adds the other entries when it runs.
+        if (work) {
+            double s = 0.0;
 #pragma unroll
-                for (int k = 0; k < NORB; ++k) s = fma(m.C[i * LD + k], m.Y[j * LD + k], s);
-                y[i] = s;
-            }
-            for (int i = 0; i < NORB; ++i) m.A[j * LD + i] = y[i];
+            for (int k = 0; k < NORB; ++k) s = fma(m.C[j * LD + k], m.Y[j * LD + k], s);
+            m.A[j * LD + j] = s;
         }
         __syncwarp();
         // aufbau occupation from the diagonal of A
@@ -431,6 +432,20 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             }
             m.occf[j] = rank < m.nocc;
             if (rank < m.nocc) m.occ_list[rank] = j;
+            else m.virt_list[rank - m.nocc] = j;
+        }
+        __syncwarp();
+        if (work) {   // occupied-virtual block
+            const int nv = NORB - m.nocc;
+            for (int t = j; t < m.nocc * nv; t += NORB) {
+                const int oi = t / nv;
+                const int o = m.occ_list[oi], v = m.virt_list[t - oi * nv];
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < NORB; ++k) s = fma(m.C[v * LD + k], m.Y[o * LD + k], s);
+                m.A[o * LD + v] = s;
+                m.A[v * LD + o] = s;
+            }
         }
         __syncwarp();
         // first-order occupied-virtual generator, column j, into Y (FP32: it only steers)
@@ -445,7 +460,7 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             same_mask = m.occf[j] ? om : (~om & ((1u << NORB) - 1u));
             other_mask = ~same_mask & ((1u << NORB) - 1u);
 #pragma unroll
-            for (int k = 0; k < NORB; ++k) m.Y[j * LD + k] = 0.0;
+            for (int k = 0; k < NORB; ++k) m.P[j * LD + k] = 0.0;   // K column j (P is free until the density)
             const float dj = m.diagf[j];
             bool small = true;
             for (unsigned om = other_mask; om; om &= om - 1u) {
@@ -454,7 +469,7 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
                 if (!abs_lt(akj, EIG_TOL)) small = false;
                 float kf = (float)akj / (dj - m.diagf[k]);
                 if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
-                m.Y[j * LD + k] = (double)kf;
+                m.P[j * LD + k] = (double)kf;
                 kmax = fmaxf(kmax, fabsf(kf));
             }
             m.eok[j] = small;
@@ -473,17 +488,17 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
                     double acc = 0.0;
                     for (unsigned om = other_mask; om; om &= om - 1u) {
                         const int mm = __ffs(om) - 1;
-                        acc = fma(m.Y[mm * LD + i], m.Y[j * LD + mm], acc);
+                        acc = fma(m.P[mm * LD + i], m.P[j * LD + mm], acc);
                     }
                     m.A[j * LD + i] = acc;
                 }
+                // (K + K^2 / 2) e_j; the identity part of V is C's own column, the start of C V
                 double v[NORB];
 #pragma unroll
                 for (int i = 0; i < NORB; ++i)
-                    v[i] = fma(0.5, ((same_mask >> i) & 1u) ? m.A[j * LD + i] : 0.0,
-                               m.Y[j * LD + i] + (i == j ? 1.0 : 0.0));
+                    v[i] = fma(0.5, ((same_mask >> i) & 1u) ? m.A[j * LD + i] : 0.0, m.P[j * LD + i]);
 #pragma unroll
-                for (int i = 0; i < NORB; ++i) cn[i] = 0.0;
+                for (int i = 0; i < NORB; ++i) cn[i] = m.C[j * LD + i];
                 for (int k = 0; k < NORB; ++k) {
                     const double vk = v[k];
 #pragma unroll
@@ -497,6 +512,26 @@ __global__ void __launch_bounds__(256) dftb_kernel(const DevSK *__restrict__ skp
             }
             __syncwarp();
         } else {
+            // the sweeps need all of A: add the off-diagonal entries inside the occupied and the
+            // virtual blocks (Y still holds H C), one (a, b) pair per task, stored symmetric
+            if (work) {
+                for (int t = j; t < NORB * (NORB - 1) / 2; t += NORB) {
+                    int pa_ = 0, rem = t;
+                    while (rem >= NORB - 1 - pa_) {
+                        rem -= NORB - 1 - pa_;
+                        ++pa_;
+                    }
+                    const int pb_ = pa_ + 1 + rem;
+                    if (m.occf[pa_] == m.occf[pb_]) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int k = 0; k < NORB; ++k) s = fma(m.C[pa_ * LD + k], m.Y[pb_ * LD + k], s);
+                        m.A[pb_ * LD + pa_] = s;
+                        m.A[pa_ * LD + pb_] = s;
+                    }
+                }
+            }
+            __syncwarp();
             const int sweeps_per_iter = cold_first ? MAX_SWEEPS : 1;
             for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
                 bool small = true;
