@@ -150,6 +150,59 @@ def cluster_batch(rng: np.random.Generator, sizes, centres, noise: float = 0.02,
                   r=np.concatenate(pos), p=np.zeros((off[-1], 3)), R_ref=centres.copy())
 
 
+def periodic_water_cells(rng: np.random.Generator, centres, n_waters: int = 33,
+                         side: float = 10.0 * 1.8897261, noise: float = 0.02, d_min: float = 4.8,
+                         d_atom: float = 3.0, ref=None):
+    """Cubic periodic cells of n_waters waters each (33 per 10 Angstrom cube is liquid density).
+    Each water is a rotated, noisy water as in water_batch whose centre of mass is uniform in the
+    cube; it is kept when, under the minimum-image convention, its centre is at least d_min from
+    every placed centre and each of its atoms at least d_atom from every atom of the other waters.
+    After 400 rejected candidates for one water the cell restarts. Positions are unwrapped (each
+    water whole) and the cube of cell i is centred on centres[i]. Returns (System, lattice) with
+    lattice = side * I."""
+    centres = np.asarray(centres, float)
+    g = _centred_water(ref)
+    lat = side * np.eye(3)
+    species, pos, off = [], [], [0]
+
+    def min_image(x):
+        return x - side * np.round(x / side)
+
+    for c in centres:
+        while True:
+            coms, waters = [], []
+            for _ in range(n_waters):
+                found = None
+                for _batch in range(25):                     # 400 candidates
+                    x = rng.uniform(0.0, side, (16, 3))
+                    rot = random_rotations(rng, 16)
+                    wat = np.einsum("kij,aj->kai", rot, g) + rng.normal(0.0, noise, (16, 3, 3)) + x[:, None, :]
+                    good = np.ones(16, bool)
+                    if coms:
+                        dc = min_image(x[:, None, :] - np.array(coms)[None])
+                        good &= np.sqrt((dc * dc).sum(2)).min(1) >= d_min
+                        placed = np.concatenate(waters)
+                        da = min_image(wat[:, :, None, :] - placed[None, None])
+                        good &= np.sqrt((da * da).sum(3)).min(axis=(1, 2)) >= d_atom
+                    k = np.flatnonzero(good)
+                    if len(k):
+                        found = k[0]
+                        break
+                if found is None:
+                    break
+                coms.append(x[found])
+                waters.append(wat[found])
+            if len(coms) == n_waters:
+                break
+        w = np.stack(waters) + (c - 0.5 * side)
+        pos.append(w.reshape(-1, 3))
+        species.append(np.tile(np.array([ELEM_O, ELEM_H, ELEM_H], np.int32), n_waters))
+        off.append(off[-1] + 3 * n_waters)
+    system = System(species=np.concatenate(species), cell_offset=np.array(off, np.int32),
+                    r=np.concatenate(pos), p=np.zeros((off[-1], 3)), R_ref=centres.copy())
+    return system, lat
+
+
 def mb_momenta(rng: np.random.Generator, system: System, temperature: float = 300.0) -> np.ndarray:
     """Maxwell-Boltzmann momenta, centre-of-mass velocity removed in every cell."""
     m = np.array(MASS_AMU)[system.species] * AMU
