@@ -57,6 +57,8 @@ extern "C" {
                                    /* CAVMD_ERR_UNSUPPORTED. Cells of 3 atoms and 6       */
                                    /* orbitals take a lane-group kernel; any other mix of  */
                                    /* cells takes the persistent cluster kernel.           */
+#define CAVMD_MAX_PERIODIC_ORBITALS 256 /* periodic cells (cavmd_system.lattice): orbitals  */
+#define CAVMD_MAX_PERIODIC_ATOMS 128    /* and atoms per cell                             */
 /* Dipole derivative b_j = dM_n/dr_j used by the coupling force:
  *   MULLIKEN     b_j = Q_j pol (the paper's cheap replacement; not conservative);
  *   BORN_FD      forward differences [M(r + h e) - M(r)] / h, the paper's choice, from 3 N_at
@@ -100,6 +102,17 @@ typedef struct {
     const double *p;            /* [3 n_atoms] momenta                                          */
     const double *R_ref;        /* [3 n_cells] fixed mode-function centres R_n, or NULL for the
                                    initial centre of mass of each cell                           */
+    const double *lattice;      /* NULL: isolated cells. Otherwise [9] lattice vectors a_1, a_2,
+                                   a_3 as rows (bohr), shared by every cell, and each cell is
+                                   periodic (the paper's cubic 33-water cells, section
+                                   "Computational details") and evaluated at the Gamma point:
+                                   H0 and S summed over lattice images within r_cut, gamma as the
+                                   Ewald sum of 1/r (tin-foil boundary) plus the Klopman-Ohno
+                                   remainder over images with the cosine taper at r_cut. Positions
+                                   are unwrapped (molecules stay whole); the cell dipole is
+                                   sum_j Q_j r_j. Cells up to CAVMD_MAX_PERIODIC_ORBITALS orbitals
+                                   and CAVMD_MAX_PERIODIC_ATOMS atoms, Mulliken charges only (other
+                                   charge models return CAVMD_ERR_UNSUPPORTED)                   */
 } cavmd_system;
 
 /* Slater-Koster parameter set. Every radial integral is

@@ -33,7 +33,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 class cavmd_system(C.Structure):
     _fields_ = [("n_cells", C.c_int32), ("n_atoms", C.c_int32), ("cell_offset", _ip), ("species", _ip),
-                ("r", _dp), ("p", _dp), ("R_ref", _dp)]
+                ("r", _dp), ("p", _dp), ("R_ref", _dp), ("lattice", _dp)]
 
 
 class cavmd_sk_tables(C.Structure):
@@ -253,10 +253,14 @@ class BornMLP:
 class Context:
     """Owns one cavmd_ctx plus the host arrays and callbacks it was built from.
 
+    lattice: None for isolated cells, else the (3, 3) lattice vectors (rows, bohr) of periodic
+    cells evaluated at the Gamma point (cavmd_system.lattice).
+
     device memory: from torch's caching allocator through the allocator callback (torch=True),
     else the library's own cudaMalloc; stream: a torch stream the library runs on."""
 
-    def __init__(self, system, params, modes, options: cavmd_options | None = None, torch_memory=True):
+    def __init__(self, system, params, modes, options: cavmd_options | None = None, torch_memory=True,
+                 lattice=None):
         lib = load_library()
         self.lib = lib
         self.opt = default_options() if options is None else options
@@ -295,6 +299,9 @@ class Context:
         if getattr(system, "R_ref", None) is not None:
             arrs["R"] = np.ascontiguousarray(system.R_ref, np.float64).ravel()
             sysc.R_ref = _ptr(arrs["R"])
+        if lattice is not None:   # periodic cells: lattice vectors as rows, shared by every cell
+            arrs["lat"] = np.ascontiguousarray(lattice, np.float64).reshape(9)
+            sysc.lattice = _ptr(arrs["lat"])
         md = cavmd_modes()
         marr = dict(k=np.ascontiguousarray(modes.k, np.float64).ravel(),
                     w=np.ascontiguousarray(modes.omega, np.float64),

@@ -49,6 +49,8 @@ struct cavmd_ctx {
     bool mixed = false;                      // tensor-core coupling (modes on a grid)
     bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
     bool moving = false;                     // mode functions at the cells' centres of mass
+    bool periodic = false;                   // periodic cells (Gamma point): their own kernel
+    PbcPlan pplan{};
     double *d_Us = nullptr, *d_Wk2 = nullptr, *d_Wk1 = nullptr, *d_watom = nullptr;
     double *d_G1 = nullptr, *d_Ginst = nullptr;
     double *d_U0 = nullptr, *d_Us0 = nullptr;   // mode functions and sines at the reference positions
@@ -219,6 +221,7 @@ void collect_phase_times(cavmd_ctx *c) {
 cudaError_t run_dftb(cavmd_ctx *c, int have_warm) {
     PhaseScope ps(c, 0);
     c->da.have_warm = have_warm;
+    if (c->periodic) return launch_dftb_periodic(c->d_sk, c->da, c->pplan, c->stream);
     if (c->generic) return launch_dftb_generic(c->d_sk, c->da, c->gplan, c->stream);
     return launch_dftb_water(c->d_sk, c->da, c->stream, c->water_warps, c->water_per_warp);
 }
@@ -316,7 +319,7 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     // SCC-DFTB kernel kicks and drifts the atoms of its cells before reading their positions, and
     // the photon kernel rotates the modes before their second half-flow. The cluster kernel takes
     // two launches of their own.
-    const bool fold = !c->generic && !c->moving;
+    const bool fold = !c->generic && !c->moving && !c->periodic;
     if (!fold) {
         if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
         if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
@@ -359,6 +362,10 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
 // the converged state) twice, timed with CUDA events on the context's stream; the fastest is kept.
 // The context's own state is not touched.
 int autotune(cavmd_ctx *c) {
+    if (c->periodic) {
+        c->tuning = "k_dftb_periodic: one 256-thread block per cell, two per SM (no candidates)";
+        return CAVMD_OK;
+    }
     const int NA = c->n_atoms, N = c->N;
     cudaStream_t st = c->stream;
     const long long ncw = c->n_cwarm;
@@ -550,6 +557,17 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         if (sys->species[i] < 0 || sys->species[i] >= sk->n_elem) return fail(c, CAVMD_ERR_INVALID_ARG, "species id out of range");
     for (int i = 0; i < 3 * sys->n_atoms; ++i)
         if (!std::isfinite(sys->r[i]) || !std::isfinite(sys->p[i])) return fail(c, CAVMD_ERR_INVALID_ARG, "non-finite position or momentum");
+    const bool per = sys->lattice != nullptr;
+    if (per) {
+        const double *L = sys->lattice;
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(L[k])) return fail(c, CAVMD_ERR_INVALID_ARG, "non-finite lattice vector");
+        const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
+                           L[2] * (L[3] * L[7] - L[4] * L[6]);
+        if (!(std::fabs(det) > 1e-6)) return fail(c, CAVMD_ERR_INVALID_ARG, "lattice vectors are linearly dependent");
+        if (o->charge_model != CAVMD_CHARGE_MULLIKEN)
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "periodic cells take Mulliken charges only");
+    }
     for (int n = 0; n < sys->n_cells; ++n) {
         const int a0 = sys->cell_offset[n], a1 = sys->cell_offset[n + 1];
         if (a1 <= a0) return fail(c, CAVMD_ERR_INVALID_ARG, "every cell needs at least one atom");
@@ -559,10 +577,16 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         const long ne = std::lround(nel);
         if (std::fabs(nel - ne) > 1e-12 || (ne & 1) || ne <= 0 || ne > 2 * norb)
             return fail(c, CAVMD_ERR_INVALID_ARG, "cells must be neutral and closed shell");
-        if (norb > CAVMD_MAX_CELL_ORBITALS || (norb & 1))
+        if (per) {
+            if (norb > CAVMD_MAX_PERIODIC_ORBITALS || (norb & 1) || a1 - a0 > CAVMD_MAX_PERIODIC_ATOMS)
+                return fail(c, CAVMD_ERR_UNSUPPORTED, "periodic cells need an even number of orbitals, at most 256, "
+                                                      "and at most 128 atoms");
+            if (ne / 2 >= norb) return fail(c, CAVMD_ERR_UNSUPPORTED, "periodic cells need an empty orbital");
+        } else if (norb > CAVMD_MAX_CELL_ORBITALS || (norb & 1)) {
             return fail(c, CAVMD_ERR_UNSUPPORTED, "cells need an even number of orbitals, at most 64");
+        }
     }
-    {   // shared memory of the persistent kernel for the largest cells
+    if (!per) {   // shared memory of the persistent kernel for the largest cells
         std::vector<int> norb_e(sk->norb, sk->norb + sk->n_elem);
         GenericPlan gp{};
         std::vector<int2> it, dit;
@@ -694,12 +718,13 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     for (int n = 0; n < N; ++n) {
         int no = 0;
         for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) no += sk->norb[sys->species[i]];
-        if (no != 6 || sys->cell_offset[n + 1] - sys->cell_offset[n] != 3) c->generic = true;
+        if (!sys->lattice && (no != 6 || sys->cell_offset[n + 1] - sys->cell_offset[n] != 3)) c->generic = true;
         coff[n + 1] = coff[n] + (long long)no * no;
     }
     c->n_cwarm = coff[N];
     AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)coff[N]); AL(c->d_E, N); AL(c->d_Mc, N);
-    if (!c->generic) CK(prepare_dftb_water(8));
+    c->periodic = sys->lattice != nullptr;
+    if (!c->generic && !c->periodic) CK(prepare_dftb_water(8));
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N); AL(c->d_E1, N);
     c->mixed = c->opt.precision == CAVMD_PREC_MIXED_BF16X3;
     if (!c->mixed) AL(c->d_U, (size_t)M * N);
@@ -824,6 +849,32 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         CK(prepare_dftb_generic(g));
         // the host vectors must outlive the copies
         CK(cudaStreamSynchronize(st));
+    }
+
+    if (c->periodic) {
+        PbcPlan &pp = c->pplan;
+        std::vector<double> img, gw;
+        plan_dftb_periodic(sys->lattice, sk->r_cut, pp, img, gw);
+        if (pp.n_img > 200000 || pp.n_g > 20000)
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "lattice too thin: " + std::to_string(pp.n_img) + " lattice images");
+        pp.nmax = 0;
+        pp.amax = 0;
+        for (int n = 0; n < N; ++n) {
+            pp.nmax = std::max(pp.nmax, (int)std::lround(std::sqrt((double)(coff[n + 1] - coff[n]))));
+            pp.amax = std::max(pp.amax, sys->cell_offset[n + 1] - sys->cell_offset[n]);
+        }
+        int nsm = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+        pp.blocks = std::max(1, std::min(N, 2 * nsm));
+        AL(pp.d_img, img.size());
+        AL(pp.d_gw, gw.size());
+        AL(pp.work, pbc_workspace_doubles(pp.nmax, pp.amax, pp.n_g) * (size_t)pp.blocks);
+        CK(cudaMemcpyAsync(pp.d_img, img.data(), sizeof(double) * img.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(pp.d_gw, gw.data(), sizeof(double) * gw.size(), cudaMemcpyHostToDevice, st));
+        AL(c->d_Coff, N);
+        CK(cudaMemcpyAsync(c->d_Coff, coff.data(), sizeof(long long) * N, cudaMemcpyHostToDevice, st));
+        CK(prepare_dftb_periodic());
+        CK(cudaStreamSynchronize(st));   // the host vectors must outlive the copies
     }
 
     DftbArgs &d = c->da;

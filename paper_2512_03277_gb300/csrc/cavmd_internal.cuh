@@ -194,6 +194,21 @@ void plan_dftb_generic(const int *cell_offset, const int *species, const int *no
                        std::vector<int2> &disp_items);
 cudaError_t prepare_dftb_generic(GenericPlan &p);   // kernel attribute and occupancy, once per plan
 cudaError_t launch_dftb_generic(const DevSK *sk_dev, const DftbArgs &a, const GenericPlan &p, cudaStream_t st);
+// Plan of the Gamma-point SCC-DFTB launch over periodic cells (one lattice for all cells).
+struct PbcPlan {
+    double lat[9], inv[9];                // lattice vectors as rows; inverse (f = r inv)
+    double alpha, bg, self_e, r_real;     // Ewald splitting, background and self terms, real-space cutoff
+    int n_img, n_g;                       // lattice translations; half-space reciprocal vectors
+    int nmax, amax, blocks;               // largest cell; persistent blocks (2 per SM)
+    double *d_img, *d_gw;                 // device: [n_img][3], [n_g][4] (G, 2 w_G)
+    double *work;                         // device: per-block workspaces
+};
+size_t pbc_workspace_doubles(int nmax, int amax, int n_g);
+size_t pbc_smem();
+void plan_dftb_periodic(const double *lat, double r_cut, PbcPlan &p, std::vector<double> &img,
+                        std::vector<double> &gw);
+cudaError_t prepare_dftb_periodic();
+cudaError_t launch_dftb_periodic(const DevSK *sk_dev, const DftbArgs &a, const PbcPlan &p, cudaStream_t st);
 // b_j = dM/dr_j from the displaced dipoles (forward or central differences)
 cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const double *M_cell,
                                  const double *M_disp, int n_disp, int central, double h, double *b,

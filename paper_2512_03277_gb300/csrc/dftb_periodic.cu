@@ -1,0 +1,1006 @@
+// Batched Gamma-point SCC-DFTB of periodic cells: the paper's per-molecule systems are cubic cells
+// of 33 waters with periodic boundaries in all three directions and Gamma-point sampling (section
+// "Computational details").
+//
+// What is computed (the textbook Gamma-point forms):
+//   * H0 and S: the (A, B) block is the sum over lattice images T of the Slater-Koster block at
+//     d = r_B + T - r_A, |d| < r_cut (for A = B the T = 0 term is the on-site block);
+//   * gamma: Ewald lattice sum of 1/r (tin-foil boundary, neutralising background) plus the
+//     Klopman-Ohno remainder 1/sqrt(r^2 + c^2) - 1/r over images with the cosine taper at r_cut,
+//     and U_A on the diagonal. The real-space part is a matrix formed once per evaluation; the
+//     reciprocal part acts on the charges through structure factors in every SCC iteration;
+//   * the SCC loop, band + second-order + repulsion energy and its analytic gradient, every term
+//     summed over the same images.
+//
+// Mapping to the machine. A 33-water cell has 198 orbitals: one 198 x 198 FP64 matrix is 313 KB,
+// more than a block's shared memory, and GB300's FP64 pipe (2 FMA per clock per SM) is the only
+// bottleneck. So each cell is one 256-thread block of a persistent grid (two per SM), its
+// matrices live in a per-block global workspace (L2-resident while the cell runs), and every
+// product stages k-chunks of its operands in shared memory and spreads its output entries
+// evenly over the threads (8 per thread per pass, each summed over k in increasing order), so the
+// results do not depend on the launch shape. Per SCC iteration only what the update needs is
+// formed: H, Y = H C, the diagonal and the occupied-virtual block of C^T Y, and the Cayley
+// rotation C <- C (I - K/2)^-1 (I + K/2) with the occupied-virtual generator
+// K(v, o) = A_vo / (A_oo - A_vv), which is orthogonal to rounding for any K (it needs two small
+// Cholesky factorisations, I + X^T X / 4 and I + X X^T / 4, X = K_vo). A cold start diagonalises
+// C^T H C once by cyclic Jacobi sweeps; warm starts re-orthonormalise the previous step's C under
+// the new overlap by a Cholesky factor of C^T S C.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "cavmd_internal.cuh"
+
+namespace {
+
+constexpr int PT = 256;          // threads per block (one cell at a time)
+constexpr int PE = 8;            // product entries per thread per pass
+constexpr int KC = 24;           // contraction chunk staged in shared memory
+constexpr int ZC = 80;           // columns of the second operand staged per pass
+constexpr int PNMAX = 256;       // orbitals per cell
+constexpr int PAMAX = 128;       // atoms per cell
+constexpr int PHIST = 6;         // largest Anderson history
+constexpr int P_MAX_SWEEPS = 40;
+constexpr double P_JACOBI_TOL = 1e-11;   // cold start: off-diagonal size where the sweeps stop
+constexpr double P_MIN_GAP = 1e-3;
+constexpr double P_EIG_TOL = 1e-10;
+constexpr double PI_D = 3.141592653589793;
+
+// Shared memory of one block.
+struct PShared {
+    double Xs[KC * PNMAX];
+    double Zs[KC * ZC];
+    double pos[PAMAX][3];
+    double zv[PAMAX], q[PAMAX], qout[PAMAX], qst[PAMAX], dq[PAMAX], shift[PAMAX];
+    double hq[PHIST][PAMAX], hf[PHIST][PAMAX];
+    double diag[PNMAX], red[PNMAX], invd[PNMAX];
+    double cs[PNMAX];            // Jacobi (c, s) of the rotations of one round
+    double th[PHIST];
+    double gred[PT / 32][3];
+    int spec[PAMAX], atom_off[PAMAX + 1], orb_atom[PNMAX];
+    int occ_list[PNMAX], virt_list[PNMAX], occf[PNMAX];
+    int pp[PNMAX / 2], pq[PNMAX / 2];
+    int fl[8];                   // 0 error bits, 1 n, 2 iterations, 3 occupied orbitals
+    int vote[PT / 32];
+};
+
+__device__ __forceinline__ bool blk_all(bool p) { return __syncthreads_and(p) != 0; }
+
+__device__ __forceinline__ void cutoff_fn(double r, const DevSK &sk, double &f, double &df) {
+    const double x = (r - (sk.r_cut - sk.taper)) * sk.inv_taper;
+    f = 1.0;
+    df = 0.0;
+    if (x > 0.0) {
+        if (x < 1.0) {
+            double sn, cn;
+            sincospi(x, &sn, &cn);
+            f = 0.5 * (1.0 + cn);
+            df = -0.5 * PI_D * sk.inv_taper * sn;
+        } else {
+            f = 0.0;
+        }
+    }
+}
+
+// V(r) = a exp(-b r) (1 + c1 r + c2 r^2) f_cut(r) and dV/dr.
+__device__ __forceinline__ void radial_p(const double *par, double r, const DevSK &sk, double &v, double &dv) {
+    const double a = par[0], b = par[1], c1 = par[2], c2 = par[3];
+    const double e = a * exp(-b * r);
+    const double poly = fma(fma(c2, r, c1), r, 1.0);
+    const double dpoly = fma(2.0 * c2, r, c1);
+    double f, df;
+    cutoff_fn(r, sk, f, df);
+    v = e * poly * f;
+    dv = e * (fma(-b * poly, f, dpoly * f) + poly * df);
+}
+
+// Column of entry e of the packed lower triangle of an m x m matrix, stored column by column
+// (column c holds rows c..m-1 and starts at c m - c (c - 1) / 2).
+__device__ __forceinline__ int lower_col(int e, int m) {
+    const float b = 2.0f * (float)m + 1.0f;
+    int c = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))) * 0.5f);
+    c = max(0, min(c, m - 1));
+    while (c > 0 && c * m - c * (c - 1) / 2 > e) --c;
+    while (c + 1 < m && (c + 1) * m - (c + 1) * c / 2 <= e) ++c;
+    return c;
+}
+
+// Block-wide product: out(i, c) = sum_{k < K} xa(i, k) za(k, c) for the entries of an m x w
+// matrix (LOWER: the entries i >= c of an m x m one), the sum taken in increasing k; epi(i, c, v)
+// receives each entry once. Passes of up to PT * PE entries in column order; each k-chunk of the
+// m rows of X and of the pass's columns of Z is staged in shared memory first.
+// XK: consecutive k of X are adjacent in memory (else consecutive i); ZK: consecutive k of Z are
+// adjacent (else consecutive c). They only choose the staging order, for coalesced loads.
+template <bool LOWER, bool XK, bool ZK, class XA, class ZA, class EPI>
+__device__ void pprod(PShared &sh, int m, int w, int K, XA xa, ZA za, EPI epi) {
+    const int tid = threadIdx.x;
+    const int n_out = LOWER ? m * (m + 1) / 2 : m * w;
+    const int pe = LOWER ? PT * PE : min(PT * PE, m * (ZC - 2));
+    for (int e0 = 0; e0 < n_out; e0 += pe) {
+        const int e1 = min(e0 + pe, n_out);
+        const int c_lo = LOWER ? lower_col(e0, m) : e0 / m;
+        const int c_hi = LOWER ? lower_col(e1 - 1, m) : (e1 - 1) / m;
+        const int ncol = c_hi - c_lo + 1;
+        int ii[PE], cc[PE];
+        double acc[PE];
+#pragma unroll
+        for (int r = 0; r < PE; ++r) {
+            const int e = min(e0 + tid + r * PT, e1 - 1);
+            int i, c;
+            if (LOWER) {
+                c = lower_col(e, m);
+                i = c + (e - (c * m - c * (c - 1) / 2));
+            } else {
+                c = e / m;
+                i = e - c * m;
+            }
+            ii[r] = i;
+            cc[r] = c - c_lo;
+            acc[r] = 0.0;
+        }
+        for (int k0 = 0; k0 < K; k0 += KC) {
+            const int kc = min(KC, K - k0);
+            __syncthreads();
+            for (int idx = tid; idx < kc * m; idx += PT) {
+                int kk, i;
+                if (XK) { i = idx / kc; kk = idx - i * kc; } else { kk = idx / m; i = idx - kk * m; }
+                sh.Xs[kk * m + i] = xa(i, k0 + kk);
+            }
+            for (int idx = tid; idx < kc * ncol; idx += PT) {
+                int kk, cl;
+                if (ZK) { cl = idx / kc; kk = idx - cl * kc; } else { kk = idx / ncol; cl = idx - kk * ncol; }
+                sh.Zs[kk * ZC + cl] = za(k0 + kk, c_lo + cl);
+            }
+            __syncthreads();
+            for (int kk = 0; kk < kc; ++kk) {
+#pragma unroll
+                for (int r = 0; r < PE; ++r) acc[r] = fma(sh.Xs[kk * m + ii[r]], sh.Zs[kk * ZC + cc[r]], acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < PE; ++r)
+            if (e0 + tid + r * PT < e1) epi(ii[r], cc[r] + c_lo, acc[r]);
+    }
+    __syncthreads();
+}
+
+// In-place lower Cholesky factor of the m x m matrix A (column-major, leading dimension m; the
+// lower triangle is read and written), right-looking with one thread per trailing column.
+// Returns false (in every thread) when a pivot is not positive.
+__device__ bool pchol(double *A, int m, PShared &sh) {
+    const int j = threadIdx.x;
+    if (j == 0) sh.fl[4] = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+        if (j == 0) {
+            double d = A[k * m + k];
+            if (!(d > 1e-300)) { sh.fl[4] = 1; d = 1.0; }
+            const double y = rsqrt_nr(d);
+            sh.invd[k] = y;
+            A[k * m + k] = d * y;
+        }
+        __syncthreads();
+        const double y = sh.invd[k];
+        for (int i = k + 1 + j; i < m; i += PT) A[k * m + i] *= y;
+        __syncthreads();
+        for (int jj = k + 1 + j; jj < m; jj += PT) {
+            const double ljk = A[k * m + jj];
+            for (int i = jj; i < m; ++i) A[jj * m + i] = fma(-A[k * m + i], ljk, A[jj * m + i]);
+        }
+        __syncthreads();
+    }
+    const bool ok = sh.fl[4] == 0;
+    __syncthreads();
+    return ok;
+}
+
+// Row solve x L^T = z (forward substitution) for one row of length m with stride xs, in place.
+__device__ __forceinline__ void row_solve_lt(const double *L, int m, const double *invd, double *x, int xs) {
+    for (int c = 0; c < m; ++c) {
+        double v = x[c * xs];
+        for (int k = 0; k < c; ++k) v = fma(-x[k * xs], L[k * m + c], v);
+        x[c * xs] = v * invd[c];
+    }
+}
+
+// Row solve x L L^T = z for one row (z, x of length m, strides zs and xs), L the lower factor
+// above: forward u L^T = z, then backward x L = u. x may alias z.
+__device__ __forceinline__ void row_solve_llt(const double *L, int m, const double *invd, const double *z, int zs,
+                                              double *x, int xs) {
+    for (int c = 0; c < m; ++c) {   // u_c = (z_c - sum_{k<c} u_k L(c, k)) / L(c, c)
+        double v = z[c * zs];
+        for (int k = 0; k < c; ++k) v = fma(-x[k * xs], L[k * m + c], v);
+        x[c * xs] = v * invd[c];
+    }
+    for (int c = m - 1; c >= 0; --c) {   // x_c = (u_c - sum_{k>c} x_k L(k, c)) / L(c, c)
+        double v = x[c * xs];
+        for (int k = c + 1; k < m; ++k) v = fma(-x[k * xs], L[c * m + k], v);
+        x[c * xs] = v * invd[c];
+    }
+}
+
+// Round-robin Jacobi schedule for even n: pair k of round r (0..n-2); index n-1 meets r.
+__device__ __forceinline__ void p_pair(int k, int r, int n, int &p, int &q) {
+    const int m = n - 1;
+    if (k == 0) { p = r; q = m; return; }
+    const int x = (r + k) % m, y = (r - k + m) % m;
+    p = min(x, y);
+    q = max(x, y);
+}
+
+// Rotation annihilating a_pq: angle from FP32, (c, s) normalised in FP64 by two Newton steps.
+__device__ __forceinline__ void p_jacobi_cs(double app, double aqq, double apq, double &c, double &s) {
+    const float d = (float)(aqq - app);
+    const float o = 2.0f * (float)apq;
+    float t = 0.0f;
+    if (o != 0.0f) t = o / (d + copysignf(sqrtf(fmaf(d, d, o * o)), d));
+    const float cf = rsqrtf(fmaf(t, t, 1.0f));
+    c = (double)cf;
+    s = (double)(t * cf);
+    for (int it = 0; it < 2; ++it) {
+        const double nrm = fma(c, c, s * s);
+        const double f = fma(-0.5, nrm, 1.5);
+        c *= f;
+        s *= f;
+    }
+}
+
+
+// Device view of the periodic plan (by value).
+struct PbcDev {
+    double lat[9], inv[9];       // lattice vectors as rows; fractional coordinates f = r inv
+    double alpha, bg, self_e;    // Ewald alpha, -pi / (alpha^2 V), -2 alpha / sqrt(pi)
+    double r_real2;              // real-space cutoff squared
+    int n_img, n_g, nmax, amax;
+    const double *img;           // [n_img][3] lattice translations (every image within reach)
+    const double *gw;            // [n_g][4] half-space reciprocal vectors G and 2 w_G
+    double *work;                // per-block workspaces
+    long long work_stride;       // doubles per block
+};
+
+// One cell, evaluated by the whole block.
+__device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PShared &sh, double *wk, int cell) {
+    const int j = threadIdx.x;
+    const int a0 = a.cell_offset[cell];
+    const int nat = a.cell_offset[cell + 1] - a0;
+    const long long n2max = (long long)pl.nmax * pl.nmax;
+    double *H0 = wk, *S = wk + n2max, *H = wk + 2 * n2max, *Y = wk + 3 * n2max, *P = wk + 4 * n2max;
+    double *Xg = wk + 5 * n2max, *Mo = wk + 6 * n2max, *Mv = wk + 7 * n2max;
+    double *gam = wk + 8 * n2max;
+    double *csg = gam + (long long)pl.amax * pl.amax;     // [g][atom] (cos, sin)
+    double *sgf = csg + 2LL * pl.amax * pl.n_g;           // [g] (S_c, S_s)
+    double *pbuf = sgf + 2LL * pl.n_g;                    // [atom * nat + atom] gradient (3) + energy
+    double *C = a.Cwarm + a.Cwarm_off[cell];
+
+    if (j < nat) {
+        sh.spec[j] = a.species[a0 + j];
+        for (int k = 0; k < 3; ++k) sh.pos[j][k] = a.r[3 * (a0 + j) + k];
+    }
+    __syncthreads();
+    if (j == 0) {
+        int o = 0;
+        double nel = 0.0;
+        for (int at = 0; at < nat; ++at) {
+            sh.atom_off[at] = o;
+            const int no = sk.norb[sh.spec[at]];
+            for (int k = 0; k < no; ++k) sh.orb_atom[o + k] = at;
+            o += no;
+            sh.zv[at] = sk.zval[sh.spec[at]];
+            nel += sh.zv[at];
+        }
+        sh.atom_off[nat] = o;
+        sh.fl[0] = 0;
+        sh.fl[1] = o;
+        sh.fl[2] = 0;
+        sh.fl[3] = (int)(nel * 0.5 + 0.25);
+    }
+    __syncthreads();
+    const int n = sh.fl[1], nocc = sh.fl[3];
+    const int nv = n - nocc, nn = n * n;
+
+    // ---------------------------------------------------------------- H0, S, real-space gamma
+    for (int e = j; e < nn; e += PT) {
+        const int c = e / n, i = e - c * n;
+        double h = 0.0, s = 0.0;
+        if (i == c) {
+            const int at = sh.orb_atom[c], el = sh.spec[at];
+            h = (c == sh.atom_off[at]) ? sk.onsite[el][0] : sk.onsite[el][1];
+            s = 1.0;
+        }
+        H0[e] = h;
+        S[e] = s;
+    }
+    __syncthreads();
+    for (int t = j; t < nat * nat; t += PT) {
+        const int A = t / nat, B = t - A * nat;
+        if (B < A) continue;
+        const int eA = sh.spec[A], eB = sh.spec[B];
+        const int oA = sh.atom_off[A], oB = sh.atom_off[B];
+        const int na = sk.norb[eA], nb = sk.norb[eB];
+        double d[3], f[3], dw[3];
+        for (int k = 0; k < 3; ++k) d[k] = sh.pos[B][k] - sh.pos[A][k];
+        for (int k = 0; k < 3; ++k) f[k] = rint(fma(d[0], pl.inv[k], fma(d[1], pl.inv[3 + k], d[2] * pl.inv[6 + k])));
+        for (int k = 0; k < 3; ++k) dw[k] = d[k] - fma(f[0], pl.lat[k], fma(f[1], pl.lat[3 + k], f[2] * pl.lat[6 + k]));
+        double hb[16], sb[16];
+        for (int u = 0; u < 16; ++u) { hb[u] = 0.0; sb[u] = 0.0; }
+        double g_re = 0.0, g_sr = 0.0;
+        const double c2 = sk.gamma_c2[eA][eB];
+        const double rc2 = sk.r_cut * sk.r_cut;
+        for (int im = 0; im < pl.n_img; ++im) {
+            const double x0 = dw[0] + pl.img[3 * im], x1 = dw[1] + pl.img[3 * im + 1], x2 = dw[2] + pl.img[3 * im + 2];
+            const double r2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            if (!(r2 < pl.r_real2) || r2 == 0.0) continue;
+            const double ir = rsqrt_nr(r2);
+            const double r = r2 * ir;
+            g_re = fma(erfc(pl.alpha * r), ir, g_re);
+            if (!(r2 < rc2)) continue;
+            const double e[3] = {x0 * ir, x1 * ir, x2 * ir};
+            for (int tb = 0; tb < 2; ++tb) {
+                const double(*tab)[CAVMD_MAX_ELEM][4][4] = tb == 0 ? sk.h0 : sk.s;
+                double *acc = tb == 0 ? hb : sb;
+                double v, dv;
+                radial_p(tab[eA][eB][CAVMD_SK_SS], r, sk, v, dv);
+                acc[0] += v;
+                if (nb == 4) {
+                    radial_p(tab[eA][eB][CAVMD_SK_SP], r, sk, v, dv);
+                    for (int i = 0; i < 3; ++i) acc[1 + i] = fma(e[i], v, acc[1 + i]);
+                }
+                if (na == 4) {
+                    radial_p(tab[eB][eA][CAVMD_SK_SP], r, sk, v, dv);
+                    for (int i = 0; i < 3; ++i) acc[4 * (1 + i)] = fma(-e[i], v, acc[4 * (1 + i)]);
+                }
+                if (na == 4 && nb == 4) {
+                    double vs, vp;
+                    radial_p(tab[eA][eB][CAVMD_SK_PPS], r, sk, vs, dv);
+                    radial_p(tab[eA][eB][CAVMD_SK_PPP], r, sk, vp, dv);
+                    const double dl = vs - vp;
+                    for (int i = 0; i < 3; ++i)
+                        for (int k = 0; k < 3; ++k)
+                            acc[4 * (1 + i) + 1 + k] += fma(e[i] * e[k], dl, (i == k) ? vp : 0.0);
+                }
+            }
+            double fc, dfc;
+            cutoff_fn(r, sk, fc, dfc);
+            g_sr = fma(rsqrt_nr(r2 + c2) - ir, fc, g_sr);
+        }
+        // block (mu of A, nu of B) at column oB + nu, row oA + mu, and its transpose; a block of an
+        // atom with its own images is symmetric, written as the mean of the two halves
+        for (int mu = 0; mu < na; ++mu)
+            for (int nu = 0; nu < nb; ++nu) {
+                const double hv = A == B ? 0.5 * (hb[4 * mu + nu] + hb[4 * nu + mu]) : hb[4 * mu + nu];
+                const double sv = A == B ? 0.5 * (sb[4 * mu + nu] + sb[4 * nu + mu]) : sb[4 * mu + nu];
+                H0[(oB + nu) * n + oA + mu] += hv;
+                S[(oB + nu) * n + oA + mu] += sv;
+                if (A != B) {
+                    H0[(oA + mu) * n + oB + nu] = hv;
+                    S[(oA + mu) * n + oB + nu] = sv;
+                }
+            }
+        double gv = g_re + g_sr + pl.bg;
+        if (A == B) gv += sk.hubbard[eA] + pl.self_e;
+        gam[A * pl.amax + B] = gv;
+        gam[B * pl.amax + A] = gv;
+    }
+    // cos and sin of G . (r_A - r_0) for the reciprocal sum
+    for (int e = j; e < nat * pl.n_g; e += PT) {
+        const int g = e / nat, at = e - g * nat;
+        const double *G = pl.gw + 4 * g;
+        const double ph = fma(G[0], sh.pos[at][0] - sh.pos[0][0],
+                              fma(G[1], sh.pos[at][1] - sh.pos[0][1], G[2] * (sh.pos[at][2] - sh.pos[0][2])));
+        double sn, cn;
+        sincos(ph, &sn, &cn);
+        csg[2LL * e] = cn;
+        csg[2LL * e + 1] = sn;
+    }
+    __syncthreads();
+
+    // atomic shifts eps_A = sum_B gamma_AB dq_B + reciprocal part, from sh.dq
+    auto shifts = [&]() {
+        for (int g = j; g < pl.n_g; g += PT) {
+            double sc = 0.0, ss = 0.0;
+            const double *t = csg + 2LL * g * nat;
+            for (int at = 0; at < nat; ++at) {
+                sc = fma(sh.dq[at], t[2 * at], sc);
+                ss = fma(sh.dq[at], t[2 * at + 1], ss);
+            }
+            sgf[2 * g] = sc;
+            sgf[2 * g + 1] = ss;
+        }
+        __syncthreads();
+        if (j < nat) {
+            double v = 0.0;
+            for (int k = 0; k < nat; ++k) v = fma(gam[j * pl.amax + k], sh.dq[k], v);
+            double rr = 0.0;
+            for (int g = 0; g < pl.n_g; ++g) {
+                const double *t = csg + 2LL * (g * nat + j);
+                rr = fma(pl.gw[4 * g + 3], fma(t[0], sgf[2 * g], t[1] * sgf[2 * g + 1]), rr);
+            }
+            sh.shift[j] = v + rr;
+        }
+        __syncthreads();
+    };
+    auto build_h = [&]() {
+        for (int e = j; e < nn; e += PT) {
+            const int c = e / n, i = e - c * n;
+            H[e] = fma(0.5 * S[e], sh.shift[sh.orb_atom[i]] + sh.shift[sh.orb_atom[c]], H0[e]);
+        }
+        __syncthreads();
+    };
+    auto rank_occupation = [&]() {
+        if (j < n) {
+            const long long kj = order_key(sh.diag[j]);
+            int rank = 0;
+            for (int i = 0; i < n; ++i) {
+                const long long ki = order_key(sh.diag[i]);
+                rank += (ki < kj) || (ki == kj && i < j);
+            }
+            sh.occf[j] = rank < nocc;
+            if (rank < nocc) sh.occ_list[rank] = j; else sh.virt_list[rank - nocc] = j;
+        }
+        __syncthreads();
+    };
+    auto Cat = [&](int i, int c) -> double { return C[c * n + i]; };
+
+    // ---------------------------------------------------------------- S-orthonormal start
+    if (!a.have_warm)
+        for (int e = j; e < nn; e += PT) C[e] = (e / n == e % n) ? 1.0 : 0.0;
+    if (j < nat) {
+        if (a.have_warm) {   // predictor 2 q(t) - q(t - dt)
+            const double qt = a.qpop[a0 + j];
+            sh.qst[j] = qt;
+            sh.q[j] = fma(2.0, qt, -a.qprev[a0 + j]);
+        } else {
+            sh.q[j] = sh.zv[j];
+        }
+    }
+    __syncthreads();
+    // Mo <- lower of C^T S C (Y = S C first), its Cholesky factor L, then C <- C L^-T
+    pprod<false, false, true>(sh, n, n, n, [&](int i, int k) { return S[k * n + i]; }, Cat,
+                              [&](int i, int c, double v) { Y[c * n + i] = v; });
+    pprod<true, true, true>(sh, n, n, n, [&](int i, int k) { return C[i * n + k]; },
+                            [&](int k, int c) { return Y[c * n + k]; }, [&](int i, int c, double v) { Mo[c * n + i] = v; });
+    if (!pchol(Mo, n, sh) && j == 0) sh.fl[0] |= ERRBIT_S_NOT_PD;
+    if (j < n) row_solve_lt(Mo, n, sh.invd, C + j, n);
+    __syncthreads();
+
+    // ---------------------------------------------------------------- SCC loop
+    // Per iteration: shifts, H, Y = H C, the diagonal of C^T Y and the occupation by rank; then the
+    // occupied-virtual block A_vo, the generator X(v, o) = A_vo / (A_oo - A_vv) (FP32: it only
+    // steers) and the Cayley rotation
+    //   C_o <- (2 C_o + C_v X) (I + X^T X / 4)^-1 - C_o,  C_v <- (2 C_v - C_o X^T) (I + X X^T / 4)^-1 - C_v,
+    // which is C (I - K/2)^-1 (I + K/2) for the antisymmetric K with K_vo = X. A cold start instead
+    // forms all of C^T H C and runs Jacobi sweeps on its first iteration. Then P = 2 C_o C_o^T,
+    // the Mulliken populations and Anderson mixing.
+    int it;
+    for (it = 1; it <= a.max_iter; ++it) {
+        if (j < nat) sh.dq[j] = sh.q[j] - sh.zv[j];
+        __syncthreads();
+        shifts();
+        build_h();
+        pprod<false, false, true>(sh, n, n, n, [&](int i, int k) { return H[k * n + i]; }, Cat,
+                                  [&](int i, int c, double v) { Y[c * n + i] = v; });
+        if (j < n) {
+            double dg = 0.0;
+            for (int k = 0; k < n; ++k) dg = fma(C[j * n + k], Y[j * n + k], dg);
+            sh.diag[j] = dg;
+        }
+        __syncthreads();
+        bool eok = false;
+        const bool cold_first = !a.have_warm && it == 1;
+        if (cold_first) {
+            // all of A = C^T H C into P, then Jacobi sweeps on A accumulated into C
+            pprod<false, true, true>(sh, n, n, n, [&](int i, int k) { return C[i * n + k]; },
+                                     [&](int k, int c) { return Y[c * n + k]; },
+                                     [&](int i, int c, double v) { P[c * n + i] = v; });
+            double *Am = P;
+            for (int sweep = 0; sweep < P_MAX_SWEEPS; ++sweep) {
+                bool off_small = true;
+                for (int e = j; e < nn; e += PT) {
+                    const int c = e / n, i = e - c * n;
+                    if (i != c && !abs_lt(Am[c * n + i], P_JACOBI_TOL)) off_small = false;
+                }
+                if (blk_all(off_small)) break;
+                for (int rd = 0; rd < n - 1; ++rd) {
+                    if (j < n / 2) {
+                        int p, qq;
+                        p_pair(j, rd, n, p, qq);
+                        double c, s;
+                        p_jacobi_cs(Am[p * n + p], Am[qq * n + qq], Am[qq * n + p], c, s);
+                        sh.pp[j] = p;
+                        sh.pq[j] = qq;
+                        sh.cs[2 * j] = c;
+                        sh.cs[2 * j + 1] = s;
+                    }
+                    __syncthreads();
+                    for (int e = j; e < n * (n / 2); e += PT) {   // columns p, q of A and C, row i
+                        const int k = e / n, i = e - k * n;
+                        const int p = sh.pp[k], qq = sh.pq[k];
+                        const double c = sh.cs[2 * k], s = sh.cs[2 * k + 1];
+                        const double ap = Am[p * n + i], aq = Am[qq * n + i];
+                        Am[p * n + i] = fma(c, ap, -s * aq);
+                        Am[qq * n + i] = fma(s, ap, c * aq);
+                        const double cp = C[p * n + i], cq = C[qq * n + i];
+                        C[p * n + i] = fma(c, cp, -s * cq);
+                        C[qq * n + i] = fma(s, cp, c * cq);
+                    }
+                    __syncthreads();
+                    for (int e = j; e < n * (n / 2); e += PT) {   // rows p, q of A, column c
+                        const int k = e / n, c = e - k * n;
+                        const int p = sh.pp[k], qq = sh.pq[k];
+                        const double ck = sh.cs[2 * k], sk_ = sh.cs[2 * k + 1];
+                        const double x = Am[c * n + p], y = Am[c * n + qq];
+                        Am[c * n + p] = fma(ck, x, -sk_ * y);
+                        Am[c * n + qq] = fma(sk_, x, ck * y);
+                    }
+                    __syncthreads();
+                }
+            }
+            if (j < n) sh.diag[j] = Am[j * n + j];
+            __syncthreads();
+            rank_occupation();
+        } else {
+            rank_occupation();
+            bool small = true;
+            // A_vo (entry (v, o), v fastest) and the generator, stored X[o nv + v]
+            pprod<false, true, true>(sh, nv, nocc, n, [&](int v, int k) { return C[sh.virt_list[v] * n + k]; },
+                                     [&](int k, int o) { return Y[sh.occ_list[o] * n + k]; },
+                                     [&](int v, int o, double val) {
+                                         if (!abs_lt(val, P_EIG_TOL)) small = false;
+                                         const float den = (float)(sh.diag[sh.occ_list[o]] - sh.diag[sh.virt_list[v]]);
+                                         float kf = (float)val / den;
+                                         if (!(fabsf(kf) <= 1e3f)) kf = copysignf(1e3f, kf);
+                                         Xg[o * nv + v] = (double)kf;
+                                     });
+            eok = blk_all(small);
+            // I + X^T X / 4 and I + X X^T / 4 (lower triangles)
+            pprod<true, true, true>(sh, nocc, nocc, nv, [&](int o1, int v) { return Xg[o1 * nv + v]; },
+                                    [&](int v, int o2) { return Xg[o2 * nv + v]; },
+                                    [&](int i, int c, double v) { Mo[c * nocc + i] = fma(0.25, v, i == c ? 1.0 : 0.0); });
+            pprod<true, false, false>(sh, nv, nv, nocc, [&](int v1, int o) { return Xg[o * nv + v1]; },
+                                      [&](int o, int v2) { return Xg[o * nv + v2]; },
+                                      [&](int i, int c, double v) { Mv[c * nv + i] = fma(0.25, v, i == c ? 1.0 : 0.0); });
+            // Z1 = 2 C_o + C_v X into Y[o n + i]; Z2 = 2 C_v - C_o X^T into Y[(nocc + v) n + i]
+            pprod<false, false, true>(sh, n, nocc, nv, [&](int i, int v) { return C[sh.virt_list[v] * n + i]; },
+                                      [&](int v, int o) { return Xg[o * nv + v]; },
+                                      [&](int i, int o, double v) { Y[o * n + i] = fma(2.0, C[sh.occ_list[o] * n + i], v); });
+            pprod<false, false, false>(sh, n, nv, nocc, [&](int i, int o) { return C[sh.occ_list[o] * n + i]; },
+                                       [&](int o, int v) { return Xg[o * nv + v]; },
+                                       [&](int i, int v, double val) {
+                                           Y[(nocc + v) * n + i] = fma(2.0, C[sh.virt_list[v] * n + i], -val);
+                                       });
+            pchol(Mo, nocc, sh);
+            if (j < n) row_solve_llt(Mo, nocc, sh.invd, Y + j, n, Y + j, n);
+            __syncthreads();
+            if (nv > 0) {
+                pchol(Mv, nv, sh);
+                if (j < n) row_solve_llt(Mv, nv, sh.invd, Y + nocc * n + j, n, Y + nocc * n + j, n);
+            }
+            __syncthreads();
+            for (int e = j; e < nn; e += PT) {
+                const int c = e / n, i = e - c * n;   // c < nocc: occupied column c, else virtual c - nocc
+                const int col = c < nocc ? sh.occ_list[c] : sh.virt_list[c - nocc];
+                C[col * n + i] = Y[e] - C[col * n + i];
+            }
+            __syncthreads();
+        }
+        // P = 2 C_o C_o^T (lower triangle) and the Mulliken populations
+        pprod<true, false, false>(sh, n, n, nocc, [&](int i, int o) { return C[sh.occ_list[o] * n + i]; },
+                                  [&](int o, int c) { return C[sh.occ_list[o] * n + c]; },
+                                  [&](int i, int c, double v) { P[c * n + i] = 2.0 * v; });
+        if (j < n) {
+            double qo = 0.0;
+            for (int k = 0; k < n; ++k) {
+                const int lo = min(j, k), hi = max(j, k);
+                qo = fma(P[lo * n + hi], S[k * n + j], qo);
+            }
+            sh.red[j] = qo;
+        }
+        __syncthreads();
+        const int NH = a.hist;
+        const int hs = (it - 1) % NH;
+        if (j < nat) {
+            double qa = 0.0;
+            for (int o = sh.atom_off[j]; o < sh.atom_off[j + 1]; ++o) qa += sh.red[o];
+            sh.qout[j] = qa;
+            sh.hq[hs][j] = sh.q[j];
+            sh.hf[hs][j] = qa - sh.q[j];
+        }
+        __syncthreads();
+        bool conv = eok;
+        for (int at = 0; at < nat; ++at)
+            if (!abs_lt(sh.hf[hs][at], a.scc_tol)) conv = false;
+        const int h = min(it, NH);
+        if (!conv && j == 0) {
+            // Anderson coefficients over the h - 1 previous iterates: normal equations in FP32 with
+            // a small diagonal shift, solved by Cholesky (they only steer the iteration)
+            float Mx[PHIST - 1][PHIST - 1], bv[PHIST - 1], x[PHIST - 1];
+            const int m = h - 1;
+            for (int u = 0; u < m; ++u) {
+                const int hu = (hs + NH - 1 - u) % NH;
+                float b = 0.f;
+                for (int w = 0; w <= u; ++w) {
+                    const int hw = (hs + NH - 1 - w) % NH;
+                    float sacc = 0.f;
+                    for (int at = 0; at < nat; ++at) {
+                        const float du = (float)(sh.hf[hu][at] - sh.hf[hs][at]);
+                        const float dw = (float)(sh.hf[hw][at] - sh.hf[hs][at]);
+                        sacc = fmaf(du, dw, sacc);
+                    }
+                    Mx[u][w] = sacc;
+                }
+                for (int at = 0; at < nat; ++at)
+                    b = fmaf(-(float)(sh.hf[hu][at] - sh.hf[hs][at]), (float)sh.hf[hs][at], b);
+                bv[u] = b;
+            }
+            float dmax = 0.f;
+            for (int u = 0; u < m; ++u) dmax = fmaxf(dmax, Mx[u][u]);
+            bool ok = m > 0 && dmax > 0.f;
+            for (int u = 0; u < m && ok; ++u) {
+                for (int w = 0; w <= u && ok; ++w) {
+                    float sacc = Mx[u][w] + (u == w ? 1e-6f * dmax : 0.f);
+                    for (int l = 0; l < w; ++l) sacc -= Mx[u][l] * Mx[w][l];
+                    if (u == w) {
+                        if (!(sacc > 0.f)) ok = false; else Mx[u][u] = sqrtf(sacc);
+                    } else {
+                        Mx[u][w] = sacc / Mx[w][w];
+                    }
+                }
+            }
+            if (ok) {
+                for (int u = 0; u < m; ++u) {
+                    float sacc = bv[u];
+                    for (int l = 0; l < u; ++l) sacc -= Mx[u][l] * x[l];
+                    x[u] = sacc / Mx[u][u];
+                }
+                for (int u = m - 1; u >= 0; --u) {
+                    float sacc = x[u];
+                    for (int l = u + 1; l < m; ++l) sacc -= Mx[l][u] * x[l];
+                    x[u] = sacc / Mx[u][u];
+                }
+                for (int u = 0; u < m; ++u)
+                    if (!(fabsf(x[u]) < 50.f)) ok = false;
+            }
+            for (int u = 0; u < PHIST - 1; ++u) sh.th[u] = (ok && u < m) ? (double)x[u] : 0.0;
+        }
+        __syncthreads();
+        if (j < nat) {
+            if (conv) {
+                sh.q[j] = sh.qout[j];
+            } else {
+                const double q0 = sh.hq[hs][j], f0 = sh.hf[hs][j];
+                double qb = q0, fb = f0;
+                for (int u = 0; u < h - 1; ++u) {
+                    const int hu = (hs + NH - 1 - u) % NH;
+                    qb = fma(sh.th[u], sh.hq[hu][j] - q0, qb);
+                    fb = fma(sh.th[u], sh.hf[hu][j] - f0, fb);
+                }
+                sh.q[j] = fma(a.beta, fb, qb);
+            }
+        }
+        __syncthreads();
+        if (conv) {
+            if (j == 0) sh.fl[2] = it;
+            break;
+        }
+    }
+    __syncthreads();
+    if (j == 0 && it > a.max_iter) {
+        sh.fl[0] |= ERRBIT_SCC_NOCONV;
+        sh.fl[2] = a.max_iter;
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- energy and forces
+    // Shifts of the converged charges; H; T = H C_o into Y; Aoo = C_o^T T (lower) into Mo;
+    // t = 2 Aoo C_o^T into Mv; W = C_o t (lower) into H; P = 2 C_o C_o^T (lower) into P.
+    if (j < nat) sh.dq[j] = sh.q[j] - sh.zv[j];
+    __syncthreads();
+    shifts();
+    build_h();
+    pprod<false, false, true>(sh, n, nocc, n, [&](int i, int k) { return H[k * n + i]; },
+                              [&](int k, int o) { return C[sh.occ_list[o] * n + k]; },
+                              [&](int i, int o, double v) { Y[o * n + i] = v; });
+    pprod<true, true, true>(sh, nocc, nocc, n, [&](int o1, int k) { return C[sh.occ_list[o1] * n + k]; },
+                            [&](int k, int o2) { return Y[o2 * n + k]; },
+                            [&](int i, int c, double v) { Mo[c * nocc + i] = v; });
+    pprod<false, false, false>(sh, nocc, n, nocc,
+                               [&](int o, int o2) { return Mo[min(o, o2) * nocc + max(o, o2)]; },
+                               [&](int o2, int c) { return C[sh.occ_list[o2] * n + c]; },
+                               [&](int o, int c, double v) { Mv[c * nocc + o] = 2.0 * v; });
+    pprod<true, false, true>(sh, n, n, nocc, [&](int i, int o) { return C[sh.occ_list[o] * n + i]; },
+                             [&](int o, int c) { return Mv[c * nocc + o]; },
+                             [&](int i, int c, double v) { H[c * n + i] = v; });
+    pprod<true, false, false>(sh, n, n, nocc, [&](int i, int o) { return C[sh.occ_list[o] * n + i]; },
+                              [&](int o, int c) { return C[sh.occ_list[o] * n + c]; },
+                              [&](int i, int c, double v) { P[c * n + i] = 2.0 * v; });
+    if (j == 0 && nocc < n) {   // HOMO-LUMO gap of the last iteration
+        double homo = -1e300, lumo = 1e300;
+        for (int c = 0; c < n; ++c) {
+            if (sh.occf[c]) homo = fmax(homo, sh.diag[c]); else lumo = fmin(lumo, sh.diag[c]);
+        }
+        if (!(lumo - homo > P_MIN_GAP)) sh.fl[0] |= ERRBIT_ZERO_GAP;
+    }
+    if (j < n) {   // band energy sum P H0, by column of the lower triangle
+        double eb = 0.0;
+        for (int i = j; i < n; ++i) eb = fma((i == j ? 1.0 : 2.0) * P[j * n + i], H0[j * n + i], eb);
+        sh.red[j] = eb;
+    }
+    __syncthreads();
+    const double *W = H;
+    // pair tasks A <= B: d/dr_B of every image term (band, overlap, second order, repulsion), and
+    // the repulsion energy (an atom with its own images counts each image pair once)
+    for (int t = j; t < nat * nat; t += PT) {
+        const int A = t / nat, B = t - A * nat;
+        if (B < A) continue;
+        const int eA = sh.spec[A], eB = sh.spec[B];
+        const int oA = sh.atom_off[A], oB = sh.atom_off[B];
+        const int na = sk.norb[eA], nb = sk.norb[eB];
+        double d[3], f[3], dw[3];
+        for (int k = 0; k < 3; ++k) d[k] = sh.pos[B][k] - sh.pos[A][k];
+        for (int k = 0; k < 3; ++k) f[k] = rint(fma(d[0], pl.inv[k], fma(d[1], pl.inv[3 + k], d[2] * pl.inv[6 + k])));
+        for (int k = 0; k < 3; ++k) dw[k] = d[k] - fma(f[0], pl.lat[k], fma(f[1], pl.lat[3 + k], f[2] * pl.lat[6 + k]));
+        const double hshift = 0.5 * (sh.shift[A] + sh.shift[B]);
+        const double qq = sh.dq[A] * sh.dq[B];
+        const double c2 = sk.gamma_c2[eA][eB];
+        const double rc2 = sk.r_cut * sk.r_cut;
+        const double arep = sk.rep[eA][eB][0], brep = sk.rep[eA][eB][1];
+        const double two_a_spi = 2.0 * pl.alpha * 0.5641895835477563;   // 2 alpha / sqrt(pi)
+        double gk[3] = {0.0, 0.0, 0.0};
+        double erep = 0.0;
+        for (int im = 0; im < pl.n_img; ++im) {
+            const double x0 = dw[0] + pl.img[3 * im], x1 = dw[1] + pl.img[3 * im + 1], x2 = dw[2] + pl.img[3 * im + 2];
+            const double r2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            if (!(r2 < pl.r_real2) || r2 == 0.0) continue;
+            const double ir = rsqrt_nr(r2);
+            const double r = r2 * ir;
+            const double e[3] = {x0 * ir, x1 * ir, x2 * ir};
+            double rad = 0.0;   // d/dr of the radial terms, along e
+            if (A != B) {
+                const double ar = pl.alpha * r;
+                rad = -qq * (erfc(ar) * ir + two_a_spi * exp(-ar * ar)) * ir;
+            }
+            if (r2 < rc2) {
+                double fc, dfc;
+                cutoff_fn(r, sk, fc, dfc);
+                if (arep != 0.0) {
+                    const double vr = arep * exp(-brep * r);
+                    erep = fma(vr, fc, erep);
+                    if (A != B) rad = fma(vr, dfc - brep * fc, rad);
+                }
+                if (A != B) {
+                    const double gi = rsqrt_nr(r2 + c2);
+                    const double s_ = gi - ir;
+                    const double ds = fma(-r * gi, gi * gi, ir * ir);
+                    rad = fma(qq, fma(ds, fc, s_ * dfc), rad);
+                    // band and overlap terms: weights P and P (eps_A + eps_B) / 2 - W of the block
+                    double g[3] = {0.0, 0.0, 0.0};
+                    for (int tb = 0; tb < 2; ++tb) {
+                        const double(*tab)[CAVMD_MAX_ELEM][4][4] = tb == 0 ? sk.h0 : sk.s;
+                        auto wt = [&](int mu, int nu) -> double {   // mu of A < nu of B: lower entry (nu, mu)
+                            const double pv = P[mu * n + nu];
+                            return tb == 0 ? pv : fma(pv, hshift, -W[mu * n + nu]);
+                        };
+                        double v, dv;
+                        radial_p(tab[eA][eB][CAVMD_SK_SS], r, sk, v, dv);
+                        {
+                            const double w = wt(oA, oB) * dv;
+                            for (int k = 0; k < 3; ++k) g[k] = fma(w, e[k], g[k]);
+                        }
+                        if (nb == 4) {
+                            radial_p(tab[eA][eB][CAVMD_SK_SP], r, sk, v, dv);
+                            double w[3], we = 0.0;
+                            for (int i = 0; i < 3; ++i) { w[i] = wt(oA, oB + 1 + i); we = fma(w[i], e[i], we); }
+                            for (int k = 0; k < 3; ++k) g[k] += fma(w[k] - we * e[k], v * ir, we * e[k] * dv);
+                        }
+                        if (na == 4) {
+                            radial_p(tab[eB][eA][CAVMD_SK_SP], r, sk, v, dv);
+                            double w[3], we = 0.0;
+                            for (int i = 0; i < 3; ++i) { w[i] = wt(oA + 1 + i, oB); we = fma(w[i], e[i], we); }
+                            for (int k = 0; k < 3; ++k) g[k] -= fma(w[k] - we * e[k], v * ir, we * e[k] * dv);
+                        }
+                        if (na == 4 && nb == 4) {
+                            double vs, dvs, vp, dvp;
+                            radial_p(tab[eA][eB][CAVMD_SK_PPS], r, sk, vs, dvs);
+                            radial_p(tab[eA][eB][CAVMD_SK_PPP], r, sk, vp, dvp);
+                            double Wm[3][3], We[3] = {0, 0, 0}, WTe[3] = {0, 0, 0}, tr = 0.0;
+                            for (int i = 0; i < 3; ++i)
+                                for (int k = 0; k < 3; ++k) Wm[i][k] = wt(oA + 1 + i, oB + 1 + k);
+                            for (int i = 0; i < 3; ++i) {
+                                tr += Wm[i][i];
+                                for (int k = 0; k < 3; ++k) {
+                                    We[i] = fma(Wm[i][k], e[k], We[i]);
+                                    WTe[k] = fma(Wm[i][k], e[i], WTe[k]);
+                                }
+                            }
+                            double eWe = 0.0;
+                            for (int i = 0; i < 3; ++i) eWe = fma(e[i], We[i], eWe);
+                            const double dl = vs - vp, ddl = dvs - dvp;
+                            for (int k = 0; k < 3; ++k)
+                                g[k] += (We[k] + WTe[k] - 2.0 * eWe * e[k]) * dl * ir + eWe * e[k] * ddl + tr * e[k] * dvp;
+                        }
+                    }
+                    for (int k = 0; k < 3; ++k) gk[k] = fma(2.0, g[k], gk[k]);
+                }
+            }
+            for (int k = 0; k < 3; ++k) gk[k] = fma(rad, e[k], gk[k]);
+        }
+        double *pb = pbuf + 4LL * (A * nat + B);
+        pb[0] = gk[0];
+        pb[1] = gk[1];
+        pb[2] = gk[2];
+        pb[3] = A == B ? 0.5 * erep : erep;
+    }
+    __syncthreads();
+    if (j < nat) {
+        // reciprocal part: d/dr_A of 1/2 sum_G w_G |S(G)|^2 = dq_A sum_G w_G G (c_A S_s - s_A S_c)
+        double gr[3] = {0.0, 0.0, 0.0};
+        for (int g = 0; g < pl.n_g; ++g) {
+            const double *t = csg + 2LL * (g * nat + j);
+            const double amp = pl.gw[4 * g + 3] * fma(t[0], sgf[2 * g + 1], -t[1] * sgf[2 * g]);
+            for (int k = 0; k < 3; ++k) gr[k] = fma(amp, pl.gw[4 * g + k], gr[k]);
+        }
+        double G[3];
+        for (int k = 0; k < 3; ++k) G[k] = sh.dq[j] * gr[k];
+        for (int A = 0; A < nat; ++A) {
+            if (A == j) continue;
+            const double *pb = pbuf + 4LL * (A < j ? A * nat + j : j * nat + A);
+            const double sg = A < j ? 1.0 : -1.0;
+            for (int k = 0; k < 3; ++k) G[k] = fma(sg, pb[k], G[k]);
+        }
+        const int at = a0 + j;
+        for (int k = 0; k < 3; ++k) a.F[3 * at + k] = -G[k];
+        a.qprev[at] = a.have_warm ? sh.qst[j] : sh.q[j];
+        a.qpop[at] = sh.q[j];
+        if (a.Qout) a.Qout[at] = sh.zv[j] - sh.q[j];
+        if (a.write_b) {
+            const double Q = sh.zv[j] - sh.q[j];
+            a.b[3 * at + 0] = Q * a.pol0;
+            a.b[3 * at + 1] = Q * a.pol1;
+            a.b[3 * at + 2] = Q * a.pol2;
+        }
+    }
+    if (j == 0) {
+        double E = 0.0;
+        for (int i = 0; i < n; ++i) E += sh.red[i];
+        double e2 = 0.0;
+        for (int x = 0; x < nat; ++x) e2 = fma(sh.dq[x], sh.shift[x], e2);
+        E = fma(0.5, e2, E);
+        for (int A = 0; A < nat; ++A)
+            for (int B = A; B < nat; ++B) E += pbuf[4LL * (A * nat + B) + 3];
+        double mu[3] = {0.0, 0.0, 0.0};
+        for (int at = 0; at < nat; ++at) {
+            const double Q = sh.zv[at] - sh.q[at];
+            for (int k = 0; k < 3; ++k) mu[k] = fma(Q, sh.pos[at][k] - sh.pos[0][k], mu[k]);
+        }
+        a.E_cell[cell] = E;
+        a.M_cell[cell] = fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
+        a.iters[cell] = sh.fl[2];
+        if (sh.fl[0]) atomicOr(a.status, (unsigned)sh.fl[0]);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(PT, 2) k_dftb_periodic(const DevSK *__restrict__ skp, const DftbArgs a, const PbcDev pl) {
+    extern __shared__ __align__(16) unsigned char p_smem[];
+    PShared &sh = *reinterpret_cast<PShared *>(p_smem);
+    const DevSK &sk = *skp;
+    double *wk = pl.work + (long long)blockIdx.x * pl.work_stride;
+    for (int cell = blockIdx.x; cell < a.n_cells; cell += gridDim.x) p_cell(sk, a, pl, sh, wk, cell);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Host side
+
+size_t pbc_workspace_doubles(int nmax, int amax, int n_g) {
+    const size_t n2 = (size_t)nmax * nmax;
+    return 8 * n2 + (size_t)amax * amax + 2 * (size_t)amax * n_g + 2 * (size_t)n_g + 4 * (size_t)amax * amax + 32;
+}
+
+// Lattice images and reciprocal vectors for one lattice (rows a_i), and the Ewald constants. The
+// splitting parameter is chosen so the half-space reciprocal list holds about 1000 vectors; every
+// term left out of either sum is below 1e-18 (erfc(6.5) and exp(-6.5^2)).
+void plan_dftb_periodic(const double *lat, double r_cut, PbcPlan &p, std::vector<double> &img,
+                        std::vector<double> &gw) {
+    for (int k = 0; k < 9; ++k) p.lat[k] = lat[k];
+    const double a0 = lat[0], a1 = lat[1], a2 = lat[2], b0 = lat[3], b1 = lat[4], b2 = lat[5], c0 = lat[6],
+                 c1 = lat[7], c2 = lat[8];
+    const double det = a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0);
+    // inverse (f = r inv with r a row vector): inv = lat^-1
+    double inv[9];
+    inv[0] = (b1 * c2 - b2 * c1) / det; inv[1] = (a2 * c1 - a1 * c2) / det; inv[2] = (a1 * b2 - a2 * b1) / det;
+    inv[3] = (b2 * c0 - b0 * c2) / det; inv[4] = (a0 * c2 - a2 * c0) / det; inv[5] = (a2 * b0 - a0 * b2) / det;
+    inv[6] = (b0 * c1 - b1 * c0) / det; inv[7] = (a1 * c0 - a0 * c1) / det; inv[8] = (a0 * b1 - a1 * b0) / det;
+    for (int k = 0; k < 9; ++k) p.inv[k] = inv[k];
+    const double V = std::fabs(det);
+    const double EX = 6.5;
+    const double pi = 3.141592653589793;
+    // half-space count N ~ (4 pi / 3) (2 alpha EX)^3 V / (2 (2 pi)^3)  ->  alpha for N = 1000
+    const double g_cube = 1000.0 * 2.0 * std::pow(2.0 * pi, 3) * 3.0 / (4.0 * pi * V);
+    const double alpha = std::cbrt(g_cube) / (2.0 * EX);
+    p.alpha = alpha;
+    p.bg = -pi / (alpha * alpha * V);
+    p.self_e = -2.0 * alpha / std::sqrt(pi);
+    const double r_real = std::max(EX / alpha, r_cut);
+    p.r_real = r_real;
+    // farthest point of a wrapped separation (fractional coordinates in [-1/2, 1/2]): a corner
+    double hmax = 0.0;
+    for (int s = 0; s < 8; ++s) {
+        const double f0 = (s & 1) ? 0.5 : -0.5, f1 = (s & 2) ? 0.5 : -0.5, f2 = (s & 4) ? 0.5 : -0.5;
+        double x[3];
+        for (int k = 0; k < 3; ++k) x[k] = f0 * lat[k] + f1 * lat[3 + k] + f2 * lat[6 + k];
+        hmax = std::max(hmax, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]));
+    }
+    // heights across the faces: h_i = 1 / |column i of inv|
+    int N[3];
+    for (int i = 0; i < 3; ++i) {
+        const double h = 1.0 / std::sqrt(inv[i] * inv[i] + inv[3 + i] * inv[3 + i] + inv[6 + i] * inv[6 + i]);
+        N[i] = (int)std::ceil((r_real + hmax) / h) + 1;
+    }
+    img.clear();
+    const double reach = r_real + hmax;
+    for (int n0 = -N[0]; n0 <= N[0]; ++n0)
+        for (int n1 = -N[1]; n1 <= N[1]; ++n1)
+            for (int n2 = -N[2]; n2 <= N[2]; ++n2) {
+                double T[3];
+                for (int k = 0; k < 3; ++k) T[k] = n0 * lat[k] + n1 * lat[3 + k] + n2 * lat[6 + k];
+                if (std::sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]) < reach)
+                    img.insert(img.end(), T, T + 3);
+            }
+    p.n_img = (int)(img.size() / 3);
+    // reciprocal rows b_j = 2 pi (column j of inv), G = m b; half space: first nonzero m positive
+    double B[9];
+    for (int jx = 0; jx < 3; ++jx)
+        for (int k = 0; k < 3; ++k) B[3 * jx + k] = 2.0 * pi * inv[3 * k + jx];
+    const double g_max = 2.0 * alpha * EX;
+    int M[3];
+    for (int i = 0; i < 3; ++i) {   // heights of the reciprocal cell: 2 pi / |a_i|
+        const double an = std::sqrt(lat[3 * i] * lat[3 * i] + lat[3 * i + 1] * lat[3 * i + 1] + lat[3 * i + 2] * lat[3 * i + 2]);
+        M[i] = (int)std::ceil(g_max * an / (2.0 * pi)) + 1;
+    }
+    gw.clear();
+    for (int m0 = -M[0]; m0 <= M[0]; ++m0)
+        for (int m1 = -M[1]; m1 <= M[1]; ++m1)
+            for (int m2 = -M[2]; m2 <= M[2]; ++m2) {
+                const bool pos = m0 > 0 || (m0 == 0 && (m1 > 0 || (m1 == 0 && m2 > 0)));
+                if (!pos) continue;
+                double G[3];
+                for (int k = 0; k < 3; ++k) G[k] = m0 * B[k] + m1 * B[3 + k] + m2 * B[6 + k];
+                const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+                if (!(g2 < g_max * g_max)) continue;
+                const double w = 4.0 * pi / V * std::exp(-g2 / (4.0 * alpha * alpha)) / g2;
+                gw.push_back(G[0]);
+                gw.push_back(G[1]);
+                gw.push_back(G[2]);
+                gw.push_back(2.0 * w);
+            }
+    p.n_g = (int)(gw.size() / 4);
+}
+
+size_t pbc_smem() { return sizeof(PShared); }
+
+cudaError_t prepare_dftb_periodic() {
+    return cudaFuncSetAttribute(k_dftb_periodic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PShared));
+}
+
+cudaError_t launch_dftb_periodic(const DevSK *sk_dev, const DftbArgs &a, const PbcPlan &p, cudaStream_t st) {
+    if (a.n_cells <= 0) return cudaSuccess;
+    PbcDev d;
+    for (int k = 0; k < 9; ++k) { d.lat[k] = p.lat[k]; d.inv[k] = p.inv[k]; }
+    d.alpha = p.alpha;
+    d.bg = p.bg;
+    d.self_e = p.self_e;
+    d.r_real2 = p.r_real * p.r_real;
+    d.n_img = p.n_img;
+    d.n_g = p.n_g;
+    d.nmax = p.nmax;
+    d.amax = p.amax;
+    d.img = p.d_img;
+    d.gw = p.d_gw;
+    d.work = p.work;
+    d.work_stride = (long long)pbc_workspace_doubles(p.nmax, p.amax, p.n_g);
+    const int grid = std::min(a.n_cells, p.blocks);
+    k_dftb_periodic<<<grid, PT, sizeof(PShared), st>>>(sk_dev, a, d);
+    return cudaGetLastError();
+}

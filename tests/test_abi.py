@@ -54,7 +54,7 @@ def test_default_options(lib):
     assert o.scc_tol == 1e-12 and o.precision == 0 and o.charge_model == 0 and o.splitting == 0
 
 
-def _init_rc(lib, system, params, modes, opt=None):
+def _init_rc(lib, system, params, modes, opt=None, lattice=None):
     """Call cavmd_init through the C ABI and return (rc, message). Invalid inputs are rejected
     by host-side validation before any CUDA call, so this runs without a GPU."""
     from paper_2512_03277_gb300 import cavmd as B
@@ -67,6 +67,9 @@ def _init_rc(lib, system, params, modes, opt=None):
     sysc.n_cells, sysc.n_atoms = len(off) - 1, len(spec)
     sysc.cell_offset, sysc.species = B._ptr(off, C.c_int32), B._ptr(spec, C.c_int32)
     sysc.r, sysc.p = B._ptr(r), B._ptr(p)
+    if lattice is not None:
+        lat = np.ascontiguousarray(lattice, np.float64).reshape(9)
+        sysc.lattice = B._ptr(lat)
     md = B.cavmd_modes()
     k = np.ascontiguousarray(modes.k, np.float64).ravel()
     w, lam, phi = (np.ascontiguousarray(x, np.float64) for x in (modes.omega, modes.lam, modes.phi))
@@ -158,3 +161,19 @@ def test_rejects_empty_inputs(lib, small):
     mo = small["modes"]
     none = cs.Modes(k=np.zeros((0, 3)), omega=np.zeros(0), lam=np.zeros(0), phi=np.zeros(0))
     assert _init_rc(lib, s, small["params"], none)[0] == -1
+
+
+def test_periodic_cells_validation(lib, small):
+    """Periodic cells: linearly dependent lattice vectors are invalid; charge models other than
+    Mulliken are refused as unsupported; both before any device work."""
+    sy, lat = cs.periodic_water_cells(np.random.default_rng(5), np.zeros((1, 3)), n_waters=2, side=8.5,
+                                      d_min=4.0, d_atom=2.8)
+    flat = lat.copy()
+    flat[2] = flat[0] + flat[1]
+    rc, msg = _init_rc(lib, sy, small["params"], small["modes"], lattice=flat)
+    assert rc == -1 and "lattice" in msg
+    import paper_2512_03277_gb300 as P
+    o = P.default_options()
+    o.charge_model = 1
+    rc, msg = _init_rc(lib, sy, small["params"], small["modes"], opt=o, lattice=lat)
+    assert rc == -8 and "Mulliken" in msg
