@@ -55,6 +55,26 @@ def _dftb_flops_per_cell(iters, n=6, nocc=4, npair=3):
     return per_iter * np.asarray(iters, float) + 1000.0 * npair
 
 
+def _periodic_flops_per_cell(iters, n, nocc):
+    """FP64 flops of the products one periodic cell needs per time step in the warm-started Gamma-point
+    SCC (n orbitals, o = n_occ occupied, v = n - o virtual):
+      start, once: S C (2n^3), C^T S C lower (n^3), its Cholesky (n^3/3), C L^-T (n^3);
+      per SCC iteration: H C (2n^3), the occupied-virtual block of C^T H C (2 n o v), X^T X and X X^T
+        lower (o^2 v + v^2 o), C_v X and C_o X^T (4 n o v), Cholesky factors (o^3/3 + v^3/3), their
+        row solves (2 n (o^2 + v^2)), P lower (n^2 o), H, the diagonal and Mulliken (7 n^2);
+      forces, once: H C_o (2 n^2 o), C_o^T H C_o lower (n o^2), t = 2 Aoo C_o^T (2 n o^2),
+        W and P lower (2 n^2 o).
+    A full eigensolve per iteration (the 9 n^3 of the isolated-cell count) is never done."""
+    n = float(n)
+    o = float(nocc)
+    v = n - o
+    start = (2.0 + 1.0 + 1.0 / 3.0 + 1.0) * n ** 3
+    per_iter = (2 * n ** 3 + 2 * n * o * v + o * o * v + v * v * o + 4 * n * o * v + (o ** 3 + v ** 3) / 3
+                + 2 * n * (o * o + v * v) + n * n * o + 7 * n * n)
+    forces = 2 * n * n * o + n * o * o + 2 * n * o * o + 2 * n * n * o
+    return start + per_iter * np.asarray(iters, float) + forces
+
+
 def _cell_shapes(system):
     """Orbitals, occupied orbitals and atom pairs of every cell of a water or cluster system."""
     nat = np.diff(system.cell_offset)
@@ -114,13 +134,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _oracle_matter(w):
+    from oracle import cavity as OC
+    from oracle import periodic as PR
+    if w.get("lattice") is not None:
+        return PR.PeriodicDFTBMatter(w["params"], w["system"], w["lattice"])
+    return OC.DFTBMatter(w["params"], w["system"])
+
+
 def cpu_baseline(workload, seconds=12.0, n_sample=None):
     """The oracle as it stands, on a bounded sample of the workload, on this host."""
     import cavmd_synth as cs
     from oracle import cavity as OC
     w = cs.make_workload(workload, n_cells=n_sample)
     sy, mo, pa = w["system"], w["modes"], w["params"]
-    mat = OC.DFTBMatter(pa, sy)
+    mat = _oracle_matter(w)
     md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
     md.step()                                   # warm start of the charges
     t0 = time.perf_counter()
@@ -142,11 +170,11 @@ def run_reference(args):
         return
     import cavmd_synth as cs
     from oracle import cavity as OC
-    n_sample = 512
+    n_sample = 1 if args.workload == "p33" else 512
     w = cs.make_workload(args.workload)
     sub = cs.make_workload(args.workload, n_cells=n_sample)
     sy, mo, pa = sub["system"], w["modes"], sub["params"]
-    mat = OC.DFTBMatter(pa, sy)
+    mat = _oracle_matter(sub)
     md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
     for _ in range(args.warmup):
         md.step()
@@ -173,6 +201,9 @@ def _config(workload, w, charge_model="mulliken", precision="fp64", mode_positio
     nw = sy.n_atoms // 3
     cells = (f"{nw} water" if nw == sy.n_cells else
              f"{sy.n_cells} clusters (H2O)_n, n = 1..8 ({nw} water molecules, up to 48 orbitals)")
+    if w.get("lattice") is not None:
+        cells = (f"{sy.n_cells} periodic cells of {nw // sy.n_cells} water (10 Angstrom cubes, Gamma point, "
+                 f"{nw} water molecules, {2 * nw // sy.n_cells * 3} orbitals per cell)")
     cm = {"mulliken": "Mulliken", "born_fd": "forward-FD Born every 3 steps",
           "born_central": "central-FD Born every 3 steps", "born_mlp": "network Born charges"}[charge_model]
     cp = "FP64 coupling" if precision == "fp64" else "BF16x3 tensor-core coupling"
@@ -247,7 +278,7 @@ def main():
     if args.acf_lags is None:
         args.acf_lags = 1024 if args.workload == "c5" else 0
     opt.acf_lags = args.acf_lags
-    ctx = P.Context(w["system"], w["params"], w["modes"], opt)
+    ctx = P.Context(w["system"], w["params"], w["modes"], opt, lattice=w.get("lattice"))
     if args.charge_model == "born_mlp":
         # a seeded network: the cost of a time step does not depend on the weight values
         rng = np.random.default_rng(4)
@@ -308,7 +339,12 @@ def main():
         dftb_ms = phase_ms[0] / max(phase_cnt[0], 1)
     else:   # measured inside the timed region
         dftb_ms = timed_ms[0] / max(timed_cnt[0], 1)
-    flops = float(_dftb_flops_per_cell(ev["scc_iters"], *_cell_shapes(w["system"])).sum())
+    periodic = w.get("lattice") is not None
+    if periodic:
+        n_orb = 2 * np.diff(w["system"].cell_offset)          # 6 per water: 2 per atom
+        flops = float(sum(_periodic_flops_per_cell(i, n, n * 2 // 3) for i, n in zip(ev["scc_iters"], n_orb)))
+    else:
+        flops = float(_dftb_flops_per_cell(ev["scc_iters"], *_cell_shapes(w["system"])).sum())
     generic = not np.all(np.diff(w["system"].cell_offset) == 3)
     achieved = flops / (dftb_ms * 1e-3) / 1e12
     peak = N_SM * FP64_FLOPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
@@ -346,7 +382,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": _config(args.workload, w, args.charge_model, args.precision, args.mode_positions),
-        "roofline": {"bound": "alu", "kernel": "k_dftb_generic" if generic else "dftb_kernel<3,6>",
+        "roofline": {"bound": "alu",
+                     "kernel": "k_dftb_periodic" if periodic else ("k_dftb_generic" if generic else "dftb_kernel<3,6>"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": DFTB_DRAM_BYTES_PER_LAUNCH if (args.workload == "c2" and args.n_cells is None) else None,
                      "flops_per_launch": flops, "avg_launch_ms": dftb_ms,
@@ -368,6 +405,8 @@ def main():
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n_sample = None if w["system"].n_cells <= 4096 else (1024 if generic else 4096)
+        if periodic:
+            n_sample = 1
         line["cpu_baseline"] = cpu_baseline(args.workload, n_sample=n_sample)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -276,10 +276,10 @@ def grid_modes(Kx: int, Ky: int, dkx: float, dky: float, L: float, g: float, n_r
 
 
 # ---------------------------------------------------------------------------------------------
-# The five workloads. ``n_cells`` trims a workload to fewer cells with the same recipe (the box
+# The workloads (c1..c5, and p33, periodic cells). ``n_cells`` trims a workload to fewer cells with the same recipe (the box
 # shrinks so the density stays the same); ``n_modes`` does the same for the mode count.
 
-WORKLOADS = ("c1", "c2", "c3", "c4", "c5")
+WORKLOADS = ("c1", "c2", "c3", "c4", "c5", "p33")
 
 
 def _slab_box(n_waters: float, thickness: float = 30.0):
@@ -336,7 +336,19 @@ def make_workload(name: str, n_cells: Optional[int] = None, n_modes: Optional[in
         modes = grid_modes(Kx, Ky, 2 * np.pi / box0[0], 2 * np.pi / box0[1], 2000.0, 0.001)
         opts.update(steps=10000 if name == "c4" else 20000, g=0.001, charge_model="born_mlp",
                     precision="mixed")
+    elif name == "p33":
+        # the paper's cell: 33 waters in a periodic 10 Angstrom cube; the cubes sit side by side
+        # along the cavity line (x), 304 of them (10,032 waters), 512 line modes as in c2
+        n = 304 if n_cells is None else n_cells
+        side = 10.0 * 1.8897261
+        centres = np.zeros((n, 3))
+        centres[:, 0] = (np.arange(n) + 0.5) * side
+        system, lattice = periodic_water_cells(rg, centres, side=side)
+        L0 = 304 * side
+        modes = line_modes(512 if n_modes is None else n_modes, L0, 0.001, k_max=10.0 * np.pi / L0)
+        opts.update(steps=2000, g=0.001, lattice=lattice)
     else:
         raise ValueError(f"unknown workload {name!r}")
     system.p = mb_momenta(rv, system, opts["temperature"])
-    return {"name": name, "system": system, "modes": modes, "params": params, "options": opts}
+    return {"name": name, "system": system, "modes": modes, "params": params, "options": opts,
+            "lattice": opts.get("lattice")}

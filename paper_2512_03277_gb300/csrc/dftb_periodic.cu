@@ -24,7 +24,10 @@
 // K(v, o) = A_vo / (A_oo - A_vv), which is orthogonal to rounding for any K (it needs two small
 // Cholesky factorisations, I + X^T X / 4 and I + X X^T / 4, X = K_vo). A cold start diagonalises
 // C^T H C once by cyclic Jacobi sweeps; warm starts re-orthonormalise the previous step's C under
-// the new overlap by a Cholesky factor of C^T S C.
+// the new overlap by a Cholesky factor of C^T S C, and their first iteration runs one Jacobi sweep
+// inside the occupied and inside the virtual block: the diagonal denominators need those blocks
+// diagonal, and without the sweep their off-diagonal part grows with every step (its norm over
+// 132 nearly degenerate occupied orbitals reaches the gap) and the iteration count with it.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -440,6 +443,62 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         __syncthreads();
     };
     auto Cat = [&](int i, int c) -> double { return C[c * n + i]; };
+    // One cyclic Jacobi sweep on the block Ab = C_b^T Y_b of the columns list[0..m-1] (occupied or
+    // virtual), every rotation applied to those columns of C and Y as well: it keeps the diagonal
+    // blocks of C^T H C diagonal, which the generator's diagonal denominators need (the
+    // occupied-virtual rotations leave them alone, and within a block they drift with every step).
+    auto block_sweep = [&](const int *list, int m, double *Ab) {
+        pprod<false, true, true>(sh, m, m, n, [&](int i, int k) { return C[list[i] * n + k]; },
+                                 [&](int k, int c) { return Y[list[c] * n + k]; },
+                                 [&](int i, int c, double v) { Ab[c * m + i] = v; });
+        const int mm = m + (m & 1), half = mm / 2, span = m + 2 * n;
+        for (int rd = 0; rd < mm - 1; ++rd) {
+            if (j < half) {
+                int p, qq;
+                p_pair(j, rd, mm, p, qq);
+                double c = 1.0, s = 0.0;
+                if (qq < m) p_jacobi_cs(Ab[p * m + p], Ab[qq * m + qq], Ab[qq * m + p], c, s);
+                sh.pp[j] = p;
+                sh.pq[j] = qq;
+                sh.cs[2 * j] = c;
+                sh.cs[2 * j + 1] = s;
+            }
+            __syncthreads();
+            for (int e = j; e < half * span; e += PT) {   // columns p, q of Ab, C and Y
+                const int k = e / span, r = e - k * span;
+                const int p = sh.pp[k], qq = sh.pq[k];
+                if (qq >= m) continue;
+                const double c = sh.cs[2 * k], s = sh.cs[2 * k + 1];
+                double *x, *y;
+                if (r < m) {
+                    x = Ab + p * m + r;
+                    y = Ab + qq * m + r;
+                } else if (r < m + n) {
+                    x = C + list[p] * n + (r - m);
+                    y = C + list[qq] * n + (r - m);
+                } else {
+                    x = Y + list[p] * n + (r - m - n);
+                    y = Y + list[qq] * n + (r - m - n);
+                }
+                const double xp = *x, yq = *y;
+                *x = fma(c, xp, -s * yq);
+                *y = fma(s, xp, c * yq);
+            }
+            __syncthreads();
+            for (int e = j; e < half * m; e += PT) {   // rows p, q of Ab
+                const int k = e / m, cc = e - k * m;
+                const int p = sh.pp[k], qq = sh.pq[k];
+                if (qq >= m) continue;
+                const double ck = sh.cs[2 * k], sk_ = sh.cs[2 * k + 1];
+                const double x = Ab[cc * m + p], y = Ab[cc * m + qq];
+                Ab[cc * m + p] = fma(ck, x, -sk_ * y);
+                Ab[cc * m + qq] = fma(sk_, x, ck * y);
+            }
+            __syncthreads();
+        }
+        if (j < m) sh.diag[list[j]] = Ab[j * m + j];
+        __syncthreads();
+    };
 
     // ---------------------------------------------------------------- S-orthonormal start
     if (!a.have_warm)
@@ -540,6 +599,10 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
             rank_occupation();
         } else {
             rank_occupation();
+            if (a.have_warm && it == 1) {   // first iteration after a geometry change
+                block_sweep(sh.occ_list, nocc, Mo);
+                block_sweep(sh.virt_list, nv, Mv);
+            }
             bool small = true;
             // A_vo (entry (v, o), v fastest) and the generator, stored X[o nv + v]
             pprod<false, true, true>(sh, nv, nocc, n, [&](int v, int k) { return C[sh.virt_list[v] * n + k]; },

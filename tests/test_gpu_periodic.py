@@ -118,6 +118,33 @@ def test_trajectory_matches_oracle(P):
         np.testing.assert_allclose(ctx.cavmd_observables()["e_total"], md.energies()["total"], rtol=1e-11)
 
 
+def test_liquid_cell_warm_steps(P):
+    """The paper's cell through warm steps: three steps against the oracle (the within-block
+    Jacobi sweep and the Cayley updates at 198 orbitals), then 30 more in which the SCC iteration
+    count stays flat (without the sweep it grew step by step until the SCC failed)."""
+    sy, lat = _cells(1, n_waters=33, side=10.0 * cs.ANGSTROM, seed=5)
+    params = cs.load_water_params()
+    mo = cs.make_workload("c1", n_cells=2)["modes"]
+    ctx = _ctx(P, sy, lat, modes=mo, graph_chunk=0)
+    md = OC.CavityMD(PR.PeriodicDFTBMatter(params, sy, lat), sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi,
+                     sy.R_ref, cs.make_workload("c1", n_cells=2)["options"]["dt"])
+    x0 = sy.r.copy()
+    for s in range(3):
+        ctx.cavmd_step(1)
+        md.step()
+        st = ctx.cavmd_get_state()
+        tol = 1e-9 * (1 + s)
+        dr = md.r - x0
+        np.testing.assert_allclose(st["r"] - x0, dr, rtol=0, atol=tol * np.abs(dr).max())
+        np.testing.assert_allclose(st["p"], md.p, rtol=0, atol=tol * np.abs(md.p).max())
+        np.testing.assert_allclose(ctx.cavmd_get_eval()["q_pop"], md.matter.q, rtol=0, atol=1e-10)
+    its = []
+    for s in range(30):
+        ctx.cavmd_step(1)
+        its.append(ctx.cavmd_observables(want_arrays=False)["scc_iter_max"])
+    assert max(its) <= 16, its
+
+
 def test_graph_replay_is_bitwise_identical(P):
     sy, lat = _cells(3)
     a = _ctx(P, sy, lat, graph_chunk=0)
