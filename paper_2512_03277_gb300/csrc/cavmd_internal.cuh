@@ -198,7 +198,8 @@ cudaError_t launch_dftb_generic(const DevSK *sk_dev, const DftbArgs &a, const Ge
 struct PbcPlan {
     double lat[9], inv[9];                // lattice vectors as rows; inverse (f = r inv)
     double alpha, bg, self_e, r_real;     // Ewald splitting, background and self terms, real-space cutoff
-    int n_img, n_g;                       // lattice translations; half-space reciprocal vectors
+    int n_img, n_img_sk, n_g;             // lattice translations (by length; the first n_img_sk reach
+                                          // r_cut); half-space reciprocal vectors
     int nmax, amax, blocks;               // largest cell; persistent blocks (2 per SM)
     double *d_img, *d_gw;                 // device: [n_img][3], [n_g][4] (G, 2 w_G)
     double *work;                         // device: per-block workspaces

@@ -254,8 +254,9 @@ struct PbcDev {
     double lat[9], inv[9];       // lattice vectors as rows; fractional coordinates f = r inv
     double alpha, bg, self_e;    // Ewald alpha, -pi / (alpha^2 V), -2 alpha / sqrt(pi)
     double r_real2;              // real-space cutoff squared
-    int n_img, n_g, nmax, amax;
-    const double *img;           // [n_img][3] lattice translations (every image within reach)
+    int n_img, n_img_sk, n_g, nmax, amax;
+    const double *img;           // [n_img][3] lattice translations by increasing length; the first
+                                 // n_img_sk reach every image within r_cut
     const double *gw;            // [n_g][4] half-space reciprocal vectors G and 2 w_G
     double *work;                // per-block workspaces
     long long work_stride;       // doubles per block
@@ -329,14 +330,19 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         double g_re = 0.0, g_sr = 0.0;
         const double c2 = sk.gamma_c2[eA][eB];
         const double rc2 = sk.r_cut * sk.r_cut;
-        for (int im = 0; im < pl.n_img; ++im) {
+        for (int im = 0; im < pl.n_img; ++im) {   // real-space Ewald sum
             const double x0 = dw[0] + pl.img[3 * im], x1 = dw[1] + pl.img[3 * im + 1], x2 = dw[2] + pl.img[3 * im + 2];
             const double r2 = fma(x0, x0, fma(x1, x1, x2 * x2));
             if (!(r2 < pl.r_real2) || r2 == 0.0) continue;
             const double ir = rsqrt_nr(r2);
+            g_re = fma(erfc(pl.alpha * (r2 * ir)), ir, g_re);
+        }
+        for (int im = 0; im < pl.n_img_sk; ++im) {   // images within r_cut
+            const double x0 = dw[0] + pl.img[3 * im], x1 = dw[1] + pl.img[3 * im + 1], x2 = dw[2] + pl.img[3 * im + 2];
+            const double r2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+            if (!(r2 < rc2) || r2 == 0.0) continue;
+            const double ir = rsqrt_nr(r2);
             const double r = r2 * ir;
-            g_re = fma(erfc(pl.alpha * r), ir, g_re);
-            if (!(r2 < rc2)) continue;
             const double e[3] = {x0 * ir, x1 * ir, x2 * ir};
             for (int tb = 0; tb < 2; ++tb) {
                 const double(*tab)[CAVMD_MAX_ELEM][4][4] = tb == 0 ? sk.h0 : sk.s;
@@ -810,19 +816,28 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         const double two_a_spi = 2.0 * pl.alpha * 0.5641895835477563;   // 2 alpha / sqrt(pi)
         double gk[3] = {0.0, 0.0, 0.0};
         double erep = 0.0;
-        for (int im = 0; im < pl.n_img; ++im) {
+        if (A != B) {
+            for (int im = 0; im < pl.n_img; ++im) {   // real-space Ewald gradient
+                const double x0 = dw[0] + pl.img[3 * im], x1 = dw[1] + pl.img[3 * im + 1], x2 = dw[2] + pl.img[3 * im + 2];
+                const double r2 = fma(x0, x0, fma(x1, x1, x2 * x2));
+                if (!(r2 < pl.r_real2) || r2 == 0.0) continue;
+                const double ir = rsqrt_nr(r2);
+                const double ar = pl.alpha * (r2 * ir);
+                const double rad = -qq * (erfc(ar) * ir + two_a_spi * exp(-ar * ar)) * ir * ir;
+                gk[0] = fma(rad, x0, gk[0]);
+                gk[1] = fma(rad, x1, gk[1]);
+                gk[2] = fma(rad, x2, gk[2]);
+            }
+        }
+        for (int im = 0; im < pl.n_img_sk; ++im) {   // images within r_cut
             const double x0 = dw[0] + pl.img[3 * im], x1 = dw[1] + pl.img[3 * im + 1], x2 = dw[2] + pl.img[3 * im + 2];
             const double r2 = fma(x0, x0, fma(x1, x1, x2 * x2));
-            if (!(r2 < pl.r_real2) || r2 == 0.0) continue;
+            if (!(r2 < rc2) || r2 == 0.0) continue;
             const double ir = rsqrt_nr(r2);
             const double r = r2 * ir;
             const double e[3] = {x0 * ir, x1 * ir, x2 * ir};
             double rad = 0.0;   // d/dr of the radial terms, along e
-            if (A != B) {
-                const double ar = pl.alpha * r;
-                rad = -qq * (erfc(ar) * ir + two_a_spi * exp(-ar * ar)) * ir;
-            }
-            if (r2 < rc2) {
+            {
                 double fc, dfc;
                 cutoff_fn(r, sk, fc, dfc);
                 if (arep != 0.0) {
@@ -1001,16 +1016,26 @@ void plan_dftb_periodic(const double *lat, double r_cut, PbcPlan &p, std::vector
         const double h = 1.0 / std::sqrt(inv[i] * inv[i] + inv[3 + i] * inv[3 + i] + inv[6 + i] * inv[6 + i]);
         N[i] = (int)std::ceil((r_real + hmax) / h) + 1;
     }
-    img.clear();
+    // translations by increasing length (ties in the order generated); a wrapped separation
+    // reaches an image within r_cut only through a translation shorter than r_cut + hmax
+    struct Tr { double len, t[3]; };
+    std::vector<Tr> trs;
     const double reach = r_real + hmax;
     for (int n0 = -N[0]; n0 <= N[0]; ++n0)
         for (int n1 = -N[1]; n1 <= N[1]; ++n1)
             for (int n2 = -N[2]; n2 <= N[2]; ++n2) {
-                double T[3];
-                for (int k = 0; k < 3; ++k) T[k] = n0 * lat[k] + n1 * lat[3 + k] + n2 * lat[6 + k];
-                if (std::sqrt(T[0] * T[0] + T[1] * T[1] + T[2] * T[2]) < reach)
-                    img.insert(img.end(), T, T + 3);
+                Tr t;
+                for (int k = 0; k < 3; ++k) t.t[k] = n0 * lat[k] + n1 * lat[3 + k] + n2 * lat[6 + k];
+                t.len = std::sqrt(t.t[0] * t.t[0] + t.t[1] * t.t[1] + t.t[2] * t.t[2]);
+                if (t.len < reach) trs.push_back(t);
             }
+    std::stable_sort(trs.begin(), trs.end(), [](const Tr &a, const Tr &b) { return a.len < b.len; });
+    img.clear();
+    p.n_img_sk = 0;
+    for (const Tr &t : trs) {
+        img.insert(img.end(), t.t, t.t + 3);
+        if (t.len < r_cut + hmax) ++p.n_img_sk;
+    }
     p.n_img = (int)(img.size() / 3);
     // reciprocal rows b_j = 2 pi (column j of inv), G = m b; half space: first nonzero m positive
     double B[9];
@@ -1056,6 +1081,7 @@ cudaError_t launch_dftb_periodic(const DevSK *sk_dev, const DftbArgs &a, const P
     d.self_e = p.self_e;
     d.r_real2 = p.r_real * p.r_real;
     d.n_img = p.n_img;
+    d.n_img_sk = p.n_img_sk;
     d.n_g = p.n_g;
     d.nmax = p.nmax;
     d.amax = p.amax;
