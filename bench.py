@@ -59,20 +59,27 @@ def _periodic_flops_per_cell(iters, n, nocc):
     """FP64 flops of the products one periodic cell needs per time step in the warm-started Gamma-point
     SCC (n orbitals, o = n_occ occupied, v = n - o virtual):
       start, once: S C (2n^3), C^T S C lower (n^3), its Cholesky (n^3/3), C L^-T (n^3);
-      per SCC iteration: H C (2n^3), the occupied-virtual block of C^T H C (2 n o v), X^T X and X X^T
-        lower (o^2 v + v^2 o), C_v X and C_o X^T (4 n o v), Cholesky factors (o^3/3 + v^3/3), their
-        row solves (2 n (o^2 + v^2)), P lower (n^2 o), H, the diagonal and Mulliken (7 n^2);
+      every SCC iteration: H C (2n^3), the occupied-virtual block of C^T H C (2 n o v), X^T X and X X^T
+        lower (o^2 v + v^2 o), P lower (n^2 o), H, the diagonal and Mulliken (7 n^2);
+      the rotation: on the first iteration the Cayley form, C_v X and C_o X^T (4 n o v), two Cholesky
+        factors (o^3/3 + v^3/3) and their row solves (2 n (o^2 + v^2)); on the others
+        C (I + K + K^2/2) as products over [C_o | C_v] (2 n^3);
+      every step, one Jacobi sweep inside each block: the blocks C_b^T Y_b (2 n (o^2 + v^2)) and the
+        rotations (6 m^2 (m + n) for a block of m);
       forces, once: H C_o (2 n^2 o), C_o^T H C_o lower (n o^2), t = 2 Aoo C_o^T (2 n o^2),
         W and P lower (2 n^2 o).
     A full eigensolve per iteration (the 9 n^3 of the isolated-cell count) is never done."""
     n = float(n)
     o = float(nocc)
     v = n - o
+    it = np.asarray(iters, float)
     start = (2.0 + 1.0 + 1.0 / 3.0 + 1.0) * n ** 3
-    per_iter = (2 * n ** 3 + 2 * n * o * v + o * o * v + v * v * o + 4 * n * o * v + (o ** 3 + v ** 3) / 3
-                + 2 * n * (o * o + v * v) + n * n * o + 7 * n * n)
+    common = 2 * n ** 3 + 2 * n * o * v + o * o * v + v * v * o + n * n * o + 7 * n * n
+    cayley = 4 * n * o * v + (o ** 3 + v ** 3) / 3 + 2 * n * (o * o + v * v)
+    second = 2 * n ** 3
+    sweep = 2 * n * (o * o + v * v) + 6 * o * o * (o + n) + 6 * v * v * (v + n)
     forces = 2 * n * n * o + n * o * o + 2 * n * o * o + 2 * n * n * o
-    return start + per_iter * np.asarray(iters, float) + forces
+    return start + common * it + cayley + second * np.maximum(it - 1, 0) + sweep + forces
 
 
 def _cell_shapes(system):

@@ -925,6 +925,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.paper = c->opt.splitting == CAVMD_SPLIT_PAPER;
     d.E_open = nullptr;   // set for the first evaluation of a call (water kernel)
     d.p_open = c->d_p; d.r_open = c->d_r; d.inv_mass = c->d_imass; d.tau = tau; d.dt = c->opt.dt;
+    d.step_counter = c->d_step;
     return CAVMD_OK;
 }
 

@@ -71,6 +71,7 @@ struct DftbArgs {
     double *r_open;            // [3 n_atoms] positions, drifted in place (the array r points to)
     const double *inv_mass;    // [n_atoms]
     double tau, dt;
+    const long long *step_counter;   // device step counter (periodic kernel: which steps re-diagonalise)
 };
 
 // Arguments of the coupling / integrator kernels.
