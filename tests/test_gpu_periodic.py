@@ -154,3 +154,23 @@ def test_graph_replay_is_bitwise_identical(P):
     sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
     for k in ("r", "p", "q", "pq"):
         assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_full_size_p33_sampled(P):
+    """The p33 workload at the size bench.py times (304 cells of 33 waters, 10,032 waters, 512
+    modes): three sampled cells against the oracle, every cell's population sum (264 electrons),
+    and one step."""
+    w = cs.make_workload("p33")
+    sy, lat = w["system"], w["lattice"]
+    ctx = P.Context(sy, w["params"], w["modes"], P.default_options(), lattice=lat)
+    ev = ctx.cavmd_get_eval()
+    np.testing.assert_allclose(ev["q_pop"].reshape(sy.n_cells, -1).sum(1), 264.0, rtol=0, atol=1e-9)
+    pick = [0, 151, 303]
+    idx = np.concatenate([np.arange(sy.cell_offset[c], sy.cell_offset[c + 1]) for c in pick])
+    sub = cs.System(species=sy.species[idx], cell_offset=np.arange(len(pick) + 1, dtype=np.int32) * 99,
+                    r=sy.r[idx], p=sy.p[idx], R_ref=sy.R_ref[pick])
+    sev = {k: (ev[k][idx] if k in ("F_dftb", "q_pop") else ev[k][pick]) for k in ("F_dftb", "q_pop", "E_cell", "M")}
+    _check_eval(sev, sub, lat, w["params"])
+    ctx.cavmd_step(1)
+    st = ctx.cavmd_get_state()
+    assert st["step"] == 1 and np.all(np.isfinite(st["p"])) and np.all(np.isfinite(st["q"]))
