@@ -279,6 +279,157 @@ def dftb_periodic(params, species, pos, lattice, q0=None, alpha=None, beta=0.5, 
     return out
 
 
+# ---------------------------------------------------------------------------- k-point sampling
+#
+# The paper samples the Brillouin zone at the Gamma point of a 3 x 3 x 3 folded supercell, i.e. on
+# the Gamma-centred 3 x 3 x 3 grid of the cell itself. At each k the Bloch sums
+#     H0(k)_{mu nu} = sum_T exp(i k.T) h_{mu nu}(r_B + T - r_A),  S(k) likewise,
+# give a Hermitian generalised eigenproblem; the lowest n_occ bands are occupied at every k (an
+# insulator); populations, band energy and forces are the k averages, and the force weights of an
+# image T are the real-space densities rho_{mu nu}(T) = sum_k w_k Re[P(k)_{nu mu} exp(i k.T)].
+
+def kgrid_points(kgrid):
+    """Gamma-centred grid: fractional k = (i/n1, j/n2, l/n3) in units of the reciprocal lattice
+    vectors (k.T = 2 pi f.n for T = n @ lattice), equal weights."""
+    n1, n2, n3 = kgrid
+    f = np.array([(i / n1, j / n2, l / n3) for i in range(n1) for j in range(n2) for l in range(n3)])
+    return f, np.full(len(f), 1.0 / len(f))
+
+
+def pair_images_n(lattice, d, r_max, shifts=None):
+    """pair_images, with the integer translation n (T = n @ lattice, taken from r_B - r_A) of each."""
+    if shifts is None:
+        shifts = image_shifts(lattice, r_max)
+    n0 = np.round(d @ np.linalg.inv(lattice))
+    x = (d - n0 @ lattice)[None, :] + shifts @ lattice
+    n = shifts - n0[None, :]
+    r = np.linalg.norm(x, axis=1)
+    keep = (r < r_max) & (r > 0.0)
+    return x[keep], n[keep]
+
+
+def build_hk_sk(params, lay, pos, lattice, fk):
+    """H0(k), S(k) (K, n, n) complex for the fractional k-points fk (K, 3); and, per pair A < B,
+    the image vectors, their integer translations and the derivative blocks of each image."""
+    n = lay.norb
+    K = len(fk)
+    H0 = np.zeros((K, n, n), complex)
+    S = np.zeros((K, n, n), complex)
+    shifts = image_shifts(lattice, params.r_cut)
+    for a in range(lay.nat):
+        e = lay.species[a]
+        o = lay.off[a]
+        H0[:, o, o] = params.onsite[e, 0]
+        S[:, o, o] = 1.0
+        if lay.norb_atom[a] == 4:
+            for i in range(1, 4):
+                H0[:, o + i, o + i] = params.onsite[e, 1]
+                S[:, o + i, o + i] = 1.0
+    grads = {}
+    for a in range(lay.nat):
+        for b in range(a, lay.nat):
+            x, nT = pair_images_n(lattice, pos[b] - pos[a], params.r_cut, shifts)
+            if len(x) == 0:
+                continue
+            r = np.linalg.norm(x, axis=1)
+            e = x / r[:, None]
+            ph = np.exp(2j * np.pi * (fk @ nT.T))           # (K, images)
+            ea, eb = lay.species[a], lay.species[b]
+            na, nb = lay.norb_atom[a], lay.norb_atom[b]
+            sa, sb = slice(lay.off[a], lay.off[a + 1]), slice(lay.off[b], lay.off[b + 1])
+            for M, table, key in ((H0, params.h0, "h"), (S, params.s, "s")):
+                vals, dvals = D._pair_integrals(table, params, ea, eb, r)
+                blk = np.einsum("kt,tij->kij", ph, D.sk_block(vals, e, na, nb))
+                if a == b:
+                    M[:, sa, sa] += blk                      # images of the atom itself: Hermitian
+                else:
+                    M[:, sa, sb] += blk
+                    M[:, sb, sa] += np.conj(np.swapaxes(blk, -1, -2))
+                    grads[(a, b, key)] = D.sk_block_grad(vals, dvals, e, r, na, nb)
+            if a != b:
+                grads[(a, b, "x")] = x
+                grads[(a, b, "n")] = nT
+    return H0, S, grads
+
+
+def dftb_periodic_k(params, species, pos, lattice, kgrid=(3, 3, 3), q0=None, alpha=None, beta=0.5,
+                    tol=1e-12, max_iter=400, forces=True):
+    """SCC-DFTB of one periodic cell sampled on the Gamma-centred k-grid ``kgrid``.
+
+    Returns E (per cell), F, q, Q, mu = sum_A Q_A r_A, iters, eps (K, n) and gap (the smallest
+    LUMO - HOMO over the grid)."""
+    pos = np.asarray(pos, float)
+    lattice = np.asarray(lattice, float)
+    lay = D.Layout(params, species)
+    fk, wk = kgrid_points(kgrid)
+    H0, S, grads = build_hk_sk(params, lay, pos, lattice, fk)
+    gam, dgam = gamma_periodic(params, lay, pos, lattice, alpha, with_grad=True)
+    Z = lay.zval
+    nocc = lay.n_occ
+    q = Z.copy() if q0 is None else np.array(q0, float, copy=True)
+    for it in range(1, max_iter + 1):
+        shift = gam @ (q - Z)
+        so = shift[lay.atom_of_orb]
+        qorb = np.zeros(lay.norb)
+        for k in range(len(fk)):
+            Hk = H0[k] + 0.5 * S[k] * (so[:, None] + so[None, :])
+            eps, C = scipy_eigh(Hk, S[k])
+            Co = C[:, :nocc]
+            Pk = 2.0 * Co @ Co.conj().T
+            qorb += wk[k] * np.sum(Pk * S[k].conj(), axis=1).real      # (P(k) S(k))_mu mu
+        q_out = np.array([qorb[lay.off[a]:lay.off[a + 1]].sum() for a in range(lay.nat)])
+        if np.max(np.abs(q_out - q)) < tol:
+            q = q_out
+            break
+        q = q + beta * (q_out - q)
+    else:
+        raise D.SCCError(f"SCC did not converge in {max_iter} iterations")
+    dq = q - Z
+    shift = gam @ dq
+    so = shift[lay.atom_of_orb]
+    n = lay.norb
+    P = np.zeros((len(fk), n, n), complex)
+    W = np.zeros((len(fk), n, n), complex)
+    eps_all = np.zeros((len(fk), n))
+    for k in range(len(fk)):
+        Hk = H0[k] + 0.5 * S[k] * (so[:, None] + so[None, :])
+        eps, C = scipy_eigh(Hk, S[k])
+        Co = C[:, :nocc]
+        P[k] = 2.0 * Co @ Co.conj().T
+        W[k] = 2.0 * (Co * eps[None, :nocc]) @ Co.conj().T
+        eps_all[k] = eps
+    erep, G = e_rep_periodic(params, lay, pos, lattice)
+    E = float(np.sum(wk[:, None, None] * P * H0.conj()).real) + 0.5 * dq @ gam @ dq + erep
+    Q = Z - q
+    out = {"E": E, "q": q, "Q": Q, "mu": Q @ pos, "iters": it, "eps": eps_all,
+           "gap": (eps_all[:, nocc].min() - eps_all[:, nocc - 1].max()) if nocc < n else np.inf}
+    if not forces:
+        return out
+    for a in range(lay.nat):
+        for b in range(a + 1, lay.nat):
+            if (a, b, "x") not in grads:
+                continue
+            sa, sb = slice(lay.off[a], lay.off[a + 1]), slice(lay.off[b], lay.off[b + 1])
+            ph = np.exp(2j * np.pi * (fk @ grads[(a, b, "n")].T))   # (K, images)
+            # rho(T)_{mu nu} = sum_k w_k Re[P(k)_{nu mu} exp(i k.T)], mu of A, nu of B
+            rho = np.einsum("k,kt,kji->tij", wk, ph, P[:, sb, sa]).real
+            om = np.einsum("k,kt,kji->tij", wk, ph, W[:, sb, sa]).real
+            X = rho * 0.5 * (shift[a] + shift[b]) - om
+            g = 2.0 * (np.einsum("tij,tkij->k", rho, grads[(a, b, "h")])
+                       + np.einsum("tij,tkij->k", X, grads[(a, b, "s")]))
+            G[b] += g
+            G[a] -= g
+    G += dq[:, None] * np.einsum("a,abk->bk", dq, dgam)
+    out["F"] = -G
+    return out
+
+
+def scipy_eigh(H, S):
+    """Generalised Hermitian eigenproblem H c = e S c, eigenvalues ascending (library routine)."""
+    from scipy.linalg import eigh
+    return eigh(H, S)
+
+
 # ---------------------------------------------------------------------------- cells for the cavity step
 
 class PeriodicDFTBMatter:

@@ -14,6 +14,10 @@
   every term has images.
 * Lattice translations of one molecule and rigid shifts of the whole cell change nothing; the
   populations sum to the valence electron count.
+* k-point sampling: the Gamma-centred 3 x 3 x 3 grid of a cell equals the Gamma point of the
+  explicit 3 x 3 x 3 supercell (energy per cell, populations, forces and the whole band spectrum,
+  by Bloch's theorem); a 1 x 1 x 1 grid is the Gamma point; forces on a 2 x 2 x 1 grid against
+  central finite differences.
 """
 import math
 
@@ -235,3 +239,51 @@ def test_liquid_cell_of_33_waters(params):
     np.testing.assert_allclose(out["q"].sum(), 264.0, rtol=0, atol=1e-9)
     assert np.linalg.eigvalsh(out["S"]).min() > 0.1 and out["gap"] > 0.3
     np.testing.assert_allclose(out["F"].sum(0), 0.0, rtol=0, atol=1e-10 * np.abs(out["F"]).max())
+
+
+def _supercell(pos, species, lat, m=3):
+    cells = np.stack(np.meshgrid(*[np.arange(m)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    return (pos[None, :, :] + (cells @ lat)[:, None, :]).reshape(-1, 3), np.tile(species, len(cells)), m * lat
+
+
+def test_kgrid_equals_gamma_point_of_the_supercell(params):
+    sy, lat = _two_waters()
+    k3 = PR.dftb_periodic_k(params, sy.species, sy.r, lat, (3, 3, 3))
+    pos_s, spec_s, lat_s = _supercell(sy.r, sy.species, lat)
+    sc = PR.dftb_periodic(params, spec_s, pos_s, lat_s)
+    nat = len(sy.species)
+    np.testing.assert_allclose(sc["E"] / 27.0, k3["E"], rtol=0, atol=1e-12)
+    for c in range(27):   # every copy carries the cell's populations and forces
+        np.testing.assert_allclose(sc["q"][c * nat:(c + 1) * nat], k3["q"], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(sc["F"][c * nat:(c + 1) * nat], k3["F"], rtol=0, atol=1e-11 * np.abs(k3["F"]).max())
+    np.testing.assert_allclose(np.sort(sc["eps"]), np.sort(k3["eps"].ravel()), rtol=0, atol=1e-11)
+    # the grid matters in this small cube: the Gamma point alone is another answer
+    g = PR.dftb_periodic(params, sy.species, sy.r, lat)
+    assert abs(g["E"] - k3["E"]) > 1e-3
+
+
+def test_kgrid_111_is_the_gamma_point(params):
+    sy, lat = _two_waters()
+    g = PR.dftb_periodic(params, sy.species, sy.r, lat)
+    k1 = PR.dftb_periodic_k(params, sy.species, sy.r, lat, (1, 1, 1))
+    np.testing.assert_allclose(k1["E"], g["E"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(k1["q"], g["q"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(k1["F"], g["F"], rtol=0, atol=1e-12)
+
+
+def test_kgrid_forces_against_finite_differences(params):
+    sy, lat = _two_waters()
+    pos = sy.r.copy()
+    out = PR.dftb_periodic_k(params, sy.species, pos, lat, (2, 2, 1), tol=1e-13)
+    h = 1e-4
+    fd = np.zeros_like(pos)
+    for j in range(len(pos)):
+        for k in range(3):
+            e = []
+            for sg in (1.0, -1.0):
+                p = pos.copy()
+                p[j, k] += sg * h
+                e.append(PR.dftb_periodic_k(params, sy.species, p, lat, (2, 2, 1), q0=out["q"], tol=1e-13,
+                                            forces=False)["E"])
+            fd[j, k] = -(e[0] - e[1]) / (2.0 * h)
+    np.testing.assert_allclose(out["F"], fd, rtol=0, atol=1e-7 * np.abs(out["F"]).max())
