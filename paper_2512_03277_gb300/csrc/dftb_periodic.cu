@@ -321,9 +321,8 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         S[e] = s;
     }
     __syncthreads();
-    for (int t = j; t < nat * nat; t += PT) {
-        const int A = t / nat, B = t - A * nat;
-        if (B < A) continue;
+    for (int t = j; t < nat * (nat + 1) / 2; t += PT) {   // pairs A <= B, packed by A
+        const int A = lower_col(t, nat), B = A + (t - (A * nat - A * (A - 1) / 2));
         const int eA = sh.spec[A], eB = sh.spec[B];
         const int oA = sh.atom_off[A], oB = sh.atom_off[B];
         const int na = sk.norb[eA], nb = sk.norb[eB];
@@ -849,9 +848,8 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
     const double *W = H;
     // pair tasks A <= B: d/dr_B of every image term (band, overlap, second order, repulsion), and
     // the repulsion energy (an atom with its own images counts each image pair once)
-    for (int t = j; t < nat * nat; t += PT) {
-        const int A = t / nat, B = t - A * nat;
-        if (B < A) continue;
+    for (int t = j; t < nat * (nat + 1) / 2; t += PT) {   // pairs A <= B, packed by A
+        const int A = lower_col(t, nat), B = A + (t - (A * nat - A * (A - 1) / 2));
         const int eA = sh.spec[A], eB = sh.spec[B];
         const int oA = sh.atom_off[A], oB = sh.atom_off[B];
         const int na = sk.norb[eA], nb = sk.norb[eB];
