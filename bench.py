@@ -45,6 +45,23 @@ def _dist():
     return ws, rank, local
 
 
+def _reduce_max(x, ws, device):
+    """The largest x over the ranks of the process group (x itself on one process)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _whole_job_value(n_mol_per_rank, steps, ws, max_ms):
+    """Molecule-steps per second of the whole job: every rank's replica over the slowest rank's
+    time (each rank runs the same workload)."""
+    return n_mol_per_rank * steps * ws / (max_ms * 1e-3)
+
+
 def _dftb_flops_per_cell(iters, n=6, nocc=4, npair=3):
     """Algorithmic FP64 flops of one cell (n orbitals, n_occ occupied, npair atom pairs) per time
     step: per SCC iteration 2n^3 (basis transform) + 9n^3 (symmetric eigensolve with vectors)
@@ -335,11 +352,8 @@ def main():
     ev = ctx.cavmd_get_eval()
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     total_ms = float(step_ms.sum())
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n_mol * args.steps * ws / (total_ms * 1e-3)
+    total_ms = _reduce_max(total_ms, ws, f"cuda:{local}")
+    value = _whole_job_value(n_mol, args.steps, ws, total_ms)
 
     # roofline of the dominant kernel (SCC-DFTB, FP64-ALU bound)
     if args.phase_events == "off":
