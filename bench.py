@@ -81,8 +81,8 @@ def _periodic_flops_per_cell(iters, n, nocc):
       the rotation: on the first iteration the Cayley form, C_v X and C_o X^T (4 n o v), two Cholesky
         factors (o^3/3 + v^3/3) and their row solves (2 n (o^2 + v^2)); on the others
         C (I + K + K^2/2) as products over [C_o | C_v] (2 n^3);
-      every step, one Jacobi sweep inside each block: the blocks C_b^T Y_b (2 n (o^2 + v^2)) and the
-        rotations (6 m^2 (m + n) for a block of m);
+      every step, one Jacobi sweep inside each block of m columns: the block C_b^T Y_b (2 n m^2),
+        its rotations accumulated in V (9 m^3), and C_b V, Y_b V (4 n m^2);
       forces, once: H C_o (2 n^2 o), C_o^T H C_o lower (n o^2), t = 2 Aoo C_o^T (2 n o^2),
         W and P lower (2 n^2 o).
     A full eigensolve per iteration (the 9 n^3 of the isolated-cell count) is never done."""
@@ -94,7 +94,7 @@ def _periodic_flops_per_cell(iters, n, nocc):
     common = 2 * n ** 3 + 2 * n * o * v + o * o * v + v * v * o + n * n * o + 7 * n * n
     cayley = 4 * n * o * v + (o ** 3 + v ** 3) / 3 + 2 * n * (o * o + v * v)
     second = 2 * n ** 3
-    sweep = 2 * n * (o * o + v * v) + 6 * o * o * (o + n) + 6 * v * v * (v + n)
+    sweep = sum(6 * n * m * m + 9 * m ** 3 for m in (o, v))
     forces = 2 * n * n * o + n * o * o + 2 * n * o * o + 2 * n * n * o
     return start + common * it + cayley + second * np.maximum(it - 1, 0) + sweep + forces
 

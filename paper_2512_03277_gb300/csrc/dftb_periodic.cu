@@ -455,14 +455,18 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
     };
     auto Cat = [&](int i, int c) -> double { return C[c * n + i]; };
     // One cyclic Jacobi sweep on the block Ab = C_b^T Y_b of the columns list[0..m-1] (occupied or
-    // virtual), every rotation applied to those columns of C and Y as well: it keeps the diagonal
-    // blocks of C^T H C diagonal, which the generator's diagonal denominators need (the
-    // occupied-virtual rotations leave them alone, and within a block they drift with every step).
-    auto block_sweep = [&](const int *list, int m, double *Ab) {
+    // virtual). It keeps the diagonal blocks of C^T H C diagonal, which the generator's diagonal
+    // denominators need (the occupied-virtual rotations leave them alone, and within a block they
+    // drift with every step). The rounds rotate Ab and accumulate the rotations in Vb (m x m,
+    // starting from I); then C_b <- C_b Vb and Y_b <- Y_b Vb as staged products through H, which
+    // is free until the next iteration builds it.
+    auto block_sweep = [&](const int *list, int m, double *Ab, double *Vb) {
         pprod<false, true, true>(sh, m, m, n, [&](int i, int k) { return C[list[i] * n + k]; },
                                  [&](int k, int c) { return Y[list[c] * n + k]; },
                                  [&](int i, int c, double v) { Ab[c * m + i] = v; });
-        const int mm = m + (m & 1), half = mm / 2, span = m + 2 * n;
+        for (int e = j; e < m * m; e += PT) Vb[e] = (e / m == e % m) ? 1.0 : 0.0;
+        __syncthreads();
+        const int mm = m + (m & 1), half = mm / 2, span = 2 * m;
         for (int rd = 0; rd < mm - 1; ++rd) {
             if (j < half) {
                 int p, qq;
@@ -475,25 +479,16 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
                 sh.cs[2 * j + 1] = s;
             }
             __syncthreads();
-            for (int e = j; e < half * span; e += PT) {   // columns p, q of Ab, C and Y
+            for (int e = j; e < half * span; e += PT) {   // columns p, q of Ab and Vb
                 const int k = e / span, r = e - k * span;
                 const int p = sh.pp[k], qq = sh.pq[k];
                 if (qq >= m) continue;
                 const double c = sh.cs[2 * k], s = sh.cs[2 * k + 1];
-                double *x, *y;
-                if (r < m) {
-                    x = Ab + p * m + r;
-                    y = Ab + qq * m + r;
-                } else if (r < m + n) {
-                    x = C + list[p] * n + (r - m);
-                    y = C + list[qq] * n + (r - m);
-                } else {
-                    x = Y + list[p] * n + (r - m - n);
-                    y = Y + list[qq] * n + (r - m - n);
-                }
-                const double xp = *x, yq = *y;
-                *x = fma(c, xp, -s * yq);
-                *y = fma(s, xp, c * yq);
+                double *base = r < m ? Ab : Vb;
+                const int rr = r < m ? r : r - m;
+                const double xp = base[p * m + rr], yq = base[qq * m + rr];
+                base[p * m + rr] = fma(c, xp, -s * yq);
+                base[qq * m + rr] = fma(s, xp, c * yq);
             }
             __syncthreads();
             for (int e = j; e < half * m; e += PT) {   // rows p, q of Ab
@@ -504,6 +499,17 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
                 const double x = Ab[cc * m + p], y = Ab[cc * m + qq];
                 Ab[cc * m + p] = fma(ck, x, -sk_ * y);
                 Ab[cc * m + qq] = fma(sk_, x, ck * y);
+            }
+            __syncthreads();
+        }
+        for (int t = 0; t < 2; ++t) {   // C_b <- C_b Vb, then Y_b <- Y_b Vb
+            double *M_ = t == 0 ? C : Y;
+            pprod<false, false, true>(sh, n, m, m, [&](int i, int k) { return M_[list[k] * n + i]; },
+                                      [&](int k, int c) { return Vb[c * m + k]; },
+                                      [&](int i, int c, double v) { H[c * n + i] = v; });
+            for (int e = j; e < n * m; e += PT) {
+                const int c = e / n, i = e - c * n;
+                M_[list[c] * n + i] = H[e];
             }
             __syncthreads();
         }
@@ -616,8 +622,8 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         } else {
             rank_occupation();
             if (sweep_now && it == 1) {   // first iteration after a geometry change
-                block_sweep(sh.occ_list, nocc, Mo);
-                block_sweep(sh.virt_list, nv, Mv);
+                block_sweep(sh.occ_list, nocc, Mo, P);
+                block_sweep(sh.virt_list, nv, Mv, P);
             }
             bool small = true;
             float kmax = 0.0f;
