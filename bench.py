@@ -1,23 +1,37 @@
-"""Benchmark: molecule-steps/s of the cavity-MD hot path on one GB300 (or N replicas).
+"""Benchmark: molecule-steps/s of the cavity-MD hot path on one GB300 (or N replicas), the
+surrogate/mixed form against the plain FP64 form on the same workload.
 
-Workload (default "c2"): 4096 synthetic waters (12,288 atoms) in a 919 x 30 x 30 bohr slab at
-liquid density, 512 real cavity modes on an in-plane line of wave vectors, g = 0.001 a.u.,
-dt = 0.5 fs, FP64 SCC-DFTB with Mulliken charges, photons initially at rest.
+Workload (default "c5"): 262,144 synthetic waters (786,432 atoms) in a 30 bohr slab at liquid
+density, 8192 real cavity modes on a 64 x 128 in-plane wave-vector grid, g = 0.001 a.u.,
+dt = 0.5 fs, FP64 SCC-DFTB, photons initially at rest, on-device autocorrelation of the photon
+coordinates and the total dipole (1024 lags). Two arms run on it, one after the other:
+  surrogate/mixed (the headline): network Born charges, BF16x3 coupling on the tensor cores;
+  plain FP64: forward finite-difference Born charges refreshed every 3 steps (the paper's scheme),
+              FP64 coupling.
+Both keep the SCC, the charge mixing and the Verlet update in FP64.
 
-One timed step = one cavmd_step(ctx, 1) call: the whole hot path (SCC-DFTB of every cell,
-dipoles, forward contraction, photon half-flows, field on every cell, kicks and drift,
-energies). Each step is bracketed by CUDA events on the library's stream; a 256 MB buffer
-(larger than the 129 MB L2) is rewritten between steps, outside the events.
+One timed step = one cavmd_step(ctx, 1) call: the whole hot path (SCC-DFTB of every cell, the
+dipole derivatives, forward contraction, photon half-flows, field on every cell, kicks and drift,
+energies, the autocorrelation sample). Each step is bracketed by CUDA events on the library's
+stream; a 256 MB buffer (larger than the 129 MB L2) is rewritten between steps, outside the events.
+The headline arm is also timed as CUDA-graph replay (cavmd_step(chunk), one event pair per chunk,
+no flush: the state a step reads is larger than L2) and end to end through the C ABI.
+
+The judge (drift, heating and band error of each arm's dipole derivative and coupling against
+explicit central-difference Born charges) runs on a resonant single-box cavity of 33 waters for
+10^4 steps, four replicas (paper_2512_03277_gb300/judge.py).
 
 Multi-GPU (torchrun): every rank propagates its own independent replica (its own velocities),
 no data-path collective; value = all ranks' molecule-steps / max-over-ranks time (weak scaling).
 
---impl reference times the FP64 oracle (oracle/) on the host cores instead: each step runs the
-oracle's full time step on a bounded sample of the same workload (its first 512 cells).
+cpu_baseline: the FP64 oracle (oracle/) as it stands, on a bounded sample of the headline arm's
+workload, on one core and on every core of the host (one process per core, cells split between
+them). --impl reference times the same oracle the same way, one oracle time step per step.
 """
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -30,12 +44,12 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 FP64_FLOPS_PER_CLK_SM = 4.0      # 2 FP64 FMA per clock per SM (1.25 TFLOP/s nominal at 2.07 GHz)
-N_SM = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ_NOMINAL = 2070.0
 FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one dftb_kernel<3,6> launch on this workload, from one ncu capture
-# (profiles/dftb_kernel_c2_4096x512.md); None once the kernel has changed since that capture.
-DFTB_DRAM_BYTES_PER_LAUNCH = (2908928 + 2905856 + 2907904 + 256) // 3   # mean of three in-step launches
+CHARGE = {"mulliken": 0, "born_fd": 1, "born_central": 2, "born_mlp": 3}
+PREC = {"fp64": 0, "mixed": 2}
+ORACLE_CHARGE = {"mulliken": "mulliken", "born_fd": "born_fd", "born_central": "born_central",
+                 "born_mlp": "network"}
 
 
 def _dist():
@@ -158,34 +172,138 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _oracle_matter(w):
-    from oracle import cavity as OC
-    from oracle import periodic as PR
-    if w.get("lattice") is not None:
-        return PR.PeriodicDFTBMatter(w["params"], w["system"], w["lattice"])
-    return OC.DFTBMatter(w["params"], w["system"])
+# ------------------------------------------------------------------------------ the host oracle
+
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
-def cpu_baseline(workload, seconds=12.0, n_sample=None):
-    """The oracle as it stands, on a bounded sample of the workload, on this host."""
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_shard(workload, lo, hi, charge_model, mlp, warmup, steps, seconds, barrier, out):
+    """One process: the oracle's time step on cells lo..hi-1 of the workload (all its modes);
+    `warmup` untimed steps, the barrier, then `steps` timed steps (or as many as `seconds` allow
+    when steps is None). Puts (molecules, steps, t0, t1) on `out` (system-wide monotonic clock)."""
     import cavmd_synth as cs
     from oracle import cavity as OC
-    w = cs.make_workload(workload, n_cells=n_sample)
-    sy, mo, pa = w["system"], w["modes"], w["params"]
-    mat = _oracle_matter(w)
-    md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
-    md.step()                                   # warm start of the charges
-    t0 = time.perf_counter()
+    from oracle import periodic as PR
+    w = cs.make_workload(workload)
+    sy = w["system"]
+    off = sy.cell_offset
+    a0, a1 = off[lo], off[hi]
+    sub = cs.System(species=sy.species[a0:a1], cell_offset=(off[lo:hi + 1] - a0).astype(np.int32),
+                    r=sy.r[a0:a1], p=sy.p[a0:a1], R_ref=sy.R_ref[lo:hi])
+    mo = w["modes"]
+    if w.get("lattice") is not None:
+        mat = PR.PeriodicDFTBMatter(w["params"], sub, w["lattice"])
+    else:
+        kw = {"mlp_params": mlp} if charge_model == "network" else {}
+        mat = OC.DFTBMatter(w["params"], sub, charge_model=charge_model,
+                            born_interval=3 if charge_model == "born_fd" else 1, **kw)
+    md = OC.CavityMD(mat, sub.r, sub.p, mo.k, mo.omega, mo.lam, mo.phi, sub.R_ref, w["options"]["dt"])
+    for _ in range(warmup):
+        md.step()
+    if barrier is not None:
+        barrier.wait()
+    t0 = time.monotonic()
     n = 0
     while True:
         md.step()
         n += 1
-        el = time.perf_counter() - t0
-        if (el >= seconds and n >= 3) or n >= 1000:
+        if steps is not None and n >= steps:
             break
-    return {"value": (sy.n_atoms // 3) * n / el, "unit": "molecule-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sy.n_cells} cells x {mo.n_modes} modes of workload {workload}, {n} oracle time "
-                      f"steps after one warm-up step ({el:.1f} s, NumPy, one thread)"}
+        if steps is None and time.monotonic() - t0 >= seconds:
+            break
+    t1 = time.monotonic()
+    out.put(((a1 - a0) // 3, n, t0, t1))
+
+
+def oracle_throughput(workload, charge_model, mlp, workers, cells_per_worker, warmup, steps=None, seconds=10.0):
+    """molecule-steps/s of the oracle on `workers` processes (one thread each, started with spawn),
+    each stepping its own `cells_per_worker` cells; the time is that of the whole group (first
+    start to last finish). Returns (value, total molecule-steps, seconds, steps per worker)."""
+    import multiprocessing as mp
+    import cavmd_synth as cs
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        n_cells = cs.make_workload(workload)["system"].n_cells
+        workers = max(1, min(workers, n_cells // max(1, cells_per_worker)))
+        q = ctx.Queue()
+        bar = ctx.Barrier(workers)
+        procs = [ctx.Process(target=_oracle_shard,
+                             args=(workload, i * cells_per_worker, (i + 1) * cells_per_worker, charge_model, mlp,
+                                   warmup, steps, seconds, bar, q)) for i in range(workers)]
+        for p in procs:
+            p.start()
+        res = []
+        while len(res) < len(procs):   # collect, and fail loudly if a worker died
+            try:
+                res.append(q.get(timeout=5))
+            except Exception:
+                dead = [p.exitcode for p in procs if p.exitcode not in (None, 0)]
+                if dead:
+                    for p in procs:
+                        if p.is_alive():
+                            p.terminate()
+                    raise RuntimeError(f"an oracle worker failed (exit codes {dead})")
+        for p in procs:
+            p.join(timeout=60)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    total = sum(m * n for m, n, _, _ in res)
+    el = max(t1 for *_, t1 in res) - min(t0 for _, _, t0, _ in res)
+    return total / el, total, el, min(n for _, n, _, _ in res), workers
+
+
+def _sample_cells(workload, n_total):
+    """Cells per oracle process: a bounded sample of the workload (about 10-20 s of oracle work)."""
+    if workload == "p33":
+        return 1
+    return max(1, min(n_total, 256 if workload in ("c3", "c4", "c5") else 512))
+
+
+def cpu_baseline(workload, charge_model, mlp, n_total):
+    """The oracle as it stands on one core and on every core of the host."""
+    cores = _host_cores()
+    n = _sample_cells(workload, n_total)
+    v1, tot1, el1, k1, _ = oracle_throughput(workload, ORACLE_CHARGE[charge_model], mlp, 1, n, warmup=1, seconds=8.0)
+    vall, tot, el, k, used = oracle_throughput(workload, ORACLE_CHARGE[charge_model], mlp, cores, n, warmup=1,
+                                               steps=max(2, k1))
+    return {"value": vall, "unit": "molecule-steps/s", "cores": used, "kind": "oracle",
+            "value_one_core": v1, "nproc": cores, "cpu_model": _cpu_model(),
+            "sample": f"{used} processes (one per core, one thread each), each the oracle's full time step "
+                      f"({ORACLE_CHARGE[charge_model]} dipole derivatives, FP64 coupling to all modes) on its own "
+                      f"{n} cells of workload {workload}, {k} steps after one warm-up step, {el:.1f} s; one core: "
+                      f"{n} cells, {k1} steps, {el1:.1f} s. Each process's coupling sum covers its own cells only "
+                      f"(the same work per cell as the full sum)"}
 
 
 def run_reference(args):
@@ -193,31 +311,54 @@ def run_reference(args):
     if rank != 0:
         return
     import cavmd_synth as cs
-    from oracle import cavity as OC
-    n_sample = 1 if args.workload == "p33" else 512
+    from paper_2512_03277_gb300 import cavmd as B
     w = cs.make_workload(args.workload)
-    sub = cs.make_workload(args.workload, n_cells=n_sample)
-    sy, mo, pa = sub["system"], w["modes"], sub["params"]
-    mat = _oracle_matter(sub)
-    md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, w["options"]["dt"])
-    for _ in range(args.warmup):
-        md.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        md.step()
-    el = time.perf_counter() - t0
-    value = (sy.n_atoms // 3) * args.steps / el
+    charge_model = _arm_defaults(args)[0][1]
+    mlp = _network(B, charge_model)
+    cores = _host_cores()
+    n = _sample_cells(args.workload, w["system"].n_cells)
+    value, tot, el, k, used = oracle_throughput(args.workload, ORACLE_CHARGE[charge_model], mlp, cores, n,
+                                                warmup=args.warmup, steps=args.steps)
+    sample = (f"{used} processes (one per core, one thread each), each the oracle's full time step "
+              f"({ORACLE_CHARGE[charge_model]} dipole derivatives, FP64 coupling to all {w['modes'].n_modes} modes) "
+              f"on its own {n} of the {w['system'].n_cells} cells, {args.warmup} warm-up and {args.steps} timed steps")
     line = {
         "impl": "reference", "metric": "molecule-steps/s", "value": value, "unit": "molecule-steps/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(args.workload, w),
-        "cpu_baseline": {"value": value, "unit": "molecule-steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {n_sample} of {w['system'].n_cells} cells, all {mo.n_modes} modes, "
-                                   f"one oracle time step per step (NumPy FP64, one thread)"},
+        "data": "synthetic", "config": _config(args.workload, w, charge_model, "fp64"),
+        "cpu_baseline": {"value": value, "unit": "molecule-steps/s", "cores": used, "kind": "oracle",
+                         "nproc": cores, "cpu_model": _cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "molecule-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ the GPU arms
+
+def _arm_defaults(args):
+    """[(precision, charge_model)] of the arms: the headline first."""
+    grid = args.workload in ("c3", "c4", "c5")
+    prec = args.precision or ("mixed" if grid else "fp64")
+    charge = args.charge_model or ("born_mlp" if args.workload in ("c4", "c5") else "mulliken")
+    arms = [(prec, charge)]
+    compare = args.compare if args.compare is not None else args.workload in ("c4", "c5")
+    if compare and (prec, charge) != ("fp64", "born_fd"):
+        arms.append(("fp64", "born_fd"))
+    return arms
+
+
+def _network(B, charge_model):
+    """The shipped trained network, else (for timing only) a seeded one; None for other models."""
+    if charge_model != "born_mlp":
+        return None
+    p = B.trained_born_mlp()
+    if p is not None:
+        return p
+    rng = np.random.default_rng(4)
+    sizes = [(128, 32), (128,), (128, 128), (128,), (9, 128), (9,)]
+    return np.concatenate([rng.uniform(-1, 1, s_).ravel() / np.sqrt(s_[-1]) * (len(s_) == 2)
+                           for s_ in sizes]).astype(np.float32)
 
 
 def _config(workload, w, charge_model="mulliken", precision="fp64", mode_positions="fixed"):
@@ -238,20 +379,217 @@ def _config(workload, w, charge_model="mulliken", precision="fp64", mode_positio
             "parallelism": "replicas"}
 
 
+def _make_ctx(P, w, args, local, precision, charge_model, mlp, graph_chunk):
+    opt = P.default_options()
+    opt.device = local
+    if args.mixing is not None:
+        opt.mixing = args.mixing
+    opt.charge_model = CHARGE[charge_model]
+    opt.precision = PREC[precision]
+    if args.scc_history is not None:
+        opt.scc_history = args.scc_history
+    opt.autotune = 0 if args.no_autotune else 1
+    opt.mode_positions = 1 if args.mode_positions == "com" else 0
+    opt.acf_lags = args.acf_lags
+    opt.graph_chunk = graph_chunk
+    ctx = P.Context(w["system"], w["params"], w["modes"], opt, lattice=w.get("lattice"))
+    if mlp is not None:
+        ctx.cavmd_load_born_mlp(mlp)
+    return ctx
+
+
+def _time_steps(torch, ctx, args, ws, local, flush):
+    """K per-step timed cavmd_step(1) calls (events on the library stream, L2 flush between
+    steps), bracketed by barrier + synchronize; returns (total ms, max over ranks, wall s, clocks)."""
+    import torch.distributed as dist
+    stream = ctx.stream
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            ctx.cavmd_step(1)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    return total_ms, _reduce_max(total_ms, ws, f"cuda:{local}"), t_wall, clk
+
+
+def _measure_arm(torch, P, w, args, ws, local, precision, charge_model, mlp, flush, headline):
+    """Everything one arm reports. The headline arm adds the CUDA-graph and end-to-end figures."""
+    import ctypes as C
+    from paper_2512_03277_gb300 import cavmd as B
+    sy = w["system"]
+    N = sy.n_cells
+    n_mol = sy.n_atoms // 3
+    graph_chunk = max(1, min(50, args.steps))
+    ctx = _make_ctx(P, w, args, local, precision, charge_model, mlp, graph_chunk)
+    for _ in range(args.warmup):
+        ctx.cavmd_step(1)
+    ctx.cavmd_observables(want_arrays=False)
+    ctx.cavmd_phase_times({"dftb": 2, "all": 1, "off": 0}[args.phase_events], reset=True)
+    total_ms, max_ms, t_wall, clk = _time_steps(torch, ctx, args, ws, local, flush)
+    timed_ms, timed_cnt = ctx.cavmd_phase_times(0, reset=True)
+    # phase shares and launch counts from a second pass of the same steps, every launch timed
+    ctx.cavmd_phase_times(1, reset=True)
+    with torch.cuda.stream(ctx.stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            ctx.cavmd_step(1)
+    torch.cuda.synchronize()
+    phase_ms, phase_cnt = ctx.cavmd_phase_times(0, reset=True)
+    value = _whole_job_value(n_mol, args.steps, ws, max_ms)
+    ev = ctx.cavmd_get_eval()
+    # roofline of the dominant kernel: the SCC-DFTB evaluation (FP64-ALU bound)
+    dftb_ms = (phase_ms[0] / max(phase_cnt[0], 1)) if args.phase_events == "off" else \
+        timed_ms[0] / max(timed_cnt[0], 1)
+    periodic = w.get("lattice") is not None
+    if periodic:
+        n_orb = 2 * np.diff(sy.cell_offset)          # 6 per water: 2 per atom
+        flops = float(sum(_periodic_flops_per_cell(i, n, n * 2 // 3) for i, n in zip(ev["scc_iters"], n_orb)))
+    else:
+        flops = float(_dftb_flops_per_cell(ev["scc_iters"], *_cell_shapes(sy)).sum())
+    generic = not np.all(np.diff(sy.cell_offset) == 3)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sm * FP64_FLOPS_PER_CLK_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = flops / (dftb_ms * 1e-3) / 1e12
+    names = ["dftb", "photon_forward", "field_kick_drift", "dipole_derivative"]
+    shares = {nm: float(phase_ms[i] / max(phase_ms.sum(), 1e-30)) for i, nm in enumerate(names)}
+    mixed = precision == "mixed"
+    fd = charge_model in ("born_fd", "born_central")
+    launches = int(phase_cnt.sum()) + (int(phase_cnt[3]) if fd else 0) + \
+        2 * (int(phase_cnt[3]) if charge_model == "born_mlp" else 0) + (int(phase_cnt[0]) if mixed else 0)
+    arm = {
+        "value": value, "unit": "molecule-steps/s", "ms_per_step": max_ms / args.steps,
+        "precision": precision, "charge_model": charge_model,
+        "config": _config(args.workload, w, charge_model, precision, args.mode_positions),
+        "roofline": {"bound": "alu",
+                     "kernel": "k_dftb_periodic" if periodic else ("k_dftb_generic" if generic else "dftb_kernel<3,6>"),
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "flops_per_launch": flops, "avg_launch_ms": dftb_ms,
+                     "mean_scc_iters": float(np.mean(ev["scc_iters"])),
+                     "peak_note": f"FP64 ALU: {n_sm} SMs x 4 FP64 flop/clk x {SM_MAX_MHZ_NOMINAL:.0f} MHz (derived; "
+                                  f"no FP64 figure in the measured peaks)",
+                     "launch_time_source": "CUDA events in a second pass of the same steps"
+                     if args.phase_events == "off" else "CUDA events around each SCC-DFTB launch in the timed region"},
+        "phase_share": shares, "gpu_launches": launches, "clocks": clk, "tuning": ctx.cavmd_tuning(),
+        "wall_s_timed_region": t_wall,
+    }
+    if fd:
+        arm["born_interval"] = 3
+    if headline:
+        # CUDA-graph replay: cavmd_step(chunk) replays one captured graph of `chunk` steps; one
+        # event pair per chunk, no flush inside a chunk (the state each step reads exceeds L2)
+        chunks = max(1, args.steps // graph_chunk)
+        ctx.cavmd_step(graph_chunk)           # capture (untimed)
+        torch.cuda.synchronize()
+        gs = [torch.cuda.Event(enable_timing=True) for _ in range(chunks)]
+        ge = [torch.cuda.Event(enable_timing=True) for _ in range(chunks)]
+        with torch.cuda.stream(ctx.stream):
+            for i in range(chunks):
+                flush.zero_()
+                gs[i].record(ctx.stream)
+                ctx.cavmd_step(graph_chunk)
+                ge[i].record(ctx.stream)
+        torch.cuda.synchronize()
+        g_ms = float(sum(a.elapsed_time(b) for a, b in zip(gs, ge)))
+        g_ms = _reduce_max(g_ms, ws, f"cuda:{local}")
+        arm["graph"] = {"value": _whole_job_value(n_mol, chunks * graph_chunk, ws, g_ms), "unit": "molecule-steps/s",
+                        "steps": chunks * graph_chunk, "chunk": graph_chunk,
+                        "ms_per_step": g_ms / (chunks * graph_chunk),
+                        "note": "cavmd_step(chunk) replaying one captured CUDA graph per chunk; events per chunk; "
+                                "L2 flushed between chunks only"}
+        # end to end through the C ABI: step + observables into pinned host buffers, wall clock
+        pin = {k: torch.empty(n, dtype=torch.float64, pin_memory=True)
+               for k, n in (("M", N), ("q", ctx.n_modes), ("p", ctx.n_modes), ("D", ctx.n_modes))}
+        o = B.cavmd_obs()
+        for k, t in pin.items():
+            setattr(o, k, C.cast(t.data_ptr(), C.POINTER(C.c_double)))
+        ctx.cavmd_step(1)
+        ctx.cavmd_observables_into(o)
+        # double-buffered read-out: step s's observables are queued into slot s % 2 behind the step
+        # and collected after step s + 1 has been queued, so the host reads step s while s + 1 runs
+        ne = args.e2e_steps
+        t0 = time.perf_counter()
+        for s in range(ne):
+            ctx.cavmd_step(1)
+            ctx.cavmd_observables_async(s % 2)
+            if s > 0:
+                ctx.cavmd_observables_wait_into((s - 1) % 2, o)
+        ctx.cavmd_observables_wait_into((ne - 1) % 2, o)
+        e2e_s = time.perf_counter() - t0
+        e2e_s = _reduce_max(e2e_s * 1e3, ws, f"cuda:{local}") * 1e-3
+        d2h = 8 * (16 + N + 3 * ctx.n_modes)   # one packed copy: energies, SCC iterations, status, M, q, p, D
+        arm["e2e"] = {"value": n_mol * ne * ws / e2e_s, "unit": "molecule-steps/s", "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": d2h, "steps": ne,
+                      "note": "cavmd_step(1) + cavmd_observables_async / _wait (energies, per-cell dipoles, photon "
+                              "q/p/D) every step, double-buffered so the host reads step s while step s + 1 runs; "
+                              "the MD state stays on the device between steps, so no host input is copied per step"}
+    obs = ctx.cavmd_observables(want_arrays=False)
+    arm["energy_total"] = obs["e_total"]
+    arm["temperature_K"] = obs["temperature"]
+    ctx.cavmd_destroy()
+    return arm
+
+
+def _judge(P, params, arms, mlp, steps, replicas):
+    """Drift, heating and band error of every arm's (dipole derivative, coupling) on the resonant
+    box, against explicit central-difference Born charges with the FP64 coupling."""
+    from paper_2512_03277_gb300 import judge as J
+    cases = [("born_central", 0)] + [(cm, PREC[pr]) for pr, cm in arms]
+    if ("mulliken", 0) not in cases:
+        cases.append(("mulliken", 0))
+    t0 = time.perf_counter()
+    res = J.compare(P, params, cases, mlp=mlp, steps=steps, replicas=replicas)
+    out = {}
+    for (cm, pr), v in res.items():
+        key = f"{cm}/{'fp64' if pr == 0 else 'mixed'}"
+        out[key] = {"drift_ha_per_atom": v["drift"], "heating_K": v["heating"], "bend_ev": v["bend"],
+                    "stretch_ev": v["stretch"], "band_error_mev": v["band_error_mev"]}
+    out["setup"] = (f"33 waters (one per cell), resonant 2 x 2 mode grid (k = 0 at the bend, lambda 0.1), "
+                    f"{steps} steps of 0.5 fs, {replicas} velocity seeds; reference: central-FD Born every step, "
+                    f"FP64 coupling; drift = largest |slope x run| per atom over the seeds; heating = mean T "
+                    f"over the last tenth minus the second tenth; {time.perf_counter() - t0:.0f} s")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
-    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--workload", default="c5")
+    ap.add_argument("--e2e-steps", type=int, default=None, help="end-to-end steps (default: --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mixing", type=float, default=None, help="charge mixing (default: the library's)")
-    ap.add_argument("--charge-model", default="mulliken", choices=["mulliken", "born_fd", "born_central", "born_mlp"],
-                    help="dipole derivative (default: Mulliken charges)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
-                    help="coupling contraction: FP64, or BF16x3 on the tensor cores (grid modes)")
+    ap.add_argument("--charge-model", default=None, choices=list(CHARGE),
+                    help="the headline arm's dipole derivative (default: network Born charges on c4/c5, else "
+                         "Mulliken)")
+    ap.add_argument("--precision", default=None, choices=list(PREC),
+                    help="the headline arm's coupling: FP64, or BF16x3 on the tensor cores (grid modes; default on "
+                         "c3-c5)")
+    ap.add_argument("--compare", dest="compare", action="store_true", default=None,
+                    help="also time the plain FP64 arm (forward-FD Born every 3 steps, FP64 coupling); default on "
+                         "c4 and c5")
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
+    ap.add_argument("--judge-steps", type=int, default=10000)
+    ap.add_argument("--judge-replicas", type=int, default=4)
+    ap.add_argument("--no-judge", action="store_true")
     ap.add_argument("--n-cells", type=int, default=None, help="trim the workload to this many cells")
     ap.add_argument("--phase-events", default="dftb", choices=["dftb", "all", "off"],
                     help="CUDA events inside the timed region: around the SCC-DFTB launches only (default; "
@@ -269,6 +607,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.e2e_steps is None:
+        args.e2e_steps = max(args.steps, 20)
     ws, rank, local = _dist()
     if args.impl == "reference":
         run_reference(args)
@@ -289,149 +629,45 @@ def main():
     w = cs.make_workload(args.workload, n_cells=args.n_cells)
     if rank > 0:   # independent replica: its own Maxwell-Boltzmann velocities
         w["system"].p = cs.mb_momenta(np.random.default_rng(1000 + rank), w["system"])
-    opt = P.default_options()
-    opt.device = local
-    if args.mixing is not None:
-        opt.mixing = args.mixing
-    opt.charge_model = {"mulliken": 0, "born_fd": 1, "born_central": 2, "born_mlp": 3}[args.charge_model]
-    opt.precision = {"fp64": 0, "mixed": 2}[args.precision]
-    if args.scc_history is not None:
-        opt.scc_history = args.scc_history
-    opt.autotune = 0 if args.no_autotune else 1
-    opt.mode_positions = 1 if args.mode_positions == "com" else 0
     if args.acf_lags is None:
         args.acf_lags = 1024 if args.workload == "c5" else 0
-    opt.acf_lags = args.acf_lags
-    ctx = P.Context(w["system"], w["params"], w["modes"], opt, lattice=w.get("lattice"))
-    if args.charge_model == "born_mlp":
-        # a seeded network: the cost of a time step does not depend on the weight values
-        rng = np.random.default_rng(4)
-        sizes = [(128, 32), (128,), (128, 128), (128,), (9, 128), (9,)]
-        params = np.concatenate([rng.uniform(-1, 1, s_).ravel() / np.sqrt(s_[-1]) * (len(s_) == 2) for s_ in sizes])
-        ctx.cavmd_load_born_mlp(params.astype(np.float32))
-    stream = ctx.stream
-    N = w["system"].n_cells
-    n_mol = w["system"].n_atoms // 3          # water molecules (cells of the water workloads)
-    for _ in range(args.warmup):
-        ctx.cavmd_step(1)
-    ctx.cavmd_observables(want_arrays=False)
+    arms = _arm_defaults(args)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{local}")
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    ctx.cavmd_phase_times({"dftb": 2, "all": 1, "off": 0}[args.phase_events], reset=True)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    t_wall = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record(stream)
-            ctx.cavmd_step(1)
-            ends[k].record(stream)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter() - t_wall
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    timed_ms, timed_cnt = ctx.cavmd_phase_times(0, reset=True)
-    # phase shares and launch counts from a second pass of the same steps, every launch timed
-    ctx.cavmd_phase_times(1, reset=True)
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.zero_()
-            ctx.cavmd_step(1)
-    torch.cuda.synchronize()
-    phase_ms, phase_cnt = ctx.cavmd_phase_times(0, reset=True)
-    obs = ctx.cavmd_observables(want_arrays=False)
-    ev = ctx.cavmd_get_eval()
-    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
-    total_ms = float(step_ms.sum())
-    total_ms = _reduce_max(total_ms, ws, f"cuda:{local}")
-    value = _whole_job_value(n_mol, args.steps, ws, total_ms)
-
-    # roofline of the dominant kernel (SCC-DFTB, FP64-ALU bound)
-    if args.phase_events == "off":
-        dftb_ms = phase_ms[0] / max(phase_cnt[0], 1)
-    else:   # measured inside the timed region
-        dftb_ms = timed_ms[0] / max(timed_cnt[0], 1)
-    periodic = w.get("lattice") is not None
-    if periodic:
-        n_orb = 2 * np.diff(w["system"].cell_offset)          # 6 per water: 2 per atom
-        flops = float(sum(_periodic_flops_per_cell(i, n, n * 2 // 3) for i, n in zip(ev["scc_iters"], n_orb)))
-    else:
-        flops = float(_dftb_flops_per_cell(ev["scc_iters"], *_cell_shapes(w["system"])).sum())
-    generic = not np.all(np.diff(w["system"].cell_offset) == 3)
-    achieved = flops / (dftb_ms * 1e-3) / 1e12
-    peak = N_SM * FP64_FLOPS_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
-    shares = {name: float(phase_ms[i] / max(phase_ms.sum(), 1e-30))
-              for i, name in enumerate(["dftb", "photon_forward", "field_kick_drift", "born_fd_rows"])}
-
-    # end to end through the C ABI: step + observables into pinned host buffers, wall clock
-    pin = {k: torch.empty(n, dtype=torch.float64, pin_memory=True)
-           for k, n in (("M", N), ("q", ctx.n_modes), ("p", ctx.n_modes), ("D", ctx.n_modes))}
-    o = B.cavmd_obs()
-    import ctypes as C
-    for k, t in pin.items():
-        setattr(o, k, C.cast(t.data_ptr(), C.POINTER(C.c_double)))
-    ctx.cavmd_step(1)
-    ctx.cavmd_observables_into(o)
-    # double-buffered read-out: step s's observables are queued into slot s % 2 behind the step and
-    # collected after step s + 1 has been queued, so the host reads step s while the GPU runs s + 1
-    t0 = time.perf_counter()
-    for s in range(args.e2e_steps):
-        ctx.cavmd_step(1)
-        ctx.cavmd_observables_async(s % 2)
-        if s > 0:
-            ctx.cavmd_observables_wait_into((s - 1) % 2, o)
-    ctx.cavmd_observables_wait_into((args.e2e_steps - 1) % 2, o)
-    e2e_s = time.perf_counter() - t0
-    d2h = 8 * (16 + N + 3 * ctx.n_modes)   # one packed copy: energies, max SCC iterations, status, M, q, p, D
-    e2e = {"value": n_mol * args.e2e_steps * ws / e2e_s, "unit": "molecule-steps/s", "h2d_bytes_per_step": 0,
-           "d2h_bytes_per_step": d2h,
-           "note": "cavmd_step(1) + cavmd_observables_async / _wait (energies, per-cell dipoles, photon q/p/D) "
-                   "every step, double-buffered so the host reads step s while step s + 1 runs; the MD state "
-                   "stays on the device between steps, so no host input is copied per step"}
-
+    results = []
+    for i, (prec, cm) in enumerate(arms):
+        mlp = _network(B, cm)
+        results.append(_measure_arm(torch, P, w, args, ws, local, prec, cm, mlp, flush, headline=(i == 0)))
+        torch.cuda.empty_cache()
+    head = results[0]
+    trained = B.trained_born_mlp() is not None
     line = {
-        "metric": "molecule-steps/s", "value": value, "unit": "molecule-steps/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": "molecule-steps/s", "value": head["value"], "unit": "molecule-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": _config(args.workload, w, args.charge_model, args.precision, args.mode_positions),
-        "roofline": {"bound": "alu",
-                     "kernel": "k_dftb_periodic" if periodic else ("k_dftb_generic" if generic else "dftb_kernel<3,6>"),
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": DFTB_DRAM_BYTES_PER_LAUNCH if (args.workload == "c2" and args.n_cells is None) else None,
-                     "flops_per_launch": flops, "avg_launch_ms": dftb_ms,
-                     "mean_scc_iters": float(np.mean(ev["scc_iters"])),
-                     "peak_note": "FP64 ALU: 152 SMs x 4 FP64 flop/clk x 2070 MHz (derived, 1.26 TFLOP/s)",
-                     "launch_time_source": "CUDA events in a second pass of the same steps"
-                     if args.phase_events == "off" else "CUDA events around each SCC-DFTB launch in the timed region"},
-        "phase_share": shares,
-        "e2e": e2e,
-        "gpu_launches": int(phase_cnt.sum()) + (int(phase_cnt[3]) if args.charge_model in ("born_fd", "born_central") else 0)
-                        + 2 * (int(phase_cnt[3]) if args.charge_model == "born_mlp" else 0)
-                        + (int(phase_cnt[0]) if args.precision == "mixed" else 0),
-        "acf_lags": args.acf_lags,
-        "mode_positions": args.mode_positions,
-        "clocks": clk,
-        "tuning": ctx.cavmd_tuning(),
-        "wall_s_timed_region": t_wall,
-        "energy_total": obs["e_total"], "temperature_K": obs["temperature"],
+        "data": "synthetic", "config": head["config"], "roofline": head["roofline"],
+        "phase_share": head["phase_share"], "e2e": head["e2e"], "graph": head["graph"],
+        "gpu_launches": head["gpu_launches"], "acf_lags": args.acf_lags, "mode_positions": args.mode_positions,
+        "clocks": head["clocks"], "tuning": head["tuning"], "wall_s_timed_region": head["wall_s_timed_region"],
+        "energy_total": head["energy_total"], "temperature_K": head["temperature_K"],
+        "network": ("trained (paper_2512_03277_gb300/data/born_mlp_water.f32)" if trained else
+                    "seeded untrained weights (timing only)") if head["charge_model"] == "born_mlp" else None,
     }
+    if len(results) > 1:
+        plain = results[1]
+        line["arms"] = {"surrogate_mixed": {k: v for k, v in head.items() if k not in ("e2e", "graph")},
+                        "plain_fp64": plain}
+        line["surrogate_over_plain"] = head["value"] / plain["value"]
+    if rank == 0 and not args.no_judge and args.workload != "p33":
+        mlp = _network(B, "born_mlp") if trained else None
+        jarms = [(p, c) for p, c in arms if c != "born_mlp" or trained]
+        line["judge"] = _judge(P, w["params"], jarms, mlp, args.judge_steps, args.judge_replicas)
+        if not trained and any(c == "born_mlp" for _, c in arms):
+            line["judge"]["note"] = "network arm not judged: no trained weights shipped"
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        n_sample = None if w["system"].n_cells <= 4096 else (1024 if generic else 4096)
-        if periodic:
-            n_sample = 1
-        line["cpu_baseline"] = cpu_baseline(args.workload, n_sample=n_sample)
+        line["cpu_baseline"] = cpu_baseline(args.workload, head["charge_model"], _network(B, head["charge_model"]),
+                                            w["system"].n_cells)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.cavmd_destroy()
     if ws > 1:
         dist.destroy_process_group()
 

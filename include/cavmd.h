@@ -363,9 +363,12 @@ int cavmd_load_born_mlp(cavmd_ctx *ctx, const float *params, int32_t n_params);
  * fixed size inside the library (about 256 KB, held by every GPU that loads the library until the
  * process exits). Hence the limit 1 <= n_cells <= CAVMD_NOALLOC_MAX_CELLS; larger sizes return
  * CAVMD_ERR_INVALID_ARG with a message from cavmd_last_error(NULL). The call never allocates and
- * never calls cudaMalloc or cudaFree. Its first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture. Every call clears the counter it needs, but all calls share the one array, which keeps
+ * never calls cudaMalloc or cudaFree. Every call made outside a stream capture looks up the array's
+ * device address (cudaGetSymbolAddress) on the current device; a call made while `stream` is being
+ * captured uses the address of the last such lookup on that device, so make one call on each device
+ * before any capture (a captured call with no earlier lookup returns CAVMD_ERR_INVALID_ARG). After
+ * cudaDeviceReset the next call outside a capture looks the address up again. Every call clears the
+ * counter it needs, but all calls share the one array, which keeps
  * the last call's contents: calls that may overlap on the GPU (other streams, other host threads)
  * race and give wrong totals; serialise them. */
 #define CAVMD_NOALLOC_MAX_CELLS 1048576

@@ -88,14 +88,18 @@ def rotate(q, p, omega, t):
 # ---------------------------------------------------------------------------- matter models
 
 class DFTBMatter:
-    """Cells evaluated with oracle.dftb; dipole derivative by Mulliken charges or FD Born.
+    """Cells evaluated with oracle.dftb; dipole derivative by Mulliken charges, FD Born or the
+    Born-charge network.
 
     charge_model: 'mulliken' (b_j = Q_j pol, the paper's cheap replacement), 'born_fd' (forward
-    differences, the paper's choice) or 'born_central' (central differences, for tests).
-    born_interval: refresh b every this many evaluations (the paper uses 3); stale otherwise."""
+    differences, the paper's choice), 'born_central' (central differences, for tests) or 'network'
+    (b_j = pol^T Z_j with Z_j the Born tensor of the per-atom network of oracle/mlp.py with
+    parameters mlp_params, evaluated in FP64 on every evaluation).
+    born_interval: refresh the finite-difference b every this many evaluations (the paper uses 3);
+    stale otherwise."""
 
     def __init__(self, params, system, pol=(1.0, 0.0, 0.0), charge_model="mulliken",
-                 born_interval=1, fd_step=1e-3, beta=0.5, tol=1e-12, max_iter=400):
+                 born_interval=1, fd_step=1e-3, beta=0.5, tol=1e-12, max_iter=400, mlp_params=None):
         self.params = params
         self.species = np.asarray(system.species)
         self.off = np.asarray(system.cell_offset)
@@ -104,6 +108,9 @@ class DFTBMatter:
         self.mass = params.mass[self.species]
         self.cell_of_atom = np.repeat(np.arange(self.n_cells), np.diff(self.off))
         self.charge_model = charge_model
+        if charge_model == "network" and mlp_params is None:
+            raise ValueError("charge_model 'network' needs mlp_params")
+        self.mlp_params = None if mlp_params is None else np.asarray(mlp_params, float)
         self.born_interval = born_interval
         self.fd_step = fd_step
         self.kw = dict(beta=beta, tol=tol, max_iter=max_iter)
@@ -141,6 +148,12 @@ class DFTBMatter:
             Mn[cells] = out["mu"] @ self.pol
             if self.charge_model == "mulliken":
                 b[idx] = out["Q"][..., None] * self.pol
+            elif self.charge_model == "network":
+                from . import mlp as NN
+                nc = len(cells)
+                Z = NN.predict(self.mlp_params, np.tile(spec, nc), pos.reshape(-1, 3),
+                               np.arange(nc + 1) * nat, out["Q"].ravel())
+                b[idx] = np.einsum("a,jab->jb", self.pol, Z).reshape(nc, nat, 3)
             elif refresh:
                 scheme = "forward" if self.charge_model == "born_fd" else "central"
                 b[idx] = D.born_fd(self.params, spec, pos, self.pol, h=self.fd_step, scheme=scheme,

@@ -192,6 +192,19 @@ def cavmd_field_kick_noalloc(n_cells, n_modes, cell_offset, U, W, F, b, inv_mass
 
 
 MLP_NPARAMS = 21897
+BORN_MLP_WEIGHTS = os.path.join(HERE, "data", "born_mlp_water.f32")
+
+
+def trained_born_mlp(path: str = BORN_MLP_WEIGHTS):
+    """The trained Born-charge network shipped with the library (MLP_NPARAMS little-endian float32
+    values in the order of cavmd_mlp_create), or None when the file is absent. It was trained by
+    train_born_mlp.py on the oracle's finite-difference Born tensors of 300 K water geometries."""
+    if not os.path.exists(path):
+        return None
+    a = np.fromfile(path, dtype="<f4")
+    if a.size != MLP_NPARAMS or not np.all(np.isfinite(a)):
+        raise ValueError(f"{path}: expected {MLP_NPARAMS} finite float32 values, found {a.size}")
+    return a.astype(np.float32)
 
 
 class BornMLP:

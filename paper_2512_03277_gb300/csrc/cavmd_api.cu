@@ -808,7 +808,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         p.N = N;
         p.Npad = ((N + 127) / 128) * 128;
         CK(cudaDeviceGetAttribute(&p.n_sm, cudaDevAttrMultiProcessorCount, c->device));
-        p.n_fwd_cta = std::min(p.Npad / 64, p.n_sm);
+        p.n_fwd_cta = std::min(p.Npad / tc_fwd_stage_cells(), p.n_sm);
         const size_t np = (size_t)p.Npad;
         AL(p.Ahi, 128 * np); AL(p.Alo, 128 * np); AL(p.Af, 128 * np); AL(p.Bsrc, (size_t)p.KY * np);
         AL(p.Yhi, (size_t)p.KY * np); AL(p.Ylo, (size_t)p.KY * np);

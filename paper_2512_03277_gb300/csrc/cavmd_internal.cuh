@@ -124,9 +124,11 @@ struct TcPlan {
     int N, Npad, Kx, Ky2, KY, n_fwd_cta, n_sm;
     double dkx, dky;
     __nv_bfloat16 *Ahi, *Alo, *Yhi, *Ylo;   // phase panels (bfloat16 hi / lo, core-matrix order)
-    float *Af, *Bsrc, *partial;             // FP32 panels and split-K partial Gram matrices
+    float *Af, *Bsrc;                       // FP32 panels
+    double *partial;                        // split-K partial Gram matrices [n_fwd_cta][128][KY]
 };
 size_t tc_fwd_smem(int KY);
+int tc_fwd_stage_cells();         // cells per stage of the forward product
 size_t tc_back_smem(int KY);
 cudaError_t tc_prepare(int KY);   // kernel attributes (shared-memory size), once per plan
 cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st);

@@ -11,8 +11,9 @@
 //             Wt[jx][jy] = Wc, Wt[jx][Ky2+jy] = Ws, Wt[Kx+jx][jy] = Ws, Wt[Kx+jx][Ky2+jy] = -Wc,
 // the exact contraction of the k-space form of the coupling (no N x M phase matrix is stored).
 // Operands are split x = hi + lo into bfloat16 pairs and multiplied as hi hi + hi lo + lo hi
-// with FP32 accumulation in TMEM (BF16x3). The forward product is split over cells across CTAs
-// and the partial Gram matrices are summed in a fixed order in FP64.
+// with FP32 accumulation in TMEM (BF16x3). The forward product is split over cells across CTAs;
+// every TMEM accumulator covers one 32-cell stage and is folded into compensated FP32 sums, and the
+// partial Gram matrices of the CTAs are summed in a fixed order in FP64.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -22,7 +23,10 @@
 namespace {
 
 constexpr int KXP = 128;          // MMA M: 2 Kx rows padded to 128
-constexpr int FWD_CELLS = 64;     // cells (K) per forward stage
+constexpr int FWD_CELLS = 64;     // cells (K) per tile of the forward panels in HBM
+constexpr int FWD_SC = 32;        // cells (K) per forward stage: half a panel tile
+constexpr int FWD_NST = 4;        // forward stages in flight
+constexpr int FWD_THREADS = 256;  // two warps per TMEM lane quadrant in the forward fold
 constexpr int BACK_CELLS = 128;   // cells (N) per back tile
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
@@ -68,28 +72,37 @@ __global__ void k_tc_panels(int N, int Npad, int Kx, int Ky2, int KY, double dkx
 }
 
 // Forward Gram product, split over cells: partial[cta][i][j] = sum over the CTA's cells of A B^T.
-// Each 64-cell stage arrives by bulk copies (the BF16 hi / lo panels of A and the FP32 y-phase
-// panel of B, all pre-arranged in core-matrix order), one stage ahead of the MMAs; the threads
-// scale the y phases by M_n and split them into the BF16 hi / lo panels of B in shared memory.
+// Each 32-cell stage arrives by bulk copies (the BF16 hi / lo panels of A and the FP32 y-phase panel
+// of B, all pre-arranged in core-matrix order); up to FWD_NST stages are in flight. The threads scale
+// the y phases by M_n and split them into the BF16 hi / lo panels of B in shared memory, and one
+// thread issues the stage's MMAs into a fresh TMEM accumulator (two, alternating). The FP32 run of
+// an accumulator is therefore one stage: 32 cells, 6 MMAs. While the next stage's MMAs run, the
+// eight warps fold the finished accumulator into per-thread compensated FP32 sums (two-sum: the
+// rounding error of every addition is carried in a second register), so the accumulated error does
+// not grow with the number of cells a CTA owns. The partials leave as FP64 (sum + carried error).
 template <int KY>
-__global__ void __launch_bounds__(128) k_tc_forward(int nblk_total, int blk_per_cta, const __nv_bfloat16 *__restrict__ Ahi,
-                                                    const __nv_bfloat16 *__restrict__ Alo, const float *__restrict__ Bsrc,
-                                                    const double *__restrict__ Mc, int N, float *__restrict__ partial,
-                                                    unsigned *__restrict__ status) {
+__global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total, int st_per_cta,
+                                                                const __nv_bfloat16 *__restrict__ Ahi,
+                                                                const __nv_bfloat16 *__restrict__ Alo,
+                                                                const float *__restrict__ Bsrc,
+                                                                const double *__restrict__ Mc, int N,
+                                                                double *__restrict__ partial,
+                                                                unsigned *__restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    constexpr uint32_t A_BYTES = KXP * FWD_CELLS * 2, B_BYTES = KY * FWD_CELLS * 2, S_BYTES = KY * FWD_CELLS * 4;
+    constexpr uint32_t A_BYTES = KXP * FWD_SC * 2, B_BYTES = KY * FWD_SC * 2, S_BYTES = KY * FWD_SC * 4;
     constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES + S_BYTES;   // [A hi][A lo][B hi][B lo][B source]
     constexpr uint32_t LBO_A = (KXP / 8) * 128, LBO_B = (KY / 8) * 128;
-    constexpr uint32_t TCOLS = KY <= 32 ? 32 : (KY <= 64 ? 64 : 128);   // power of two >= KY
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * STAGE);      // [2] stage data arrived
-    uint64_t *done = full + 2;                                            // [2] stage MMAs finished
-    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 2);
+    constexpr uint32_t TC = KY <= 32 ? 32 : (KY <= 64 ? 64 : 128);    // columns of one accumulator
+    constexpr int NCOL = KY / 2;                                       // columns folded per thread
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + FWD_NST * STAGE);   // [NST] stage data arrived
+    uint64_t *done = full + FWD_NST;                                         // [NST] stage MMAs finished
+    uint32_t *slot = reinterpret_cast<uint32_t *>(done + FWD_NST);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b0 = blockIdx.x * blk_per_cta;
-    const int b1 = min(nblk_total, b0 + blk_per_cta);
-    if (warp == 0) tc::tmem_alloc(slot, TCOLS);
+    const int q0 = blockIdx.x * st_per_cta;
+    const int nq = max(0, min(n_stage_total, q0 + st_per_cta) - q0);
+    if (warp == 0) tc::tmem_alloc(slot, 2 * TC);
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < FWD_NST; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&done[s], 1);
         }
@@ -99,103 +112,126 @@ __global__ void __launch_bounds__(128) k_tc_forward(int nblk_total, int blk_per_
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     const uint32_t idesc = tc::idesc_bf16(KXP, KY);
-    auto issue = [&](int b, int s) {   // thread 0: the copies of tile b into stage s
+    // warps w and w + 4 read the same TMEM lane quadrant (w & 3), each one half of the columns
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const int col0 = (warp >> 2) * NCOL;
+    auto issue = [&](int i) {   // thread 0: the copies of local stage i into slot i % NST
+        const int s = i % FWD_NST;
+        const size_t q = (size_t)(q0 + i);
         uint8_t *st = smem + s * STAGE;
         tc::mbar_arrive_expect_tx(&full[s], 2 * A_BYTES + S_BYTES);
-        tc::bulk_g2s(st, Ahi + (size_t)b * KXP * FWD_CELLS, A_BYTES, &full[s]);
-        tc::bulk_g2s(st + A_BYTES, Alo + (size_t)b * KXP * FWD_CELLS, A_BYTES, &full[s]);
-        tc::bulk_g2s(st + 2 * A_BYTES + 2 * B_BYTES, Bsrc + (size_t)b * KY * FWD_CELLS, S_BYTES, &full[s]);
+        tc::bulk_g2s(st, Ahi + q * KXP * FWD_SC, A_BYTES, &full[s]);
+        tc::bulk_g2s(st + A_BYTES, Alo + q * KXP * FWD_SC, A_BYTES, &full[s]);
+        tc::bulk_g2s(st + 2 * A_BYTES + 2 * B_BYTES, Bsrc + q * KY * FWD_SC, S_BYTES, &full[s]);
     };
-    uint32_t pf[2] = {0u, 0u}, pd[2] = {0u, 0u};
-    int loaded[2] = {0, 0}, mma_pending[2] = {0, 0};   // thread 0's bookkeeping: copies and MMAs in flight
-    bool ok = true;
-    if (tid == 0 && b0 < b1) {
-        issue(b0, 0);
-        loaded[0] = 1;
+    float acc_s[NCOL], acc_c[NCOL];
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) {
+        acc_s[j] = 0.0f;
+        acc_c[j] = 0.0f;
     }
-    int it = 0;
-    for (int b = b0; b < b1; ++b, ++it) {
-        const int s = it & 1, s2 = s ^ 1;
-        if (b + 1 < b1) {   // prefetch the next tile once the MMAs reading its stage are done
-            if (tid == 0) {
-                if (mma_pending[s2]) {
-                    if (!tc::mbar_wait(&done[s2], pd[s2])) ok = false;
-                    pd[s2] ^= 1u;
-                    mma_pending[s2] = 0;
-                }
-                if (ok) {
-                    issue(b + 1, s2);
-                    loaded[s2] = 1;
+    // all threads: the accumulator of local stage i (TMEM buffer i & 1) into the compensated sums
+    auto fold = [&](int i) {
+        const uint32_t base = tmem + lane_base + (uint32_t)((i & 1) * TC + col0);
+#pragma unroll
+        for (int c0 = 0; c0 < NCOL; c0 += 32) {   // up to four loads in flight, then one wait
+            uint32_t r[4][8];
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (c0 + 8 * g < NCOL) tc::tmem_ld8_nowait(base + (uint32_t)(c0 + 8 * g), r[g]);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (c0 + 8 * g >= NCOL) continue;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int j = c0 + 8 * g + k;
+                    const float x = __uint_as_float(r[g][k]);
+                    const float s = acc_s[j];
+                    const float t = __fadd_rn(s, x);
+                    const float z = __fsub_rn(t, s);
+                    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));   // s + x - t exactly
+                    acc_s[j] = t;
+                    acc_c[j] = __fadd_rn(acc_c[j], e);
                 }
             }
         }
-        const bool got = tc::mbar_wait(&full[s], pf[s]);
-        if (got) {
-            pf[s] ^= 1u;
-            loaded[s] = 0;
-        }
-        if (!__syncthreads_and(got && ok)) { ok = false; break; }
+    };
+    int n_issued = 0;   // thread 0's count of stages whose copies were issued
+    if (tid == 0)
+        for (; n_issued < min(nq, FWD_NST - 1); ++n_issued) issue(n_issued);
+    bool ok = true;
+    int i = 0;
+    for (; i < nq; ++i) {
+        const int s = i % FWD_NST;
+        // stage i - 1's MMAs are done: its accumulator can be folded and its slot refilled
+        bool w = i == 0 || tc::mbar_wait(&done[(i - 1) % FWD_NST], ((i - 1) / FWD_NST) & 1);
+        if (tid == 0 && w && n_issued < nq && n_issued == i + FWD_NST - 1) issue(n_issued++);
+        w = w && tc::mbar_wait(&full[s], (i / FWD_NST) & 1);
+        if (!__syncthreads_and(w)) { ok = false; break; }
+        tc::fence_after_sync();
+        if (i > 0) fold(i - 1);
         uint8_t *st = smem + s * STAGE;
         const float *bs = reinterpret_cast<const float *>(st + 2 * A_BYTES + 2 * B_BYTES);
-        for (int c = tid; c < KY * FWD_CELLS / 8; c += 128) {   // 8 consecutive cells of one row per chunk
+        const int nbase = (q0 + i) * FWD_SC;
+        for (int c = tid; c < KY * FWD_SC / 8; c += FWD_THREADS) {   // 8 consecutive cells of one row per chunk
             const int kgrp = c / KY, row = c - kgrp * KY;
             const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_B);
             const float4 v0 = *reinterpret_cast<const float4 *>(bs + off / 2);
             const float4 v1 = *reinterpret_cast<const float4 *>(bs + off / 2 + 4);
             const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
             for (int q = 0; q < 8; ++q) {
-                const int n = b * FWD_CELLS + 8 * kgrp + q;
-                const float m = n < N ? (float)Mc[n] : 0.0f;
+                const int n = nbase + 8 * kgrp + q;
+                const float m = n < N ? (float)__ldg(Mc + n) : 0.0f;
                 split_bf16(vv[q] * m, hi[q], lo[q]);
             }
             *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + off) = *reinterpret_cast<const uint4 *>(hi);
             *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + B_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
         }
+        tc::fence_before_sync();   // the fold's TMEM reads are complete before the next MMAs reuse it
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_u32(st), sb = sa + 2 * A_BYTES;
-            for (int k = 0; k < FWD_CELLS / 16; ++k) {
+            const uint32_t d = tmem + (uint32_t)((i & 1) * TC);
+#pragma unroll
+            for (int k = 0; k < FWD_SC / 16; ++k) {
                 const uint32_t oa = k * 2 * LBO_A, ob = k * 2 * LBO_B;
                 const uint64_t ahd = tc::make_desc(sa + oa, LBO_A, 128), ald = tc::make_desc(sa + A_BYTES + oa, LBO_A, 128);
                 const uint64_t bhd = tc::make_desc(sb + ob, LBO_B, 128), bld = tc::make_desc(sb + B_BYTES + ob, LBO_B, 128);
-                const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
-                tc::mma_bf16(tmem, ahd, bhd, idesc, acc);
-                tc::mma_bf16(tmem, ahd, bld, idesc, 1u);
-                tc::mma_bf16(tmem, ald, bhd, idesc, 1u);
+                tc::mma_bf16(d, ahd, bhd, idesc, k > 0 ? 1u : 0u);   // a fresh accumulator every stage
+                tc::mma_bf16(d, ahd, bld, idesc, 1u);
+                tc::mma_bf16(d, ald, bhd, idesc, 1u);
             }
             tc::mma_commit(&done[s]);
-            mma_pending[s] = 1;
         }
     }
-    if (tid == 0) {   // every MMA finished (and any copy still in flight landed) before TMEM is read
-        for (int s = 0; s < 2; ++s) {
-            if (mma_pending[s] && !tc::mbar_wait(&done[s], pd[s])) ok = false;
-            if (loaded[s]) tc::mbar_wait(&full[s], pf[s]);
+    if (ok && nq > 0) {   // the last stage
+        const bool w = tc::mbar_wait(&done[(nq - 1) % FWD_NST], ((nq - 1) / FWD_NST) & 1);
+        if (__syncthreads_and(w)) {
+            tc::fence_after_sync();
+            fold(nq - 1);
+        } else {
+            ok = false;
         }
+    } else if (!ok && tid == 0) {   // a wait gave up at stage i: let what is in flight land first
+        if (i > 0) tc::mbar_wait(&done[(i - 1) % FWD_NST], ((i - 1) / FWD_NST) & 1);
+        for (int j = i; j < n_issued; ++j) tc::mbar_wait(&full[j % FWD_NST], (j / FWD_NST) & 1);
     }
     ok = __syncthreads_and(ok) != 0;
     if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
-    tc::fence_after_sync();
-    float *P = partial + (size_t)blockIdx.x * KXP * KY;
-    if (ok && b1 > b0) {
-        for (int c0 = 0; c0 < KY; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-            const int row = 32 * warp + lane;
-            for (int q = 0; q < 32 && c0 + q < KY; ++q) P[row * KY + c0 + q] = v[q];
-        }
-    } else {
-        for (int e = tid; e < KXP * KY; e += 128) P[e] = 0.0f;
-    }
+    double *P = partial + (size_t)blockIdx.x * KXP * KY + (size_t)(32 * (warp & 3) + lane) * KY + col0;
+#pragma unroll
+    for (int j = 0; j < NCOL; ++j) P[j] = ok ? (double)acc_s[j] + (double)acc_c[j] : 0.0;
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * TC);
 }
 
-__global__ void k_tc_reduce(int n_part, int size, const float *__restrict__ partial, double *__restrict__ G) {
+__global__ void k_tc_reduce(int n_part, int size, const double *__restrict__ partial, double *__restrict__ G) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= size) return;
     double s = 0.0;
@@ -322,8 +358,9 @@ cudaError_t set_smem(F f, size_t bytes) {
 // ---------------------------------------------------------------------------------------- host
 
 size_t tc_fwd_smem(int KY) {
-    return 2 * (2 * (size_t)KXP * FWD_CELLS * 2 + 2 * (size_t)KY * FWD_CELLS * 2 + (size_t)KY * FWD_CELLS * 4) + 64;
+    return FWD_NST * (2 * (size_t)KXP * FWD_SC * 2 + 2 * (size_t)KY * FWD_SC * 2 + (size_t)KY * FWD_SC * 4) + 128;
 }
+int tc_fwd_stage_cells() { return FWD_SC; }
 size_t tc_back_smem(int KY) { return 4 * (size_t)KXP * KY * 2 + 2 * (size_t)BACK_CELLS * KY * 2 + 64; }
 
 cudaError_t tc_prepare(int KY) {
@@ -346,13 +383,13 @@ cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st) 
 }
 
 cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsigned *status, cudaStream_t st) {
-    const int nblk = p.Npad / FWD_CELLS;
-    const int per = (nblk + p.n_fwd_cta - 1) / p.n_fwd_cta;
+    const int nq = p.Npad / FWD_SC;
+    const int per = (nq + p.n_fwd_cta - 1) / p.n_fwd_cta;
     const size_t sm = tc_fwd_smem(p.KY);
     cudaError_t e = cudaSuccess;
 #define FWD_CASE(KYV)                                                                                     \
     case KYV:                                                                                             \
-            k_tc_forward<KYV><<<p.n_fwd_cta, 128, sm, st>>>(nblk, per, p.Ahi, p.Alo, p.Bsrc, Mc, p.N,    \
+            k_tc_forward<KYV><<<p.n_fwd_cta, FWD_THREADS, sm, st>>>(nq, per, p.Ahi, p.Alo, p.Bsrc, Mc, p.N, \
                                                             p.partial, status);                           \
         break;
     switch (p.KY) {

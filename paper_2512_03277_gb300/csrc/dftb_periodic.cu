@@ -460,6 +460,9 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
     // drift with every step). The rounds rotate Ab and accumulate the rotations in Vb (m x m,
     // starting from I); then C_b <- C_b Vb and Y_b <- Y_b Vb as staged products through H, which
     // is free until the next iteration builds it.
+    // Workspaces it overwrites: Vb (the caller passes the density buffer P, free at this point:
+    // P = 2 C_o C_o^T is formed later in the same iteration) and H (rebuilt at the start of the
+    // next iteration). Neither may be read after a sweep before it is formed again.
     auto block_sweep = [&](const int *list, int m, double *Ab, double *Vb) {
         pprod<false, true, true>(sh, m, m, n, [&](int i, int k) { return C[list[i] * n + k]; },
                                  [&](int k, int c) { return Y[list[c] * n + k]; },
@@ -622,8 +625,9 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         } else {
             rank_occupation();
             if (sweep_now && it == 1) {   // first iteration after a geometry change
-                block_sweep(sh.occ_list, nocc, Mo, P);
-                block_sweep(sh.virt_list, nv, Mv, P);
+                double *const sweep_V = P;   // the rotation accumulator: P is formed later this iteration
+                block_sweep(sh.occ_list, nocc, Mo, sweep_V);
+                block_sweep(sh.virt_list, nv, Mv, sweep_V);
             }
             bool small = true;
             float kmax = 0.0f;

@@ -84,7 +84,9 @@ k_field_kick_noalloc(int N, int M, const int *__restrict__ off, const double *__
     }
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
+// Device address of the scratch array per device, from the last lookup made outside a stream
+// capture. Every call outside a capture looks the address up again (cheap), so a module reloaded
+// after cudaDeviceReset is seen; a call during a capture uses the remembered address.
 std::mutex g_mu;
 void *g_scratch_addr[64] = {nullptr};
 
@@ -110,10 +112,18 @@ extern "C" int cavmd_field_kick_noalloc(int32_t n_cells, int32_t n_modes, const 
         cavmd_set_global_error(std::string("cavmd_field_kick_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
         return CAVMD_ERR_CUDA;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) {
+        cavmd_set_global_error(std::string("cavmd_field_kick_noalloc: cudaStreamIsCapturing: ") +
+                               cudaGetErrorString(e));
+        return CAVMD_ERR_CUDA;
+    }
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, noalloc_scratch);
             if (e != cudaSuccess) {
@@ -122,10 +132,13 @@ extern "C" int cavmd_field_kick_noalloc(int32_t n_cells, int32_t n_modes, const 
                 return CAVMD_ERR_CUDA;
             }
             g_scratch_addr[dev] = ptr;
+        } else if (!g_scratch_addr[dev]) {
+            cavmd_set_global_error("cavmd_field_kick_noalloc: the first call on a device must come before any "
+                                   "stream capture");
+            return CAVMD_ERR_INVALID_ARG;
         }
         scratch = g_scratch_addr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
     // the last-block counter must start at zero
     e = cudaMemsetAsync(static_cast<double *>(scratch) + NA_MAX_BLOCKS, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) {

@@ -1,18 +1,20 @@
 """Mixed-precision coupling (tensor cores, BF16x3 with FP32 accumulation) against the FP64 oracle.
 
-Error bound used below: each operand x is split x = hi + lo with hi = bf16(x), lo = bf16(x - hi),
-so |x - hi - lo| <= 2^-18 |x|; a product is formed as hi hi + hi lo + lo hi, dropping lo lo
-(<= 2^-18 |ab|); with the FP32 inputs (2^-24) and FP32 accumulation over at most 64 cells per
-CTA in these tests (64 * 2^-24), every D_a and E_n lies within 3e-5 of the sum of the absolute
-values of its terms, lambda_a sum_n |u_a(R_n) M_n| and sum_a |u_a(R_n) W_a|."""
+The error bound is derived in tests/bf16x3.py from what the kernels do: every D_a lies within
+EPS_D = 5e-5 of lambda_a sum_n mag(a, n) |M_n| of the exact contraction of the same dipoles, and
+every field E_n within EPS_E = 6e-5 of sum_a mag(a, n) |W_a|, where mag(a, n) <= 1 is the
+magnitude of the factorised phase product (Eq. hlm2 is the contraction). The bound does not grow
+with the number of cells: each TMEM accumulator covers one 32-cell stage and the stages are folded
+into compensated sums. The largest ratio of error to bound is printed."""
 import numpy as np
 import pytest
 
 import cavmd_synth as cs
 from oracle import cavity as OC
 
+from bf16x3 import bounds
+
 pytestmark = pytest.mark.gpu
-REL = 3e-5
 
 
 @pytest.fixture(scope="module")
@@ -34,7 +36,7 @@ def _ctx(P, w, **opt):
     return P.Context(w["system"], w["params"], w["modes"], o)
 
 
-@pytest.mark.parametrize("name,n", [("c4", 300), ("c5", 700)])
+@pytest.mark.parametrize("name,n", [("c4", 300), ("c5", 700), ("c4", 5000)])
 def test_mixed_coupling_within_bf16x3_bound(P, name, n):
     w = cs.make_workload(name, n_cells=n)
     sy, mo, pa = w["system"], w["modes"], w["params"]
@@ -45,16 +47,19 @@ def test_mixed_coupling_within_bf16x3_bound(P, name, n):
     obs = ctx.cavmd_observables()
     U = md.U
     M_gpu = ev["M"]
-    bound_D = REL * np.abs(mo.lam) * (np.abs(U) @ np.abs(M_gpu))
-    own = OC.forward(U, mo.lam, M_gpu)            # exact contraction of the GPU's own dipoles
-    assert np.all(np.abs(obs["D"] - own) <= bound_D + 1e-300)
-    # total force: the DFTB part is FP64, the field part carries the BF16x3 bound
     W = mo.lam * (mo.omega * obs["q"] - obs["D"])
+    bound_D, bound_E = bounds(mo, sy.R_ref, M_gpu, W)
+    own = OC.forward(U, mo.lam, M_gpu)            # exact contraction of the GPU's own dipoles
+    err_D = np.abs(obs["D"] - own)
+    assert np.all(err_D <= bound_D + 1e-300)
+    # total force: the DFTB part is FP64, the field part carries the BF16x3 bound
     E_exact = U.T @ W
-    bound_E = REL * (np.abs(U).T @ np.abs(W))
     F_ref = ev["F_dftb"] + E_exact[md.cell][:, None] * ev["b"]
+    err_F = np.abs(ev["F_total"] - F_ref)
     bound_F = bound_E[md.cell][:, None] * np.abs(ev["b"]) + 1e-12
-    assert np.all(np.abs(ev["F_total"] - F_ref) <= bound_F)
+    assert np.all(err_F <= bound_F)
+    print(f"\n{name} {n} cells: max |dD| / bound {np.max(err_D / (bound_D + 1e-300)):.3f}, "
+          f"max |dF| / bound {np.max(err_F / bound_F):.3f}")
     # and the FP64 parts still match the oracle
     fs = np.abs(md.out["F"]).max()
     np.testing.assert_allclose(ev["F_dftb"], md.out["F"], rtol=0, atol=1e-9 * fs)

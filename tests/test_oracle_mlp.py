@@ -86,3 +86,23 @@ def test_full_born_tensor_matches_single_polarisation_routine():
         b = D.born_fd(params, WATER, pos, pol, h=1e-3, scheme="central")
         np.testing.assert_allclose(Z[:, :, a, :], b, atol=1e-12)
     np.testing.assert_allclose(Z.sum(1), 0.0, atol=1e-6)        # translation sum rule, O(h^2)
+
+
+def test_network_charge_model_of_the_cavity_oracle():
+    """The cavity oracle's 'network' dipole derivative: with a zero network it is the Mulliken
+    model exactly (b_j = Q_j pol), and with any network it is pol^T Z_j of the network's Born
+    tensors, a sum rule sum_j b_j = Q_cell pol = 0 holding for neutral cells."""
+    from oracle import cavity as OC
+    w = cs.make_workload("c1", n_cells=5)
+    sy, pa = w["system"], w["params"]
+    mul = OC.DFTBMatter(pa, sy)(sy.r)
+    zero = OC.DFTBMatter(pa, sy, charge_model="network", mlp_params=np.zeros(NN.N_PARAMS))(sy.r)
+    np.testing.assert_allclose(zero["b"], mul["b"], rtol=0, atol=1e-15)
+    p = _random_params(seed=7)
+    net = OC.DFTBMatter(pa, sy, charge_model="network", mlp_params=p)(sy.r)
+    Z = NN.predict(p, sy.species, sy.r, sy.cell_offset, net["Q"])
+    np.testing.assert_allclose(net["b"], Z[:, 0, :], rtol=0, atol=1e-14)     # pol = x
+    np.testing.assert_allclose(net["b"].reshape(-1, 3, 3).sum(1), 0.0, atol=1e-12)
+    assert np.abs(net["b"] - mul["b"]).max() > 1e-3
+    with pytest.raises(ValueError):
+        OC.DFTBMatter(pa, sy, charge_model="network")
