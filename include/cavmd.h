@@ -179,6 +179,12 @@ typedef struct {
                                    up to scc_history-1 previous iterates (1..6; 1 = linear mixing).
                                    Cells of 3 atoms / 6 orbitals use a fixed history of 3.        */
     int32_t mode_positions;     /* CAVMD_MODES_FIXED (default) or CAVMD_MODES_CENTRE_OF_MASS    */
+    int32_t jacobi_max_sweeps;  /* bound on the Jacobi sweeps of a cold start (the first evaluation,
+                                   and the first SCC iteration after cavmd_set_state): 0 = the
+                                   kernels' defaults (24 for waters, 40 for clusters and periodic
+                                   cells), else 1..1000. A cell whose off-diagonal elements are
+                                   still above tolerance at the bound makes the call report
+                                   CAVMD_ERR_DEVICE_TIMEOUT. Later SCC iterations take one sweep. */
 } cavmd_options;
 
 /* Observables at the current (synchronised) time. Optional arrays may be NULL. */

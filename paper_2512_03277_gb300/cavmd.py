@@ -57,7 +57,7 @@ class cavmd_options(C.Structure):
                 ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", C.c_void_p), ("energy_history", C.c_int32), ("acf_lags", C.c_int32),
                 ("autotune", C.c_int32), ("scc_history", C.c_int32),
-                ("mode_positions", C.c_int32)]
+                ("mode_positions", C.c_int32), ("jacobi_max_sweeps", C.c_int32)]
 
 
 class cavmd_obs(C.Structure):

@@ -156,8 +156,11 @@ int status_to_code(cavmd_ctx *c, unsigned st) {
     if (st & ERRBIT_NONFINITE) return fail(c, CAVMD_ERR_NONFINITE, "non-finite energy in the state");
     if (st & ERRBIT_S_NOT_PD) return fail(c, CAVMD_ERR_S_NOT_PD, "an overlap matrix is not positive definite");
     if (st & ERRBIT_ZERO_GAP) return fail(c, CAVMD_ERR_ZERO_GAP, "HOMO-LUMO gap below threshold");
+    // a bounded loop that ran out is the cause of any non-convergence that follows it
+    if (st & ERRBIT_TIMEOUT)
+        return fail(c, CAVMD_ERR_DEVICE_TIMEOUT,
+                    "a bounded device loop ran out (the Jacobi sweeps of a cold start, or a tensor-core wait)");
     if (st & ERRBIT_SCC_NOCONV) return fail(c, CAVMD_ERR_SCC_NOCONV, "SCC charges did not converge within scc_max_iter");
-    if (st & ERRBIT_TIMEOUT) return fail(c, CAVMD_ERR_DEVICE_TIMEOUT, "Jacobi sweep limit reached");
     return fail(c, CAVMD_ERR_CUDA, "unknown device status");
 }
 
@@ -623,6 +626,8 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if (o->acf_lags < 0 || (o->autotune != 0 && o->autotune != 1))
         return fail(c, CAVMD_ERR_INVALID_ARG, "acf_lags must be >= 0 and autotune 0 or 1");
     if (o->scc_history < 1 || o->scc_history > 6) return fail(c, CAVMD_ERR_INVALID_ARG, "scc_history must be 1..6");
+    if (o->jacobi_max_sweeps < 0 || o->jacobi_max_sweeps > 1000)
+        return fail(c, CAVMD_ERR_INVALID_ARG, "jacobi_max_sweeps must be 0..1000");
     if (o->mode_positions != CAVMD_MODES_FIXED && o->mode_positions != CAVMD_MODES_CENTRE_OF_MASS)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad mode_positions");
     if (o->mode_positions == CAVMD_MODES_CENTRE_OF_MASS && o->precision != CAVMD_PREC_FP64)
@@ -901,6 +906,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.max_iter = c->opt.scc_max_iter;
     d.hist = c->opt.scc_history;
     d.have_warm = 0;
+    d.max_sweeps = c->opt.jacobi_max_sweeps;
     d.write_b = c->opt.charge_model == CAVMD_CHARGE_MULLIKEN;
     d.n_disp = 0;
     d.fd_central = 0;

@@ -55,6 +55,7 @@ struct DftbArgs {
     int max_iter;
     int hist;                  // Anderson history (cluster kernel): current + hist-1 previous iterates
     int have_warm;             // 1: Cwarm and qpop hold a previous solution
+    int max_sweeps;            // bound on the Jacobi sweeps of a cold start (0: the kernel's default)
     int write_b;               // 1: write Mulliken b
     // finite-difference rows: n_disp > 0 turns every cell into displaced copies that only compute
     // their dipole (3 per atom forward, or 6 per atom central in +h, -h pairs)

@@ -28,7 +28,7 @@
 namespace {
 
 constexpr int GNHIST = 6;              // largest Anderson history (current + 5 previous iterates)
-constexpr int G_MAX_SWEEPS = 40;
+constexpr int G_MAX_SWEEPS = 40;            // default bound on the Jacobi sweeps of a cold start
 constexpr double G_JACOBI_TOL = 1e-15;
 constexpr double G_MIN_GAP = 1e-3;
 constexpr double G_EIG_TOL = 1e-10;
@@ -464,17 +464,18 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
                        [&](int e) { return Y + virt_list[e / nv] * LD; },
                        [&](int e, double v) { A[virt_list[e / nv] * LD + virt_list[e % nv]] = v; });
             g.sync();
-            const int sweeps = cold_first ? G_MAX_SWEEPS : 1;
-            for (int sweep = 0; sweep < G_MAX_SWEEPS; ++sweep) {
+            // a cold start sweeps until the off-diagonal entries are below tolerance, at most `cap`
+            // sweeps (then DEVICE_TIMEOUT); later iterations take one sweep
+            const int cap = cold_first ? (a.max_sweeps > 0 ? a.max_sweeps : G_MAX_SWEEPS) : 1;
+            for (int sweep = 0;; ++sweep) {
                 bool off_small = true;
                 for (int e = j; e < nn; e += T) {
                     const int c = e / n, i = e - c * n;
                     if (i != c && !abs_lt(A[c * LD + i], G_JACOBI_TOL)) off_small = false;
                 }
                 if (g.all(off_small)) break;
-                if (sweep >= sweeps) break;
-                if (sweep == G_MAX_SWEEPS - 1) {
-                    if (j == 0) atomicOr(&fl[0], ERRBIT_TIMEOUT);
+                if (sweep >= cap) {
+                    if (cold_first && j == 0) atomicOr(&fl[0], ERRBIT_TIMEOUT);
                     break;
                 }
                 for (int rd = 0; rd < n - 1; ++rd) {

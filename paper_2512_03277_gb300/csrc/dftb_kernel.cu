@@ -23,7 +23,7 @@
 namespace {
 
 constexpr int NHIST = 3;          // Anderson history (current + 2 previous iterates)
-constexpr int MAX_SWEEPS = 24;    // bound on Jacobi sweeps per SCC iteration
+constexpr int MAX_SWEEPS = 24;    // default bound on the Jacobi sweeps of a cold start
 constexpr double JACOBI_TOL = 1e-15;   // off-diagonal magnitude treated as converged (Hartree)
 constexpr double MIN_GAP = 1e-3;       // closed-shell HOMO-LUMO threshold (Hartree)
 constexpr double EIG_TOL = 1e-10;      // occupied-virtual coupling treated as converged (Hartree)
@@ -532,17 +532,18 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
                 }
             }
             __syncwarp();
-            const int sweeps_per_iter = cold_first ? MAX_SWEEPS : 1;
-            for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+            // a cold start sweeps until the off-diagonal entries are below tolerance, at most `cap`
+            // sweeps (then DEVICE_TIMEOUT); later iterations take one sweep
+            const int cap = cold_first ? (a.max_sweeps > 0 ? a.max_sweeps : MAX_SWEEPS) : 1;
+            for (int sweep = 0;; ++sweep) {
                 bool small = true;
                 if (work) {
                     for (int i = 0; i < NORB; ++i)
                         if (i != j && !abs_lt(m.A[j * LD + i], JACOBI_TOL)) small = false;
                 }
                 if (__all_sync(CAVMD_FULL_MASK, small)) break;
-                if (sweep >= sweeps_per_iter) break;
-                if (sweep == MAX_SWEEPS - 1) {
-                    if (work && !small) m.flag |= ERRBIT_TIMEOUT;
+                if (sweep >= cap) {
+                    if (cold_first && work && !small) m.flag |= ERRBIT_TIMEOUT;
                     break;
                 }
                 for (int rd = 0; rd < NORB - 1; ++rd) {

@@ -45,7 +45,7 @@ constexpr int ZC = 80;           // columns of the second operand staged per pas
 constexpr int PNMAX = 256;       // orbitals per cell
 constexpr int PAMAX = 128;       // atoms per cell
 constexpr int PHIST = 6;         // largest Anderson history
-constexpr int P_MAX_SWEEPS = 40;
+constexpr int P_MAX_SWEEPS = 40;   // default bound on the Jacobi sweeps of a cold start
 constexpr double P_JACOBI_TOL = 1e-11;   // cold start: off-diagonal size where the sweeps stop
 constexpr double P_MIN_GAP = 1e-3;
 constexpr double P_EIG_TOL = 1e-10;
@@ -577,13 +577,18 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
                                      [&](int k, int c) { return Y[c * n + k]; },
                                      [&](int i, int c, double v) { P[c * n + i] = v; });
             double *Am = P;
-            for (int sweep = 0; sweep < P_MAX_SWEEPS; ++sweep) {
+            const int cap = a.max_sweeps > 0 ? a.max_sweeps : P_MAX_SWEEPS;
+            for (int sweep = 0;; ++sweep) {
                 bool off_small = true;
                 for (int e = j; e < nn; e += PT) {
                     const int c = e / n, i = e - c * n;
                     if (i != c && !abs_lt(Am[c * n + i], P_JACOBI_TOL)) off_small = false;
                 }
                 if (blk_all(off_small)) break;
+                if (sweep >= cap) {   // the cold start's sweeps ran out: DEVICE_TIMEOUT
+                    if (j == 0) sh.fl[0] |= ERRBIT_TIMEOUT;
+                    break;
+                }
                 for (int rd = 0; rd < n - 1; ++rd) {
                     if (j < n / 2) {
                         int p, qq;
