@@ -8,12 +8,14 @@
 //             exp(-0.05 (r_k^2 + r_l^2)) fc fc for z in {1,2,4,8}, lam = +-1, element one-hot;
 //             cosine cutoff fc at 8 bohr, neighbours = the other atoms of the cell;
 //   R_j      : rows e1 (to the nearest neighbour), e2 (second-nearest, orthogonalised), e3 = e1 x e2;
-//   y_j      : W3 silu(W2 silu(W1 x + b1) + b2) + b3, 32 -> 128 -> 128 -> 9, BF16 weights, FP32 math;
+//   y_j      : W3 silu(W2 silu(W1 x + b1) + b2) + b3, 32 -> 128 -> 128 -> 9, BF16 weights, FP32 math
+//              (tcgen05 MMAs with the activations split into BF16 parts, FP32 accumulation);
 //   Z_j      = Q_j I + R_j^T T_j R_j - mean over the cell (T_j = y_j as 3 x 3), so the sum rule
 //              sum_j Z_j = Q_cell I holds and a zero network is the Mulliken model;
 //   b_j      = pol^T Z_j.
-// Training minimises sum |Z - Z_ref|^2 / (9 n_atoms) with AdamW on FP32 master weights; the
-// gradient reduction over atom tiles is a fixed-order sum (bitwise reproducible).
+// Training minimises sum |Z - Z_ref|^2 / (9 n_atoms) with AdamW on FP32 master weights. Forward,
+// backward and weight gradients run on the tensor cores; the gradient reduction over CTAs is a
+// fixed-order sum (bitwise reproducible).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -34,10 +36,8 @@ constexpr int NO = 9;
 constexpr int OFF_W1 = 0, OFF_B1 = NH * NF, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH,
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NO * NH, NPAR = OFF_B3 + NO;
 static_assert(NPAR == CAVMD_MLP_NPARAMS, "parameter count");
-constexpr int TILE = 16;          // atoms per block in the forward and backward kernels
 constexpr float RC = 8.0f;
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
 __device__ __forceinline__ float dsilu(float z) {
     const float s = 1.0f / (1.0f + __expf(-z));
     return s * (1.0f + z * (1.0f - s));
@@ -127,81 +127,8 @@ __global__ void k_features(int n_cells, const int *__restrict__ off, const int *
     }
 }
 
-// forward over a tile of TILE atoms: Zl = R^T T R; with `store`, keeps z1, z2, h1, h2 for backward
-__global__ void __launch_bounds__(NH) k_forward(int n, const float *__restrict__ X, const float *__restrict__ R,
-                                                const __nv_bfloat16 *__restrict__ w, float *__restrict__ Zl,
-                                                float *__restrict__ z1g, float *__restrict__ z2g,
-                                                float *__restrict__ h1g, float *__restrict__ h2g) {
-    __shared__ float xs[TILE][NF + 1];
-    __shared__ float h1[TILE][NH + 1];
-    __shared__ float h2[TILE][NH + 1];
-    __shared__ float ys[TILE][NO];
-    const int t0 = blockIdx.x * TILE;
-    const int u = threadIdx.x;
-    for (int e = u; e < TILE * NF; e += NH) {
-        const int a = e / NF, i = e - a * NF;
-        xs[a][i] = (t0 + a < n) ? X[(size_t)(t0 + a) * NF + i] : 0.0f;
-    }
-    __syncthreads();
-    {
-        float wr[NF];
-        for (int i = 0; i < NF; ++i) wr[i] = wv(w, OFF_W1 + u * NF + i);
-        const float b = wv(w, OFF_B1 + u);
-        for (int a = 0; a < TILE; ++a) {
-            float z = b;
-#pragma unroll
-            for (int i = 0; i < NF; ++i) z = fmaf(wr[i], xs[a][i], z);
-            h1[a][u] = silu(z);
-            if (z1g && t0 + a < n) z1g[(size_t)(t0 + a) * NH + u] = z;
-        }
-    }
-    __syncthreads();
-    {
-        float acc[TILE];
-        const float b = wv(w, OFF_B2 + u);
-        for (int a = 0; a < TILE; ++a) acc[a] = b;
-        for (int v0 = 0; v0 < NH; v0 += 16) {
-            float wr[16];
-#pragma unroll
-            for (int t = 0; t < 16; ++t) wr[t] = wv(w, OFF_W2 + u * NH + v0 + t);
-#pragma unroll
-            for (int a = 0; a < TILE; ++a)
-#pragma unroll
-                for (int t = 0; t < 16; ++t) acc[a] = fmaf(wr[t], h1[a][v0 + t], acc[a]);
-        }
-        for (int a = 0; a < TILE; ++a) {
-            h2[a][u] = silu(acc[a]);
-            if (z2g && t0 + a < n) {
-                z2g[(size_t)(t0 + a) * NH + u] = acc[a];
-                h1g[(size_t)(t0 + a) * NH + u] = h1[a][u];
-            }
-        }
-    }
-    __syncthreads();
-    if (h2g)
-        for (int a = 0; a < TILE; ++a)
-            if (t0 + a < n) h2g[(size_t)(t0 + a) * NH + u] = h2[a][u];
-    for (int e = u; e < TILE * NO; e += NH) {
-        const int a = e / NO, o = e - a * NO;
-        float y = wv(w, OFF_B3 + o);
-        for (int v = 0; v < NH; ++v) y = fmaf(wv(w, OFF_W3 + o * NH + v), h2[a][v], y);
-        ys[a][o] = y;
-    }
-    __syncthreads();
-    if (u < TILE && t0 + u < n) {
-        const float *Rj = R + (size_t)(t0 + u) * 9;
-        // Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
-        for (int i = 0; i < 3; ++i)
-            for (int k = 0; k < 3; ++k) {
-                float s = 0.0f;
-                for (int aa = 0; aa < 3; ++aa)
-                    for (int bb = 0; bb < 3; ++bb) s = fmaf(Rj[3 * aa + i] * ys[u][3 * aa + bb], Rj[3 * bb + k], s);
-                Zl[(size_t)(t0 + u) * 9 + 3 * i + k] = s;
-            }
-    }
-}
-
-// Inference forward for the time step on the fifth-generation tensor cores (tcgen05). A tile of
+// Network forward on the fifth-generation tensor cores (tcgen05), for the time step and for
+// training (the same kernel, so inference and training see the same numbers). A tile of
 // 128 atoms sits on the 128 TMEM lanes and each layer is one BF16 MMA chain D = A B^T with FP32
 // accumulation in TMEM:
 //   A = the layer input, 128 atoms x K, split into three BF16 parts: hi + mid + lo carries a
@@ -213,6 +140,9 @@ __global__ void __launch_bounds__(NH) k_forward(int n, const float *__restrict__
 // columns 32 (w div 4) .. + 31), add the bias, apply silu and write the next layer's split operand to
 // shared memory; the last forms Zl = R^T T R for its atom. One persistent CTA per SM loads the
 // weights once; every mbarrier wait is bounded (timeout: status bit, TMEM still released).
+// Training keeps what the backward pass reads (FwdStore): the pre-activations z1, z2 atom-major,
+// and the layer inputs x, h1, h2 feature-major per tile ([tile][feature][atom of the tile]), the
+// layout in which the weight-gradient kernel stages them as K-major operands over atoms.
 constexpr int MT = 128;                              // atoms per tile = TMEM lanes
 constexpr int FWD_THREADS = 512;                     // 16 warps: four per TMEM lane quadrant
 constexpr uint32_t LBO_A = (MT / 8) * 128;           // A operand: K-group stride (128 rows)
@@ -250,8 +180,7 @@ __device__ __forceinline__ void split_store8(uint8_t *sa, uint32_t off, const fl
     *reinterpret_cast<uint4 *>(sa + 2 * A_SPLIT + off) = part[2];
 }
 
-// silu with the reciprocal of the special-function unit (the training kernels divide exactly; the
-// two differ by a few ulp)
+// silu with the reciprocal of the special-function unit
 __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // BF16 weights [rows][K] (row-major in the parameter vector) into the K-major core-matrix layout;
@@ -279,15 +208,34 @@ __device__ __forceinline__ void layer_mma(uint32_t tmem_d, uint32_t sa, uint32_t
     }
 }
 
-// Hidden-layer epilogue: 32 TMEM columns of this thread's atom -> silu(d + b) -> split A operand.
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, int col0, const float *b, uint8_t *sa, int row) {
+struct FwdStore {       // training outputs of the forward (all NULL in the time step)
+    float *z1, *z2;     // [atoms][128] pre-activations
+    float *h1t, *h2t;   // [tile][128][128] silu(z1), silu(z2), feature-major per tile
+    float *xt;          // [tile][32][128] network inputs, feature-major per tile
+};
+
+// Hidden-layer epilogue: 32 TMEM columns of this thread's atom -> z = d + b -> silu -> split A
+// operand; zg (this atom's row of z) and ht (this atom's column of the tile's activations) may be
+// NULL.
+__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, int col0, const float *b, uint8_t *sa, int row,
+                                                float *zg, float *ht) {
     float v[32];
     tc::tmem_ld32(taddr, v);
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        float x[8];
+        float x[8], z[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) x[q] = silu_fast(v[8 * g + q] + b[col0 + 8 * g + q]);
+        for (int q = 0; q < 8; ++q) {
+            z[q] = v[8 * g + q] + b[col0 + 8 * g + q];
+            x[q] = silu_fast(z[q]);
+        }
+        if (zg) {
+            *reinterpret_cast<float4 *>(zg + col0 + 8 * g) = make_float4(z[0], z[1], z[2], z[3]);
+            *reinterpret_cast<float4 *>(zg + col0 + 8 * g + 4) = make_float4(z[4], z[5], z[6], z[7]);
+        }
+        if (ht)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ht[(size_t)(col0 + 8 * g + q) * MT] = x[q];
         split_store8(sa, tc::core_offset(row, col0 + 8 * g, LBO_A), x);
     }
 }
@@ -295,7 +243,8 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t taddr, int col0, const 
 __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const float *__restrict__ X,
                                                              const float *__restrict__ R,
                                                              const __nv_bfloat16 *__restrict__ w,
-                                                             float *__restrict__ Zl, unsigned *__restrict__ status) {
+                                                             float *__restrict__ Zl, unsigned *__restrict__ status,
+                                                             const FwdStore st) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sw1 = smem, *sw2 = sw1 + SW1, *sw3 = sw2 + SW2, *sa = sw3 + SW3;   // sa: [hi][mid][lo]
     float *bias = reinterpret_cast<float *>(sa + 3 * A_SPLIT);                  // b1 [128] b2 [128] b3 [16]
@@ -340,6 +289,9 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const floa
 #pragma unroll
                 for (int q = 0; q < 8; ++q) x[q] = 0.0f;
             }
+            if (st.xt)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) st.xt[((size_t)t * NF + 8 * g + q) * MT + r] = x[q];
             split_store8(sa, tc::core_offset(r, 8 * g, LBO_A), x);
         }
         for (int layer = 0; layer < 3; ++layer) {
@@ -357,8 +309,13 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const floa
             pd ^= 1u;
             if (!__syncthreads_and(mg)) { ok = false; break; }
             tc::fence_after_sync();
-            if (layer == 0) hidden_epilogue(lanes + 32 * slice, 32 * slice, b1, sa, row);
-            else if (layer == 1) hidden_epilogue(lanes + NH + 32 * slice, 32 * slice, b2, sa, row);
+            if (layer < 2) {
+                float *zb = layer == 0 ? st.z1 : st.z2;
+                float *hb = layer == 0 ? st.h1t : st.h2t;
+                hidden_epilogue(lanes + (layer == 0 ? 0 : NH) + 32 * slice, 32 * slice, layer == 0 ? b1 : b2, sa, row,
+                                zb ? zb + (size_t)(t0 + row) * NH : nullptr,
+                                hb ? hb + (size_t)t * NH * MT + row : nullptr);
+            }
             else if (slice == 0) {   // outputs: Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
                 float v[32];
                 tc::tmem_ld32(lanes, v);
@@ -380,6 +337,270 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const floa
         if (!ok) break;
     }
     if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// BF16 weights W[K][rows] (row-major) into the K-major core-matrix layout of B[row][k] = W[k][row].
+__device__ __forceinline__ void load_weights_t(uint8_t *dst, const uint16_t *src, int rows, int K, uint32_t lbo) {
+    for (int c = threadIdx.x; c < rows * (K / 8); c += blockDim.x) {
+        const int g = c / rows, row = c - g * rows;
+        __align__(16) uint16_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = src[(8 * g + q) * rows + row];
+        *reinterpret_cast<uint4 *>(dst + tc::core_offset(row, 8 * g, lbo)) = *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
+// Backward through the activations, per 128-atom tile on the tensor cores. With gy = dL/dy (the
+// 9 outputs, from the cell tensors):
+//   gz2[a][u] = silu'(z2[a][u]) sum_o gy[a][o] W3[o][u]      (CUDA cores, 9 terms)
+//   gh1[a][v] = sum_u gz2[a][u] W2[u][v]                      (MMA: A = gz2 in three BF16 parts, so the
+//                                                              products are the FP32 ones; B = W2^T, BF16)
+//   gz1[a][v] = silu'(z1[a][v]) gh1[a][v]                     (TMEM epilogue)
+// gz2, gz1 and gy leave feature-major per tile ([tile][feature][atom]) for the weight gradients;
+// atoms beyond n get zeros, so they add nothing there.
+constexpr size_t BWA_SMEM = SW2 + 3 * (size_t)A_SPLIT + ((size_t)NO * NH + MT * 16) * 4 + 64;
+
+__global__ void __launch_bounds__(FWD_THREADS, 1) k_backward_act_tc(int n, const float *__restrict__ gy,
+                                                                  const float *__restrict__ z1,
+                                                                  const float *__restrict__ z2,
+                                                                  const __nv_bfloat16 *__restrict__ w,
+                                                                  float *__restrict__ gz2t, float *__restrict__ gz1t,
+                                                                  float *__restrict__ gyt, unsigned *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *sw2t = smem, *sa = sw2t + SW2;                       // W2^T (rows v, K = u); gz2 [hi][mid][lo]
+    float *w3 = reinterpret_cast<float *>(sa + 3 * A_SPLIT);     // [9][128]
+    float *gys = w3 + NO * NH;                                   // [128 atoms][16]
+    uint64_t *done = reinterpret_cast<uint64_t *>(gys + MT * 16);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(slot, NH);
+    if (tid == 0) tc::mbar_init(done, 1);
+    load_weights_t(sw2t, reinterpret_cast<const uint16_t *>(w) + OFF_W2, NH, NH, LBO_W);
+    for (int e = tid; e < NO * NH; e += FWD_THREADS) w3[e] = wv(w, OFF_W3 + e);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t sa_u = tc::smem_u32(sa), sw_u = tc::smem_u32(sw2t);
+    const uint32_t quad = warp & 3, slice = warp >> 2;
+    const uint32_t lanes = tmem + ((32u * quad) << 16);
+    const int row = 32 * quad + lane;
+    constexpr uint32_t ID128 = tc::idesc_bf16(MT, NH);
+    const int n_tiles = (n + MT - 1) / MT;
+    uint32_t pd = 0u;
+    bool ok = true;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int t0 = t * MT;
+        const bool real = t0 + row < n;
+        for (int e = tid; e < MT * 16; e += FWD_THREADS) {
+            const int at = e >> 4, o = e & 15;
+            const float v = (o < NO && t0 + at < n) ? gy[(size_t)(t0 + at) * NO + o] : 0.0f;
+            gys[e] = v;
+            gyt[((size_t)t * 16 + o) * MT + at] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            float x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int u = 32 * slice + 8 * g + q;
+                float acc = 0.0f;
+#pragma unroll
+                for (int o = 0; o < NO; ++o) acc = fmaf(gys[row * 16 + o], w3[o * NH + u], acc);
+                const float gz = real ? acc * dsilu(z2[(size_t)(t0 + row) * NH + u]) : 0.0f;
+                x[q] = gz;
+                gz2t[((size_t)t * NH + u) * MT + row] = gz;
+            }
+            split_store8(sa, tc::core_offset(row, 32 * slice + 8 * g, LBO_A), x);
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            layer_mma(tmem, sa_u, sw_u, LBO_W, NH, ID128);
+            tc::mma_commit(done);
+        }
+        const bool mg = tc::mbar_wait(done, pd);
+        pd ^= 1u;
+        if (!__syncthreads_and(mg)) { ok = false; break; }
+        tc::fence_after_sync();
+        float v[32];
+        tc::tmem_ld32(lanes + 32 * slice, v);
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int u = 32 * slice + q;
+            gz1t[((size_t)t * NH + u) * MT + row] = real ? v[q] * dsilu(z1[(size_t)(t0 + row) * NH + u]) : 0.0f;
+        }
+        tc::fence_before_sync();
+        __syncthreads();   // TMEM read and gy tile consumed before the next tile
+    }
+    if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NH);
+}
+
+// Weight gradients on the tensor cores: contractions over atoms, split over CTAs (each CTA sums its
+// tiles in TMEM and writes one partial gradient; the partials are added in a fixed order). Per chunk
+// of 32 atoms, with the feature-major tiles of the forward and backward kernels as K-major operands
+// (K = atoms), each split into BF16 hi and lo and multiplied as hi hi + hi lo + lo hi:
+//   D1[u][v] = sum_a gz2[a][u] [h1 | 1][a][v]   -> dW2[u][v] (v < 128) and db2[u] (column 128)
+//   D2[u][i] = sum_a gz1[a][u] [x | 1][a][i]    -> dW1[u][i] (i < 32) and db1[u] (column 32)
+//   D3[u][o] = sum_a h2[a][u] gy[a][o]           -> dW3[o][u]
+// and db3[o] = sum_a gy[a][o] on the CUDA cores. TMEM columns: D1 0..143, D2 160..207, D3 224..239.
+constexpr int WG_THREADS = 256;
+constexpr int WG_K = 32;                                      // atoms per chunk
+constexpr int WN1 = NH + 16, WN2 = NF + 16, WN3 = 16;         // B rows (the ones row, then zero rows)
+constexpr uint32_t WGA = NH * WG_K * 2;                       // one BF16 part of a 128-row A operand
+constexpr uint32_t WGB1 = WN1 * WG_K * 2, WGB2 = WN2 * WG_K * 2, WGB3 = WN3 * WG_K * 2;
+constexpr uint32_t WG_OP = 2 * (3 * WGA + WGB1 + WGB2 + WGB3);
+constexpr size_t WG_SMEM = WG_OP + 64;
+constexpr uint32_t D2COL = 160, D3COL = 224;
+
+// Rows [0, R_src) of a feature-major tile (rows of MT atoms) for atoms chunk*32 .. +31, the ones row
+// (if any) and zero rows up to R, split into BF16 hi / lo in the K-major core layout (K = atoms).
+__device__ __forceinline__ void wg_operand(uint8_t *hi, uint8_t *lo, const float *src, int R_src, int ones, int R,
+                                           int chunk) {
+    const uint32_t lbo = (uint32_t)(R / 8) * 128;
+    for (int c = threadIdx.x; c < R * (WG_K / 8); c += WG_THREADS) {
+        const int g = c / R, r = c - g * R;
+        float x[8];
+        if (r < R_src) {
+            const float *p = src + (size_t)r * MT + chunk * WG_K + 8 * g;
+            const float4 u0 = *reinterpret_cast<const float4 *>(p), u1 = *reinterpret_cast<const float4 *>(p + 4);
+            x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
+            x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
+        } else {
+            const float f = r == ones ? 1.0f : 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = f;
+        }
+        uint4 ph, pl;
+        ph.x = bf16x2_split(x[0], x[1]); ph.y = bf16x2_split(x[2], x[3]);
+        ph.z = bf16x2_split(x[4], x[5]); ph.w = bf16x2_split(x[6], x[7]);
+        pl.x = bf16x2_split(x[0], x[1]); pl.y = bf16x2_split(x[2], x[3]);
+        pl.z = bf16x2_split(x[4], x[5]); pl.w = bf16x2_split(x[6], x[7]);
+        const uint32_t off = tc::core_offset(r, 8 * g, lbo);
+        *reinterpret_cast<uint4 *>(hi + off) = ph;
+        *reinterpret_cast<uint4 *>(lo + off) = pl;
+    }
+}
+
+__global__ void __launch_bounds__(WG_THREADS, 1) k_weight_grad_tc(int n, const float *__restrict__ gz2t,
+                                                                const float *__restrict__ gz1t,
+                                                                const float *__restrict__ h1t,
+                                                                const float *__restrict__ h2t,
+                                                                const float *__restrict__ xt,
+                                                                const float *__restrict__ gyt,
+                                                                float *__restrict__ part, unsigned *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t *a1h = smem, *a1l = a1h + WGA, *a2h = a1l + WGA, *a2l = a2h + WGA, *a3h = a2l + WGA, *a3l = a3h + WGA;
+    uint8_t *b1h = a3l + WGA, *b1l = b1h + WGB1, *b2h = b1l + WGB1, *b2l = b2h + WGB2, *b3h = b2l + WGB2,
+            *b3l = b3h + WGB3;
+    uint64_t *done = reinterpret_cast<uint64_t *>(smem + WG_OP);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(slot, 256);
+    if (tid == 0) tc::mbar_init(done, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *slot;
+    constexpr uint32_t LA = (NH / 8) * 128, L1 = (WN1 / 8) * 128, L2 = (WN2 / 8) * 128, L3 = (WN3 / 8) * 128;
+    constexpr uint32_t I1 = tc::idesc_bf16(NH, WN1), I2 = tc::idesc_bf16(NH, WN2), I3 = tc::idesc_bf16(NH, WN3);
+    const int n_tiles = (n + MT - 1) / MT;
+    float db3 = 0.0f;   // thread o < 9: sum over this CTA's atoms of gy[.][o]
+    uint32_t pd = 0u;
+    bool ok = true, first = true, pending = false;
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+        if (tid < NO)
+            for (int at = 0; at < MT; ++at) db3 += gyt[((size_t)t * 16 + tid) * MT + at];
+        for (int ch = 0; ch < MT / WG_K; ++ch) {
+            if (pending) {   // the previous chunk's MMAs read the operands: wait before overwriting
+                const bool mg = tc::mbar_wait(done, pd);
+                pd ^= 1u;
+                pending = false;
+                if (!__syncthreads_and(mg)) { ok = false; break; }
+            }
+            wg_operand(a1h, a1l, gz2t + (size_t)t * NH * MT, NH, -1, NH, ch);
+            wg_operand(a2h, a2l, gz1t + (size_t)t * NH * MT, NH, -1, NH, ch);
+            wg_operand(a3h, a3l, h2t + (size_t)t * NH * MT, NH, -1, NH, ch);
+            wg_operand(b1h, b1l, h1t + (size_t)t * NH * MT, NH, NH, WN1, ch);
+            wg_operand(b2h, b2l, xt + (size_t)t * NF * MT, NF, NF, WN2, ch);
+            wg_operand(b3h, b3l, gyt + (size_t)t * 16 * MT, NO, -1, WN3, ch);
+            tc::fence_proxy_async();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t s0 = tc::smem_u32(smem);
+                const uint32_t A1h = s0, A1l = A1h + WGA, A2h = A1l + WGA, A2l = A2h + WGA, A3h = A2l + WGA,
+                               A3l = A3h + WGA, B1h = A3l + WGA, B1l = B1h + WGB1, B2h = B1l + WGB1,
+                               B2l = B2h + WGB2, B3h = B2l + WGB2, B3l = B3h + WGB3;
+                for (int k = 0; k < WG_K / 16; ++k) {
+                    const uint32_t acc = (first && k == 0) ? 0u : 1u;
+                    const uint32_t oa = k * 2 * LA;
+                    const uint64_t a1hd = tc::make_desc(A1h + oa, LA, 128), a1ld = tc::make_desc(A1l + oa, LA, 128);
+                    const uint64_t a2hd = tc::make_desc(A2h + oa, LA, 128), a2ld = tc::make_desc(A2l + oa, LA, 128);
+                    const uint64_t a3hd = tc::make_desc(A3h + oa, LA, 128), a3ld = tc::make_desc(A3l + oa, LA, 128);
+                    const uint64_t b1hd = tc::make_desc(B1h + k * 2 * L1, L1, 128), b1ld = tc::make_desc(B1l + k * 2 * L1, L1, 128);
+                    const uint64_t b2hd = tc::make_desc(B2h + k * 2 * L2, L2, 128), b2ld = tc::make_desc(B2l + k * 2 * L2, L2, 128);
+                    const uint64_t b3hd = tc::make_desc(B3h + k * 2 * L3, L3, 128), b3ld = tc::make_desc(B3l + k * 2 * L3, L3, 128);
+                    tc::mma_bf16(tmem, a1hd, b1hd, I1, acc);
+                    tc::mma_bf16(tmem, a1hd, b1ld, I1, 1u);
+                    tc::mma_bf16(tmem, a1ld, b1hd, I1, 1u);
+                    tc::mma_bf16(tmem + D2COL, a2hd, b2hd, I2, acc);
+                    tc::mma_bf16(tmem + D2COL, a2hd, b2ld, I2, 1u);
+                    tc::mma_bf16(tmem + D2COL, a2ld, b2hd, I2, 1u);
+                    tc::mma_bf16(tmem + D3COL, a3hd, b3hd, I3, acc);
+                    tc::mma_bf16(tmem + D3COL, a3hd, b3ld, I3, 1u);
+                    tc::mma_bf16(tmem + D3COL, a3ld, b3hd, I3, 1u);
+                }
+                tc::mma_commit(done);
+            }
+            pending = true;
+            first = false;
+        }
+    }
+    if (pending) {
+        const bool mg = tc::mbar_wait(done, pd);
+        if (!__syncthreads_and(mg)) ok = false;
+    }
+    ok = __syncthreads_and(ok) != 0;
+    if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    tc::fence_after_sync();
+    float *P = part + (size_t)blockIdx.x * NPAR;
+    if (warp < 4) {   // one weight row u per thread (TMEM lane u)
+        const int u = 32 * warp + lane;
+        const uint32_t lanes = tmem + ((32u * warp) << 16);
+        const bool have = ok && !first;
+        float v[32];
+        for (int c0 = 0; c0 < WN1; c0 += 32) {
+            tc::tmem_ld32(lanes + c0, v);
+            for (int q = 0; q < 32 && c0 + q <= NH; ++q) {
+                const float x = have ? v[q] : 0.0f;
+                if (c0 + q < NH) P[OFF_W2 + u * NH + c0 + q] = x;
+                else P[OFF_B2 + u] = x;
+            }
+        }
+        for (int c0 = 0; c0 < WN2; c0 += 32) {
+            tc::tmem_ld32(lanes + D2COL + c0, v);
+            for (int q = 0; q < 32 && c0 + q <= NF; ++q) {
+                const float x = have ? v[q] : 0.0f;
+                if (c0 + q < NF) P[OFF_W1 + u * NF + c0 + q] = x;
+                else P[OFF_B1 + u] = x;
+            }
+        }
+        tc::tmem_ld32(lanes + D3COL, v);
+        for (int o = 0; o < NO; ++o) P[OFF_W3 + o * NH + u] = have ? v[o] : 0.0f;
+    }
+    if (tid < NO) P[OFF_B3 + tid] = ok ? db3 : 0.0f;
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
@@ -465,92 +686,6 @@ __global__ void k_cell_tensors(int n_cells, const int *__restrict__ off, const f
     }
 }
 
-// backward over a tile: per-tile partial gradient of every parameter (fixed-order sums)
-__global__ void __launch_bounds__(NH) k_backward(int n, const float *__restrict__ X, const float *__restrict__ gy,
-                                                 const float *__restrict__ z1g, const float *__restrict__ z2g,
-                                                 const float *__restrict__ h1g, const float *__restrict__ h2g,
-                                                 const __nv_bfloat16 *__restrict__ w, float *__restrict__ part) {
-    __shared__ float xs[TILE][NF + 1];
-    __shared__ float bufA[TILE][NH + 1];   // h2, then gz1
-    __shared__ float gz2[TILE][NH + 1];
-    __shared__ float h1[TILE][NH + 1];
-    __shared__ float gys[TILE][NO];
-    const int t0 = blockIdx.x * TILE;
-    const int u = threadIdx.x;
-    float *P = part + (size_t)blockIdx.x * NPAR;
-    for (int e = u; e < TILE * NF; e += NH) {
-        const int a = e / NF, i = e - a * NF;
-        xs[a][i] = (t0 + a < n) ? X[(size_t)(t0 + a) * NF + i] : 0.0f;
-    }
-    for (int e = u; e < TILE * NO; e += NH) {
-        const int a = e / NO, o = e - a * NO;
-        gys[a][o] = (t0 + a < n) ? gy[(size_t)(t0 + a) * NO + o] : 0.0f;
-    }
-    for (int a = 0; a < TILE; ++a) {
-        const bool ok = t0 + a < n;
-        bufA[a][u] = ok ? h2g[(size_t)(t0 + a) * NH + u] : 0.0f;
-        h1[a][u] = ok ? h1g[(size_t)(t0 + a) * NH + u] : 0.0f;
-    }
-    __syncthreads();
-    // layer 3: dW3[o][u] = sum_a gy[a][o] h2[a][u], db3; gz2[a][u] = silu'(z2) sum_o gy[a][o] W3[o][u]
-    {
-        float w3[NO];
-        for (int o = 0; o < NO; ++o) w3[o] = wv(w, OFF_W3 + o * NH + u);
-        for (int o = 0; o < NO; ++o) {
-            float s = 0.0f;
-            for (int a = 0; a < TILE; ++a) s = fmaf(gys[a][o], bufA[a][u], s);
-            P[OFF_W3 + o * NH + u] = s;
-        }
-        if (u < NO) {
-            float s = 0.0f;
-            for (int a = 0; a < TILE; ++a) s += gys[a][u];
-            P[OFF_B3 + u] = s;
-        }
-        for (int a = 0; a < TILE; ++a) {
-            float s = 0.0f;
-            for (int o = 0; o < NO; ++o) s = fmaf(gys[a][o], w3[o], s);
-            gz2[a][u] = (t0 + a < n) ? s * dsilu(z2g[(size_t)(t0 + a) * NH + u]) : 0.0f;
-        }
-    }
-    __syncthreads();
-    // layer 2: dW2[u][v] = sum_a gz2[a][u] h1[a][v]; db2; gh1[a][v] = sum_u gz2[a][u] W2[u][v]
-    {
-        float b = 0.0f;
-        for (int a = 0; a < TILE; ++a) b += gz2[a][u];
-        P[OFF_B2 + u] = b;
-        for (int v = 0; v < NH; ++v) {
-            float s = 0.0f;
-#pragma unroll
-            for (int a = 0; a < TILE; ++a) s = fmaf(gz2[a][u], h1[a][v], s);
-            P[OFF_W2 + u * NH + v] = s;
-        }
-        // thread u now plays the role of input unit v = u
-        float acc[TILE];
-        for (int a = 0; a < TILE; ++a) acc[a] = 0.0f;
-        for (int uu = 0; uu < NH; ++uu) {
-            const float wuv = wv(w, OFF_W2 + uu * NH + u);
-#pragma unroll
-            for (int a = 0; a < TILE; ++a) acc[a] = fmaf(gz2[a][uu], wuv, acc[a]);
-        }
-        __syncthreads();   // bufA (h2) is no longer read
-        for (int a = 0; a < TILE; ++a)
-            bufA[a][u] = (t0 + a < n) ? acc[a] * dsilu(z1g[(size_t)(t0 + a) * NH + u]) : 0.0f;
-    }
-    __syncthreads();
-    // layer 1: dW1[u][i] = sum_a gz1[a][u] x[a][i]; db1
-    {
-        float b = 0.0f;
-        for (int a = 0; a < TILE; ++a) b += bufA[a][u];
-        P[OFF_B1 + u] = b;
-        for (int i = 0; i < NF; ++i) {
-            float s = 0.0f;
-#pragma unroll
-            for (int a = 0; a < TILE; ++a) s = fmaf(bufA[a][u], xs[a][i], s);
-            P[OFF_W1 + u * NF + i] = s;
-        }
-    }
-}
-
 __global__ void k_reduce_grad(int n_tiles, const float *__restrict__ part, float *__restrict__ g) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= NPAR) return;
@@ -626,6 +761,15 @@ cudaError_t prepare_mlp_forward() {
     return cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FWD_SMEM);
 }
 
+static cudaError_t prepare_mlp_training() {
+    cudaError_t e = prepare_mlp_forward();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_backward_act_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BWA_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_weight_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM);
+    return e;
+}
+
 cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, const void *w_bf16, float *Zl,
                                unsigned *status, cudaStream_t st) {
     if (n_atoms <= 0) return cudaSuccess;
@@ -635,7 +779,8 @@ cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, cons
     if (e != cudaSuccess) return e;
     const int tiles = (n_atoms + MT - 1) / MT;
     const int grid = std::min(tiles, n_sm);
-    k_forward_tc<<<grid, FWD_THREADS, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl, status);
+    k_forward_tc<<<grid, FWD_THREADS, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl, status,
+                                                    FwdStore{nullptr, nullptr, nullptr, nullptr, nullptr});
     return cudaGetLastError();
 }
 
@@ -660,7 +805,10 @@ struct cavmd_mlp {
     int *off = nullptr, *species = nullptr, *perm = nullptr;
     double *r = nullptr, *Q = nullptr, *Zref = nullptr, *Zout = nullptr, *lpart = nullptr, *loss = nullptr;
     float *X = nullptr, *R = nullptr, *Xp = nullptr, *Rp = nullptr, *Zl = nullptr, *gy = nullptr;
-    float *z1 = nullptr, *z2 = nullptr, *h1 = nullptr, *h2 = nullptr;
+    // training activations: z1, z2 atom-major; h1t, h2t, gz2t, gz1t, xt, gyt feature-major per tile
+    float *z1 = nullptr, *z2 = nullptr, *h1t = nullptr, *h2t = nullptr, *gz2t = nullptr, *gz1t = nullptr;
+    float *xt = nullptr, *gyt = nullptr;
+    int n_sm = 0;
     double *Qp = nullptr, *Zp = nullptr;
     unsigned *status = nullptr;
     int64_t adam_t = 0;
@@ -704,22 +852,41 @@ void mlp_free_data(cavmd_mlp *m, size_t keep) {
     m->allocs.resize(keep);
 }
 
-// forward + loss + gradient over atoms [0, n) of the (permuted) arrays
+// forward + loss + gradient over the cells [cell0, cell0 + ncells) of the (permuted) arrays, every
+// product on the tensor cores: forward (the time step's kernel, keeping its activations), cell
+// tensors and dL/dy, backward through the activations, weight gradients split over CTAs, and a
+// fixed-order FP64 sum of the CTA partials
 int mlp_loss_grad_range(cavmd_mlp *m, int cell0, int ncells, const float *X, const float *R, const double *Q,
                         const double *Zr, double inv_count) {
     const int a0 = 3 * cell0, na = 3 * ncells;
-    const int tiles = (na + TILE - 1) / TILE;
-    k_forward<<<tiles, NH, 0, m->stream>>>(na, X + (size_t)a0 * NF, R + (size_t)a0 * 9, m->w, m->Zl, m->z1, m->z2,
-                                           m->h1, m->h2);
+    const int tiles = (na + MT - 1) / MT;
+    const int grid = std::min(tiles, m->n_sm);
+    k_forward_tc<<<grid, FWD_THREADS, FWD_SMEM, m->stream>>>(na, X + (size_t)a0 * NF, R + (size_t)a0 * 9, m->w,
+                                                             m->Zl, m->status,
+                                                             FwdStore{m->z1, m->z2, m->h1t, m->h2t, m->xt});
     k_cell_tensors<<<(ncells + 127) / 128, 128, 0, m->stream>>>(ncells, m->off, m->Zl, R + (size_t)a0 * 9, Q + a0,
                                                                 Zr + (size_t)a0 * 9, inv_count, nullptr, m->gy,
                                                                 m->lpart, 0, 0, 0, nullptr);
-    k_backward<<<tiles, NH, 0, m->stream>>>(na, X + (size_t)a0 * NF, m->gy, m->z1, m->z2, m->h1, m->h2, m->w,
-                                            m->part);
-    k_reduce_grad<<<(NPAR + 255) / 256, 256, 0, m->stream>>>(tiles, m->part, m->g);
+    k_backward_act_tc<<<grid, FWD_THREADS, BWA_SMEM, m->stream>>>(na, m->gy, m->z1, m->z2, m->w, m->gz2t, m->gz1t,
+                                                                  m->gyt, m->status);
+    k_weight_grad_tc<<<grid, WG_THREADS, WG_SMEM, m->stream>>>(na, m->gz2t, m->gz1t, m->h1t, m->h2t, m->xt, m->gyt,
+                                                               m->part, m->status);
+    k_reduce_grad<<<(NPAR + 255) / 256, 256, 0, m->stream>>>(grid, m->part, m->g);
     k_reduce_loss<<<1, 256, 0, m->stream>>>(ncells, m->lpart, inv_count, m->loss);
     MCK(cudaGetLastError());
     return CAVMD_OK;
+}
+
+// Reads and clears the device status word of the network's kernels.
+int mlp_status(cavmd_mlp *m) {
+    unsigned st = 0;
+    MCK(cudaStreamSynchronize(m->stream));
+    MCK(cudaMemcpy(&st, m->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (!st) return CAVMD_OK;
+    MCK(cudaMemset(m->status, 0, sizeof(unsigned)));
+    if (st & ERRBIT_TIMEOUT)
+        return mlp_fail(m, CAVMD_ERR_DEVICE_TIMEOUT, "a tensor-core wait of the network kernels ran out");
+    return mlp_fail(m, CAVMD_ERR_NONFINITE, "an atom has fewer than two neighbours within the cutoff (no local frame)");
 }
 
 }  // namespace
@@ -747,8 +914,10 @@ int cavmd_mlp_create(cavmd_mlp **out, const float *params, int32_t n_params, int
     if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e)));
     e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, "cudaStreamCreate"));
-    e = prepare_mlp_forward();
-    if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, "cudaFuncSetAttribute (network forward)"));
+    e = prepare_mlp_training();
+    if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, "cudaFuncSetAttribute (network kernels)"));
+    e = cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return done(mlp_fail(nullptr, CAVMD_ERR_CUDA, "cudaDeviceGetAttribute"));
     if ((rc = mlp_alloc(m, &m->master, NPAR)) || (rc = mlp_alloc(m, &m->m1, NPAR)) ||
         (rc = mlp_alloc(m, &m->m2, NPAR)) || (rc = mlp_alloc(m, &m->g, NPAR)) || (rc = mlp_alloc(m, &m->w, NPAR)) ||
         (rc = mlp_alloc(m, &m->loss, 1)) || (rc = mlp_alloc(m, &m->status, 1)))
@@ -780,8 +949,11 @@ int cavmd_mlp_set_data(cavmd_mlp *m, int32_t n_cells, const int32_t *species, co
     MAL(m->r, 3 * na); MAL(m->Q, na); MAL(m->Zref, 9 * na); MAL(m->Zout, 9 * na); MAL(m->lpart, n_cells);
     MAL(m->X, (size_t)na * NF); MAL(m->R, 9 * na); MAL(m->Xp, (size_t)na * NF); MAL(m->Rp, 9 * na);
     MAL(m->Qp, na); MAL(m->Zp, 9 * na); MAL(m->Zl, 9 * na); MAL(m->gy, 9 * na);
-    MAL(m->z1, (size_t)na * NH); MAL(m->z2, (size_t)na * NH); MAL(m->h1, (size_t)na * NH); MAL(m->h2, (size_t)na * NH);
-    MAL(m->part, (size_t)((na + TILE - 1) / TILE) * NPAR);
+    const size_t tiles = (size_t)(na + MT - 1) / MT, npad = tiles * MT;
+    MAL(m->z1, npad * NH); MAL(m->z2, npad * NH);
+    MAL(m->h1t, npad * NH); MAL(m->h2t, npad * NH); MAL(m->gz2t, npad * NH); MAL(m->gz1t, npad * NH);
+    MAL(m->xt, npad * NF); MAL(m->gyt, npad * 16);
+    MAL(m->part, (size_t)m->n_sm * NPAR);
     MCK(cudaMemcpy(m->off, off.data(), sizeof(int) * (n_cells + 1), cudaMemcpyHostToDevice));
     MCK(cudaMemcpy(m->species, species, sizeof(int) * na, cudaMemcpyHostToDevice));
     MCK(cudaMemcpy(m->r, r, sizeof(double) * 3 * na, cudaMemcpyHostToDevice));
@@ -789,8 +961,7 @@ int cavmd_mlp_set_data(cavmd_mlp *m, int32_t n_cells, const int32_t *species, co
     if (Z_ref) MCK(cudaMemcpy(m->Zref, Z_ref, sizeof(double) * 9 * na, cudaMemcpyHostToDevice));
     else MCK(cudaMemset(m->Zref, 0, sizeof(double) * 9 * na));
     MCK(launch_mlp_features(n_cells, m->off, m->species, m->r, m->X, m->R, m->status, m->stream));
-    MCK(cudaStreamSynchronize(m->stream));
-    return CAVMD_OK;
+    return mlp_status(m);
 }
 
 int cavmd_mlp_loss_grad(cavmd_mlp *m, double *loss, float *grad) {
@@ -800,8 +971,7 @@ int cavmd_mlp_loss_grad(cavmd_mlp *m, double *loss, float *grad) {
     if (rc) return rc;
     MCK(cudaMemcpyAsync(loss, m->loss, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
     if (grad) MCK(cudaMemcpyAsync(grad, m->g, sizeof(float) * NPAR, cudaMemcpyDeviceToHost, m->stream));
-    MCK(cudaStreamSynchronize(m->stream));
-    return CAVMD_OK;
+    return mlp_status(m);
 }
 
 int cavmd_mlp_train(cavmd_mlp *m, int32_t epochs, int32_t batch_cells, float lr, float weight_decay,
@@ -836,8 +1006,7 @@ int cavmd_mlp_train(cavmd_mlp *m, int32_t epochs, int32_t batch_cells, float lr,
         }
         if (epoch_loss) epoch_loss[ep] = ep_loss / m->n_cells;
     }
-    MCK(cudaStreamSynchronize(m->stream));
-    return CAVMD_OK;
+    return mlp_status(m);
 }
 
 int cavmd_mlp_predict(cavmd_mlp *m, double *Z_out) {
@@ -848,8 +1017,7 @@ int cavmd_mlp_predict(cavmd_mlp *m, double *Z_out) {
                                                                     0.0, m->Zout, nullptr, nullptr, 0, 0, 0, nullptr);
     MCK(cudaGetLastError());
     MCK(cudaMemcpyAsync(Z_out, m->Zout, sizeof(double) * 9 * m->n_atoms, cudaMemcpyDeviceToHost, m->stream));
-    MCK(cudaStreamSynchronize(m->stream));
-    return CAVMD_OK;
+    return mlp_status(m);
 }
 
 int cavmd_mlp_get_params(cavmd_mlp *m, float *params) {

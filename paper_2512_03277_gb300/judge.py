@@ -47,6 +47,26 @@ def resonant_box(params, n_waters: int = 33, seed: int = 0, lam: float = 0.1, sp
     return sy, modes, wb
 
 
+def resonant_workload(params, name: str = "c4", coupling: float = 0.1 * np.sqrt(33.0)):
+    """(system, modes, w_bend): the cells of a grid workload (c4: 16,384 waters) with its in-plane mode
+    grid (c4: 32 x 32, 1024 modes), but the cavity length set so that the k = 0 mode sits at the
+    bend, and the amplitudes scaled so that lambda_0 sqrt(N) equals the resonant box's 0.1 sqrt(33)
+    (the same collective coupling); the other modes of the grid lie far above both bands."""
+    w = cs.make_workload(name, params=params)
+    g = w["modes"].grid
+    wb = params.meta["harmonic_freq_hartree"][0]
+    lam0 = coupling / np.sqrt(w["system"].n_cells)
+    L = cs.units.C_LIGHT * np.pi / wb
+    modes = cs.grid_modes(g["Kx"], g["Ky"], g["dkx"], g["dky"], L, lam0 / np.sqrt(2.0))
+    return w["system"], modes, wb
+
+
+def temperature_curve(T, points: int = 11):
+    """The temperature at `points` evenly spaced steps of a run (K)."""
+    idx = np.linspace(0, len(T) - 1, points).astype(int)
+    return [(int(i), float(T[i])) for i in idx]
+
+
 def run(P, params, system, modes, model: str, precision: int, steps: int, mlp=None,
         born_interval: int | None = None, lags: int | None = None, lattice=None):
     """One trajectory of `steps` steps. model: 'mulliken', 'born_fd' (forward differences, every

@@ -1,5 +1,6 @@
 """The Born-charge network on the GPU against the FP64 oracle of the same network, and what the
-trained network gains over the Mulliken model it starts from.
+trained network gains over the Mulliken model it starts from. Forward, backward and weight
+gradients run on the tcgen05 tensor cores (BF16 operands, FP32 accumulation).
 
 Tolerances: the GPU evaluates the network in FP32 with the same bfloat16 weights the oracle uses
 in FP64; a 128-term FP32 dot product with O(1) terms carries up to about 1e-5 absolute error, so
@@ -64,10 +65,24 @@ def test_network_forward_and_gradient_match_oracle(P):
     np.testing.assert_array_equal(net.cavmd_mlp_get_params(), NN.bf16_round(p).astype(np.float32))
 
 
+def _trajectory_labelled(worker, cells, samples):
+    """Geometries of one oracle 300 K trajectory (the recipe of oracle/born_dataset.py) and their
+    oracle central-FD Born tensors and Mulliken charges."""
+    from oracle import born_dataset as BD
+    params = cs.load_water_params()
+    pos = BD.trajectory_samples(worker, cells, equil=200, stride=10, samples=samples)
+    Z, Q = NN.born_fd_tensors(params, WATER, pos)
+    return pos, Z.reshape(-1, 3, 3), Q.ravel()
+
+
 def test_trained_network_beats_mulliken_and_drives_the_dynamics(P):
+    """Trained on the tensor cores on geometries of two 300 K oracle trajectories, tested on a third."""
     from paper_2512_03277_gb300.cavmd import BornMLP
-    pos_tr, Z_tr, Q_tr = _labelled(1536, seed=21)
-    pos_te, Z_te, Q_te = _labelled(512, seed=22)
+    parts = [_trajectory_labelled(w, 120, 12) for w in (0, 1)]
+    pos_tr = np.concatenate([p[0] for p in parts])
+    Z_tr = np.concatenate([p[1] for p in parts])
+    Q_tr = np.concatenate([p[2] for p in parts])
+    pos_te, Z_te, Q_te = _trajectory_labelled(2, 120, 5)
     net = BornMLP(NN.init_params(np.random.default_rng(4)).astype(np.float32))
     net.cavmd_mlp_set_data(np.tile(WATER, len(pos_tr)), pos_tr.reshape(-1, 3), Q_tr, Z_tr)
     losses = net.cavmd_mlp_train(epochs=120, batch_cells=64, lr=2e-3, weight_decay=0.0, seed=5)
@@ -94,3 +109,25 @@ def test_trained_network_beats_mulliken_and_drives_the_dynamics(P):
     ctx.cavmd_step(20)
     obs = ctx.cavmd_observables()
     assert np.isfinite(obs["e_total"])
+
+
+def test_shipped_network_on_fresh_trajectory_geometries(P):
+    """The network shipped with the library (paper_2512_03277_gb300/data/born_mlp_water.f32, trained by
+    train_born_mlp.py on the oracle's 300 K trajectory data) against the oracle's finite-difference
+    Born tensors of geometries from a trajectory it never saw: its error is well below the Mulliken
+    model's, and inside a time step it gives the oracle network's b."""
+    from paper_2512_03277_gb300 import cavmd as B
+    params = B.trained_born_mlp()
+    if params is None:
+        pytest.skip("no trained network shipped")
+    pos, Z, Q = _trajectory_labelled(101, 150, 4)
+    net = B.BornMLP(params)
+    net.cavmd_mlp_set_data(np.tile(WATER, len(pos)), pos.reshape(-1, 3), Q, None)
+    Zp = net.cavmd_mlp_predict()
+    err_net = np.sqrt(np.mean((Zp - Z) ** 2))
+    err_mul = np.sqrt(np.mean((Q[:, None, None] * np.eye(3) - Z) ** 2))
+    print(f"\nshipped network: held-out RMS {err_net:.4f} e, Mulliken {err_mul:.4f} e")
+    assert err_net < 0.35 * err_mul, (err_net, err_mul)
+    X, R = NN.features_and_frames(np.tile(WATER, len(pos)), pos.reshape(-1, 3), 3 * np.arange(len(pos) + 1))
+    Zo = NN.born_tensors(NN.forward(NN.bf16_round(params.astype(float)), X)[0], R, Q, 3 * np.arange(len(pos) + 1))
+    np.testing.assert_allclose(Zp, Zo, rtol=0, atol=2e-5)
