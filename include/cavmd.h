@@ -79,7 +79,10 @@ enum { CAVMD_CHARGE_MULLIKEN = 0, CAVMD_CHARGE_BORN_FD = 1, CAVMD_CHARGE_BORN_CE
  * momenta with the instantaneous force (p_a += dt/2 omega_a D_a), drift, evaluate, half-kick again,
  * then turn every mode freely by omega_a dt (Eq. qknk). With cells on a line lattice, modes on its
  * DFT grid and a flat dispersion, PAPER reproduces the paper's real-space / reciprocal-space
- * Steps 1-4 exactly. STRANG is not built (CAVMD_ERR_UNSUPPORTED). */
+ * Steps 1-4 exactly. STRANG: kick(dt/2) with the instantaneous force, then the free flow of the
+ * nuclei (drift) and of every mode (turn by omega_a dt) over dt, evaluate, kick(dt/2): the
+ * textbook split of H into the free part and V - sum_a omega_a q_a D_a + 1/2 sum_a D_a^2. Like
+ * PAPER it needs omega_a dt below about 1 for stability. */
 enum { CAVMD_SPLIT_PHOTON_EXACT = 0, CAVMD_SPLIT_STRANG = 1, CAVMD_SPLIT_PAPER = 2 };
 enum { CAVMD_PHOTON_RELAXED = 0, CAVMD_PHOTON_ZERO = 1 };
 /* Where the mode functions u_a are evaluated. FIXED: at the cells' reference positions R_n (the

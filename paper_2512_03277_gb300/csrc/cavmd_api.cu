@@ -615,9 +615,8 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad charge_model");
     if (o->charge_model != CAVMD_CHARGE_MULLIKEN && (o->born_interval < 1 || !(o->fd_step > 0.0)))
         return fail(c, CAVMD_ERR_INVALID_ARG, "Born charges need born_interval >= 1 and fd_step > 0");
-    if (o->splitting == CAVMD_SPLIT_STRANG)
-        return fail(c, CAVMD_ERR_UNSUPPORTED, "CAVMD_SPLIT_STRANG is not built; use PHOTON_EXACT or PAPER");
-    if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT && o->splitting != CAVMD_SPLIT_PAPER)
+    if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT && o->splitting != CAVMD_SPLIT_PAPER &&
+        o->splitting != CAVMD_SPLIT_STRANG)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad splitting");
     if (o->photon_init != CAVMD_PHOTON_RELAXED && o->photon_init != CAVMD_PHOTON_ZERO)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
@@ -928,7 +927,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     s.Us = c->d_Us; s.kvec = c->d_k; s.Wk2 = c->d_Wk2; s.Wk1 = c->d_Wk1; s.w_atom = c->d_watom;
     s.G1store = c->d_G1; s.G1in = c->d_G1;   // all NULL with fixed mode positions
-    s.paper = c->opt.splitting == CAVMD_SPLIT_PAPER;
+    s.paper = c->opt.splitting == CAVMD_SPLIT_PAPER || c->opt.splitting == CAVMD_SPLIT_STRANG;
+    s.strang = c->opt.splitting == CAVMD_SPLIT_STRANG;
     d.E_open = nullptr;   // set for the first evaluation of a call (water kernel)
     d.p_open = c->d_p; d.r_open = c->d_r; d.inv_mass = c->d_imass; d.tau = tau; d.dt = c->opt.dt;
     d.step_counter = c->d_step;

@@ -117,7 +117,8 @@ struct StepArgs {
     const double *w_atom;      // [n_atoms] m_j / m_n
     double *G1store;           // [N][3] G_n of the next first half-flow, kept for the next call
     const double *G1in;        // [N][3] G_n of the opening first half-flow (FLD_E_GIVEN)
-    int paper;                 // 1: the paper's step order (CAVMD_SPLIT_PAPER), 0: exact half-flows
+    int paper;                 // 1: kicks with the instantaneous force (CAVMD_SPLIT_PAPER or STRANG), 0: exact half-flows
+    int strang;                // 1: the modes turn between the two kicks (CAVMD_SPLIT_STRANG)
 };
 
 // Plan of the tensor-core coupling contraction for modes on a uniform in-plane grid.

@@ -87,6 +87,9 @@ __device__ __forceinline__ double mode_weight(double q, double p, double cen, do
 // field weights W_a = h lambda_a (omega_a q_a - D_a), h = dt/2; after the second half-kick each
 // mode turns freely by omega_a dt. The synchronised state is the rotated one. The same weights
 // feed the field, tensor-core and position-term kernels as the exact half-flows' do.
+// CAVMD_SPLIT_STRANG (a.strang) takes the same kicks but turns the modes between them, together
+// with the nuclear drift: kick(h), free flow of the nuclei and the modes over dt, kick(h), so the
+// second kick sees the turned coordinates and the synchronised state is the kicked one.
 __device__ __forceinline__ double paper_weight(double q, double D, double w, double lam, double h) {
     return __dmul_rn(h * lam, fma(w, q, -D));
 }
@@ -99,6 +102,12 @@ __device__ __forceinline__ void put_weights(const StepArgs &a, int al, double W,
 __device__ __forceinline__ void photon_paper_order(const StepArgs &a, int flags, int al, double D, double D_sync,
                                                    double w, double iw, double lam, double c, double s, double cen) {
     const double h = a.tau, hw = h * w;
+    const double cdt = fma(c, c, -s * s), sdt = 2.0 * s * c;   // cos, sin of omega dt
+    auto turn = [&](double &q, double &p) {                    // free rotation by omega dt
+        const double qn = fma(q, cdt, p * sdt * iw);
+        p = fma(p, cdt, -w * q * sdt);
+        q = qn;
+    };
     double qs, ps;
     if (flags & PH_INIT_RELAXED) {
         qs = cen;
@@ -111,15 +120,16 @@ __device__ __forceinline__ void photon_paper_order(const StepArgs &a, int flags,
         if (flags & PH_OPEN) {   // the opening first half-kick, from the synchronised state
             q = a.q_sync[al];
             p = fma(hw, D_sync, a.pq_sync[al]);
+            if (a.strang) turn(q, p);
         } else {
             q = a.q[al];
             p = a.pq[al];
         }
         put_weights(a, al, paper_weight(q, D, w, lam, h), a.W2, a.Wt2, a.Wk2);
         p = fma(hw, D, p);
-        const double cdt = fma(c, c, -s * s), sdt = 2.0 * s * c;   // cos, sin of omega dt
-        qs = fma(q, cdt, p * sdt * iw);
-        ps = fma(p, cdt, -w * q * sdt);
+        if (!a.strang) turn(q, p);
+        qs = q;
+        ps = p;
     } else {
         qs = a.q_sync[al];
         ps = a.pq_sync[al];
@@ -135,8 +145,13 @@ __device__ __forceinline__ void photon_paper_order(const StepArgs &a, int flags,
         e[3] = 0.5 * fma(ps, ps, (w * qs) * (w * qs));
     }
     if (flags & (PH_FIRST | PH_W1)) put_weights(a, al, paper_weight(qs, D, w, lam, h), a.W1, a.Wt1, a.Wk1);
-    a.q[al] = qs;
-    a.pq[al] = (flags & PH_FIRST) ? fma(hw, D, ps) : ps;
+    double q1 = qs, p1 = ps;
+    if (flags & PH_FIRST) {
+        p1 = fma(hw, D, ps);
+        if (a.strang) turn(q1, p1);
+    }
+    a.q[al] = q1;
+    a.pq[al] = p1;
 }
 
 __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {

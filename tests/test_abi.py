@@ -145,8 +145,8 @@ def test_rejects_bad_options(lib, small):
     o.precision = 2      # moving mode positions need the FP64 coupling
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -8
     o = P.default_options()
-    o.splitting = 1      # Strang: not built
-    assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -8
+    o.jacobi_max_sweeps = 1001
+    assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
     o = P.default_options()
     o.splitting = 3
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
