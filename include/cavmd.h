@@ -83,7 +83,19 @@ enum { CAVMD_CHARGE_MULLIKEN = 0, CAVMD_CHARGE_BORN_FD = 1, CAVMD_CHARGE_BORN_CE
  * nuclei (drift) and of every mode (turn by omega_a dt) over dt, evaluate, kick(dt/2): the
  * textbook split of H into the free part and V - sum_a omega_a q_a D_a + 1/2 sum_a D_a^2. Like
  * PAPER it needs omega_a dt below about 1 for stability. */
-enum { CAVMD_SPLIT_PHOTON_EXACT = 0, CAVMD_SPLIT_STRANG = 1, CAVMD_SPLIT_PAPER = 2 };
+/* REAL_SPACE: the paper's real-space / reciprocal-space scheme as printed (Eq. hlm3; Step 1,
+ * Eq. pj1; Steps 2-4, Eqs. qkink_ak, qknk, qkink_an). Each cell n carries a real-space photon
+ * coordinate q_n and momentum p_n; the coupling takes sqrt(omega_k) ~ sqrt(omega_0) and is local,
+ * eta q_n M_n + eta^2 M_n^2 / (2 omega_0^2) with eta = sqrt(2N) g0 omega_0 (options.real_space_g0,
+ * real_space_omega0); Step 1 kicks p_n by -eta M_n and the nuclei by -(eta q_n + eta^2 M_n /
+ * omega_0^2) dM_n/dr_j around the drift, then the omega_0-normalised amplitudes sqrt(omega_0/2) q_n
+ * + i p_n / sqrt(2 omega_0) go to the modes, turn by omega_a dt each (any dispersion), and come
+ * back. It is the paper's scheme when the cells sit on a lattice and the modes are the real modes
+ * of its wave-vector grid (cos and sin of each +-k pair with lambda = 2 g0, single modes sqrt(2) g0);
+ * it needs as many modes as cells, the FP64 coupling and fixed mode positions. In cavmd_obs and
+ * cavmd_state the arrays q and p (pq) then hold q_n and p_n of the cells (D is zero), and the
+ * energy record's free-photon term is the k-space sum_a omega_a |a_a|^2. */
+enum { CAVMD_SPLIT_PHOTON_EXACT = 0, CAVMD_SPLIT_STRANG = 1, CAVMD_SPLIT_PAPER = 2, CAVMD_SPLIT_REAL_SPACE = 3 };
 enum { CAVMD_PHOTON_RELAXED = 0, CAVMD_PHOTON_ZERO = 1 };
 /* Where the mode functions u_a are evaluated. FIXED: at the cells' reference positions R_n (the
  * paper's boxes sit at fixed positions, Eq. hlm2). CENTRE_OF_MASS: at every cell's instantaneous
@@ -188,6 +200,8 @@ typedef struct {
                                    cells), else 1..1000. A cell whose off-diagonal elements are
                                    still above tolerance at the bound makes the call report
                                    CAVMD_ERR_DEVICE_TIMEOUT. Later SCC iterations take one sweep. */
+    double real_space_g0;       /* CAVMD_SPLIT_REAL_SPACE: the coupling constant g0 (> 0)         */
+    double real_space_omega0;   /* CAVMD_SPLIT_REAL_SPACE: the reference frequency omega_0 (> 0)  */
 } cavmd_options;
 
 /* Observables at the current (synchronised) time. Optional arrays may be NULL. */

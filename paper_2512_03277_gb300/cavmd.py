@@ -22,7 +22,7 @@ ERR = {-1: "INVALID_ARG", -2: "CUDA", -3: "SCC_NOCONV", -4: "NONFINITE", -5: "S_
        -6: "ZERO_GAP", -7: "DEVICE_TIMEOUT", -8: "UNSUPPORTED", -9: "NOMEM"}
 PREC_FP64, PREC_MIXED_TF32, PREC_MIXED_BF16X3 = 0, 1, 2
 CHARGE_MULLIKEN, CHARGE_BORN_FD, CHARGE_BORN_CENTRAL, CHARGE_BORN_MLP = 0, 1, 2, 3
-SPLIT_PHOTON_EXACT, SPLIT_STRANG, SPLIT_PAPER = 0, 1, 2
+SPLIT_PHOTON_EXACT, SPLIT_STRANG, SPLIT_PAPER, SPLIT_REAL_SPACE = 0, 1, 2, 3
 PHOTON_RELAXED, PHOTON_ZERO = 0, 1
 
 _dp = C.POINTER(C.c_double)
@@ -57,7 +57,8 @@ class cavmd_options(C.Structure):
                 ("stream", C.c_void_p), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
                 ("alloc_user", C.c_void_p), ("energy_history", C.c_int32), ("acf_lags", C.c_int32),
                 ("autotune", C.c_int32), ("scc_history", C.c_int32),
-                ("mode_positions", C.c_int32), ("jacobi_max_sweeps", C.c_int32)]
+                ("mode_positions", C.c_int32), ("jacobi_max_sweeps", C.c_int32),
+                ("real_space_g0", C.c_double), ("real_space_omega0", C.c_double)]
 
 
 class cavmd_obs(C.Structure):

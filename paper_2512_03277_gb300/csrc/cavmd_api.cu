@@ -50,6 +50,8 @@ struct cavmd_ctx {
     bool generic = false;                    // cells other than 3-atom, 6-orbital ones: persistent kernel
     bool moving = false;                     // mode functions at the cells' centres of mass
     bool periodic = false;                   // periodic cells (Gamma point): their own kernel
+    bool rs = false;                         // the paper's real-space photon scheme
+    RsArgs rsa{};
     PbcPlan pplan{};
     double *d_Us = nullptr, *d_Wk2 = nullptr, *d_Wk1 = nullptr, *d_watom = nullptr;
     double *d_G1 = nullptr, *d_Ginst = nullptr;
@@ -288,6 +290,11 @@ cudaError_t run_modes(cavmd_ctx *c) {
                                      c->d_U, c->d_Us, c->stream);
 }
 
+cudaError_t run_rs(cavmd_ctx *c, int what, int flags) {
+    PhaseScope ps(c, 1);
+    return launch_rs(c->rsa, c->sa, what, flags, c->stream);
+}
+
 cudaError_t run_field(cavmd_ctx *c, int flags) {
     PhaseScope ps(c, 2);
     return launch_field(c->sa, flags, c->stream);
@@ -322,8 +329,11 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
     // SCC-DFTB kernel kicks and drifts the atoms of its cells before reading their positions, and
     // the photon kernel rotates the modes before their second half-flow. The cluster kernel takes
     // two launches of their own.
-    const bool fold = !c->generic && !c->moving && !c->periodic;
-    if (!fold) {
+    const bool fold = !c->generic && !c->moving && !c->periodic && !c->rs;
+    if (c->rs) {
+        if ((e = run_rs(c, RS_OPEN, 0)) != cudaSuccess) return e;
+        if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
+    } else if (!fold) {
         if ((e = run_photon(c, PH_FIRST)) != cudaSuccess) return e;
         if ((e = run_field(c, FLD_FIRST | FLD_E_GIVEN)) != cudaSuccess) return e;
     }
@@ -337,7 +347,13 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
         if (c->moving && (e = run_modes(c)) != cudaSuccess) return e;   // positions of this step
         if (born_refresh(c, first_step + s) && (e = run_born(c)) != cudaSuccess) return e;
         if (c->d_mlpw && (e = run_mlp(c)) != cudaSuccess) return e;
-        if (c->mixed) {
+        if (c->rs) {   // Step 1's second half-kick, Steps 2-4, the next first half-kick
+            if ((e = run_rs(c, RS_SECOND, 0)) != cudaSuccess) return e;
+            if ((e = run_rs(c, RS_FORWARD, 1)) != cudaSuccess) return e;
+            if ((e = run_rs(c, RS_BACK, 1 | (last ? 0 : 2))) != cudaSuccess) return e;
+            if ((e = run_field(c, FLD_SECOND | FLD_ENERGY | FLD_E_GIVEN | (last ? 0 : FLD_FIRST))) != cudaSuccess)
+                return e;
+        } else if (c->mixed) {
             if ((e = run_tc_forward(c)) != cudaSuccess) return e;
             if ((e = run_photon(c, open | PH_FORWARD_G | PH_SECOND | PH_ENERGY | (last ? PH_W1 : PH_FIRST))) !=
                 cudaSuccess)
@@ -456,6 +472,14 @@ int initial_evaluation(cavmd_ctx *c, bool init_photons) {
     if (c->moving) CK(run_modes(c));
     if (c->n_disp > 0) CK(run_born(c));
     if (c->d_mlpw) CK(run_mlp(c));
+    if (c->rs) {   // the synchronised photons, their energies and the next first half-kick's field
+        const int mode = !init_photons ? 0 : (c->opt.photon_init == CAVMD_PHOTON_ZERO ? 2 : 1);
+        CK(run_rs(c, RS_INIT, mode));
+        CK(run_rs(c, RS_FORWARD, 0));
+        CK(run_rs(c, RS_BACK, 0));
+        CK(run_field(c, FLD_ENERGY | FLD_E_GIVEN));
+        return sync_status(c);
+    }
     int fwd = PH_FORWARD;
     if (c->mixed) {
         CK(run_tc_forward(c));
@@ -616,8 +640,17 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
     if (o->charge_model != CAVMD_CHARGE_MULLIKEN && (o->born_interval < 1 || !(o->fd_step > 0.0)))
         return fail(c, CAVMD_ERR_INVALID_ARG, "Born charges need born_interval >= 1 and fd_step > 0");
     if (o->splitting != CAVMD_SPLIT_PHOTON_EXACT && o->splitting != CAVMD_SPLIT_PAPER &&
-        o->splitting != CAVMD_SPLIT_STRANG)
+        o->splitting != CAVMD_SPLIT_STRANG && o->splitting != CAVMD_SPLIT_REAL_SPACE)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad splitting");
+    if (o->splitting == CAVMD_SPLIT_REAL_SPACE) {
+        if (!(o->real_space_g0 > 0.0) || !(o->real_space_omega0 > 0.0) || !std::isfinite(o->real_space_g0) ||
+            !std::isfinite(o->real_space_omega0))
+            return fail(c, CAVMD_ERR_INVALID_ARG, "CAVMD_SPLIT_REAL_SPACE needs real_space_g0 > 0 and real_space_omega0 > 0");
+        if (md->n_modes != sys->n_cells)
+            return fail(c, CAVMD_ERR_INVALID_ARG, "CAVMD_SPLIT_REAL_SPACE needs as many modes as cells");
+        if (o->precision != CAVMD_PREC_FP64 || o->mode_positions != CAVMD_MODES_FIXED)
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "CAVMD_SPLIT_REAL_SPACE takes the FP64 coupling and fixed mode positions");
+    }
     if (o->photon_init != CAVMD_PHOTON_RELAXED && o->photon_init != CAVMD_PHOTON_ZERO)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad photon_init");
     if (o->graph_chunk < 0 || o->energy_history < 1) return fail(c, CAVMD_ERR_INVALID_ARG, "bad graph_chunk or energy_history");
@@ -825,6 +858,38 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         CK(launch_tc_panels(p, c->d_R, st));
     }
 
+    c->rs = c->opt.splitting == CAVMD_SPLIT_REAL_SPACE;
+    if (c->rs) {
+        RsArgs &r = c->rsa;
+        const double g0 = c->opt.real_space_g0, w0 = c->opt.real_space_omega0;
+        r.eta = std::sqrt(2.0 * N) * g0 * w0;
+        r.eta2_w0sq = r.eta * r.eta / (w0 * w0);
+        r.inv_w0sq = 1.0 / (w0 * w0);
+        r.sq = std::sqrt(0.5 * w0);
+        r.isq = 1.0 / std::sqrt(2.0 * w0);
+        r.inv_sq = 1.0 / r.sq;
+        r.inv_isq = 1.0 / r.isq;
+        std::vector<double> wa(M), cd(M), sd(M);
+        for (int a = 0; a < M; ++a) {
+            wa[a] = md->lambda[a] * md->lambda[a] / (2.0 * N * g0 * g0);
+            cd[a] = std::cos(md->omega[a] * c->opt.dt);
+            sd[a] = std::sin(md->omega[a] * c->opt.dt);
+        }
+        double *w_ = nullptr, *c_ = nullptr, *s_ = nullptr;
+        AL(w_, M); AL(c_, M); AL(s_, M);
+        AL(r.x, N); AL(r.y, N); AL(r.Xw, M); AL(r.Yw, M); AL(r.E2, N);
+        r.E1 = c->d_E1;
+        r.w = w_;
+        r.cdt = c_;
+        r.sdt = s_;
+        CK(cudaMemcpyAsync(w_, wa.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c_, cd.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(s_, sd.data(), sizeof(double) * M, cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(c->d_D, 0, sizeof(double) * M, st));
+        CK(cudaMemsetAsync(c->d_emode, 0, sizeof(double) * 4 * M, st));
+        CK(cudaStreamSynchronize(st));   // the host vectors must outlive the copies
+    }
+
     if (c->opt.acf_lags > 0) {
         AcfArgs &a = c->acf;
         a.M = M;
@@ -923,7 +988,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.W1 = c->d_W1; s.W2 = c->d_W2; s.e_mode = c->d_emode; s.e_kin_part = c->d_ekp; s.e_dftb_part = c->d_edp;
     s.done_counter = c->d_done; s.hist = c->d_hist; s.hist_cap = c->opt.energy_history;
     s.step_counter = c->d_step; s.status = c->d_status; s.dt = c->opt.dt; s.tau = tau;
-    s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->d_E2; s.E1in = c->d_E1; s.E1store = c->d_E1;
+    s.G = c->d_G; s.Wt2 = c->d_Wt2; s.Wt1 = c->d_Wt1; s.E2in = c->rs ? c->rsa.E2 : c->d_E2; s.E1in = c->d_E1;
+    s.E1store = c->d_E1;
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     s.Us = c->d_Us; s.kvec = c->d_k; s.Wk2 = c->d_Wk2; s.Wk1 = c->d_Wk1; s.w_atom = c->d_watom;
     s.G1store = c->d_G1; s.G1in = c->d_G1;   // all NULL with fixed mode positions
@@ -1195,6 +1261,18 @@ int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
         CK(cudaMemcpy(w.data(), c->d_omega, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(lam.data(), c->d_lam, sizeof(double) * c->M, cudaMemcpyDeviceToHost));
         for (int a = 0; a < c->M; ++a) W[a] = lam[a] * (w[a] * q[a] - D[a]);
+        if (c->rs) {   // the local field -(eta q_n + eta^2 M_n / omega_0^2) of the real-space scheme
+            std::vector<double> Mn(N), F(3 * NA), b(3 * NA);
+            CK(cudaMemcpy(Mn.data(), c->d_Mc, sizeof(double) * N, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(F.data(), c->d_F, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(b.data(), c->d_b, sizeof(double) * 3 * NA, cudaMemcpyDeviceToHost));
+            for (size_t n = 0; n < N; ++n) {
+                const double En = -(c->rsa.eta * q[n] + c->rsa.eta2_w0sq * Mn[n]);
+                for (int i = c->h_off[n]; i < c->h_off[n + 1]; ++i)
+                    for (int k = 0; k < 3; ++k) o->F_total[3 * i + k] = F[3 * i + k] + En * b[3 * i + k];
+            }
+            return rc;
+        }
         if (c->mixed) {   // same arrangement of the weights as the photon kernel writes
             const TcPlan &p = c->tc;
             std::vector<float> Wt((size_t)128 * p.KY, 0.0f);

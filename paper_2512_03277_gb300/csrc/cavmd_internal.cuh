@@ -121,6 +121,20 @@ struct StepArgs {
     int strang;                // 1: the modes turn between the two kicks (CAVMD_SPLIT_STRANG)
 };
 
+// The paper's real-space photon scheme (CAVMD_SPLIT_REAL_SPACE, realspace.cu).
+struct RsArgs {
+    double eta, eta2_w0sq, inv_w0sq;   // eta = sqrt(2N) g0 omega_0; eta^2 / omega_0^2; 1 / omega_0^2
+    double sq, isq, inv_sq, inv_isq;   // sqrt(omega_0 / 2), 1 / sqrt(2 omega_0) and their inverses
+    const double *w, *cdt, *sdt;       // [M] lambda_a^2 / (2 N g0^2), cos and sin of omega_a dt
+    double *x, *y;                     // [N] amplitude parts of the cells
+    double *Xw, *Yw;                   // [M] weighted, turned mode amplitudes
+    double *E1, *E2;                   // [N] fields of the first and second half-kicks (times dt/2)
+};
+// RS_INIT flags: 0 keep the synchronised photons, 1 relaxed (q_n = -eta M_n / omega_0^2), 2 zero;
+// RS_FORWARD flags: 1 = turn by omega_a dt; RS_BACK flags: bit 0 = map back, bit 1 = first half-kick
+enum { RS_INIT = 0, RS_OPEN = 1, RS_SECOND = 2, RS_FORWARD = 3, RS_BACK = 4 };
+cudaError_t launch_rs(const RsArgs &r, const StepArgs &a, int what, int flags, cudaStream_t st);
+
 // Plan of the tensor-core coupling contraction for modes on a uniform in-plane grid.
 struct TcPlan {
     int N, Npad, Kx, Ky2, KY, n_fwd_cta, n_sm;

@@ -170,3 +170,89 @@ def test_strang_graph_replay_is_bitwise_direct(P):
     sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
     for k in ("r", "p", "q", "pq"):
         assert np.array_equal(sa[k], sb[k]), k
+
+
+def _lattice_case(N=8, a=12.0, w0=0.012, g0=0.002, disp=False):
+    """N waters on a line lattice (spacing a) and the real modes of its wave-vector grid; with
+    `disp` the dispersion omega_k = omega_0 sqrt(1 + 3 (k / k_max)^2) rises to twice omega_0."""
+    params = cs.load_water_params()
+    cent = np.stack([np.arange(N) * a, np.zeros(N), np.zeros(N)], 1)
+    pos = cs.water_batch(np.random.default_rng(2), cent)
+    sy = cs.systems._water_system(pos, cent)
+    sy.p = cs.mb_momenta(np.random.default_rng(3), sy, 300.0)
+    kmax = np.pi / a
+
+    def om(k):
+        return w0 * np.sqrt(1.0 + 3.0 * (k / kmax) ** 2) if disp else w0 + 0.0 * k
+
+    ks, ph, lam = [], [], []
+    for j in range(N // 2 + 1):
+        for s in ((0,) if j in (0, N // 2) else (0, 1)):
+            ks.append(2 * np.pi * j / (N * a))
+            ph.append(0.0 if s == 0 else -np.pi / 2)
+            lam.append(np.sqrt(2) * g0 if j in (0, N // 2) else 2 * g0)
+    K = np.zeros((N, 3))
+    K[:, 0] = ks
+    modes = cs.Modes(k=K, omega=om(np.array(ks)), lam=np.array(lam), phi=np.array(ph))
+    kc = 2 * np.pi * np.arange(N) / (N * a)
+    kc_fold = np.minimum(kc, 2 * np.pi / a - kc)           # k_j and k_{N-j} share omega
+    return params, cent, sy, modes, kc, om(kc_fold)
+
+
+@pytest.mark.parametrize("disp", [False, True])
+def test_real_space_scheme_matches_the_papers_steps(P, disp):
+    """splitting = CAVMD_SPLIT_REAL_SPACE, the paper's scheme as printed (Eq. hlm3 with Steps 1-4):
+    real-space photon coordinates per cell, the local coupling, the transforms and the rotation of
+    every mode with its own frequency, against oracle/paper_scheme.py; with a flat dispersion and
+    with one that rises to twice omega_0 (where the scheme is the paper's approximation, not the
+    exact k-space dynamics)."""
+    N, a, w0, g0 = 8, 12.0, 0.012, 0.002
+    params, cent, sy, modes, kc, wk = _lattice_case(N, a, w0, g0, disp)
+    dt = 0.5 * 41.341373335
+    w = {"system": sy, "modes": modes, "params": params}
+    ctx = _ctx(P, w, dt=dt, graph_chunk=0, splitting=3, real_space_g0=g0, real_space_omega0=w0)
+    ps = PS.PaperRealSpaceMD(OC.DFTBMatter(params, sy), sy.r, sy.p, cent[:, 0], kc, wk, g0, w0, dt)
+    st = ctx.cavmd_get_state()
+    np.testing.assert_allclose(st["q"], ps.qn, rtol=0, atol=1e-12 * np.abs(ps.qn).max())   # Step 0
+    x0 = sy.r.copy()
+    for s in range(6):
+        ctx.cavmd_step(1)
+        ps.step()
+        st = ctx.cavmd_get_state()
+        tol = 1e-9 * (1 + s)
+        dr = ps.r - x0
+        np.testing.assert_allclose(st["r"] - x0, dr, rtol=0, atol=tol * np.abs(dr).max())
+        np.testing.assert_allclose(st["p"], ps.p, rtol=0, atol=tol * np.abs(ps.p).max())
+        np.testing.assert_allclose(st["q"], ps.qn, rtol=0, atol=tol * np.abs(ps.qn).max())
+        np.testing.assert_allclose(st["pq"], ps.pn, rtol=0, atol=tol * np.abs(ps.pn).max())
+        if not disp:   # the oracle's local photon energy is the free energy of a flat dispersion
+            np.testing.assert_allclose(ctx.cavmd_observables()["e_total"], ps.energies()["total"], rtol=1e-11)
+    if disp:   # the dispersion changes the photon trajectory
+        flat = PS.PaperRealSpaceMD(OC.DFTBMatter(params, sy), sy.r, sy.p, cent[:, 0], kc, np.full(N, w0), g0, w0, dt)
+        for _ in range(6):
+            flat.step()
+        assert np.abs(flat.qn - ps.qn).max() > 1e3 * 6e-9 * np.abs(ps.qn).max()
+
+
+def test_real_space_scheme_graph_and_resume(P):
+    N, a, w0, g0 = 8, 12.0, 0.012, 0.002
+    params, cent, sy, modes, kc, wk = _lattice_case(N, a, w0, g0, True)
+    w = {"system": sy, "modes": modes, "params": params}
+    kw = dict(splitting=3, real_space_g0=g0, real_space_omega0=w0)
+    x = _ctx(P, w, graph_chunk=0, **kw)
+    y = _ctx(P, w, graph_chunk=4, **kw)
+    x.cavmd_step(9)
+    y.cavmd_step(9)
+    sx, sy_ = x.cavmd_get_state(), y.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        assert np.array_equal(sx[k], sy_[k]), k
+    # a run resumed from a saved state follows the original one (the re-evaluation at the saved
+    # positions converges the charges from a cold start, so to the trajectory tolerance)
+    z = _ctx(P, w, graph_chunk=0, **kw)
+    z.cavmd_set_state(sx)
+    assert z.cavmd_get_state()["step"] == 9
+    x.cavmd_step(3)
+    z.cavmd_step(3)
+    a_, b_ = x.cavmd_get_state(), z.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        np.testing.assert_allclose(b_[k], a_[k], rtol=0, atol=1e-9 * np.abs(a_[k]).max() + 1e-15)
