@@ -47,17 +47,22 @@ def resonant_box(params, n_waters: int = 33, seed: int = 0, lam: float = 0.1, sp
     return sy, modes, wb
 
 
-def resonant_workload(params, name: str = "c4", coupling: float = 0.1 * np.sqrt(33.0)):
-    """(system, modes, w_bend): the cells of a grid workload (c4: 16,384 waters) with its in-plane mode
-    grid (c4: 32 x 32, 1024 modes), but the cavity length set so that the k = 0 mode sits at the
-    bend, and the amplitudes scaled so that lambda_0 sqrt(N) equals the resonant box's 0.1 sqrt(33)
-    (the same collective coupling); the other modes of the grid lie far above both bands."""
+def resonant_workload(params, name: str = "c4", coupling: float = 0.1 * np.sqrt(33.0), top: float = 1.3):
+    """(system, modes, w_bend): the cells of a grid workload (c4: 16,384 waters) and a mode grid of its
+    size (c4: 32 x 32, 1024 modes) in a resonant cavity: the k = 0 mode at the bend and the in-plane
+    wave vectors spaced so that the largest reaches `top` times the bend (the lower polariton band
+    of the paper's angle-resolved setting; omega dt stays near 0.2, where the workload's own grid,
+    spaced by 2 pi over the slab, puts its modes hundreds of times above the bands). The amplitudes
+    make N sum_a lambda_a^2 over the cos modes, which all see nearly the same phase across the slab,
+    equal the resonant box's collective coupling 0.1^2 x 33."""
     w = cs.make_workload(name, params=params)
     g = w["modes"].grid
+    Kx, Ky2 = g["Kx"], g["Ky"] // 2
     wb = params.meta["harmonic_freq_hartree"][0]
-    lam0 = coupling / np.sqrt(w["system"].n_cells)
-    L = cs.units.C_LIGHT * np.pi / wb
-    modes = cs.grid_modes(g["Kx"], g["Ky"], g["dkx"], g["dky"], L, lam0 / np.sqrt(2.0))
+    kz = wb / cs.units.C_LIGHT
+    dk = kz * np.sqrt(top ** 2 - 1.0) / np.hypot(Kx - 1, Ky2 - 1)
+    g0 = coupling / (2.0 * np.sqrt(w["system"].n_cells * Kx * Ky2))
+    modes = cs.grid_modes(Kx, g["Ky"], dk, dk, np.pi / kz, g0)
     return w["system"], modes, wb
 
 

@@ -3,9 +3,12 @@
 (with the BF16x3 and with the FP64 coupling), explicit central finite-difference Born charges every
 step (the conservative reference) and Mulliken charges (the paper's cheap replacement).
 
-Cavity: the k = 0 mode at the bend of the synthetic water, with the collective coupling of the
-resonant single box (lambda_0 sqrt(N) = 0.1 sqrt(33)); the other 1022 modes of the grid lie far
-above both vibrational bands (paper_2512_03277_gb300/judge.py, resonant_workload).
+Cavity (paper_2512_03277_gb300/judge.py, resonant_workload): the 32 x 32 grid of a resonant
+cavity, the k = 0 mode at the bend of the synthetic water and the in-plane wave vectors spaced so
+that the band of modes spans 1 to 1.3 times the bend (below the stretch), with the collective
+coupling of the resonant single box. (The workload's own grid, spaced by 2 pi over the slab, puts
+every k != 0 mode hundreds of times above both bands, at omega dt of about 50 rad, where the step
+no longer conserves energy whatever the dipole derivative.)
 
 Reported per run: energy drift (Ha/atom over the run), heating (mean temperature of the last tenth
 minus that of the second tenth; the first tenth is the equipartition transient), the temperature
