@@ -26,7 +26,8 @@ no data-path collective; value = all ranks' molecule-steps / max-over-ranks time
 
 cpu_baseline: the FP64 oracle (oracle/) as it stands, on a bounded sample of the headline arm's
 workload, on one core and on every core of the host (one process per core, cells split between
-them). --impl reference times the same oracle the same way, one oracle time step per step.
+them); its network charge model runs a seeded network (the cost does not depend on the weights).
+--impl reference times the same oracle the same way, one oracle time step per step.
 """
 import argparse
 import json
@@ -314,7 +315,7 @@ def run_reference(args):
     from paper_2512_03277_gb300 import cavmd as B
     w = cs.make_workload(args.workload)
     charge_model = _arm_defaults(args)[0][1]
-    mlp = _network(B, charge_model)
+    mlp = _network(B, charge_model, seeded=True)
     cores = _host_cores()
     n = _sample_cells(args.workload, w["system"].n_cells)
     value, tot, el, k, used = oracle_throughput(args.workload, ORACLE_CHARGE[charge_model], mlp, cores, n,
@@ -348,11 +349,12 @@ def _arm_defaults(args):
     return arms
 
 
-def _network(B, charge_model):
-    """The shipped trained network, else (for timing only) a seeded one; None for other models."""
+def _network(B, charge_model, seeded=False):
+    """The shipped trained network, else (and always with `seeded`, for the oracle's timing runs,
+    whose inputs never come from the GPU) a seeded one; None for other models."""
     if charge_model != "born_mlp":
         return None
-    p = B.trained_born_mlp()
+    p = None if seeded else B.trained_born_mlp()
     if p is not None:
         return p
     rng = np.random.default_rng(4)
@@ -664,8 +666,8 @@ def main():
         if not trained and any(c == "born_mlp" for _, c in arms):
             line["judge"]["note"] = "network arm not judged: no trained weights shipped"
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.workload, head["charge_model"], _network(B, head["charge_model"]),
-                                            w["system"].n_cells)
+        line["cpu_baseline"] = cpu_baseline(args.workload, head["charge_model"],
+                                            _network(B, head["charge_model"], seeded=True), w["system"].n_cells)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
