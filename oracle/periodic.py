@@ -432,13 +432,45 @@ def scipy_eigh(H, S):
 
 # ---------------------------------------------------------------------------- cells for the cavity step
 
+def born_fd_periodic(params, species, pos, lattice, pol, h=1e-3, scheme="forward", q_ref=None, mu_ref=None,
+                     alpha=None, beta=0.5, tol=1e-12, max_iter=400):
+    """Finite-difference dipole derivative b_j = d(pol . mu)/dr_j of one periodic cell, shape (nat, 3):
+    the Born charges of the paper's periodic cells (Results: forward differences, refreshed every
+    3 steps). 'forward' is [M(r + h e) - M(r)] / h, 'central' [M(r + h e) - M(r - h e)] / 2h, with mu
+    the unwrapped cell dipole of dftb_periodic; every displaced solve starts from the reference
+    populations."""
+    pos = np.asarray(pos, float)
+    pol = np.asarray(pol, float)
+    if q_ref is None or mu_ref is None:
+        ref = dftb_periodic(params, species, pos, lattice, alpha=alpha, beta=beta, tol=tol, max_iter=max_iter,
+                            forces=False)
+        q_ref, mu_ref = ref["q"], ref["mu"]
+    kw = dict(q0=q_ref, alpha=alpha, beta=beta, tol=tol, max_iter=max_iter, forces=False)
+    M0 = mu_ref @ pol
+    b = np.zeros((len(pos), 3))
+    for j in range(len(pos)):
+        for k in range(3):
+            dp = pos.copy()
+            dp[j, k] += h
+            Mp = dftb_periodic(params, species, dp, lattice, **kw)["mu"] @ pol
+            if scheme == "forward":
+                b[j, k] = (Mp - M0) / h
+            else:
+                dm = pos.copy()
+                dm[j, k] -= h
+                Mm = dftb_periodic(params, species, dm, lattice, **kw)["mu"] @ pol
+                b[j, k] = (Mp - Mm) / (2.0 * h)
+    return b
+
+
 class PeriodicDFTBMatter:
     """Periodic cells evaluated with dftb_periodic, with the interface of oracle.cavity's
-    DFTBMatter (Mulliken charges: b_j = Q_j pol). lattice: (3, 3) shared by all cells or
-    (n_cells, 3, 3)."""
+    DFTBMatter: Mulliken charges (b_j = Q_j pol) or finite-difference Born charges ('born_fd',
+    forward, or 'born_central'; refreshed every born_interval evaluations). lattice: (3, 3) shared
+    by all cells or (n_cells, 3, 3)."""
 
     def __init__(self, params, system, lattice, pol=(1.0, 0.0, 0.0), alpha=None, beta=0.5,
-                 tol=1e-12, max_iter=400):
+                 tol=1e-12, max_iter=400, charge_model="mulliken", born_interval=1, fd_step=1e-3):
         self.params = params
         self.species = np.asarray(system.species)
         self.off = np.asarray(system.cell_offset)
@@ -448,7 +480,9 @@ class PeriodicDFTBMatter:
         self.pol = np.asarray(pol, float)
         self.mass = params.mass[self.species]
         self.cell_of_atom = np.repeat(np.arange(self.n_cells), np.diff(self.off))
-        self.charge_model = "mulliken"
+        self.charge_model = charge_model
+        self.born_interval = born_interval
+        self.fd_step = fd_step
         self.alpha = alpha
         self.kw = dict(beta=beta, tol=tol, max_iter=max_iter)
         self.q = None
@@ -464,6 +498,9 @@ class PeriodicDFTBMatter:
         Q = np.zeros(n_at)
         q_all = np.zeros(n_at)
         iters = []
+        refresh = self.charge_model != "mulliken" and ((self.n_eval % self.born_interval == 0) or self.b is None)
+        b = Q[:, None] * self.pol if self.charge_model == "mulliken" else (
+            np.zeros((n_at, 3)) if refresh else self.b.copy())
         for c in range(self.n_cells):
             s = slice(self.off[c], self.off[c + 1])
             q0 = None if self.q is None else self.q[s]
@@ -475,8 +512,15 @@ class PeriodicDFTBMatter:
             Q[s] = out["Q"]
             q_all[s] = out["q"]
             Mn[c] = out["mu"] @ self.pol
+            if refresh:
+                scheme = "forward" if self.charge_model == "born_fd" else "central"
+                b[s] = born_fd_periodic(self.params, self.species[s], r[s], self.lattice[c], self.pol,
+                                        h=self.fd_step, scheme=scheme, q_ref=out["q"], mu_ref=out["mu"],
+                                        alpha=self.alpha, **self.kw)
         self.q = q_all
-        self.b = Q[:, None] * self.pol
+        if self.charge_model == "mulliken":
+            b = Q[:, None] * self.pol
+        self.b = b
         self.n_eval += 1
         self.iters.append(max(iters) if iters else 0)
         return {"F": F, "E": E, "M": Mn, "b": self.b.copy(), "Q": Q}

@@ -240,8 +240,9 @@ cudaError_t run_born(cavmd_ctx *c) {
     d.fd_central = c->opt.charge_model == CAVMD_CHARGE_BORN_CENTRAL;
     d.fd_h = c->opt.fd_step;
     d.M_disp = c->d_Mdisp;
-    cudaError_t e = c->generic ? launch_dftb_generic(c->d_sk, d, c->gplan, c->stream)
-                               : launch_dftb_water(c->d_sk, d, c->stream, c->water_warps, c->water_per_warp);
+    cudaError_t e = c->periodic ? launch_dftb_periodic(c->d_sk, d, c->pplan, c->stream)
+                    : c->generic ? launch_dftb_generic(c->d_sk, d, c->gplan, c->stream)
+                                 : launch_dftb_water(c->d_sk, d, c->stream, c->water_warps, c->water_per_warp);
     if (e != cudaSuccess) return e;
     return launch_born_assemble(c->N, c->d_off, c->d_Mc, c->d_Mdisp, c->n_disp, d.fd_central, d.fd_h, c->d_b,
                                 c->stream);
@@ -592,8 +593,8 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         const double det = L[0] * (L[4] * L[8] - L[5] * L[7]) - L[1] * (L[3] * L[8] - L[5] * L[6]) +
                            L[2] * (L[3] * L[7] - L[4] * L[6]);
         if (!(std::fabs(det) > 1e-6)) return fail(c, CAVMD_ERR_INVALID_ARG, "lattice vectors are linearly dependent");
-        if (o->charge_model != CAVMD_CHARGE_MULLIKEN)
-            return fail(c, CAVMD_ERR_UNSUPPORTED, "periodic cells take Mulliken charges only");
+        if (o->charge_model == CAVMD_CHARGE_BORN_MLP)
+            return fail(c, CAVMD_ERR_UNSUPPORTED, "periodic cells take Mulliken or finite-difference Born charges");
     }
     for (int n = 0; n < sys->n_cells; ++n) {
         const int a0 = sys->cell_offset[n], a1 = sys->cell_offset[n + 1];

@@ -269,11 +269,17 @@ struct PbcDev {
 };
 
 // One cell, evaluated by the whole block.
-__device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PShared &sh, double *wk, int cell) {
+// One cell, or (disp_k >= 0) one finite-difference copy of it: atom disp_k / 3 (central: disp_k / 6)
+// moved along x, y or z by +h (central: +h and -h in turn), warm started from the cell's converged
+// basis in a private copy, and only its dipole written (M_disp, the layout of the water kernels).
+template <bool DISP>
+__device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PShared &sh, double *wk, int cell,
+                       int disp_k) {
     const int j = threadIdx.x;
     const int a0 = a.cell_offset[cell];
     const int nat = a.cell_offset[cell + 1] - a0;
     const long long n2max = (long long)pl.nmax * pl.nmax;
+    constexpr bool disp = DISP;
     double *H0 = wk, *S = wk + n2max, *H = wk + 2 * n2max, *Y = wk + 3 * n2max, *P = wk + 4 * n2max;
     double *Xg = wk + 5 * n2max, *Mo = wk + 6 * n2max, *Mv = wk + 7 * n2max;
     double *gam = wk + 8 * n2max;
@@ -285,6 +291,11 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
     if (j < nat) {
         sh.spec[j] = a.species[a0 + j];
         for (int k = 0; k < 3; ++k) sh.pos[j][k] = a.r[3 * (a0 + j) + k];
+        if (disp) {
+            const int kk = a.fd_central ? disp_k >> 1 : disp_k;
+            const double sg = (a.fd_central && (disp_k & 1)) ? -1.0 : 1.0;
+            if (j == kk / 3) sh.pos[j][kk % 3] += sg * a.fd_h;
+        }
     }
     __syncthreads();
     if (j == 0) {
@@ -307,6 +318,12 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
     __syncthreads();
     const int n = sh.fl[1], nocc = sh.fl[3];
     const int nv = n - nocc, nn = n * n;
+    if (disp) {   // a private copy of the cell's basis: the cell and its other copies read the original
+        double *Cd = pbuf + 4LL * pl.amax * pl.amax;
+        for (int e = j; e < nn; e += PT) Cd[e] = C[e];
+        C = Cd;
+        __syncthreads();
+    }
 
     // ---------------------------------------------------------------- H0, S, real-space gamma
     for (int e = j; e < nn; e += PT) {
@@ -524,10 +541,10 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
     if (!a.have_warm)
         for (int e = j; e < nn; e += PT) C[e] = (e / n == e % n) ? 1.0 : 0.0;
     if (j < nat) {
-        if (a.have_warm) {   // predictor 2 q(t) - q(t - dt)
+        if (a.have_warm) {   // predictor 2 q(t) - q(t - dt); a displaced copy starts from q(r)
             const double qt = a.qpop[a0 + j];
             sh.qst[j] = qt;
-            sh.q[j] = fma(2.0, qt, -a.qprev[a0 + j]);
+            sh.q[j] = disp ? qt : fma(2.0, qt, -a.qprev[a0 + j]);
         } else {
             sh.q[j] = sh.zv[j];
         }
@@ -823,6 +840,20 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
         sh.fl[2] = a.max_iter;
     }
     __syncthreads();
+    if (disp) {   // a finite-difference copy: only its dipole
+        if (j == 0) {
+            double mu[3] = {0.0, 0.0, 0.0};
+            for (int at = 0; at < nat; ++at) {
+                const double Q = sh.zv[at] - sh.q[at];
+                for (int k = 0; k < 3; ++k) mu[k] = fma(Q, sh.pos[at][k] - sh.pos[0][k], mu[k]);
+            }
+            a.M_disp[(long long)(a.fd_central ? 6 : 3) * a0 + disp_k] =
+                fma(a.pol0, mu[0], fma(a.pol1, mu[1], a.pol2 * mu[2]));
+            if (sh.fl[0]) atomicOr(a.status, (unsigned)sh.fl[0]);
+        }
+        __syncthreads();
+        return;
+    }
 
     // ---------------------------------------------------------------- energy and forces
     // Shifts of the converged charges; H; T = H C_o into Y; Aoo = C_o^T T (lower) into Mo;
@@ -1027,7 +1058,23 @@ __global__ void __launch_bounds__(PT, 2) k_dftb_periodic(const DevSK *__restrict
     PShared &sh = *reinterpret_cast<PShared *>(p_smem);
     const DevSK &sk = *skp;
     double *wk = pl.work + (long long)blockIdx.x * pl.work_stride;
-    for (int cell = blockIdx.x; cell < a.n_cells; cell += gridDim.x) p_cell(sk, a, pl, sh, wk, cell);
+    for (int cell = blockIdx.x; cell < a.n_cells; cell += gridDim.x) p_cell<false>(sk, a, pl, sh, wk, cell, -1);
+}
+
+// Finite-difference copies of every cell: (cell, row) items, rows_max = 3 (central: 6) x the
+// largest atom count per cell.
+__global__ void __launch_bounds__(PT, 2) k_dftb_periodic_disp(const DevSK *__restrict__ skp, const DftbArgs a,
+                                                             const PbcDev pl) {
+    extern __shared__ __align__(16) unsigned char p_smem[];
+    PShared &sh = *reinterpret_cast<PShared *>(p_smem);
+    const DevSK &sk = *skp;
+    double *wk = pl.work + (long long)blockIdx.x * pl.work_stride;
+    const int per_atom = a.fd_central ? 6 : 3;
+    const long long rows_max = (long long)per_atom * pl.amax, items = rows_max * a.n_cells;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int cell = (int)(it / rows_max), k = (int)(it - (long long)cell * rows_max);
+        if (k < per_atom * (a.cell_offset[cell + 1] - a.cell_offset[cell])) p_cell<true>(sk, a, pl, sh, wk, cell, k);
+    }
 }
 
 }  // namespace
@@ -1036,8 +1083,8 @@ __global__ void __launch_bounds__(PT, 2) k_dftb_periodic(const DevSK *__restrict
 // Host side
 
 size_t pbc_workspace_doubles(int nmax, int amax, int n_g) {
-    const size_t n2 = (size_t)nmax * nmax;
-    return 8 * n2 + (size_t)amax * amax + 2 * (size_t)amax * n_g + 2 * (size_t)n_g + 4 * (size_t)amax * amax + 32;
+    const size_t n2 = (size_t)nmax * nmax;   // the last n2: a finite-difference copy's basis
+    return 9 * n2 + (size_t)amax * amax + 2 * (size_t)amax * n_g + 2 * (size_t)n_g + 4 * (size_t)amax * amax + 32;
 }
 
 // Lattice images and reciprocal vectors for one lattice (rows a_i), and the Ewald constants. The
@@ -1133,7 +1180,10 @@ void plan_dftb_periodic(const double *lat, double r_cut, PbcPlan &p, std::vector
 size_t pbc_smem() { return sizeof(PShared); }
 
 cudaError_t prepare_dftb_periodic() {
-    return cudaFuncSetAttribute(k_dftb_periodic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PShared));
+    cudaError_t e = cudaFuncSetAttribute(k_dftb_periodic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PShared));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dftb_periodic_disp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PShared));
+    return e;
 }
 
 cudaError_t launch_dftb_periodic(const DevSK *sk_dev, const DftbArgs &a, const PbcPlan &p, cudaStream_t st) {
@@ -1153,7 +1203,9 @@ cudaError_t launch_dftb_periodic(const DevSK *sk_dev, const DftbArgs &a, const P
     d.gw = p.d_gw;
     d.work = p.work;
     d.work_stride = (long long)pbc_workspace_doubles(p.nmax, p.amax, p.n_g);
-    const int grid = std::min(a.n_cells, p.blocks);
-    k_dftb_periodic<<<grid, PT, sizeof(PShared), st>>>(sk_dev, a, d);
+    const long long items = a.n_disp > 0 ? (long long)a.n_cells * (a.fd_central ? 6 : 3) * p.amax : a.n_cells;
+    const int grid = (int)std::min<long long>(items, p.blocks);
+    if (a.n_disp > 0) k_dftb_periodic_disp<<<grid, PT, sizeof(PShared), st>>>(sk_dev, a, d);
+    else k_dftb_periodic<<<grid, PT, sizeof(PShared), st>>>(sk_dev, a, d);
     return cudaGetLastError();
 }

@@ -164,8 +164,9 @@ def test_rejects_empty_inputs(lib, small):
 
 
 def test_periodic_cells_validation(lib, small):
-    """Periodic cells: linearly dependent lattice vectors are invalid; charge models other than
-    Mulliken are refused as unsupported; both before any device work."""
+    """Periodic cells: linearly dependent lattice vectors are invalid; the network charge model is
+    refused as unsupported (Mulliken and finite-difference Born charges are built); both before any
+    device work."""
     sy, lat = cs.periodic_water_cells(np.random.default_rng(5), np.zeros((1, 3)), n_waters=2, side=8.5,
                                       d_min=4.0, d_atom=2.8)
     flat = lat.copy()
@@ -174,6 +175,6 @@ def test_periodic_cells_validation(lib, small):
     assert rc == -1 and "lattice" in msg
     import paper_2512_03277_gb300 as P
     o = P.default_options()
-    o.charge_model = 1
+    o.charge_model = 3
     rc, msg = _init_rc(lib, sy, small["params"], small["modes"], opt=o, lattice=lat)
     assert rc == -8 and "Mulliken" in msg

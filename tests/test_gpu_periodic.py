@@ -174,3 +174,30 @@ def test_full_size_p33_sampled(P):
     ctx.cavmd_step(1)
     st = ctx.cavmd_get_state()
     assert st["step"] == 1 and np.all(np.isfinite(st["p"])) and np.all(np.isfinite(st["q"]))
+
+
+@pytest.mark.parametrize("model,code", [("born_fd", 1), ("born_central", 2)])
+def test_born_charges_of_periodic_cells(P, model, code):
+    """Finite-difference Born charges of periodic cells (forward as in the paper, and central) as
+    displaced copies of every cell in the periodic kernel, against the oracle's born_fd_periodic;
+    then three coupled steps with the charges refreshed every step, against the oracle's trajectory.
+    Tolerance of b: 5e-8, the water kernels' (each side's fixed point within about 2e-12 of the
+    exact one, times the lever arm, over h = 1e-3)."""
+    sy, lat = _cells(3)
+    params = cs.load_water_params()
+    ctx = _ctx(P, sy, lat, charge_model=code, born_interval=1, graph_chunk=0)
+    ev = ctx.cavmd_get_eval()
+    mat = PR.PeriodicDFTBMatter(params, sy, lat, charge_model=model, born_interval=1)
+    mo = cs.make_workload("c1", n_cells=2)["modes"]
+    md = OC.CavityMD(mat, sy.r, sy.p, mo.k, mo.omega, mo.lam, mo.phi, sy.R_ref, 0.5 * 41.341373335)
+    np.testing.assert_allclose(ev["b"], md.out["b"], rtol=0, atol=5e-8)
+    assert np.abs(md.out["b"] - md.out["Q"][:, None] * np.array([1.0, 0.0, 0.0])).max() > 1e-3   # not Mulliken
+    x0 = sy.r.copy()
+    for s in range(3):
+        ctx.cavmd_step(1)
+        md.step()
+        st = ctx.cavmd_get_state()
+        tol = 1e-9 * (1 + s)
+        np.testing.assert_allclose(st["r"] - x0, md.r - x0, rtol=0, atol=tol * np.abs(md.r - x0).max())
+        np.testing.assert_allclose(st["p"], md.p, rtol=0, atol=tol * np.abs(md.p).max())
+    np.testing.assert_allclose(ctx.cavmd_get_eval()["b"], md.out["b"], rtol=0, atol=5e-8)

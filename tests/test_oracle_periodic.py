@@ -287,3 +287,26 @@ def test_kgrid_forces_against_finite_differences(params):
                                             forces=False)["E"])
             fd[j, k] = -(e[0] - e[1]) / (2.0 * h)
     np.testing.assert_allclose(out["F"], fd, rtol=0, atol=1e-7 * np.abs(out["F"]).max())
+
+
+def test_born_charges_of_a_periodic_cell(params):
+    """Finite-difference Born charges of a periodic cell (born_fd_periodic): central differences obey
+    the translation sum rule sum_j b_j = Q_cell pol = 0 (to O(h^2)); forward and central differences
+    differ at O(h) (halving h halves the gap); and one water in a large cube approaches the isolated
+    molecule's charges as the cube grows (the images' field falls off as 1 / V)."""
+    from oracle import dftb as D
+    sy, lat = _two_waters()
+    pos, spec = sy.r, sy.species
+    pol = np.array([1.0, 0.0, 0.0])
+    bc = PR.born_fd_periodic(params, spec, pos, lat, pol, h=1e-3, scheme="central")
+    assert np.abs(bc.sum(0)).max() < 1e-6
+    g1 = np.abs(PR.born_fd_periodic(params, spec, pos, lat, pol, h=1e-3) - bc).max()
+    g2 = np.abs(PR.born_fd_periodic(params, spec, pos, lat, pol, h=5e-4) - bc).max()
+    assert 0.35 < g2 / g1 < 0.65
+    w, _ = _one_water(params, 1.0)
+    iso = D.born_fd(params, [0, 1, 1], w[None], pol, h=1e-3, scheme="central")[0]
+    gaps = []
+    for side in (40.0, 80.0):
+        bp = PR.born_fd_periodic(params, [0, 1, 1], w, side * np.eye(3), pol, h=1e-3, scheme="central")
+        gaps.append(np.abs(bp - iso).max())
+    assert gaps[1] < 0.25 * gaps[0] and gaps[1] < 2e-3 * np.abs(iso).max()
