@@ -5,8 +5,11 @@
 // would have to copy M coordinates to the host every step; instead every synchronised state is
 // folded into running lag products on the device:
 //   channel c < M: the photon coordinate q_c; channel M: the total projected dipole sum_n M_n;
-//   acc[c][l] += x_c(t) x_c(t - l) for l = 0 .. min(t, L - 1), a ring of the last L samples,
-//   the first L samples and the running sum S_c.
+//   a ring of the last L + B samples, the first L samples and the running sum S_c; every B steps
+//   the B newest samples are folded into the lag products, acc[c][l] += sum over those samples t
+//   of x_c(t) x_c(t - l) (t in increasing order), so the L lag products are read and written once
+//   per B steps instead of every step (at 8193 channels x 1024 lags that table is 67 MB). The
+//   samples not yet folded are added at read-out from the ring.
 // From these the finalisation forms the mean-removed unbiased estimator exactly:
 //   C(l) = [P(l) - xbar (A(l) + B(l)) + (n - l) xbar^2] / (n - l),  xbar = S / n,
 //   P(l) = sum_{t=l}^{n-1} x_t x_{t-l},  A(l) = S - (last l samples),  B(l) = S - (first l samples).
@@ -39,21 +42,22 @@ __global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const doub
             xs = v;
         }
     }
-    const int L = a.L;
-    const int s = (int)(t % L);
-    double *ring = a.ring + (size_t)c * L;
+    const int L = a.L, R = a.L + a.B;
+    double *ring = a.ring + (size_t)c * R;
     if (threadIdx.x == 0) {
-        ring[s] = xs;
+        ring[t % R] = xs;
         if (t < L) a.head[(size_t)c * L + t] = xs;
         a.sum[c] += xs;
     }
     __syncthreads();
-    const double x = xs;
-    double *acc = a.acc + (size_t)c * L;
-    const int lmax = (int)(t < L - 1 ? t : L - 1);
-    for (int l = threadIdx.x; l <= lmax; l += ACF_THREADS) {
-        const int i = s - l < 0 ? s - l + L : s - l;
-        acc[l] = fma(x, ring[i], acc[l]);
+    if ((t + 1) % a.B == 0) {   // fold samples t - B + 1 .. t
+        double *acc = a.acc + (size_t)c * L;
+        for (int l = threadIdx.x; l < L; l += ACF_THREADS) {
+            double v = acc[l];
+            for (long long u = t - a.B + 1; u <= t; ++u)
+                if (u >= l) v = fma(ring[u % R], ring[(u - l) % R], v);
+            acc[l] = v;
+        }
     }
     if (threadIdx.x == 0) {
         const unsigned tk = atomicAdd(a.ticket, 1u);
@@ -70,21 +74,24 @@ __global__ void k_acf_finalize(const AcfArgs a, double *__restrict__ out) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.C) return;
     const long long n = *a.n;
-    const int L = a.L;
+    const int L = a.L, R = a.L + a.B;
     const double S = a.sum[c];
     const double xb = n > 0 ? S / (double)n : 0.0;
-    const double *ring = a.ring + (size_t)c * L, *head = a.head + (size_t)c * L, *acc = a.acc + (size_t)c * L;
+    const double *ring = a.ring + (size_t)c * R, *head = a.head + (size_t)c * L, *acc = a.acc + (size_t)c * L;
+    const long long folded = n - n % a.B;   // samples already in the lag products
     double first = 0.0, lastsum = 0.0;   // sums of the first l and of the last l samples
     for (int l = 0; l < L; ++l) {
         if (l >= n) {
             out[(size_t)c * L + l] = 0.0;
             continue;
         }
+        double P = acc[l];
+        for (long long u = folded; u < n; ++u)
+            if (u >= l) P = fma(ring[u % R], ring[(u - l) % R], P);
         const double A = S - lastsum, B = S - first, m = (double)(n - l);
-        out[(size_t)c * L + l] = (acc[l] - xb * (A + B) + m * xb * xb) / m;
+        out[(size_t)c * L + l] = (P - xb * (A + B) + m * xb * xb) / m;
         first += head[l];
-        long long i = (n - 1 - l) % L;
-        lastsum += ring[i];
+        lastsum += ring[(n - 1 - l) % R];
     }
 }
 

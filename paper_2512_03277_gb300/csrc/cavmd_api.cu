@@ -311,7 +311,8 @@ cudaError_t run_acf(cavmd_ctx *c) {
 cudaError_t reset_acf(cavmd_ctx *c) {
     if (c->acf.L <= 0) return cudaSuccess;
     const size_t cl = (size_t)c->acf.C * c->acf.L;
-    cudaError_t e = cudaMemsetAsync(c->acf.ring, 0, sizeof(double) * cl, c->stream);
+    cudaError_t e = cudaMemsetAsync(c->acf.ring, 0, sizeof(double) * (size_t)c->acf.C * (c->acf.L + c->acf.B),
+                                    c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.head, 0, sizeof(double) * cl, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.acc, 0, sizeof(double) * cl, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->acf.sum, 0, sizeof(double) * c->acf.C, c->stream);
@@ -896,8 +897,10 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         a.M = M;
         a.C = M + 1;
         a.L = c->opt.acf_lags;
+        a.B = 16;
         const size_t cl = (size_t)a.C * a.L;
-        AL(a.ring, cl); AL(a.head, cl); AL(a.acc, cl); AL(a.sum, a.C); AL(a.n, 1); AL(a.ticket, 1);
+        AL(a.ring, (size_t)a.C * (a.L + a.B)); AL(a.head, cl); AL(a.acc, cl); AL(a.sum, a.C); AL(a.n, 1);
+        AL(a.ticket, 1);
         AL(c->d_acf_out, cl);
         CK(reset_acf(c));
     }

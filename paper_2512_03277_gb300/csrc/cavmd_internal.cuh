@@ -181,7 +181,9 @@ void cavmd_set_global_error(const std::string &msg);
 // On-device autocorrelation accumulators (channels: M photon coordinates, then the total dipole).
 struct AcfArgs {
     int M, C, L;                 // modes, channels (M + 1), lags
-    double *ring, *head, *acc;   // [C][L]: last L samples, first L samples, lag products
+    int B;                       // samples folded into the lag products at a time
+    double *ring;                // [C][L + B] the last L + B samples
+    double *head, *acc;          // [C][L]: first L samples, lag products
     double *sum;                 // [C] running sums
     long long *n;                // samples so far
     unsigned *ticket;            // last-block counter
