@@ -152,6 +152,30 @@ cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsi
 cudaError_t launch_tc_back(const TcPlan &p, const float *Wt2, const float *Wt1, double *E2, double *E1,
                            unsigned *status, cudaStream_t st);
 
+// Conversions between FP64 and FP32 on the integer pipe, for quantities that only steer an
+// iteration (generator entries, rotation angles, mixing coefficients): on GB300 the hardware
+// conversions issue to the FP64 pipe, the bottleneck of the SCC kernels. d2f_steer truncates the
+// significand (magnitudes below 2^-126 give a signed zero, above the FP32 range a signed
+// infinity, and so do NaNs); f2d_steer is exact for zero, normal numbers, infinities and NaNs
+// (subnormals give a signed zero).
+__device__ __forceinline__ float d2f_steer(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(b >> 32);
+    const unsigned sgn = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu) - 896;   // rebias 1023 -> 127
+    if (e <= 0) return __uint_as_float(sgn);
+    if (e >= 255) return __uint_as_float(sgn | 0x7f800000u);
+    return __uint_as_float(sgn | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+}
+__device__ __forceinline__ double f2d_steer(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)sgn);
+    const unsigned long long ee = e == 255u ? 0x7ffull : (unsigned long long)(e + 896u);
+    return __longlong_as_double((long long)(sgn | (ee << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 // |x| < y for finite doubles and y > 0, by the ordering of the IEEE bit patterns: an integer
 // comparison that leaves the FP64 pipe free.
 __device__ __forceinline__ bool abs_lt(double x, double y) {

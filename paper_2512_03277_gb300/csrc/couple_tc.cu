@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + FWD_NST * STAGE);   // [NST] stage data arrived
     uint64_t *done = full + FWD_NST;                                         // [NST] stage MMAs finished
     uint32_t *slot = reinterpret_cast<uint32_t *>(done + FWD_NST);
+    float *ms = reinterpret_cast<float *>(slot + 4);                         // [32] M_n of the stage (FP32)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q0 = blockIdx.x * st_per_cta;
     const int nq = max(0, min(n_stage_total, q0 + st_per_cta) - q0);
@@ -168,12 +169,16 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
         bool w = i == 0 || tc::mbar_wait(&done[(i - 1) % FWD_NST], ((i - 1) / FWD_NST) & 1);
         if (tid == 0 && w && n_issued < nq && n_issued == i + FWD_NST - 1) issue(n_issued++);
         w = w && tc::mbar_wait(&full[s], (i / FWD_NST) & 1);
+        const int nbase = (q0 + i) * FWD_SC;
+        if (tid < FWD_SC) {   // the stage's dipoles, converted once (a conversion from FP64 runs on the FP64 pipe)
+            const int n = nbase + tid;
+            ms[tid] = n < N ? (float)__ldg(Mc + n) : 0.0f;
+        }
         if (!__syncthreads_and(w)) { ok = false; break; }
         tc::fence_after_sync();
         if (i > 0) fold(i - 1);
         uint8_t *st = smem + s * STAGE;
         const float *bs = reinterpret_cast<const float *>(st + 2 * A_BYTES + 2 * B_BYTES);
-        const int nbase = (q0 + i) * FWD_SC;
         for (int c = tid; c < KY * FWD_SC / 8; c += FWD_THREADS) {   // 8 consecutive cells of one row per chunk
             const int kgrp = c / KY, row = c - kgrp * KY;
             const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_B);
@@ -182,11 +187,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
             const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int n = nbase + 8 * kgrp + q;
-                const float m = n < N ? (float)__ldg(Mc + n) : 0.0f;
-                split_bf16(vv[q] * m, hi[q], lo[q]);
-            }
+            for (int q = 0; q < 8; ++q) split_bf16(vv[q] * ms[8 * kgrp + q], hi[q], lo[q]);
             *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + off) = *reinterpret_cast<const uint4 *>(hi);
             *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + B_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
         }
@@ -358,7 +359,7 @@ cudaError_t set_smem(F f, size_t bytes) {
 // ---------------------------------------------------------------------------------------- host
 
 size_t tc_fwd_smem(int KY) {
-    return FWD_NST * (2 * (size_t)KXP * FWD_SC * 2 + 2 * (size_t)KY * FWD_SC * 2 + (size_t)KY * FWD_SC * 4) + 128;
+    return FWD_NST * (2 * (size_t)KXP * FWD_SC * 2 + 2 * (size_t)KY * FWD_SC * 2 + (size_t)KY * FWD_SC * 4) + 256;
 }
 int tc_fwd_stage_cells() { return FWD_SC; }
 size_t tc_back_smem(int KY) { return 4 * (size_t)KXP * KY * 2 + 2 * (size_t)BACK_CELLS * KY * 2 + 64; }

@@ -137,13 +137,13 @@ __device__ __forceinline__ void g_pair(int k, int r, int n, int &p, int &q) {
 
 // Rotation annihilating a_pq: angle from FP32, (c, s) normalised in FP64 by two Newton steps.
 __device__ __forceinline__ void g_jacobi_cs(double app, double aqq, double apq, double &c, double &s) {
-    const float d = (float)(aqq - app);
-    const float o = 2.0f * (float)apq;
+    const float d = d2f_steer(aqq - app);
+    const float o = 2.0f * d2f_steer(apq);
     float t = 0.0f;
     if (o != 0.0f) t = o / (d + copysignf(sqrtf(fmaf(d, d, o * o)), d));
     const float cf = rsqrtf(fmaf(t, t, 1.0f));
-    c = (double)cf;
-    s = (double)(t * cf);
+    c = f2d_steer(cf);
+    s = f2d_steer(t * cf);
     for (int it = 0; it < 2; ++it) {
         const double nrm = fma(c, c, s * s);
         const double f = fma(-0.5, nrm, 1.5);
@@ -421,10 +421,10 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
                        A[oi * LD + vi] = v;
                        A[vi * LD + oi] = v;
                        if (!abs_lt(v, G_EIG_TOL)) small = false;
-                       float kf = (float)v / (float)(diag[oi] - diag[vi]);
+                       float kf = d2f_steer(v) / d2f_steer(diag[oi] - diag[vi]);
                        if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
                        kmax = fmaxf(kmax, fabsf(kf));
-                       Kc[e] = (double)kf;   // K(v, o) at [o][v]
+                       Kc[e] = f2d_steer(kf);   // K(v, o) at [o][v]
                    });
         const bool eok = g.all(small);
         const bool cold_first = !a.have_warm && it == 1;
@@ -560,14 +560,14 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
                     const int hw = (hs + NH - 1 - w) % NH;
                     float s = 0.f;
                     for (int at = 0; at < nat; ++at) {
-                        const float du = (float)(hf[hu * AM + at] - hf[hs * AM + at]);
-                        const float dw = (float)(hf[hw * AM + at] - hf[hs * AM + at]);
+                        const float du = d2f_steer(hf[hu * AM + at] - hf[hs * AM + at]);
+                        const float dw = d2f_steer(hf[hw * AM + at] - hf[hs * AM + at]);
                         s = fmaf(du, dw, s);
                     }
                     Mx[u][w] = s;
                 }
                 for (int at = 0; at < nat; ++at)
-                    b = fmaf(-(float)(hf[hu * AM + at] - hf[hs * AM + at]), (float)hf[hs * AM + at], b);
+                    b = fmaf(-d2f_steer(hf[hu * AM + at] - hf[hs * AM + at]), d2f_steer(hf[hs * AM + at]), b);
                 bv[u] = b;
             }
             float dmax = 0.f;
@@ -598,7 +598,7 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
                 for (int u = 0; u < m; ++u)
                     if (!(fabsf(x[u]) < 50.f)) ok = false;
             }
-            for (int u = 0; u < GNHIST - 1; ++u) th[u] = (ok && u < m) ? (double)x[u] : 0.0;
+            for (int u = 0; u < GNHIST - 1; ++u) th[u] = (ok && u < m) ? f2d_steer(x[u]) : 0.0;
         }
         g.sync();
         if (j < nat) {

@@ -116,13 +116,13 @@ __device__ __forceinline__ void rr_pair(int k, int r, int n, int &p, int &q) {
 // Rotation (c, s) that annihilates a_pq: tan(phi) = t from the FP32 quadratic, then (c, s) made
 // orthonormal in FP64 by two Newton steps on 1/sqrt(c^2 + s^2).
 __device__ __forceinline__ void jacobi_cs(double app, double aqq, double apq, double &c, double &s) {
-    const float d = (float)(aqq - app);
-    const float o = 2.0f * (float)apq;
+    const float d = d2f_steer(aqq - app);
+    const float o = 2.0f * d2f_steer(apq);
     float t = 0.0f;
     if (o != 0.0f) t = o / (d + copysignf(sqrtf(fmaf(d, d, o * o)), d));
     const float cf = rsqrtf(fmaf(t, t, 1.0f));
-    c = (double)cf;
-    s = (double)(t * cf);
+    c = f2d_steer(cf);
+    s = f2d_steer(t * cf);
     for (int it = 0; it < 2; ++it) {
         const double nrm = fma(c, c, s * s);
         const double f = fma(-0.5, nrm, 1.5);
@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
         __syncwarp();
         // aufbau occupation from the diagonal of A
         if (work) {
-            m.diagf[j] = (float)m.A[j * LD + j];
+            m.diagf[j] = d2f_steer(m.A[j * LD + j]);
             const long long kj = order_key(m.A[j * LD + j]);
             int rank = 0;
             for (int i = 0; i < NORB; ++i) {
@@ -467,9 +467,9 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
                 const int k = __ffs(om) - 1;
                 const double akj = m.A[j * LD + k];
                 if (!abs_lt(akj, EIG_TOL)) small = false;
-                float kf = (float)akj / (dj - m.diagf[k]);
+                float kf = d2f_steer(akj) / (dj - m.diagf[k]);
                 if (!(fabsf(kf) <= 1e30f)) kf = 1e30f;   // degenerate or non-finite: Jacobi path
-                m.P[j * LD + k] = (double)kf;
+                m.P[j * LD + k] = f2d_steer(kf);
                 kmax = fmaxf(kmax, fabsf(kf));
             }
             m.eok[j] = small;
@@ -642,9 +642,9 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
                 const int h1 = (hs + NHIST - 1) % NHIST, h2 = (hs + NHIST - 2) % NHIST;
                 float a11 = 0.f, a12 = 0.f, a22 = 0.f, b1 = 0.f, b2 = 0.f;
                 for (int at = 0; at < NAT; ++at) {
-                    const float f0 = (float)m.hf[hs][at];
-                    const float d1 = (float)(m.hf[h1][at] - m.hf[hs][at]);
-                    const float d2 = h >= 3 ? (float)(m.hf[h2][at] - m.hf[hs][at]) : 0.f;
+                    const float f0 = d2f_steer(m.hf[hs][at]);
+                    const float d1 = d2f_steer(m.hf[h1][at]) - f0;
+                    const float d2 = h >= 3 ? d2f_steer(m.hf[h2][at]) - f0 : 0.f;
                     a11 = fmaf(d1, d1, a11);
                     a12 = fmaf(d1, d2, a12);
                     a22 = fmaf(d2, d2, a22);
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
                     m.q[j] = m.qout[j];
                 } else {
                     const int h1 = (hs + NHIST - 1) % NHIST, h2 = (hs + NHIST - 2) % NHIST;
-                    const double t1 = th1, t2 = th2;
+                    const double t1 = f2d_steer(th1), t2 = f2d_steer(th2);
                     const double q0 = m.hq[hs][j], f0 = m.hf[hs][j];
                     double qb = q0, fb = f0;
                     if (h >= 2) { qb = fma(t1, m.hq[h1][j] - q0, qb); fb = fma(t1, m.hf[h1][j] - f0, fb); }

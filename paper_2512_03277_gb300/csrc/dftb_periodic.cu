@@ -239,13 +239,13 @@ __device__ __forceinline__ void p_pair(int k, int r, int n, int &p, int &q) {
 
 // Rotation annihilating a_pq: angle from FP32, (c, s) normalised in FP64 by two Newton steps.
 __device__ __forceinline__ void p_jacobi_cs(double app, double aqq, double apq, double &c, double &s) {
-    const float d = (float)(aqq - app);
-    const float o = 2.0f * (float)apq;
+    const float d = d2f_steer(aqq - app);
+    const float o = 2.0f * d2f_steer(apq);
     float t = 0.0f;
     if (o != 0.0f) t = o / (d + copysignf(sqrtf(fmaf(d, d, o * o)), d));
     const float cf = rsqrtf(fmaf(t, t, 1.0f));
-    c = (double)cf;
-    s = (double)(t * cf);
+    c = f2d_steer(cf);
+    s = f2d_steer(t * cf);
     for (int it = 0; it < 2; ++it) {
         const double nrm = fma(c, c, s * s);
         const double f = fma(-0.5, nrm, 1.5);
@@ -658,11 +658,11 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
                                      [&](int k, int o) { return Y[sh.occ_list[o] * n + k]; },
                                      [&](int v, int o, double val) {
                                          if (!abs_lt(val, P_EIG_TOL)) small = false;
-                                         const float den = (float)(sh.diag[sh.occ_list[o]] - sh.diag[sh.virt_list[v]]);
-                                         float kf = (float)val / den;
+                                         const float den = d2f_steer(sh.diag[sh.occ_list[o]] - sh.diag[sh.virt_list[v]]);
+                                         float kf = d2f_steer(val) / den;
                                          if (!(fabsf(kf) <= 1e3f)) kf = copysignf(1e3f, kf);
                                          kmax = fmaxf(kmax, fabsf(kf));
-                                         Xg[o * nv + v] = (double)kf;
+                                         Xg[o * nv + v] = f2d_steer(kf);
                                      });
             eok = blk_all(small);
             // X^T X and X X^T (lower triangles)
@@ -773,14 +773,14 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
                     const int hw = (hs + NH - 1 - w) % NH;
                     float sacc = 0.f;
                     for (int at = 0; at < nat; ++at) {
-                        const float du = (float)(sh.hf[hu][at] - sh.hf[hs][at]);
-                        const float dw = (float)(sh.hf[hw][at] - sh.hf[hs][at]);
+                        const float du = d2f_steer(sh.hf[hu][at] - sh.hf[hs][at]);
+                        const float dw = d2f_steer(sh.hf[hw][at] - sh.hf[hs][at]);
                         sacc = fmaf(du, dw, sacc);
                     }
                     Mx[u][w] = sacc;
                 }
                 for (int at = 0; at < nat; ++at)
-                    b = fmaf(-(float)(sh.hf[hu][at] - sh.hf[hs][at]), (float)sh.hf[hs][at], b);
+                    b = fmaf(-d2f_steer(sh.hf[hu][at] - sh.hf[hs][at]), d2f_steer(sh.hf[hs][at]), b);
                 bv[u] = b;
             }
             float dmax = 0.f;
@@ -811,7 +811,7 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, PSh
                 for (int u = 0; u < m; ++u)
                     if (!(fabsf(x[u]) < 50.f)) ok = false;
             }
-            for (int u = 0; u < PHIST - 1; ++u) sh.th[u] = (ok && u < m) ? (double)x[u] : 0.0;
+            for (int u = 0; u < PHIST - 1; ++u) sh.th[u] = (ok && u < m) ? f2d_steer(x[u]) : 0.0;
         }
         __syncthreads();
         if (j < nat) {
