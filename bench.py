@@ -473,8 +473,12 @@ def _measure_arm(torch, P, w, args, ws, local, precision, charge_model, mlp, flu
     shares = {nm: float(phase_ms[i] / max(phase_ms.sum(), 1e-30)) for i, nm in enumerate(names)}
     mixed = precision == "mixed"
     fd = charge_model in ("born_fd", "born_central")
+    # phase scopes count calls; some calls launch more than one kernel: the forward product and its
+    # reduction, the moving-position back product (one launch per half-flow), the network's three
+    # kernels, the finite-difference copies after the Born refresh
     launches = int(phase_cnt.sum()) + (int(phase_cnt[3]) if fd else 0) + \
-        2 * (int(phase_cnt[3]) if charge_model == "born_mlp" else 0) + (int(phase_cnt[0]) if mixed else 0)
+        2 * (int(phase_cnt[3]) if charge_model == "born_mlp" else 0) + (int(phase_cnt[0]) if mixed else 0) + \
+        (int(phase_cnt[0]) if mixed and args.mode_positions == "com" else 0)
     arm = {
         "value": value, "unit": "molecule-steps/s", "ms_per_step": max_ms / args.steps,
         "precision": precision, "charge_model": charge_model,

@@ -102,8 +102,12 @@ enum { CAVMD_PHOTON_RELAXED = 0, CAVMD_PHOTON_ZERO = 1 };
  * centre of mass R_n(t) = sum_j m_j r_j / m_n, regenerated after every drift. Then D_a also
  * depends on the positions through u_a(R_n), and each nucleus j of cell n feels the extra force
  * (m_j / m_n) M_n sum_a lambda_a (omega_a q_a - D_a) grad u_a(R_n). This extends the paper,
- * whose boxes do not move. FP64 coupling only: with CAVMD_PREC_MIXED_BF16X3, cavmd_init returns
- * CAVMD_ERR_UNSUPPORTED. Each step regenerates M x N mode functions and their sines (FP64 sincos). */
+ * whose boxes do not move. With the FP64 coupling each step regenerates M x N mode functions and
+ * their sines (FP64, by angle addition from the reference positions). With
+ * CAVMD_PREC_MIXED_BF16X3 each step rebuilds the factorised phase panels at the centres of mass
+ * (FP32 phases from an exact fixed-point reduction of the angle, relative error about 3 * 2^-24)
+ * and the back product runs once per half-flow, also forming the gradients of the field.
+ * Only with CAVMD_SPLIT_PHOTON_EXACT: other splittings return CAVMD_ERR_UNSUPPORTED. */
 enum { CAVMD_MODES_FIXED = 0, CAVMD_MODES_CENTRE_OF_MASS = 1 };
 
 /* The cells. Cell c owns atoms cell_offset[c] .. cell_offset[c+1]-1. Cells are

@@ -13,35 +13,29 @@
 // From these the finalisation forms the mean-removed unbiased estimator exactly:
 //   C(l) = [P(l) - xbar (A(l) + B(l)) + (n - l) xbar^2] / (n - l),  xbar = S / n,
 //   P(l) = sum_{t=l}^{n-1} x_t x_{t-l},  A(l) = S - (last l samples),  B(l) = S - (first l samples).
-// One block per channel; every sum runs in a fixed order, so the result is deterministic.
+// One block per photon channel; the total dipole is summed over slices of the cells by all blocks and
+// finished by the last one. Every sum runs in a fixed order, so the result is deterministic.
 #include "cavmd_internal.cuh"
 
 namespace {
 
 constexpr int ACF_THREADS = 256;
 
-__global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const double *__restrict__ q_sync,
-                                                     const double *__restrict__ M_cell, int N) {
-    __shared__ double red[ACF_THREADS / 32];
-    __shared__ double xs;
-    __shared__ bool last;
-    const int c = blockIdx.x;
-    const long long t = *a.n;   // every block reads it before the last block advances it
-    if (c < a.M) {
-        if (threadIdx.x == 0) xs = q_sync[c];
-    } else {   // total dipole: fixed-order block reduction over the cells
-        double s = 0.0;
-        for (int n = threadIdx.x; n < N; n += ACF_THREADS) s += M_cell[n];
+// Block reduction in a fixed order (threads strided, then a shuffle tree, then the warps in order).
+__device__ double block_sum(double s, double *red) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(CAVMD_FULL_MASK, s, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double v = 0.0;
-            for (int w = 0; w < ACF_THREADS / 32; ++w) v += red[w];
-            xs = v;
-        }
-    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(CAVMD_FULL_MASK, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double v = 0.0;
+    for (int w = 0; w < ACF_THREADS / 32; ++w) v += red[w];
+    __syncthreads();
+    return v;
+}
+
+// One sample of channel c: store it in the ring (and the head while t < L), add it to the running
+// sum, and fold the B newest samples into the lag products when the block of B is complete.
+__device__ void acf_push(const AcfArgs &a, int c, long long t, double xs) {
     const int L = a.L, R = a.L + a.B;
     double *ring = a.ring + (size_t)c * R;
     if (threadIdx.x == 0) {
@@ -59,12 +53,38 @@ __global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const doub
             acc[l] = v;
         }
     }
+}
+
+// Grid: G >= C blocks. Block b < M pushes the photon coordinate q_b; every block also sums its slice
+// of the per-cell dipoles into part[b]; the last block to finish (ticket) sums the G partial sums in
+// block order into the total dipole, pushes it as channel M and advances the sample counter.
+__global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const double *__restrict__ q_sync,
+                                                     const double *__restrict__ M_cell, int N) {
+    __shared__ double red[ACF_THREADS / 32];
+    __shared__ bool last;
+    const int b = blockIdx.x;
+    const long long t = *a.n;   // every block reads it before the last block advances it
+    const int slice = (N + a.G - 1) / a.G;
+    const int n0 = min(N, b * slice), n1 = min(N, n0 + slice);
+    double s = 0.0;
+    for (int n = n0 + threadIdx.x; n < n1; n += ACF_THREADS) s += M_cell[n];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) a.part[b] = s;
+    if (b < a.M) acf_push(a, b, t, q_sync[b]);
+    __threadfence();
+    __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned tk = atomicAdd(a.ticket, 1u);
         last = (tk == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int i = threadIdx.x; i < a.G; i += ACF_THREADS) v += __ldcg(a.part + i);
+    v = block_sum(v, red);
+    acf_push(a, a.M, t, v);
+    if (threadIdx.x == 0) {
         *a.n = t + 1;
         *a.ticket = 0u;
     }
@@ -98,7 +118,7 @@ __global__ void k_acf_finalize(const AcfArgs a, double *__restrict__ out) {
 }  // namespace
 
 cudaError_t launch_acf(const AcfArgs &a, const double *q_sync, const double *M_cell, int N, cudaStream_t st) {
-    k_acf<<<a.C, ACF_THREADS, 0, st>>>(a, q_sync, M_cell, N);
+    k_acf<<<a.G, ACF_THREADS, 0, st>>>(a, q_sync, M_cell, N);
     return cudaGetLastError();
 }
 

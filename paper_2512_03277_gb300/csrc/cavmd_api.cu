@@ -54,7 +54,7 @@ struct cavmd_ctx {
     RsArgs rsa{};
     PbcPlan pplan{};
     double *d_Us = nullptr, *d_Wk2 = nullptr, *d_Wk1 = nullptr, *d_watom = nullptr;
-    double *d_G1 = nullptr, *d_Ginst = nullptr;
+    double *d_G1 = nullptr, *d_Ginst = nullptr, *d_G2 = nullptr;   // [N][3] position-term gradients
     double *d_U0 = nullptr, *d_Us0 = nullptr;   // mode functions and sines at the reference positions
     std::vector<double> h_watom;             // m_j / m_n
     GenericPlan gplan{};
@@ -270,9 +270,17 @@ cudaError_t run_tc_forward(cavmd_ctx *c) {
 }
 
 // Back product for the second half-flow (Wt2 -> E2) and, when `first`, the next first half-flow
-// (Wt1 -> E1); with second = false only Wt1 -> E1.
+// (Wt1 -> E1); with second = false only Wt1 -> E1. Moving mode positions take one launch per
+// half-flow, each with the gradients (G2, G1).
 cudaError_t run_tc_back(cavmd_ctx *c, bool second, bool first) {
     PhaseScope ps(c, 2);
+    if (c->moving) {
+        cudaError_t e = cudaSuccess;
+        if (second) e = launch_tc_back(c->tc, c->d_Wt2, nullptr, c->d_E2, nullptr, c->d_status, c->stream, c->d_G2);
+        if (e == cudaSuccess && first)
+            e = launch_tc_back(c->tc, c->d_Wt1, nullptr, c->d_E1, nullptr, c->d_status, c->stream, c->d_G1);
+        return e;
+    }
     if (second)
         return launch_tc_back(c->tc, c->d_Wt2, first ? c->d_Wt1 : nullptr, c->d_E2, first ? c->d_E1 : nullptr,
                               c->d_status, c->stream);
@@ -284,9 +292,11 @@ cudaError_t run_photon(cavmd_ctx *c, int flags) {
     return launch_photon(c->sa, flags, c->stream);
 }
 
-// Mode functions and their sines at the current cell centres of mass (moving mode positions).
+// Mode functions and their sines at the current cell centres of mass (moving mode positions); with
+// the tensor-core coupling, its phase panels.
 cudaError_t run_modes(cavmd_ctx *c) {
     PhaseScope ps(c, 1);
+    if (c->mixed) return launch_tc_panels_com(c->tc, c->d_r, c->d_mass, c->d_off, c->stream);
     return launch_mode_functions_com(c->d_k, c->d_R, c->d_U0, c->d_Us0, c->d_r, c->d_mass, c->d_off, c->M, c->N,
                                      c->d_U, c->d_Us, c->stream);
 }
@@ -664,8 +674,8 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         return fail(c, CAVMD_ERR_INVALID_ARG, "jacobi_max_sweeps must be 0..1000");
     if (o->mode_positions != CAVMD_MODES_FIXED && o->mode_positions != CAVMD_MODES_CENTRE_OF_MASS)
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad mode_positions");
-    if (o->mode_positions == CAVMD_MODES_CENTRE_OF_MASS && o->precision != CAVMD_PREC_FP64)
-        return fail(c, CAVMD_ERR_UNSUPPORTED, "moving mode positions need the FP64 coupling");
+    if (o->mode_positions == CAVMD_MODES_CENTRE_OF_MASS && o->splitting != CAVMD_SPLIT_PHOTON_EXACT)
+        return fail(c, CAVMD_ERR_UNSUPPORTED, "moving mode positions take the photon-exact splitting");
     if (o->precision == CAVMD_PREC_MIXED_BF16X3) {
         int Kx, Ky2;
         double dkx, dky;
@@ -769,9 +779,13 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     if (!c->mixed) AL(c->d_U, (size_t)M * N);
     c->moving = c->opt.mode_positions == CAVMD_MODES_CENTRE_OF_MASS;
     if (c->moving) {
-        AL(c->d_Us, (size_t)M * N); AL(c->d_Wk2, 3 * M); AL(c->d_Wk1, 3 * M); AL(c->d_watom, NA);
-        AL(c->d_U0, (size_t)M * N); AL(c->d_Us0, (size_t)M * N);
-        AL(c->d_G1, 3 * N); AL(c->d_Ginst, 3 * N);
+        if (!c->mixed) {   // FP64 mode functions and sines (the tensor-core path forms phase panels)
+            AL(c->d_Us, (size_t)M * N); AL(c->d_Wk2, 3 * M); AL(c->d_Wk1, 3 * M);
+            AL(c->d_U0, (size_t)M * N); AL(c->d_Us0, (size_t)M * N);
+        } else {
+            AL(c->d_G2, 3 * N);
+        }
+        AL(c->d_watom, NA); AL(c->d_G1, 3 * N); AL(c->d_Ginst, 3 * N);
         c->h_watom.assign(NA, 0.0);
         for (int n = 0; n < N; ++n) {
             double mt = 0.0;
@@ -834,7 +848,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 8 * c->opt.energy_history, st));
     CK(cudaMemsetAsync(c->d_q, 0, sizeof(double) * M, st));
     CK(cudaMemsetAsync(c->d_pq, 0, sizeof(double) * M, st));
-    if (c->moving) {
+    if (c->moving && !c->mixed) {
         CK(launch_mode_functions_pair(c->d_k, c->d_phi, c->d_R, M, N, c->d_U0, c->d_Us0, st));
         CK(cudaMemcpyAsync(c->d_U, c->d_U0, sizeof(double) * M * N, cudaMemcpyDeviceToDevice, st));
     } else if (!c->mixed) {
@@ -857,7 +871,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         CK(cudaMemsetAsync(c->d_Wt2, 0, sizeof(float) * 128 * p.KY, st));
         CK(cudaMemsetAsync(c->d_Wt1, 0, sizeof(float) * 128 * p.KY, st));
         CK(tc_prepare(p.KY));
-        CK(launch_tc_panels(p, c->d_R, st));
+        CK(launch_tc_panels(p, c->d_R, st));   // moving positions: the zero padding; run_modes fills the rest
     }
 
     c->rs = c->opt.splitting == CAVMD_SPLIT_REAL_SPACE;
@@ -901,6 +915,8 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         const size_t cl = (size_t)a.C * a.L;
         AL(a.ring, (size_t)a.C * (a.L + a.B)); AL(a.head, cl); AL(a.acc, cl); AL(a.sum, a.C); AL(a.n, 1);
         AL(a.ticket, 1);
+        a.G = std::max(a.C, std::min(16384, (c->N + 31) / 32));
+        AL(a.part, a.G);
         AL(c->d_acf_out, cl);
         CK(reset_acf(c));
     }
@@ -997,6 +1013,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     s.Us = c->d_Us; s.kvec = c->d_k; s.Wk2 = c->d_Wk2; s.Wk1 = c->d_Wk1; s.w_atom = c->d_watom;
     s.G1store = c->d_G1; s.G1in = c->d_G1;   // all NULL with fixed mode positions
+    s.G2in = c->d_G2;                          // tensor-core coupling with moving mode positions only
     s.paper = c->opt.splitting == CAVMD_SPLIT_PAPER || c->opt.splitting == CAVMD_SPLIT_STRANG;
     s.strang = c->opt.splitting == CAVMD_SPLIT_STRANG;
     d.E_open = nullptr;   // set for the first evaluation of a call (water kernel)
@@ -1291,7 +1308,8 @@ int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
                 }
             }
             CK(cudaMemcpy(c->d_Wt1, Wt.data(), sizeof(float) * Wt.size(), cudaMemcpyHostToDevice));
-            CK(launch_tc_back(p, c->d_Wt1, nullptr, c->d_Einst, nullptr, c->d_status, c->stream));
+            CK(launch_tc_back(p, c->d_Wt1, nullptr, c->d_Einst, nullptr, c->d_status, c->stream,
+                              c->moving ? c->d_Ginst : nullptr));
         } else {
             CK(cudaMemcpy(c->d_W1, W.data(), sizeof(double) * c->M, cudaMemcpyHostToDevice));
             CK(launch_field_only(c->d_U, c->d_W1, c->M, c->N, c->d_Einst, c->stream));
@@ -1299,7 +1317,7 @@ int cavmd_get_eval(cavmd_ctx *c, cavmd_eval *o) {
         CK(cudaStreamSynchronize(c->stream));
         std::vector<double> E(N), F(3 * NA), b(3 * NA), G, Mn;
         if (c->moving) {   // position term: (m_j / m_n) M_n sum_a W_a grad u_a(R_n)
-            CK(launch_field_grad_only(c->d_Us, c->d_W1, c->d_k, c->M, c->N, c->d_Ginst, c->stream));
+            if (!c->mixed) CK(launch_field_grad_only(c->d_Us, c->d_W1, c->d_k, c->M, c->N, c->d_Ginst, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             G.resize(3 * N);
             Mn.resize(N);

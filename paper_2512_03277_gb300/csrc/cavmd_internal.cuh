@@ -117,6 +117,7 @@ struct StepArgs {
     const double *w_atom;      // [n_atoms] m_j / m_n
     double *G1store;           // [N][3] G_n of the next first half-flow, kept for the next call
     const double *G1in;        // [N][3] G_n of the opening first half-flow (FLD_E_GIVEN)
+    const double *G2in;        // [N][3] G_n of the second half-flow (FLD_E_GIVEN, tensor-core coupling)
     int paper;                 // 1: kicks with the instantaneous force (CAVMD_SPLIT_PAPER or STRANG), 0: exact half-flows
     int strang;                // 1: the modes turn between the two kicks (CAVMD_SPLIT_STRANG)
 };
@@ -149,8 +150,13 @@ size_t tc_back_smem(int KY);
 cudaError_t tc_prepare(int KY);   // kernel attributes (shared-memory size), once per plan
 cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st);
 cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsigned *status, cudaStream_t st);
+// Back product: E2 (and E1 when Wt1 is given) from the weight matrices; with G (moving mode
+// positions, Wt1 = NULL, E1 = NULL) also the gradients G[3n + k] of E2 at the cells' centres.
 cudaError_t launch_tc_back(const TcPlan &p, const float *Wt2, const float *Wt1, double *E2, double *E1,
-                           unsigned *status, cudaStream_t st);
+                           unsigned *status, cudaStream_t st, double *G = nullptr);
+// Phase panels at the cells' centres of mass (moving mode positions), every step.
+cudaError_t launch_tc_panels_com(const TcPlan &p, const double *r, const double *mass, const int *cell_offset,
+                                 cudaStream_t st);
 
 // Conversions between FP64 and FP32 on the integer pipe, for quantities that only steer an
 // iteration (generator entries, rotation angles, mixing coefficients): on GB300 the hardware
@@ -211,6 +217,8 @@ struct AcfArgs {
     double *sum;                 // [C] running sums
     long long *n;                // samples so far
     unsigned *ticket;            // last-block counter
+    int G;                       // blocks per sample (>= C): each sums a slice of the cell dipoles
+    double *part;                // [G] those slice sums
 };
 cudaError_t launch_acf(const AcfArgs &a, const double *q_sync, const double *M_cell, int N, cudaStream_t st);
 cudaError_t launch_acf_finalize(const AcfArgs &a, double *out, cudaStream_t st);

@@ -450,12 +450,15 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(const StepArgs a, const i
     if (n < a.N) {
         const double e2 = (flags & FLD_SECOND) ? a.E2in[n] : 0.0;
         const double e1 = (flags & FLD_FIRST) ? a.E1in[n] : 0.0;
-        if (a.G1in) {   // moving mode positions: the opening first half-flow only
-            const double g0[3] = {0.0, 0.0, 0.0};
-            const double g1[3] = {a.G1in[3 * n], a.G1in[3 * n + 1], a.G1in[3 * n + 2]};
+        if (a.G1in) {   // moving mode positions (G2 given by the tensor-core back product only)
+            double g2[3] = {0.0, 0.0, 0.0}, g1[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < 3; ++k) {
+                if ((flags & FLD_SECOND) && a.G2in) g2[k] = a.G2in[3 * n + k];
+                if (flags & FLD_FIRST) g1[k] = a.G1in[3 * n + k];
+            }
             const double Mn = a.M_cell[n];
             for (int j = a.cell_offset[n]; j < a.cell_offset[n + 1]; ++j)
-                kin += kick_atom_moving(a, flags, j, e2, e1, g0, g1, a.w_atom[j] * Mn);
+                kin += kick_atom_moving(a, flags, j, e2, e1, g2, g1, a.w_atom[j] * Mn);
         } else {
             kick_cell(a, flags, n, e2, e1, kin);
         }

@@ -34,40 +34,119 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Init: phase panels. Forward A (hi, lo) and back-epilogue A (FP32) from the x phases; forward B
-// source panel (FP32) and back Y (hi, lo) from the y phases. Tile-major core-matrix order.
-__global__ void k_tc_panels(int N, int Npad, int Kx, int Ky2, int KY, double dkx, double dky,
-                            const double *__restrict__ R, __nv_bfloat16 *__restrict__ Ahi,
-                            __nv_bfloat16 *__restrict__ Alo, float *__restrict__ Af, float *__restrict__ Bsrc,
-                            __nv_bfloat16 *__restrict__ Yhi, __nv_bfloat16 *__restrict__ Ylo) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= Npad) return;
-    const bool real = n < N;
-    const double tx = real ? dkx * R[3 * n] : 0.0, ty = real ? dky * R[3 * n + 1] : 0.0;
-    // forward A: tile t = n / 64, row i, k = n % 64 (LBO = 16 row groups x 128 B)
-    const int t = n / FWD_CELLS, kk = n - t * FWD_CELLS;
-    for (int i = 0; i < KXP; ++i) {
-        double v = 0.0;
-        if (real && i < 2 * Kx) v = (i < Kx) ? cos(i * tx) : sin((i - Kx) * tx);
+// Stores of one phase value into the panels, in tile-major core-matrix order.
+struct Panels {
+    int Npad, KY;
+    __nv_bfloat16 *Ahi, *Alo, *Yhi, *Ylo;
+    float *Af, *Bsrc;
+    // x phase row i of cell n: forward A (hi, lo; tile t = n / 64, K = n % 64, LBO = 16 row groups x
+    // 128 B) and the FP32 back-epilogue panel Af[i][n]
+    __device__ __forceinline__ void put_x(int n, int i, float v) const {
+        const int t = n / FWD_CELLS, kk = n - t * FWD_CELLS;
         __nv_bfloat16 hi, lo;
-        split_bf16((float)v, hi, lo);
+        split_bf16(v, hi, lo);
         const size_t e = (size_t)t * KXP * FWD_CELLS + tc::core_offset(i, kk, (KXP / 8) * 128) / 2;
         Ahi[e] = hi;
         Alo[e] = lo;
-        Af[(size_t)i * Npad + n] = (float)v;
+        Af[(size_t)i * Npad + n] = v;
     }
-    for (int j = 0; j < KY; ++j) {
-        double v = 0.0;
-        if (real && j < 2 * Ky2) v = (j < Ky2) ? cos(j * ty) : sin((j - Ky2) * ty);
-        const size_t e = (size_t)t * KY * FWD_CELLS + tc::core_offset(j, kk, (KY / 8) * 128) / 2;
-        Bsrc[e] = (float)v;
-        // back Y: tile tb = n / 128, row = n % 128, k = j (LBO = 16 row groups x 128 B)
+    // y phase column j of cell n: forward B source (FP32, same tiles as A) and back Y (hi, lo; tile
+    // tb = n / 128, row n % 128, K = j)
+    __device__ __forceinline__ void put_y(int n, int j, float v) const {
+        const int t = n / FWD_CELLS, kk = n - t * FWD_CELLS;
+        Bsrc[(size_t)t * KY * FWD_CELLS + tc::core_offset(j, kk, (KY / 8) * 128) / 2] = v;
         const int tb = n / BACK_CELLS, rb = n - tb * BACK_CELLS;
         const size_t eb = (size_t)tb * BACK_CELLS * KY + tc::core_offset(rb, j, (BACK_CELLS / 8) * 128) / 2;
         __nv_bfloat16 hi, lo;
-        split_bf16((float)v, hi, lo);
+        split_bf16(v, hi, lo);
         Yhi[eb] = hi;
         Ylo[eb] = lo;
+    }
+};
+
+// Init: phase panels from the x and y phases in FP64 (cos / sin rounded once to FP32). Padding
+// rows, columns and cells are written as zeros.
+__global__ void k_tc_panels(int N, int Kx, int Ky2, double dkx, double dky, const double *__restrict__ R,
+                            const Panels P) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= P.Npad) return;
+    const bool real = n < N;
+    const double tx = real ? dkx * R[3 * n] : 0.0, ty = real ? dky * R[3 * n + 1] : 0.0;
+    for (int i = 0; i < KXP; ++i) {
+        double v = 0.0;
+        if (real && i < 2 * Kx) v = (i < Kx) ? cos(i * tx) : sin((i - Kx) * tx);
+        P.put_x(n, i, (float)v);
+    }
+    for (int j = 0; j < P.KY; ++j) {
+        double v = 0.0;
+        if (real && j < 2 * Ky2) v = (j < Ky2) ? cos(j * ty) : sin((j - Ky2) * ty);
+        P.put_y(n, j, (float)v);
+    }
+}
+
+// A phase angle held as a fraction of a turn in 64-bit fixed point (units of 2^-64 turn, modulo
+// one turn), from t turns in FP64: t - rint(t) is exact and so is its scaling by 2^63.
+__device__ __forceinline__ uint64_t turns_fixed(double t) {
+    const double g = t - rint(t);
+    return (uint64_t)__double2ll_rn(g * 0x1p63) << 1;
+}
+
+// cos and sin of the angle j T (T in fixed-point turns). The product j T is exact modulo one turn;
+// its nearest quarter turn q comes from the top two bits (after adding 1/8 turn) and the remainder r,
+// |r| <= 1/8 turn, is converted to FP32 with integer operations only (normalised by its leading
+// zeros, significand truncated: relative error below 2^-23, also near the zeros of cos and sin);
+// sincospif evaluates the remainder (CUDA states at most 1 ulp) and the quarter turn permutes and
+// negates the pair exactly: (cos, sin)(q/4 turn + r) = (c, s), (-s, c), (-c, -s), (s, -c).
+__device__ __forceinline__ void turn_sincos(uint64_t T, unsigned j, float &c, float &s) {
+    const uint64_t u = T * (uint64_t)j + (1ull << 61);
+    const unsigned q = (unsigned)(u >> 62);
+    const long long rem = (long long)(u & ((1ull << 62) - 1ull)) - (1ll << 61);   // r in units of 2^-64 turn
+    const unsigned long long a = rem < 0 ? (unsigned long long)(-rem) : (unsigned long long)rem;
+    float x = 0.0f;   // 2 r: the remainder in half turns
+    if (a != 0ull) {
+        const int lz = __clzll((long long)a);   // >= 3, as a < 2^61
+        const unsigned long long m = a << lz;
+        const uint32_t bits = ((uint32_t)(127 - lz) << 23) | ((uint32_t)(m >> 40) & 0x7fffffu);
+        x = __uint_as_float(bits | (rem < 0 ? 0x80000000u : 0u));
+    }
+    float sr, cr;
+    sincospif(x, &sr, &cr);
+    switch (q) {
+        case 0: c = cr; s = sr; break;
+        case 1: c = -sr; s = cr; break;
+        case 2: c = -cr; s = -sr; break;
+        default: c = sr; s = -cr; break;
+    }
+}
+
+// Every step with moving mode positions: the phase panels at the cells' centres of mass
+// R_n = sum_j m_j r_j / m_n (summed over the cell's atoms in order), with the phases cos | sin(jx dkx X_n)
+// and cos | sin(jy dky Y_n) from turn_sincos (the FP32 values carry a relative error of at most
+// about 3 * 2^-24). Only the real rows and columns of the real cells are written: the padding keeps
+// the zeros of the context's initial panels.
+__global__ void k_tc_panels_com(int N, int Kx, int Ky2, double x_turns, double y_turns, const double *__restrict__ r,
+                                const double *__restrict__ mass, const int *__restrict__ off, const Panels P) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    double mt = 0.0, x0 = 0.0, x1 = 0.0;
+    for (int j = off[n]; j < off[n + 1]; ++j) {
+        const double m = mass[j];
+        mt += m;
+        x0 = fma(m, r[3 * j], x0);
+        x1 = fma(m, r[3 * j + 1], x1);
+    }
+    const uint64_t Tx = turns_fixed(x0 / mt * x_turns), Ty = turns_fixed(x1 / mt * y_turns);
+    for (int jx = 0; jx < Kx; ++jx) {
+        float c, sn;
+        turn_sincos(Tx, (unsigned)jx, c, sn);
+        P.put_x(n, jx, c);
+        P.put_x(n, Kx + jx, sn);
+    }
+    for (int jy = 0; jy < Ky2; ++jy) {
+        float c, sn;
+        turn_sincos(Ty, (unsigned)jy, c, sn);
+        P.put_y(n, jy, c);
+        P.put_y(n, Ky2 + jy, sn);
     }
 }
 
@@ -245,22 +324,31 @@ __global__ void k_tc_reduce(int n_part, int size, const double *__restrict__ par
 // with one thread per cell reading A coalesced (FP32 within each 32-row chunk, FP64 across chunks).
 // The weights are split into BF16 hi / lo once per CTA; each tile's Y panels arrive by bulk copy,
 // issued as soon as the previous tile's MMAs have finished, so the copy overlaps the epilogue.
-template <int KY>
+//
+// GRAD (moving mode positions; one weight matrix Wt2): also the gradient of E_n with respect to the
+// cell's centre, G_n = sum_a W_a grad u_a(R_n) (k_a in plane, so G_z = 0). With the factorised
+// phases, d/dX acts on the x rows: d cos(jx thx)/dX = -jx dkx sin(jx thx), d sin(jx thx)/dX =
+// jx dkx cos(jx thx), so G_x = sum_i A'[i][n] D[n][i] with A'[jx] = -jx dkx A[Kx + jx] and
+// A'[Kx + jx] = jx dkx A[jx], in the same epilogue. d/dY acts on the y columns; moved onto the
+// weights, D'[n][i] = sum_j Y[n][j] V[i][j] with V[i][jy] = jy dky Wt[i][Ky2 + jy] and
+// V[i][Ky2 + jy] = -jy dky Wt[i][jy], a second accumulator, and G_y = sum_i A[i][n] D'[n][i].
+template <int KY, bool GRAD>
 __global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, int n_tiles, const float *__restrict__ Wt2,
                                                  const float *__restrict__ Wt1, const __nv_bfloat16 *__restrict__ Yhi,
                                                  const __nv_bfloat16 *__restrict__ Ylo, const float *__restrict__ Af,
                                                  double *__restrict__ E2, double *__restrict__ E1,
+                                                 double *__restrict__ G, int Kx, int Ky2, float dkx, float dky,
                                                  unsigned *__restrict__ status) {
     extern __shared__ __align__(1024) uint8_t smem[];
     constexpr uint32_t W_BYTES = KXP * KY * 2, Y_BYTES = BACK_CELLS * KY * 2;
     constexpr uint32_t LBO_W = (KXP / 8) * 128, LBO_Y = (BACK_CELLS / 8) * 128;
-    uint8_t *sw = smem;                       // [Wt2 hi][Wt2 lo][Wt1 hi][Wt1 lo]
+    uint8_t *sw = smem;                       // [Wt2 hi][Wt2 lo][Wt1 hi][Wt1 lo] (GRAD: [.. V hi][V lo])
     uint8_t *sy = smem + 4 * W_BYTES;         // [Y hi][Y lo]
     uint64_t *full = reinterpret_cast<uint64_t *>(sy + 2 * Y_BYTES);
     uint64_t *done = full + 1;
     uint32_t *slot = reinterpret_cast<uint32_t *>(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nacc = Wt1 ? 2 : 1;
+    const int nacc = (GRAD || Wt1) ? 2 : 1;
     if (warp == 0) tc::tmem_alloc(slot, 256);
     if (tid == 0) {
         tc::mbar_init(full, 1);
@@ -278,12 +366,24 @@ __global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, int n_tiles, c
     bool pending = (int)blockIdx.x < n_tiles;
     // weights: 8 consecutive K (j) of one row i per chunk, split into hi / lo (once per CTA)
     for (int w = 0; w < nacc; ++w) {
-        const float *Wt = w == 0 ? Wt2 : Wt1;
         for (int c = tid; c < KXP * KY / 8; c += 128) {
             const int kgrp = c / KXP, row = c - kgrp * KXP;
             const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_W);
             __align__(16) __nv_bfloat16 hi[8], lo[8];
-            for (int q = 0; q < 8; ++q) split_bf16(Wt[row * KY + 8 * kgrp + q], hi[q], lo[q]);
+            for (int q = 0; q < 8; ++q) {
+                const int j = 8 * kgrp + q;
+                float v;
+                if (!GRAD || w == 0) {
+                    v = (w == 0 ? Wt2 : Wt1)[row * KY + j];
+                } else if (j < Ky2) {
+                    v = ((float)j * dky) * Wt2[row * KY + Ky2 + j];
+                } else if (j < 2 * Ky2) {
+                    v = -((float)(j - Ky2) * dky) * Wt2[row * KY + j - Ky2];
+                } else {
+                    v = 0.0f;
+                }
+                split_bf16(v, hi[q], lo[q]);
+            }
             *reinterpret_cast<uint4 *>(sw + (2 * w) * W_BYTES + off) = *reinterpret_cast<const uint4 *>(hi);
             *reinterpret_cast<uint4 *>(sw + (2 * w + 1) * W_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
         }
@@ -327,17 +427,48 @@ __global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, int n_tiles, c
             pending = true;
         }
         const int n = t * BACK_CELLS + tid;   // this thread's cell (TMEM lane)
-        for (int w = 0; w < nacc; ++w) {
-            double e = 0.0;
+        const uint32_t lanes = (uint32_t)(32 * warp) << 16;
+        if (GRAD) {
+            double e = 0.0, gx = 0.0, gy = 0.0;
             for (int c0 = 0; c0 < KXP; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(w * KXP + c0), v);
-                float s = 0.0f;
+                float v[32], vd[32];
+                tc::tmem_ld32(tmem + lanes + (uint32_t)c0, v);
+                tc::tmem_ld32(tmem + lanes + (uint32_t)(KXP + c0), vd);
+                float s = 0.0f, sx = 0.0f, sy2 = 0.0f;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) s = fmaf(Af[(size_t)(c0 + q) * Npad + n], v[q], s);
+                for (int q = 0; q < 32; ++q) {
+                    const int i = c0 + q;
+                    const float a = Af[(size_t)i * Npad + n];
+                    s = fmaf(a, v[q], s);
+                    sy2 = fmaf(a, vd[q], sy2);
+                    float ad = 0.0f;   // A'[i][n]
+                    if (i < Kx) ad = -((float)i * dkx) * Af[(size_t)(Kx + i) * Npad + n];
+                    else if (i < 2 * Kx) ad = ((float)(i - Kx) * dkx) * Af[(size_t)(i - Kx) * Npad + n];
+                    sx = fmaf(ad, v[q], sx);
+                }
                 e += (double)s;
+                gx += (double)sx;
+                gy += (double)sy2;
             }
-            if (n < N) (w == 0 ? E2 : E1)[n] = e;
+            if (n < N) {
+                E2[n] = e;
+                G[3 * n] = gx;
+                G[3 * n + 1] = gy;
+                G[3 * n + 2] = 0.0;
+            }
+        } else {
+            for (int w = 0; w < nacc; ++w) {
+                double e = 0.0;
+                for (int c0 = 0; c0 < KXP; c0 += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + lanes + (uint32_t)(w * KXP + c0), v);
+                    float s = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) s = fmaf(Af[(size_t)(c0 + q) * Npad + n], v[q], s);
+                    e += (double)s;
+                }
+                if (n < N) (w == 0 ? E2 : E1)[n] = e;
+            }
         }
         tc::fence_before_sync();
         __syncthreads();   // TMEM reads done before the next tile's MMAs
@@ -370,16 +501,32 @@ cudaError_t tc_prepare(int KY) {
 #define PREP_CASE(KYV)                                                        \
     case KYV:                                                                 \
         e = set_smem(k_tc_forward<KYV>, f);                                   \
-        if (e == cudaSuccess) e = set_smem(k_tc_back<KYV>, b);                \
+        if (e == cudaSuccess) e = set_smem(k_tc_back<KYV, false>, b);         \
+        if (e == cudaSuccess) e = set_smem(k_tc_back<KYV, true>, b);          \
         break;
     switch (KY) { PREP_CASE(16) PREP_CASE(32) PREP_CASE(48) PREP_CASE(64) PREP_CASE(96) PREP_CASE(128) }
 #undef PREP_CASE
     return e;
 }
 
+static Panels panels_of(const TcPlan &p) {
+    Panels P;
+    P.Npad = p.Npad;
+    P.KY = p.KY;
+    P.Ahi = p.Ahi; P.Alo = p.Alo; P.Yhi = p.Yhi; P.Ylo = p.Ylo; P.Af = p.Af; P.Bsrc = p.Bsrc;
+    return P;
+}
+
 cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st) {
-    k_tc_panels<<<(p.Npad + 127) / 128, 128, 0, st>>>(p.N, p.Npad, p.Kx, p.Ky2, p.KY, p.dkx, p.dky, R, p.Ahi, p.Alo,
-                                                      p.Af, p.Bsrc, p.Yhi, p.Ylo);
+    k_tc_panels<<<(p.Npad + 127) / 128, 128, 0, st>>>(p.N, p.Kx, p.Ky2, p.dkx, p.dky, R, panels_of(p));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_panels_com(const TcPlan &p, const double *r, const double *mass, const int *cell_offset,
+                                 cudaStream_t st) {
+    const double two_pi = 6.283185307179586;
+    k_tc_panels_com<<<(p.N + 127) / 128, 128, 0, st>>>(p.N, p.Kx, p.Ky2, p.dkx / two_pi, p.dky / two_pi, r, mass,
+                                                        cell_offset, panels_of(p));
     return cudaGetLastError();
 }
 
@@ -407,20 +554,24 @@ cudaError_t launch_tc_forward(const TcPlan &p, const double *Mc, double *G, unsi
 }
 
 cudaError_t launch_tc_back(const TcPlan &p, const float *Wt2, const float *Wt1, double *E2, double *E1,
-                           unsigned *status, cudaStream_t st) {
+                           unsigned *status, cudaStream_t st, double *G) {
     const size_t sm = tc_back_smem(p.KY);
     const int n_tiles = p.Npad / BACK_CELLS;
     const int grid = std::min(n_tiles, p.n_sm);
-    cudaError_t e = cudaSuccess;
-#define BACK_CASE(KYV)                                                                                    \
-    case KYV:                                                                                             \
-            k_tc_back<KYV><<<grid, 128, sm, st>>>(p.N, p.Npad, n_tiles, Wt2, Wt1, p.Yhi, p.Ylo, p.Af, E2, E1, status); \
+    const float fx = (float)p.dkx, fy = (float)p.dky;
+#define BACK_CASE(KYV)                                                                                        \
+    case KYV:                                                                                                 \
+        if (G)                                                                                                \
+            k_tc_back<KYV, true><<<grid, 128, sm, st>>>(p.N, p.Npad, n_tiles, Wt2, nullptr, p.Yhi, p.Ylo, p.Af, \
+                                                        E2, nullptr, G, p.Kx, p.Ky2, fx, fy, status);        \
+        else                                                                                                  \
+            k_tc_back<KYV, false><<<grid, 128, sm, st>>>(p.N, p.Npad, n_tiles, Wt2, Wt1, p.Yhi, p.Ylo, p.Af,  \
+                                                         E2, E1, nullptr, p.Kx, p.Ky2, fx, fy, status);      \
         break;
     switch (p.KY) {
         BACK_CASE(16) BACK_CASE(32) BACK_CASE(48) BACK_CASE(64) BACK_CASE(96) BACK_CASE(128)
         default: return cudaErrorInvalidValue;
     }
 #undef BACK_CASE
-    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

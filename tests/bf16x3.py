@@ -27,6 +27,18 @@ Back E_n = sum_i A[i][n] T[n][i], T = Wt Y^T over the KY <= 128 y-phase columns 
 accumulator: 8 K-steps x 3 MMAs = 24 MMAs, 24 * 2^-22 = 5.7e-6. The epilogue sums 32 rows at a
 time in FP32 (32 * 2^-24 = 1.9e-6) and the chunks in FP64. Total below 5.4e-5 of
 sum_a mag(a, n) |W_a| (W_a carries lambda_a): EPS_E = 6e-5.
+
+Moving mode positions. The panels are rebuilt every step at the centres of mass with FP32 phases
+from an exact fixed-point reduction of the angle: the remainder is truncated to FP32 (below 2^-23
+relative) and sincospif adds at most 1 ulp (2^-23 relative), so each phase factor carries up to
+2^-22 instead of 2^-24; with both factors of a term that adds 6 * 2^-24 = 3.6e-7 to either total.
+The field's gradient G_n = sum_a W_a grad u_a(R_n) (k_a in plane, G_z = 0) comes from the same
+products: G_x scales the x phase rows by -+ jx dkx in the FP32 epilogue, G_y uses weights scaled by
+-+ jy dky in FP32 (each scale and product adds 2^-24 twice). The magnitude it is bounded against is
+that of the derivative of the factorised phases,
+    mag'(a, n) = |sin(jx thx) cos(jy thy)| + |cos(jx thx) sin(jy thy)|   (cos modes)
+                 |cos(jx thx) cos(jy thy)| + |sin(jx thx) sin(jy thy)|   (sin modes),
+times jx dkx (G_x) or jy dky (G_y): below 5.5e-5 of sum_a |k_a,x| mag'(a, n) |W_a|, EPS_G = 6e-5.
 """
 import concurrent.futures as cf
 import os
@@ -35,6 +47,7 @@ import numpy as np
 
 EPS_D = 5e-5
 EPS_E = 6e-5
+EPS_G = 6e-5
 
 
 def grid_indices(modes):
@@ -74,6 +87,47 @@ def bounds(modes, R, M, W):
     magE = (np.sum(cx * (Wc @ cy), 0) + np.sum(sx * (Wc @ sy), 0) + np.sum(sx * (Ws @ cy), 0)
             + np.sum(cx * (Ws @ sy), 0))
     return bD, EPS_E * magE
+
+
+def grad_bounds(modes, R, W):
+    """EPS_G sum_a |k_a,x| mag'(a, n) |W_a| and the same with k_a,y for every cell: the bounds of the
+    gradient components G_x, G_y of the field at the cells' centres R (G_z = 0 on the grid)."""
+    jx, jy, s, dkx, dky = grid_indices(modes)
+    cx, sx = _tables(jx, dkx * R[:, 0])
+    cy, sy = _tables(jy, dky * R[:, 1])
+    Wc = np.zeros((cx.shape[0], cy.shape[0]))
+    Ws = np.zeros_like(Wc)
+    np.add.at(Wc, (jx[s == 0], jy[s == 0]), np.abs(W[s == 0]))
+    np.add.at(Ws, (jx[s == 1], jy[s == 1]), np.abs(W[s == 1]))
+    out = []
+    for ax, ay in ((dkx * np.arange(cx.shape[0]), np.ones(cy.shape[0])),
+                   (np.ones(cx.shape[0]), dky * np.arange(cy.shape[0]))):
+        Vc = Wc * ax[:, None] * ay[None, :]
+        Vs = Ws * ax[:, None] * ay[None, :]
+        # cos modes: |sx cy| + |cx sy|; sin modes: |cx cy| + |sx sy|
+        mag = (np.sum(sx * (Vc @ cy), 0) + np.sum(cx * (Vc @ sy), 0) + np.sum(cx * (Vs @ cy), 0)
+               + np.sum(sx * (Vs @ sy), 0))
+        out.append(EPS_G * mag)
+    return out[0], out[1]
+
+
+def direct_gradient(modes, R, W, chunk=64):
+    """The plain definition G_n = sum_a W_a grad u_a(R_n), grad u_a = -k_a sin(k_a . R + phi_a), over
+    chunks of modes on the host's cores. Returns [N, 3]."""
+    from oracle import cavity as OC
+    nm = len(modes.lam)
+    parts = [(a, min(nm, a + chunk)) for a in range(0, nm, chunk)]
+
+    def one(ab):
+        a, b = ab
+        S = OC.mode_function_sines(modes.k[a:b], modes.phi[a:b], R)
+        return -(S.T @ (W[a:b, None] * modes.k[a:b]))
+
+    G = np.zeros((len(R), 3))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        for g in ex.map(one, parts):
+            G += g
+    return G
 
 
 def direct_forward_and_field(modes, R, M, W, chunk=64):

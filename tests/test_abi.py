@@ -142,7 +142,7 @@ def test_rejects_bad_options(lib, small):
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
     o = P.default_options()
     o.mode_positions = 1
-    o.precision = 2      # moving mode positions need the FP64 coupling
+    o.splitting = 2      # moving mode positions take the photon-exact splitting
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -8
     o = P.default_options()
     o.jacobi_max_sweeps = 1001
