@@ -114,6 +114,13 @@ def _periodic_flops_per_cell(iters, n, nocc):
     return start + common * it + cayley + second * np.maximum(it - 1, 0) + sweep + forces
 
 
+def _kgrid_points(k):
+    """Irreducible points of a Gamma-centred k x k x k grid (k and -k once): each solved as the real
+    form of its complex problem, twice the orbitals."""
+    pts = [(i, j, l) for i in range(k) for j in range(k) for l in range(k)]
+    return sum(1 for (i, j, l) in pts if ((-i) % k, (-j) % k, (-l) % k) >= (i, j, l))
+
+
 def _cell_shapes(system):
     """Orbitals, occupied orbitals and atom pairs of every cell of a water or cluster system."""
     nat = np.diff(system.cell_offset)
@@ -363,13 +370,14 @@ def _network(B, charge_model, seeded=False):
                            for s_ in sizes]).astype(np.float32)
 
 
-def _config(workload, w, charge_model="mulliken", precision="fp64", mode_positions="fixed"):
+def _config(workload, w, charge_model="mulliken", precision="fp64", mode_positions="fixed", kgrid=1):
     sy, mo = w["system"], w["modes"]
     nw = sy.n_atoms // 3
     cells = (f"{nw} water" if nw == sy.n_cells else
              f"{sy.n_cells} clusters (H2O)_n, n = 1..8 ({nw} water molecules, up to 48 orbitals)")
     if w.get("lattice") is not None:
-        cells = (f"{sy.n_cells} periodic cells of {nw // sy.n_cells} water (10 Angstrom cubes, Gamma point, "
+        bz = "Gamma point" if kgrid <= 1 else f"{kgrid} x {kgrid} x {kgrid} k-grid"
+        cells = (f"{sy.n_cells} periodic cells of {nw // sy.n_cells} water (10 Angstrom cubes, {bz}, "
                  f"{nw} water molecules, {2 * nw // sy.n_cells * 3} orbitals per cell)")
     cm = {"mulliken": "Mulliken", "born_fd": "forward-FD Born every 3 steps",
           "born_central": "central-FD Born every 3 steps", "born_mlp": "network Born charges"}[charge_model]
@@ -393,6 +401,8 @@ def _make_ctx(P, w, args, local, precision, charge_model, mlp, graph_chunk):
     opt.autotune = 0 if args.no_autotune else 1
     opt.mode_positions = 1 if args.mode_positions == "com" else 0
     opt.acf_lags = args.acf_lags
+    if args.kgrid > 1:
+        opt.kgrid[:] = (args.kgrid,) * 3
     opt.graph_chunk = graph_chunk
     ctx = P.Context(w["system"], w["params"], w["modes"], opt, lattice=w.get("lattice"))
     if mlp is not None:
@@ -462,7 +472,12 @@ def _measure_arm(torch, P, w, args, ws, local, precision, charge_model, mlp, flu
     periodic = w.get("lattice") is not None
     if periodic:
         n_orb = 2 * np.diff(sy.cell_offset)          # 6 per water: 2 per atom
-        flops = float(sum(_periodic_flops_per_cell(i, n, n * 2 // 3) for i, n in zip(ev["scc_iters"], n_orb)))
+        if args.kgrid > 1:   # the same count for each k-point's real form (2n orbitals, 2 n_occ occupied)
+            nk = _kgrid_points(args.kgrid)
+            flops = float(sum(nk * _periodic_flops_per_cell(i, 2 * n, 2 * (n * 2 // 3))
+                              for i, n in zip(ev["scc_iters"], n_orb)))
+        else:
+            flops = float(sum(_periodic_flops_per_cell(i, n, n * 2 // 3) for i, n in zip(ev["scc_iters"], n_orb)))
     else:
         flops = float(_dftb_flops_per_cell(ev["scc_iters"], *_cell_shapes(sy)).sum())
     generic = not np.all(np.diff(sy.cell_offset) == 3)
@@ -482,7 +497,7 @@ def _measure_arm(torch, P, w, args, ws, local, precision, charge_model, mlp, flu
     arm = {
         "value": value, "unit": "molecule-steps/s", "ms_per_step": max_ms / args.steps,
         "precision": precision, "charge_model": charge_model,
-        "config": _config(args.workload, w, charge_model, precision, args.mode_positions),
+        "config": _config(args.workload, w, charge_model, precision, args.mode_positions, args.kgrid),
         "roofline": {"bound": "alu",
                      "kernel": "k_dftb_periodic" if periodic else ("k_dftb_generic" if generic else "dftb_kernel<3,6>"),
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -605,6 +620,9 @@ def main():
                     help="keep the default launch shapes instead of timing candidates at init")
     ap.add_argument("--scc-history", type=int, default=None,
                     help="Anderson history of the cluster kernel (default: the library's)")
+    ap.add_argument("--kgrid", type=int, default=1,
+                    help="periodic workloads: sample the Brillouin zone on a Gamma-centred k x k x k grid "
+                         "(the paper's cells: 3)")
     ap.add_argument("--mode-positions", default="fixed", choices=["fixed", "com"],
                     help="mode functions at the reference cell positions, or at the moving cell centres of mass")
     ap.add_argument("--acf-lags", type=int, default=None,

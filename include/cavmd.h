@@ -130,8 +130,9 @@ typedef struct {
                                    remainder over images with the cosine taper at r_cut. Positions
                                    are unwrapped (molecules stay whole); the cell dipole is
                                    sum_j Q_j r_j. Cells up to CAVMD_MAX_PERIODIC_ORBITALS orbitals
-                                   and CAVMD_MAX_PERIODIC_ATOMS atoms, Mulliken charges only (other
-                                   charge models return CAVMD_ERR_UNSUPPORTED)                   */
+                                   and CAVMD_MAX_PERIODIC_ATOMS atoms; Mulliken or finite-difference
+                                   Born charges (the network returns CAVMD_ERR_UNSUPPORTED); the
+                                   Brillouin zone sampled at Gamma or on cavmd_options.kgrid      */
 } cavmd_system;
 
 /* Slater-Koster parameter set. Every radial integral is
@@ -206,6 +207,15 @@ typedef struct {
                                    CAVMD_ERR_DEVICE_TIMEOUT. Later SCC iterations take one sweep. */
     double real_space_g0;       /* CAVMD_SPLIT_REAL_SPACE: the coupling constant g0 (> 0)         */
     double real_space_omega0;   /* CAVMD_SPLIT_REAL_SPACE: the reference frequency omega_0 (> 0)  */
+    int32_t kgrid[3];           /* periodic cells: Gamma-centred k-grid n1 x n2 x n3 sampling the
+                                   Brillouin zone (the paper's "Gamma point of a 3 x 3 x 3 folded
+                                   supercell" is {3, 3, 3}). {1, 1, 1} (the default; {0, 0, 0}
+                                   means the same) is the Gamma point. Each entry 1..8. k and -k
+                                   are solved once (weight 2 / (n1 n2 n3)); each remaining point is
+                                   a complex Hermitian problem, solved in its real form of twice
+                                   the size, so a step costs about 8 x the irreducible count x the
+                                   Gamma point's work (3 x 3 x 3: 14 points). Isolated cells:
+                                   must be {1, 1, 1} or {0, 0, 0}.                               */
 } cavmd_options;
 
 /* Observables at the current (synchronised) time. Optional arrays may be NULL. */

@@ -432,18 +432,26 @@ def scipy_eigh(H, S):
 
 # ---------------------------------------------------------------------------- cells for the cavity step
 
+def _cell_solver(kgrid):
+    """dftb_periodic (the Gamma point) or dftb_periodic_k on the given Gamma-centred grid."""
+    if kgrid is None or tuple(kgrid) == (1, 1, 1):
+        return dftb_periodic
+    return lambda *a, **k: dftb_periodic_k(*a, kgrid=tuple(kgrid), **k)
+
+
 def born_fd_periodic(params, species, pos, lattice, pol, h=1e-3, scheme="forward", q_ref=None, mu_ref=None,
-                     alpha=None, beta=0.5, tol=1e-12, max_iter=400):
+                     alpha=None, beta=0.5, tol=1e-12, max_iter=400, kgrid=None):
     """Finite-difference dipole derivative b_j = d(pol . mu)/dr_j of one periodic cell, shape (nat, 3):
     the Born charges of the paper's periodic cells (Results: forward differences, refreshed every
     3 steps). 'forward' is [M(r + h e) - M(r)] / h, 'central' [M(r + h e) - M(r - h e)] / 2h, with mu
-    the unwrapped cell dipole of dftb_periodic; every displaced solve starts from the reference
-    populations."""
+    the unwrapped cell dipole of dftb_periodic (or of dftb_periodic_k on the grid kgrid); every
+    displaced solve starts from the reference populations."""
     pos = np.asarray(pos, float)
     pol = np.asarray(pol, float)
+    solve = _cell_solver(kgrid)
     if q_ref is None or mu_ref is None:
-        ref = dftb_periodic(params, species, pos, lattice, alpha=alpha, beta=beta, tol=tol, max_iter=max_iter,
-                            forces=False)
+        ref = solve(params, species, pos, lattice, alpha=alpha, beta=beta, tol=tol, max_iter=max_iter,
+                    forces=False)
         q_ref, mu_ref = ref["q"], ref["mu"]
     kw = dict(q0=q_ref, alpha=alpha, beta=beta, tol=tol, max_iter=max_iter, forces=False)
     M0 = mu_ref @ pol
@@ -452,25 +460,26 @@ def born_fd_periodic(params, species, pos, lattice, pol, h=1e-3, scheme="forward
         for k in range(3):
             dp = pos.copy()
             dp[j, k] += h
-            Mp = dftb_periodic(params, species, dp, lattice, **kw)["mu"] @ pol
+            Mp = solve(params, species, dp, lattice, **kw)["mu"] @ pol
             if scheme == "forward":
                 b[j, k] = (Mp - M0) / h
             else:
                 dm = pos.copy()
                 dm[j, k] -= h
-                Mm = dftb_periodic(params, species, dm, lattice, **kw)["mu"] @ pol
+                Mm = solve(params, species, dm, lattice, **kw)["mu"] @ pol
                 b[j, k] = (Mp - Mm) / (2.0 * h)
     return b
 
 
 class PeriodicDFTBMatter:
-    """Periodic cells evaluated with dftb_periodic, with the interface of oracle.cavity's
-    DFTBMatter: Mulliken charges (b_j = Q_j pol) or finite-difference Born charges ('born_fd',
-    forward, or 'born_central'; refreshed every born_interval evaluations). lattice: (3, 3) shared
-    by all cells or (n_cells, 3, 3)."""
+    """Periodic cells evaluated with dftb_periodic (or, with kgrid, dftb_periodic_k on that
+    Gamma-centred grid), with the interface of oracle.cavity's DFTBMatter: Mulliken charges
+    (b_j = Q_j pol) or finite-difference Born charges ('born_fd', forward, or 'born_central';
+    refreshed every born_interval evaluations). lattice: (3, 3) shared by all cells or
+    (n_cells, 3, 3)."""
 
     def __init__(self, params, system, lattice, pol=(1.0, 0.0, 0.0), alpha=None, beta=0.5,
-                 tol=1e-12, max_iter=400, charge_model="mulliken", born_interval=1, fd_step=1e-3):
+                 tol=1e-12, max_iter=400, charge_model="mulliken", born_interval=1, fd_step=1e-3, kgrid=None):
         self.params = params
         self.species = np.asarray(system.species)
         self.off = np.asarray(system.cell_offset)
@@ -485,6 +494,7 @@ class PeriodicDFTBMatter:
         self.fd_step = fd_step
         self.alpha = alpha
         self.kw = dict(beta=beta, tol=tol, max_iter=max_iter)
+        self.kgrid = kgrid
         self.q = None
         self.b = None
         self.n_eval = 0
@@ -504,8 +514,8 @@ class PeriodicDFTBMatter:
         for c in range(self.n_cells):
             s = slice(self.off[c], self.off[c + 1])
             q0 = None if self.q is None else self.q[s]
-            out = dftb_periodic(self.params, self.species[s], r[s], self.lattice[c], q0=q0,
-                                alpha=self.alpha, **self.kw)
+            out = _cell_solver(self.kgrid)(self.params, self.species[s], r[s], self.lattice[c], q0=q0,
+                                           alpha=self.alpha, **self.kw)
             iters.append(out["iters"])
             F[s] = out["F"]
             E[c] = out["E"]
@@ -516,7 +526,7 @@ class PeriodicDFTBMatter:
                 scheme = "forward" if self.charge_model == "born_fd" else "central"
                 b[s] = born_fd_periodic(self.params, self.species[s], r[s], self.lattice[c], self.pol,
                                         h=self.fd_step, scheme=scheme, q_ref=out["q"], mu_ref=out["mu"],
-                                        alpha=self.alpha, **self.kw)
+                                        alpha=self.alpha, kgrid=self.kgrid, **self.kw)
         self.q = q_all
         if self.charge_model == "mulliken":
             b = Q[:, None] * self.pol

@@ -58,7 +58,8 @@ class cavmd_options(C.Structure):
                 ("alloc_user", C.c_void_p), ("energy_history", C.c_int32), ("acf_lags", C.c_int32),
                 ("autotune", C.c_int32), ("scc_history", C.c_int32),
                 ("mode_positions", C.c_int32), ("jacobi_max_sweeps", C.c_int32),
-                ("real_space_g0", C.c_double), ("real_space_omega0", C.c_double)]
+                ("real_space_g0", C.c_double), ("real_space_omega0", C.c_double),
+                ("kgrid", C.c_int32 * 3)]
 
 
 class cavmd_obs(C.Structure):

@@ -13,13 +13,15 @@
 // From these the finalisation forms the mean-removed unbiased estimator exactly:
 //   C(l) = [P(l) - xbar (A(l) + B(l)) + (n - l) xbar^2] / (n - l),  xbar = S / n,
 //   P(l) = sum_{t=l}^{n-1} x_t x_{t-l},  A(l) = S - (last l samples),  B(l) = S - (first l samples).
-// One block per photon channel; the total dipole is summed over slices of the cells by all blocks and
+// One warp per photon channel; the total dipole is summed over slices of the cells by all blocks and
 // finished by the last one. Every sum runs in a fixed order, so the result is deterministic.
 #include "cavmd_internal.cuh"
 
 namespace {
 
 constexpr int ACF_THREADS = 256;
+
+constexpr int ACF_WARPS = ACF_THREADS / 32;   // channels per block: one warp each
 
 // Block reduction in a fixed order (threads strided, then a shuffle tree, then the warps in order).
 __device__ double block_sum(double s, double *red) {
@@ -28,25 +30,26 @@ __device__ double block_sum(double s, double *red) {
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
     double v = 0.0;
-    for (int w = 0; w < ACF_THREADS / 32; ++w) v += red[w];
+    for (int w = 0; w < ACF_WARPS; ++w) v += red[w];
     __syncthreads();
     return v;
 }
 
-// One sample of channel c: store it in the ring (and the head while t < L), add it to the running
-// sum, and fold the B newest samples into the lag products when the block of B is complete.
+// One sample of channel c, by one warp: store it in the ring (and the head while t < L), add it to
+// the running sum, and fold the B newest samples into the lag products when the block of B is
+// complete (lanes over the lags).
 __device__ void acf_push(const AcfArgs &a, int c, long long t, double xs) {
-    const int L = a.L, R = a.L + a.B;
+    const int L = a.L, R = a.L + a.B, lane = threadIdx.x & 31;
     double *ring = a.ring + (size_t)c * R;
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         ring[t % R] = xs;
         if (t < L) a.head[(size_t)c * L + t] = xs;
         a.sum[c] += xs;
     }
-    __syncthreads();
+    __syncwarp();
     if ((t + 1) % a.B == 0) {   // fold samples t - B + 1 .. t
         double *acc = a.acc + (size_t)c * L;
-        for (int l = threadIdx.x; l < L; l += ACF_THREADS) {
+        for (int l = lane; l < L; l += 32) {
             double v = acc[l];
             for (long long u = t - a.B + 1; u <= t; ++u)
                 if (u >= l) v = fma(ring[u % R], ring[(u - l) % R], v);
@@ -55,12 +58,13 @@ __device__ void acf_push(const AcfArgs &a, int c, long long t, double xs) {
     }
 }
 
-// Grid: G >= C blocks. Block b < M pushes the photon coordinate q_b; every block also sums its slice
-// of the per-cell dipoles into part[b]; the last block to finish (ticket) sums the G partial sums in
-// block order into the total dipole, pushes it as channel M and advances the sample counter.
+// Grid: G blocks, G >= M / ACF_WARPS. Warp w of block b pushes the photon coordinate of channel
+// b ACF_WARPS + w (< M); every block also sums its slice of the per-cell dipoles into part[b]; the
+// last block to finish (ticket) sums the G partial sums in block order into the total dipole,
+// pushes it as channel M with its first warp and advances the sample counter.
 __global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const double *__restrict__ q_sync,
                                                      const double *__restrict__ M_cell, int N) {
-    __shared__ double red[ACF_THREADS / 32];
+    __shared__ double red[ACF_WARPS];
     __shared__ bool last;
     const int b = blockIdx.x;
     const long long t = *a.n;   // every block reads it before the last block advances it
@@ -70,7 +74,8 @@ __global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const doub
     for (int n = n0 + threadIdx.x; n < n1; n += ACF_THREADS) s += M_cell[n];
     s = block_sum(s, red);
     if (threadIdx.x == 0) a.part[b] = s;
-    if (b < a.M) acf_push(a, b, t, q_sync[b]);
+    const int c = b * ACF_WARPS + (threadIdx.x >> 5);
+    if (c < a.M) acf_push(a, c, t, q_sync[c]);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -83,7 +88,7 @@ __global__ void __launch_bounds__(ACF_THREADS) k_acf(const AcfArgs a, const doub
     double v = 0.0;
     for (int i = threadIdx.x; i < a.G; i += ACF_THREADS) v += __ldcg(a.part + i);
     v = block_sum(v, red);
-    acf_push(a, a.M, t, v);
+    if (threadIdx.x < 32) acf_push(a, a.M, t, v);
     if (threadIdx.x == 0) {
         *a.n = t + 1;
         *a.ticket = 0u;

@@ -394,7 +394,8 @@ cudaError_t enqueue_steps(cavmd_ctx *c, int64_t n, int64_t first_step) {
 // The context's own state is not touched.
 int autotune(cavmd_ctx *c) {
     if (c->periodic) {
-        c->tuning = "k_dftb_periodic: one 256-thread block per cell, two per SM (no candidates)";
+        c->tuning = c->pplan.nk > 0 ? "k_dftb_periodic_kg: one 256-thread block per cell, one per SM (no candidates)"
+                                    : "k_dftb_periodic: one 256-thread block per cell, two per SM (no candidates)";
         return CAVMD_OK;
     }
     const int NA = c->n_atoms, N = c->N;
@@ -580,6 +581,12 @@ int padded_ky(int Ky2) {
     return 0;
 }
 
+// Grid points of the k-grid option (1: the Gamma point).
+int kgrid_points(const cavmd_options *o) {
+    if (o->kgrid[0] == 0 && o->kgrid[1] == 0 && o->kgrid[2] == 0) return 1;
+    return o->kgrid[0] * o->kgrid[1] * o->kgrid[2];
+}
+
 int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_modes *md,
              const cavmd_options *o) {
     cavmd_ctx *c = nullptr;
@@ -676,6 +683,14 @@ int validate(const cavmd_system *sys, const cavmd_sk_tables *sk, const cavmd_mod
         return fail(c, CAVMD_ERR_INVALID_ARG, "bad mode_positions");
     if (o->mode_positions == CAVMD_MODES_CENTRE_OF_MASS && o->splitting != CAVMD_SPLIT_PHOTON_EXACT)
         return fail(c, CAVMD_ERR_UNSUPPORTED, "moving mode positions take the photon-exact splitting");
+    {
+        const bool zero = o->kgrid[0] == 0 && o->kgrid[1] == 0 && o->kgrid[2] == 0;
+        for (int k = 0; k < 3; ++k)
+            if (!zero && (o->kgrid[k] < 1 || o->kgrid[k] > 8))
+                return fail(c, CAVMD_ERR_INVALID_ARG, "kgrid entries must be 1..8 (or all 0)");
+        if (kgrid_points(o) > 1 && !sys->lattice)
+            return fail(c, CAVMD_ERR_INVALID_ARG, "a k-grid needs periodic cells (cavmd_system.lattice)");
+    }
     if (o->precision == CAVMD_PREC_MIXED_BF16X3) {
         int Kx, Ky2;
         double dkx, dky;
@@ -764,11 +779,15 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     // 6-orbital cells, the persistent generic kernel otherwise
     std::vector<long long> coff(N + 1, 0);
     c->generic = false;
+    // k-grid: a basis per irreducible k-point, each the real form of twice the orbitals
+    std::vector<double> kpts;
+    if (sys->lattice && kgrid_points(&c->opt) > 1) kpts = pbc_kpoints(c->opt.kgrid);
+    const int nk = (int)(kpts.size() / 4);
     for (int n = 0; n < N; ++n) {
         int no = 0;
         for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) no += sk->norb[sys->species[i]];
         if (!sys->lattice && (no != 6 || sys->cell_offset[n + 1] - sys->cell_offset[n] != 3)) c->generic = true;
-        coff[n + 1] = coff[n] + (long long)no * no;
+        coff[n + 1] = coff[n] + (nk > 0 ? 4LL * nk : 1LL) * no * no;
     }
     c->n_cwarm = coff[N];
     AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)coff[N]); AL(c->d_E, N); AL(c->d_Mc, N);
@@ -915,7 +934,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
         const size_t cl = (size_t)a.C * a.L;
         AL(a.ring, (size_t)a.C * (a.L + a.B)); AL(a.head, cl); AL(a.acc, cl); AL(a.sum, a.C); AL(a.n, 1);
         AL(a.ticket, 1);
-        a.G = std::max(a.C, std::min(16384, (c->N + 31) / 32));
+        a.G = std::max((a.M + 7) / 8, std::min(2048, (c->N + 255) / 256));   // 8 channels (warps) per block
         AL(a.part, a.G);
         AL(c->d_acf_out, cl);
         CK(reset_acf(c));
@@ -948,16 +967,22 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
             return fail(c, CAVMD_ERR_UNSUPPORTED, "lattice too thin: " + std::to_string(pp.n_img) + " lattice images");
         pp.nmax = 0;
         pp.amax = 0;
+        pp.nk = nk;
         for (int n = 0; n < N; ++n) {
-            pp.nmax = std::max(pp.nmax, (int)std::lround(std::sqrt((double)(coff[n + 1] - coff[n]))));
+            pp.nmax = std::max(pp.nmax, (int)std::lround(std::sqrt((double)(coff[n + 1] - coff[n]) /
+                                                                   (nk > 0 ? 4.0 * nk : 1.0))));
             pp.amax = std::max(pp.amax, sys->cell_offset[n + 1] - sys->cell_offset[n]);
         }
         int nsm = 0;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-        pp.blocks = std::max(1, std::min(N, 2 * nsm));
+        pp.blocks = std::max(1, std::min(N, (nk > 0 ? 1 : 2) * nsm));
         AL(pp.d_img, img.size());
         AL(pp.d_gw, gw.size());
-        AL(pp.work, pbc_workspace_doubles(pp.nmax, pp.amax, pp.n_g) * (size_t)pp.blocks);
+        AL(pp.work, pbc_workspace_doubles(pp.nmax, pp.amax, pp.n_g, nk) * (size_t)pp.blocks);
+        if (nk > 0) {
+            AL(pp.d_kpt, kpts.size());
+            CK(cudaMemcpyAsync(pp.d_kpt, kpts.data(), sizeof(double) * kpts.size(), cudaMemcpyHostToDevice, st));
+        }
         CK(cudaMemcpyAsync(pp.d_img, img.data(), sizeof(double) * img.size(), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(pp.d_gw, gw.data(), sizeof(double) * gw.size(), cudaMemcpyHostToDevice, st));
         AL(c->d_Coff, N);
@@ -1043,6 +1068,7 @@ void cavmd_default_options(cavmd_options *o) {
     o->device = 0;
     o->energy_history = 1024;
     o->scc_history = 3;
+    o->kgrid[0] = o->kgrid[1] = o->kgrid[2] = 1;
 }
 
 int cavmd_init(cavmd_ctx **out, const cavmd_system *sys, const cavmd_sk_tables *sk,

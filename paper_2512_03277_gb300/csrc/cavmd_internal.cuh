@@ -217,7 +217,8 @@ struct AcfArgs {
     double *sum;                 // [C] running sums
     long long *n;                // samples so far
     unsigned *ticket;            // last-block counter
-    int G;                       // blocks per sample (>= C): each sums a slice of the cell dipoles
+    int G;                       // blocks per sample (>= M / 8, a warp per photon channel): each also
+                                 // sums a slice of the cell dipoles
     double *part;                // [G] those slice sums
 };
 cudaError_t launch_acf(const AcfArgs &a, const double *q_sync, const double *M_cell, int N, cudaStream_t st);
@@ -253,12 +254,15 @@ struct PbcPlan {
     double alpha, bg, self_e, r_real;     // Ewald splitting, background and self terms, real-space cutoff
     int n_img, n_img_sk, n_g;             // lattice translations (by length; the first n_img_sk reach
                                           // r_cut); half-space reciprocal vectors
-    int nmax, amax, blocks;               // largest cell; persistent blocks (2 per SM)
+    int nmax, amax, blocks;               // largest cell; persistent blocks (2 per SM, k-grid 1)
     double *d_img, *d_gw;                 // device: [n_img][3], [n_g][4] (G, 2 w_G)
     double *work;                         // device: per-block workspaces
+    int nk;                               // k-grid: irreducible k-points (0: Gamma point only)
+    double *d_kpt;                        // device: [nk][4] fractional k and weight
 };
-size_t pbc_workspace_doubles(int nmax, int amax, int n_g);
-size_t pbc_smem();
+size_t pbc_workspace_doubles(int nmax, int amax, int n_g, int nk);
+std::vector<double> pbc_kpoints(const int *kgrid);
+size_t pbc_smem(bool kgrid);
 void plan_dftb_periodic(const double *lat, double r_cut, PbcPlan &p, std::vector<double> &img,
                         std::vector<double> &gw);
 cudaError_t prepare_dftb_periodic();

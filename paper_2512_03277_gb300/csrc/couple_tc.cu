@@ -434,17 +434,25 @@ __global__ void __launch_bounds__(128) k_tc_back(int N, int Npad, int n_tiles, c
                 float v[32], vd[32];
                 tc::tmem_ld32(tmem + lanes + (uint32_t)c0, v);
                 tc::tmem_ld32(tmem + lanes + (uint32_t)(KXP + c0), vd);
+                // A'[i][n] = g_i A[swap(i)][n]: swap(i) = Kx + i, g_i = -i dkx (i < Kx); swap(i) = i - Kx,
+                // g_i = (i - Kx) dkx (i < 2 Kx); padding rows g_i = 0. Loads without branches, so that
+                // the 64 loads of a chunk are all in flight before the sums.
+                float a[32], as[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int i = c0 + q;
+                    const int sw = i < Kx ? Kx + i : (i < 2 * Kx ? i - Kx : i);
+                    a[q] = Af[(size_t)i * Npad + n];
+                    as[q] = Af[(size_t)sw * Npad + n];
+                }
                 float s = 0.0f, sx = 0.0f, sy2 = 0.0f;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int i = c0 + q;
-                    const float a = Af[(size_t)i * Npad + n];
-                    s = fmaf(a, v[q], s);
-                    sy2 = fmaf(a, vd[q], sy2);
-                    float ad = 0.0f;   // A'[i][n]
-                    if (i < Kx) ad = -((float)i * dkx) * Af[(size_t)(Kx + i) * Npad + n];
-                    else if (i < 2 * Kx) ad = ((float)(i - Kx) * dkx) * Af[(size_t)(i - Kx) * Npad + n];
-                    sx = fmaf(ad, v[q], sx);
+                    const float g = i < Kx ? -((float)i * dkx) : (i < 2 * Kx ? (float)(i - Kx) * dkx : 0.0f);
+                    s = fmaf(a[q], v[q], s);
+                    sy2 = fmaf(a[q], vd[q], sy2);
+                    sx = fmaf(g * as[q], v[q], sx);
                 }
                 e += (double)s;
                 gx += (double)sx;

@@ -150,6 +150,11 @@ def test_rejects_bad_options(lib, small):
     o = P.default_options()
     o.splitting = 3
     assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1
+    assert list(P.default_options().kgrid) == [1, 1, 1]
+    for kg in ((3, 3, 3), (0, 1, 1), (9, 1, 1)):   # a grid on isolated cells; a partly zero or too fine grid
+        o = P.default_options()
+        o.kgrid[:] = kg
+        assert _init_rc(lib, small["system"], small["params"], small["modes"], o)[0] == -1, kg
 
 
 def test_rejects_empty_inputs(lib, small):

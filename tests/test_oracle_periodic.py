@@ -310,3 +310,28 @@ def test_born_charges_of_a_periodic_cell(params):
         bp = PR.born_fd_periodic(params, [0, 1, 1], w, side * np.eye(3), pol, h=1e-3, scheme="central")
         gaps.append(np.abs(bp - iso).max())
     assert gaps[1] < 0.25 * gaps[0] and gaps[1] < 2e-3 * np.abs(iso).max()
+
+
+def test_kgrid_born_charges_equal_the_supercells(params):
+    """Born charges on the 3 x 3 x 3 k-grid (born_fd_periodic with kgrid) against the explicit
+    supercell at the Gamma point: moving atom j of the cell moves it in every copy, so the cell's
+    dipole change is the supercell's divided by 27 (Bloch's theorem, exact up to rounding). Two
+    entries, forward differences from the same reference charges."""
+    sy, lat = _two_waters()
+    pol = np.array([1.0, 0.0, 0.0])
+    h = 1e-3
+    ref = PR.dftb_periodic_k(params, sy.species, sy.r, lat, (3, 3, 3), forces=False)
+    bk = PR.born_fd_periodic(params, sy.species, sy.r, lat, pol, h=h, q_ref=ref["q"], mu_ref=ref["mu"],
+                             kgrid=(3, 3, 3))
+    pos_s, spec_s, lat_s = _supercell(sy.r, sy.species, lat)
+    nat = len(sy.species)
+    q0 = np.tile(ref["q"], 27)
+    m0 = PR.dftb_periodic(params, spec_s, pos_s, lat_s, q0=q0, forces=False)["mu"] @ pol
+    for j, k in ((0, 0), (4, 2)):
+        p = pos_s.copy()
+        p[j::nat, k] += h
+        m1 = PR.dftb_periodic(params, spec_s, p, lat_s, q0=q0, forces=False)["mu"] @ pol
+        np.testing.assert_allclose(bk[j, k], (m1 - m0) / (27.0 * h), rtol=0, atol=1e-7)
+    # and the grid matters: the Gamma point's Born charges differ
+    bg = PR.born_fd_periodic(params, sy.species, sy.r, lat, pol, h=h)
+    assert np.abs(bg - bk).max() > 1e-3
