@@ -37,8 +37,6 @@ struct cavmd_ctx {
     DevSK *d_sk = nullptr;
     int *d_off = nullptr, *d_species = nullptr, *d_iters = nullptr;
     double *d_r = nullptr, *d_p = nullptr, *d_F = nullptr, *d_b = nullptr, *d_qpop = nullptr, *d_qprev = nullptr;
-    double *d_qprev2 = nullptr, *d_qprev3 = nullptr;   // the populations' history (predictor)
-    long long *d_qbase = nullptr;                     // step count at the last cold start
     double *d_C = nullptr, *d_E = nullptr, *d_Mc = nullptr, *d_mass = nullptr, *d_imass = nullptr;
     double *d_U = nullptr, *d_k = nullptr, *d_phi = nullptr, *d_R = nullptr;
     double *d_omega = nullptr, *d_lam = nullptr, *d_iomega = nullptr;
@@ -404,18 +402,16 @@ int autotune(cavmd_ctx *c) {
     cudaStream_t st = c->stream;
     const long long ncw = c->n_cwarm;
     double *r_t = nullptr, *F_t = nullptr, *b_t = nullptr, *qp_t = nullptr, *qv_t = nullptr, *C_t = nullptr;
-    double *E_t = nullptr, *M_t = nullptr, *Q_t = nullptr, *q2_t = nullptr, *q3_t = nullptr;
+    double *E_t = nullptr, *M_t = nullptr, *Q_t = nullptr;
     int *it_t = nullptr;
     unsigned *st_t = nullptr;
     AL(r_t, 3 * NA); AL(F_t, 3 * NA); AL(b_t, 3 * NA); AL(qp_t, NA); AL(qv_t, NA); AL(C_t, ncw);
-    AL(E_t, N); AL(M_t, N); AL(Q_t, NA); AL(it_t, N); AL(st_t, 1); AL(q2_t, NA); AL(q3_t, NA);
+    AL(E_t, N); AL(M_t, N); AL(Q_t, NA); AL(it_t, N); AL(st_t, 1);
     CK(launch_trial_positions(c->d_r, c->d_p, c->d_imass, c->opt.dt, NA, r_t, st));
     DftbArgs t = c->da;
     t.r = r_t; t.F = F_t; t.b = b_t; t.qpop = qp_t; t.qprev = qv_t; t.Cwarm = C_t; t.E_cell = E_t;
     t.M_cell = M_t; t.iters = it_t; t.status = st_t; t.Qout = Q_t; t.have_warm = 1; t.n_disp = 0;
     t.M_disp = nullptr;
-    t.qprev2 = q2_t;
-    t.qprev3 = q3_t;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -432,8 +428,6 @@ int autotune(cavmd_ctx *c) {
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemcpyAsync(qp_t, c->d_qpop, sizeof(double) * NA, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(qv_t, c->d_qprev, sizeof(double) * NA, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(q2_t, c->d_qprev2, sizeof(double) * NA, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(q3_t, c->d_qprev3, sizeof(double) * NA, cudaMemcpyDeviceToDevice, st));
             CK(cudaMemcpyAsync(C_t, c->d_C, sizeof(double) * ncw, cudaMemcpyDeviceToDevice, st));
             CK(cudaEventRecord(e0, st));
             if (c->generic) {
@@ -481,7 +475,7 @@ int autotune(cavmd_ctx *c) {
     }
     c->tuning = rep;
     for (void *p : {(void *)r_t, (void *)F_t, (void *)b_t, (void *)qp_t, (void *)qv_t, (void *)C_t, (void *)E_t,
-                    (void *)M_t, (void *)Q_t, (void *)it_t, (void *)st_t, (void *)q2_t, (void *)q3_t})
+                    (void *)M_t, (void *)Q_t, (void *)it_t, (void *)st_t})
         dfree(c, p);
     return CAVMD_OK;
 }
@@ -797,7 +791,6 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     }
     c->n_cwarm = coff[N];
     AL(c->d_qpop, NA); AL(c->d_qprev, NA); AL(c->d_C, (size_t)coff[N]); AL(c->d_E, N); AL(c->d_Mc, N);
-    AL(c->d_qprev2, NA); AL(c->d_qprev3, NA); AL(c->d_qbase, 1);
     c->periodic = sys->lattice != nullptr;
     if (!c->generic && !c->periodic) CK(prepare_dftb_water(8));
     AL(c->d_mass, NA); AL(c->d_imass, NA); AL(c->d_Einst, N); AL(c->d_E1, N);
@@ -871,7 +864,6 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(c->d_step, 0, sizeof(long long), st));
-    CK(cudaMemsetAsync(c->d_qbase, 0, sizeof(long long), st));
     CK(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 8 * c->opt.energy_history, st));
     CK(cudaMemsetAsync(c->d_q, 0, sizeof(double) * M, st));
     CK(cudaMemsetAsync(c->d_pq, 0, sizeof(double) * M, st));
@@ -1009,9 +1001,6 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     d.b = c->d_b;
     d.qpop = c->d_qpop;
     d.qprev = c->d_qprev;
-    d.qprev2 = c->d_qprev2;
-    d.qprev3 = c->d_qprev3;
-    d.qbase = c->d_qbase;
     d.Cwarm = c->d_C;
     d.Cwarm_off = c->d_Coff;
     d.E_cell = c->d_E;
@@ -1293,7 +1282,6 @@ int cavmd_set_state(cavmd_ctx *c, const cavmd_state *s) {
     CK(cudaMemcpy(c->d_pqs, s->pq, sizeof(double) * c->M, cudaMemcpyHostToDevice));
     long long stp = s->step;
     CK(cudaMemcpy(c->d_step, &stp, sizeof(long long), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->d_qbase, &stp, sizeof(long long), cudaMemcpyHostToDevice));   // a cold start here
     c->step = s->step;
     rc = initial_evaluation(c, false);   // Born charges, if any, are refreshed here as well
     if (rc) return rc;

@@ -43,8 +43,6 @@ struct DftbArgs {
     double *b;                 // [3 n_atoms] out: Mulliken b_j = Q_j pol (charge_model 0)
     double *qpop;              // [n_atoms] in/out: Mulliken populations (warm start)
     double *qprev;             // [n_atoms] in/out: populations of the step before (predictor)
-    double *qprev2, *qprev3;   // [n_atoms] in/out: two and three steps before
-    const long long *qbase;    // device: the step count at the last cold start (NULL: linear predictor)
     double *Cwarm;             // in/out eigenvectors of every cell (column-major, n_c x n_c each)
     const long long *Cwarm_off;   // [N] first element of each cell's block in Cwarm (NULL: 36 per cell)
     double *E_cell;            // [N] out
@@ -76,32 +74,6 @@ struct DftbArgs {
     double tau, dt;
     const long long *step_counter;   // device step counter (periodic kernel: which steps re-diagonalise)
 };
-
-// Predictor of the populations from the converged populations of the last d evaluations: the
-// polynomial through them, evaluated one step ahead (d = 1: q0; 2: 2 q0 - q1; 3: 3 q0 - 3 q1 + q2;
-// 4 and more: 4 q0 - 6 q1 + 4 q2 - q3), with q0 the latest. d counts the evaluations since the last
-// cold start (step counter - qbase + 1). Returns the prediction and q0, q1, q2 for the history.
-__device__ __forceinline__ double q_predict(const DftbArgs &a, int at, double &q0, double &q1, double &q2) {
-    q0 = a.qpop[at];
-    q1 = a.qprev[at];
-    q2 = a.qprev2[at];
-    const double q3 = a.qprev3[at];
-    const long long d = (a.step_counter && a.qbase) ? *a.step_counter - *a.qbase + 1 : 2;
-    if (d >= 4) return fma(4.0, q0 + q2, fma(-6.0, q1, -q3));
-    if (d == 3) return fma(3.0, q0 - q1, q2);
-    if (d == 2) return fma(2.0, q0, -q1);
-    return q0;
-}
-
-// The populations' history after an evaluation: each slot moves one step back and qpop takes the
-// new populations (after a cold start every slot holds them).
-__device__ __forceinline__ void q_history_push(const DftbArgs &a, int at, double qnew, double q0, double q1,
-                                               double q2) {
-    a.qprev3[at] = a.have_warm ? q2 : qnew;
-    a.qprev2[at] = a.have_warm ? q1 : qnew;
-    a.qprev[at] = a.have_warm ? q0 : qnew;
-    a.qpop[at] = qnew;
-}
 
 // Arguments of the coupling / integrator kernels.
 struct StepArgs {

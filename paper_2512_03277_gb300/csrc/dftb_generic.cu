@@ -63,7 +63,7 @@ __host__ __device__ inline GLayout g_layout(int nmax, int amax) {
     L.zv = o; o += amax * 8;
     L.q = o; o += amax * 8;
     L.qout = o; o += amax * 8;
-    L.qst = o; o += 3 * amax * 8;   // q0, q1, q2 of the history
+    L.qst = o; o += amax * 8;
     L.shift = o; o += amax * 8;
     L.shl = o; o += amax * 8;
     L.hq = o; o += GNHIST * amax * 8;
@@ -323,13 +323,10 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
         C[c * LD + i] = a.have_warm ? cw[e] : (i == c ? 1.0 : 0.0);
     }
     if (j < nat) {
-        if (a.have_warm) {   // polynomial predictor (q_predict); displaced copies start from q(t)
-            double q0, q1, q2;
-            const double qp = q_predict(a, a0 + j, q0, q1, q2);
-            qst[j] = q0;
-            qst[L.amax + j] = q1;
-            qst[2 * L.amax + j] = q2;
-            q[j] = disp ? q0 : qp;
+        if (a.have_warm) {   // predictor 2 q(t) - q(t - dt); displaced copies start from q(t)
+            const double qt = a.qpop[a0 + j];
+            qst[j] = qt;
+            q[j] = disp ? qt : fma(2.0, qt, -a.qprev[a0 + j]);
         } else {
             q[j] = zv[j];
         }
@@ -798,7 +795,8 @@ __device__ void g_molecule(const DevSK &sk, const DftbArgs &a, const GLayout &L,
         }
         const int at = a0 + j;
         for (int k = 0; k < 3; ++k) a.F[3 * at + k] = f[k];
-        q_history_push(a, at, q[j], qst[j], qst[L.amax + j], qst[2 * L.amax + j]);
+        a.qprev[at] = a.have_warm ? qst[j] : q[j];
+        a.qpop[at] = q[j];
         if (a.Qout) a.Qout[at] = zv[j] - q[j];
         if (a.write_b) {
             const double Q = zv[j] - q[j];

@@ -47,7 +47,7 @@ struct MolShared {
     double shift[NAT];
     double hq[NHIST][NAT];
     double hf[NHIST][NAT];
-    double qstart[3][NAT];   // q(t), q(t - dt), q(t - 2 dt) of the previous steps, for the history
+    double qstart[NAT];   // q(t) of the previous step, for the predictor
     double red[NORB];
     double cs[NORB / 2 + 1][2];
     double invd[NORB];
@@ -294,14 +294,12 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
         if (a.have_warm) {
             const double *cw = a.Cwarm + (a.Cwarm_off ? a.Cwarm_off[cell] : (long long)cell * NORB * NORB);
             for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = cw[j * NORB + i];
-            // polynomial predictor of the populations from the last evaluations (q_predict)
+            // linear predictor 2 q(t) - q(t - dt) of the populations (q_prev equals q after a
+            // cold start, so the first warm step starts from q(t) itself)
             if (j < NAT) {
-                double q0, q1, q2;
-                const double qp = q_predict(a, a0 + j, q0, q1, q2);
-                m.qstart[0][j] = q0;
-                m.qstart[1][j] = q1;
-                m.qstart[2][j] = q2;
-                m.q[j] = disp ? q0 : qp;   // displaced rows start at q(r)
+                const double qt = a.qpop[a0 + j];
+                m.qstart[j] = qt;
+                m.q[j] = disp ? qt : fma(2.0, qt, -a.qprev[a0 + j]);   // displaced rows start at q(r)
             }
         } else {
             for (int i = 0; i < NORB; ++i) m.C[j * LD + i] = (i == j) ? 1.0 : 0.0;
@@ -881,7 +879,8 @@ __global__ void __launch_bounds__(256, 1) dftb_kernel(const DevSK *__restrict__ 
         }
         const int at = a0 + j;
         for (int k = 0; k < 3; ++k) a.F[3 * at + k] = f[k];
-        q_history_push(a, at, m.q[j], m.qstart[0][j], m.qstart[1][j], m.qstart[2][j]);
+        a.qprev[at] = a.have_warm ? m.qstart[j] : m.q[j];
+        a.qpop[at] = m.q[j];
         if (a.Qout) a.Qout[at] = m.zv[j] - m.q[j];
         if (a.write_b) {
             const double Q = m.zv[j] - m.q[j];

@@ -62,8 +62,7 @@ struct PSharedT {
     double Xs[KC * PN];
     double Zs[KC * ZC];
     double pos[PAMAX][3];
-    double zv[PAMAX], q[PAMAX], qout[PAMAX], dq[PAMAX], shift[PAMAX];
-    double qst[3][PAMAX];        // q0, q1, q2 of the populations' history
+    double zv[PAMAX], q[PAMAX], qout[PAMAX], qst[PAMAX], dq[PAMAX], shift[PAMAX];
     double hq[PHIST][PAMAX], hf[PHIST][PAMAX];
     double diag[PN], red[PN], invd[PN];
     double cs[PN];               // Jacobi (c, s) of the rotations of one round
@@ -710,13 +709,10 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, SH 
 
     // ---------------------------------------------------------------- S-orthonormal start
     if (j < nat) {
-        if (a.have_warm) {   // polynomial predictor (q_predict); a displaced copy starts from q(r)
-            double q0, q1, q2;
-            const double qp = q_predict(a, a0 + j, q0, q1, q2);
-            sh.qst[0][j] = q0;
-            sh.qst[1][j] = q1;
-            sh.qst[2][j] = q2;
-            sh.q[j] = disp ? q0 : qp;
+        if (a.have_warm) {   // predictor 2 q(t) - q(t - dt); a displaced copy starts from q(r)
+            const double qt = a.qpop[a0 + j];
+            sh.qst[j] = qt;
+            sh.q[j] = disp ? qt : fma(2.0, qt, -a.qprev[a0 + j]);
         } else {
             sh.q[j] = sh.zv[j];
         }
@@ -1422,7 +1418,8 @@ __device__ void p_cell(const DevSK &sk, const DftbArgs &a, const PbcDev &pl, SH 
         }
         const int at = a0 + j;
         for (int k = 0; k < 3; ++k) a.F[3 * at + k] = -G[k];
-        q_history_push(a, at, sh.q[j], sh.qst[0][j], sh.qst[1][j], sh.qst[2][j]);
+        a.qprev[at] = a.have_warm ? sh.qst[j] : sh.q[j];
+        a.qpop[at] = sh.q[j];
         if (a.Qout) a.Qout[at] = sh.zv[j] - sh.q[j];
         if (a.write_b) {
             const double Q = sh.zv[j] - sh.q[j];
