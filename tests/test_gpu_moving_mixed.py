@@ -167,3 +167,14 @@ def test_full_size_c5_moving(P):
     live = bD > 0
     print(f"\nc5 moving full size: max |dD| / bound {np.max(np.abs(obs['D'] - D_ref)[live] / bD[live]):.3f} over "
           f"{mo.n_modes} modes, max |dF| / bound {np.max(np.abs(ev['F_total'] - F_ref) / bF):.3f}")
+
+
+def test_clusters_within_bound(P):
+    """Clusters of one to eight waters (the persistent cluster kernel, config 3's composition) with
+    moving mode positions on the tensor cores: the initial evaluation and three steps later, with
+    the grid's wave vectors scaled twofold (the position term stays over 100x the bound)."""
+    w = _workload("c3", n=40, scale=2.0)
+    ctx = _ctx(P, w, precision=2, graph_chunk=0)
+    _check_eval(ctx, w, w["system"].r, "moving c3 40 clusters, initial")
+    ctx.cavmd_step(3)
+    _check_eval(ctx, w, ctx.cavmd_get_state()["r"], "moving c3 40 clusters, step 3")
