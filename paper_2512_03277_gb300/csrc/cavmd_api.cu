@@ -69,6 +69,7 @@ struct cavmd_ctx {
     float *d_Wt2 = nullptr, *d_Wt1 = nullptr;
     unsigned *d_done = nullptr, *d_status = nullptr;
     long long *d_step = nullptr;
+    unsigned *d_pack = nullptr;                // read-out packing: iteration maximum and ticket
     std::vector<void *> allocs;
     // host-side bookkeeping
     unsigned *h_status = nullptr;   // pinned
@@ -818,7 +819,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     AL(c->d_W1, M); AL(c->d_W2, M); AL(c->d_emode, 4 * M);
     const int fb = field_blocks(N);
     AL(c->d_ekp, fb); AL(c->d_edp, fb); AL(c->d_hist, 8 * (size_t)c->opt.energy_history);
-    AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1);
+    AL(c->d_done, 1); AL(c->d_status, 1); AL(c->d_step, 1); AL(c->d_pack, 2);
     AL(c->d_obs, 16 + (size_t)N + 3 * (size_t)M);
     AL(c->d_obs1, 16 + (size_t)N + 3 * (size_t)M);
     // finite-difference copies: 3 per atom (forward) or 6 (central); n_disp counts them per water
@@ -864,6 +865,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(c->d_step, 0, sizeof(long long), st));
+    CK(cudaMemsetAsync(c->d_pack, 0, 2 * sizeof(unsigned), st));
     CK(cudaMemsetAsync(c->d_hist, 0, sizeof(double) * 8 * c->opt.energy_history, st));
     CK(cudaMemsetAsync(c->d_q, 0, sizeof(double) * M, st));
     CK(cudaMemsetAsync(c->d_pq, 0, sizeof(double) * M, st));
@@ -1170,7 +1172,7 @@ int cavmd_observables_async(cavmd_ctx *c, int32_t slot, int32_t with_arrays) {
     // left the device buffer before it is packed again.
     CK(cudaStreamWaitEvent(c->stream, c->obs_ev[slot], 0));
     CK(launch_obs_pack(c->d_hist + 8 * (size_t)hs, c->d_iters, c->N, c->d_status, c->d_Mc, c->d_qs, c->d_pqs,
-                       c->d_D, c->M, arrays, d, c->stream));
+                       c->d_D, c->M, arrays, d, c->d_pack, c->stream));
     CK(cudaEventRecord(c->obs_packed[slot], c->stream));
     CK(cudaStreamWaitEvent(c->copy_stream, c->obs_packed[slot], 0));
     CK(cudaMemcpyAsync(h, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->copy_stream));

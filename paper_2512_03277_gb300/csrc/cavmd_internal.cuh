@@ -310,6 +310,6 @@ int field_blocks(int N);
 // the observables of the synchronised state packed into one buffer (see couple_kernels.cu)
 cudaError_t launch_obs_pack(const double *hist_slot, const int *iters, int N, const unsigned *status,
                             const double *Mc, const double *q, const double *p, const double *D, int M,
-                            bool with_arrays, double *out, cudaStream_t st);
+                            bool with_arrays, double *out, unsigned *scr, cudaStream_t st);   // scr: 2 zeroed words
 cudaError_t launch_field_only(const double *U, const double *W, int M, int N, double *E,
                               cudaStream_t st);

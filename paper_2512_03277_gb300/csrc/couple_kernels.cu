@@ -20,6 +20,8 @@
 //           and appends the energies of the synchronised state to the history ring.
 // k_kick:   the same kicks, drift and energy record when the tensor-core back product has
 //           already formed the fields: one thread per cell.
+#include <algorithm>
+
 #include "cavmd_internal.cuh"
 
 namespace {
@@ -732,23 +734,26 @@ cudaError_t launch_trial_positions(const double *r, const double *p, const doubl
 
 // Observables of the synchronised state packed for one device-to-host copy:
 // out[0..7] the energy record, out[8] the largest SCC iteration count, out[9] the status word,
-// then M (N), q, p, D (M each) from out[16].
-static __global__ void k_obs_pack(const double *__restrict__ hist_slot, const int *__restrict__ iters, int N,
-                                  const unsigned *__restrict__ status, const double *__restrict__ Mc,
-                                  const double *__restrict__ q, const double *__restrict__ p,
-                                  const double *__restrict__ D, int M, int with_arrays,
-                                  double *__restrict__ out) {
-    __shared__ int mx[8];
+// then M (N), q, p, D (M each) from out[16]. Grid-stride copies over many blocks; the largest
+// iteration count goes through an atomic maximum in scr[0] (order-independent), and the last block
+// to finish (ticket in scr[1]) writes the scalars and resets both.
+constexpr int PACK_THREADS = 256;
+static __global__ void __launch_bounds__(PACK_THREADS) k_obs_pack(
+    const double *__restrict__ hist_slot, const int *__restrict__ iters, int N, const unsigned *__restrict__ status,
+    const double *__restrict__ Mc, const double *__restrict__ q, const double *__restrict__ p,
+    const double *__restrict__ D, int M, int with_arrays, double *__restrict__ out, unsigned *__restrict__ scr) {
+    __shared__ unsigned mx[PACK_THREADS / 32];
+    __shared__ bool last;
     const int t = threadIdx.x;
-    int m = 0;
-    for (int n = t; n < N; n += blockDim.x) m = max(m, iters[n]);
+    const long long g = (long long)blockIdx.x * PACK_THREADS + t, stride = (long long)gridDim.x * PACK_THREADS;
+    unsigned m = 0u;
+    for (long long n = g; n < N; n += stride) m = max(m, (unsigned)max(iters[n], 0));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(CAVMD_FULL_MASK, m, o));
     if ((t & 31) == 0) mx[t >> 5] = m;
-    if (t < 8) out[t] = hist_slot[t];
     if (with_arrays) {
-        for (int n = t; n < N; n += blockDim.x) out[16 + n] = Mc[n];
-        for (int a = t; a < M; a += blockDim.x) {
+        for (long long n = g; n < N; n += stride) out[16 + n] = Mc[n];
+        for (long long a = g; a < M; a += stride) {
             out[16 + N + a] = q[a];
             out[16 + N + M + a] = p[a];
             out[16 + N + 2 * M + a] = D[a];
@@ -756,17 +761,31 @@ static __global__ void k_obs_pack(const double *__restrict__ hist_slot, const in
     }
     __syncthreads();
     if (t == 0) {
-        int r = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, mx[w]);
-        out[8] = (double)r;
+        unsigned r = 0u;
+        for (int w = 0; w < PACK_THREADS / 32; ++w) r = max(r, mx[w]);
+        atomicMax(scr, r);
+        __threadfence();
+        last = atomicAdd(scr + 1, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    if (t < 8) out[t] = hist_slot[t];
+    if (t == 0) {
+        __threadfence();
+        out[8] = (double)atomicAdd(scr, 0u);
         out[9] = (double)*status;
+        scr[0] = 0u;
+        scr[1] = 0u;
     }
 }
 
 cudaError_t launch_obs_pack(const double *hist_slot, const int *iters, int N, const unsigned *status,
                             const double *Mc, const double *q, const double *p, const double *D, int M,
-                            bool with_arrays, double *out, cudaStream_t st) {
-    k_obs_pack<<<1, 1024, 0, st>>>(hist_slot, iters, N, status, Mc, q, p, D, M, with_arrays ? 1 : 0, out);
+                            bool with_arrays, double *out, unsigned *scr, cudaStream_t st) {
+    const long long work = std::max<long long>(N, M);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(1216, (work + 4 * PACK_THREADS - 1) / (4 * PACK_THREADS)));
+    k_obs_pack<<<grid, PACK_THREADS, 0, st>>>(hist_slot, iters, N, status, Mc, q, p, D, M, with_arrays ? 1 : 0, out,
+                                              scr);
     return cudaGetLastError();
 }
 

@@ -122,31 +122,89 @@ __device__ __forceinline__ void turn_sincos(uint64_t T, unsigned j, float &c, fl
 // Every step with moving mode positions: the phase panels at the cells' centres of mass
 // R_n = sum_j m_j r_j / m_n (summed over the cell's atoms in order), with the phases cos | sin(jx dkx X_n)
 // and cos | sin(jy dky Y_n) from turn_sincos (the FP32 values carry a relative error of at most
-// about 3 * 2^-24). Only the real rows and columns of the real cells are written: the padding keeps
-// the zeros of the context's initial panels.
-__global__ void k_tc_panels_com(int N, int Kx, int Ky2, double x_turns, double y_turns, const double *__restrict__ r,
-                                const double *__restrict__ mass, const int *__restrict__ off, const Panels P) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
-    double mt = 0.0, x0 = 0.0, x1 = 0.0;
-    for (int j = off[n]; j < off[n + 1]; ++j) {
-        const double m = mass[j];
-        mt += m;
-        x0 = fma(m, r[3 * j], x0);
-        x1 = fma(m, r[3 * j + 1], x1);
+// about 3 * 2^-24). One block per 64-cell forward tile, four threads per cell (each a quarter of
+// the wave numbers). The tile's forward panels and its half of a back tile are built in shared
+// memory (zeros first, so padding rows, columns and cells stay zero) and leave as 16-byte stores
+// of whole contiguous runs; the FP32 x panel goes out directly (coalesced over the cells).
+constexpr int PCOM_THREADS = 256;
+__host__ __device__ constexpr size_t pcom_smem(int KY) {
+    return 2 * (size_t)KXP * FWD_CELLS * 2 + (size_t)KY * FWD_CELLS * 4 + 2 * (size_t)KY * FWD_CELLS * 2;
+}
+__global__ void __launch_bounds__(PCOM_THREADS) k_tc_panels_com(int N, int Kx, int Ky2, double x_turns,
+                                                                  double y_turns, const double *__restrict__ r,
+                                                                  const double *__restrict__ mass,
+                                                                  const int *__restrict__ off, const Panels P) {
+    extern __shared__ __align__(16) uint8_t psm[];
+    const int KY = P.KY;
+    const uint32_t A_B = KXP * FWD_CELLS * 2, B_B = KY * FWD_CELLS * 4, Y_B = KY * FWD_CELLS * 2;
+    __nv_bfloat16 *sAhi = reinterpret_cast<__nv_bfloat16 *>(psm), *sAlo = sAhi + KXP * FWD_CELLS;
+    float *sB = reinterpret_cast<float *>(psm + 2 * A_B);
+    __nv_bfloat16 *sYhi = reinterpret_cast<__nv_bfloat16 *>(psm + 2 * A_B + B_B), *sYlo = sYhi + KY * FWD_CELLS;
+    const uint32_t total = 2 * A_B + B_B + 2 * Y_B;
+    for (uint32_t e = threadIdx.x; e < total / 16; e += PCOM_THREADS)
+        reinterpret_cast<uint4 *>(psm)[e] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    const int t = blockIdx.x, c = threadIdx.x & (FWD_CELLS - 1), qq = threadIdx.x / FWD_CELLS;
+    const int n = t * FWD_CELLS + c;
+    const int h = t & 1;   // which half of its 128-cell back tile this forward tile is
+    if (n < N) {
+        double mt = 0.0, x0 = 0.0, x1 = 0.0;
+        for (int j = off[n]; j < off[n + 1]; ++j) {
+            const double m = mass[j];
+            mt += m;
+            x0 = fma(m, r[3 * j], x0);
+            x1 = fma(m, r[3 * j + 1], x1);
+        }
+        const uint64_t Tx = turns_fixed(x0 / mt * x_turns), Ty = turns_fixed(x1 / mt * y_turns);
+        auto put_x = [&](int i, float v) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(v, hi, lo);
+            const uint32_t e = tc::core_offset(i, c, (KXP / 8) * 128) / 2;
+            sAhi[e] = hi;
+            sAlo[e] = lo;
+            P.Af[(size_t)i * P.Npad + n] = v;
+        };
+        auto put_y = [&](int j, float v) {
+            sB[tc::core_offset(j, c, (KY / 8) * 128) / 2] = v;
+            // back Y: row c of this half tile, K = j: (j / 8) runs of 1 KB in the staging buffer
+            const uint32_t e = ((uint32_t)(j >> 3) * 1024u + (uint32_t)(c >> 3) * 128u + (uint32_t)(c & 7) * 16u +
+                                (uint32_t)(j & 7) * 2u) / 2;
+            __nv_bfloat16 hi, lo;
+            split_bf16(v, hi, lo);
+            sYhi[e] = hi;
+            sYlo[e] = lo;
+        };
+        for (int jx = qq; jx < Kx; jx += PCOM_THREADS / FWD_CELLS) {
+            float cs, sn;
+            turn_sincos(Tx, (unsigned)jx, cs, sn);
+            put_x(jx, cs);
+            put_x(Kx + jx, sn);
+        }
+        for (int jy = qq; jy < Ky2; jy += PCOM_THREADS / FWD_CELLS) {
+            float cs, sn;
+            turn_sincos(Ty, (unsigned)jy, cs, sn);
+            put_y(jy, cs);
+            put_y(Ky2 + jy, sn);
+        }
     }
-    const uint64_t Tx = turns_fixed(x0 / mt * x_turns), Ty = turns_fixed(x1 / mt * y_turns);
-    for (int jx = 0; jx < Kx; ++jx) {
-        float c, sn;
-        turn_sincos(Tx, (unsigned)jx, c, sn);
-        P.put_x(n, jx, c);
-        P.put_x(n, Kx + jx, sn);
+    __syncthreads();
+    // whole runs out: the forward tile's A hi, A lo and B (contiguous), the half back tile's Y in
+    // KY / 8 runs of 1 KB (its 64 rows of every K group)
+    uint4 *gAhi = reinterpret_cast<uint4 *>(P.Ahi + (size_t)t * KXP * FWD_CELLS);
+    uint4 *gAlo = reinterpret_cast<uint4 *>(P.Alo + (size_t)t * KXP * FWD_CELLS);
+    uint4 *gB = reinterpret_cast<uint4 *>(P.Bsrc + (size_t)t * KY * FWD_CELLS);
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(psm);
+    for (uint32_t e = threadIdx.x; e < A_B / 16; e += PCOM_THREADS) {
+        gAhi[e] = s4[e];
+        gAlo[e] = s4[A_B / 16 + e];
     }
-    for (int jy = 0; jy < Ky2; ++jy) {
-        float c, sn;
-        turn_sincos(Ty, (unsigned)jy, c, sn);
-        P.put_y(n, jy, c);
-        P.put_y(n, Ky2 + jy, sn);
+    for (uint32_t e = threadIdx.x; e < B_B / 16; e += PCOM_THREADS) gB[e] = s4[2 * A_B / 16 + e];
+    const size_t ybase = (size_t)(t >> 1) * BACK_CELLS * KY;   // elements
+    for (uint32_t e = threadIdx.x; e < Y_B / 16; e += PCOM_THREADS) {
+        const uint32_t kc = e / 64, w = e - kc * 64;   // 64 uint4 per 1 KB run
+        const size_t g = ybase + ((size_t)kc * 2048 + (size_t)h * 1024) / 2;   // elements
+        reinterpret_cast<uint4 *>(P.Yhi + g)[w] = s4[(2 * A_B + B_B) / 16 + e];
+        reinterpret_cast<uint4 *>(P.Ylo + g)[w] = s4[(2 * A_B + B_B + Y_B) / 16 + e];
     }
 }
 
@@ -514,6 +572,7 @@ cudaError_t tc_prepare(int KY) {
         break;
     switch (KY) { PREP_CASE(16) PREP_CASE(32) PREP_CASE(48) PREP_CASE(64) PREP_CASE(96) PREP_CASE(128) }
 #undef PREP_CASE
+    if (e == cudaSuccess) e = set_smem(k_tc_panels_com, pcom_smem(KY));
     return e;
 }
 
@@ -533,8 +592,9 @@ cudaError_t launch_tc_panels(const TcPlan &p, const double *R, cudaStream_t st) 
 cudaError_t launch_tc_panels_com(const TcPlan &p, const double *r, const double *mass, const int *cell_offset,
                                  cudaStream_t st) {
     const double two_pi = 6.283185307179586;
-    k_tc_panels_com<<<(p.N + 127) / 128, 128, 0, st>>>(p.N, p.Kx, p.Ky2, p.dkx / two_pi, p.dky / two_pi, r, mass,
-                                                        cell_offset, panels_of(p));
+    const int tiles = (p.N + FWD_CELLS - 1) / FWD_CELLS;
+    k_tc_panels_com<<<tiles, PCOM_THREADS, pcom_smem(p.KY), st>>>(p.N, p.Kx, p.Ky2, p.dkx / two_pi, p.dky / two_pi, r,
+                                                                   mass, cell_offset, panels_of(p));
     return cudaGetLastError();
 }
 
