@@ -142,3 +142,24 @@ def test_liquid_cell_of_33_waters(P):
     np.testing.assert_allclose(ev["E_cell"][0], ref["E"], rtol=0, atol=1e-10)
     print(f"\n33-water cell on the 3 x 3 x 3 grid: {ev['scc_iters'].max()} SCC iterations, "
           f"E(k) - E(Gamma) = {ref['E'] - PR.dftb_periodic(params, sy.species, sy.r, lat, forces=False)['E']:.3e} Ha")
+
+
+def test_p33_on_the_grid_sampled(P):
+    """p33 on the 3 x 3 x 3 grid at the size bench.py times it (152 cells of 33 waters, one per SM):
+    the last cell against the oracle's k-grid (its plain NumPy solve takes about 1.5 minutes), every
+    cell's population sum (264 electrons)."""
+    kgrid = (3, 3, 3)
+    w = cs.make_workload("p33", n_cells=152)
+    sy, lat, params = w["system"], w["lattice"], w["params"]
+    o = P.default_options()
+    o.kgrid[:] = kgrid
+    ctx = P.Context(sy, params, w["modes"], o, lattice=lat)
+    ev = ctx.cavmd_get_eval()
+    np.testing.assert_allclose(ev["q_pop"].reshape(sy.n_cells, -1).sum(1), 264.0, rtol=0, atol=1e-9)
+    for c in (151,):
+        s = slice(sy.cell_offset[c], sy.cell_offset[c + 1])
+        ref = PR.dftb_periodic_k(params, sy.species[s], sy.r[s], lat, kgrid)
+        fs = np.abs(ref["F"]).max()
+        np.testing.assert_allclose(ev["F_dftb"][s], ref["F"], rtol=0, atol=1e-9 * fs)
+        np.testing.assert_allclose(ev["q_pop"][s], ref["q"], rtol=0, atol=1e-10)
+        np.testing.assert_allclose(ev["E_cell"][c], ref["E"], rtol=0, atol=1e-10)
