@@ -163,3 +163,36 @@ def test_p33_on_the_grid_sampled(P):
         np.testing.assert_allclose(ev["F_dftb"][s], ref["F"], rtol=0, atol=1e-9 * fs)
         np.testing.assert_allclose(ev["q_pop"][s], ref["q"], rtol=0, atol=1e-10)
         np.testing.assert_allclose(ev["E_cell"][c], ref["E"], rtol=0, atol=1e-10)
+
+
+def test_graph_replay_is_bitwise_identical(P):
+    """Two-water cells on the 3 x 3 x 3 grid: graph replay of four-step chunks against one call per
+    step, bitwise."""
+    sy, lat = _cells(2)
+    a = _ctx(P, sy, lat, (3, 3, 3), graph_chunk=0)
+    b = _ctx(P, sy, lat, (3, 3, 3), graph_chunk=4)
+    a.cavmd_step(6)
+    b.cavmd_step(6)
+    sa, sb = a.cavmd_get_state(), b.cavmd_get_state()
+    for k in ("r", "p", "q", "pq"):
+        assert np.array_equal(sa[k], sb[k]), k
+
+
+def test_periodic_cells_with_the_tensor_core_coupling(P):
+    """Periodic cells (Gamma point and the 3 x 3 x 3 grid) coupled to config 4's 32 x 32 grid of modes
+    through the BF16x3 tensor-core coupling: D and the total force within the bounds of
+    tests/bf16x3.py against the plain contractions of the GPU's own dipoles."""
+    from bf16x3 import bounds, direct_forward_and_field
+    sy, lat = _cells(40)
+    mo = cs.make_workload("c4", n_cells=40)["modes"]
+    for kgrid in ((1, 1, 1), (3, 3, 3)):
+        ctx = _ctx(P, sy, lat, kgrid, modes=mo, precision=2, photon_init=1)
+        ev = ctx.cavmd_get_eval()
+        obs = ctx.cavmd_observables()
+        W = mo.lam * (mo.omega * obs["q"] - obs["D"])
+        D_ref, E_ref = direct_forward_and_field(mo, sy.R_ref, ev["M"], W)
+        bD, bE = bounds(mo, sy.R_ref, ev["M"], W)
+        assert np.all(np.abs(obs["D"] - D_ref) <= bD + 1e-300)
+        cell = np.repeat(np.arange(sy.n_cells), np.diff(sy.cell_offset))
+        F_ref = ev["F_dftb"] + E_ref[cell][:, None] * ev["b"]
+        assert np.all(np.abs(ev["F_total"] - F_ref) <= bE[cell][:, None] * np.abs(ev["b"]) + 1e-12)
