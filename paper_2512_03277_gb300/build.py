@@ -34,10 +34,24 @@ def _stale(srcs, out):
 
 
 def build(force=False, verbose=False):
+    """Compile if any source is newer than the library. Processes that start together (one per
+    GPU) take a file lock, so one compiles and the others find the library fresh."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     if not force and not _stale(srcs, OUT):
         return OUT
     os.makedirs(BUILD, exist_ok=True)
+    import fcntl
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale(srcs, OUT):
+                return OUT
+            return _compile(srcs, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _compile(srcs, verbose):
     nvcc = _nvcc()
 
     def compile_one(src):
@@ -52,7 +66,7 @@ def build(force=False, verbose=False):
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = OUT + ".tmp"
+    tmp = OUT + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
