@@ -181,7 +181,10 @@ def test_graph_replay_is_bitwise_identical(P):
 def test_periodic_cells_with_the_tensor_core_coupling(P):
     """Periodic cells (Gamma point and the 3 x 3 x 3 grid) coupled to config 4's 32 x 32 grid of modes
     through the BF16x3 tensor-core coupling: D and the total force within the bounds of
-    tests/bf16x3.py against the plain contractions of the GPU's own dipoles."""
+    tests/bf16x3.py against the plain contractions of the GPU's own dipoles. The cells all sit at
+    y = 0, so the sin(jy thy) factors are exactly zero: the GPU's factorised phases give D = 0 for
+    the jx = 0 sin modes, while the reference's cos(k.R - pi/2) carries the FP64 rounding of pi/2
+    (about 6e-17); the D check adds 4 * 2^-52 lambda_a sum_n |M_n| for that."""
     from bf16x3 import bounds, direct_forward_and_field
     sy, lat = _cells(40)
     mo = cs.make_workload("c4", n_cells=40)["modes"]
@@ -192,7 +195,8 @@ def test_periodic_cells_with_the_tensor_core_coupling(P):
         W = mo.lam * (mo.omega * obs["q"] - obs["D"])
         D_ref, E_ref = direct_forward_and_field(mo, sy.R_ref, ev["M"], W)
         bD, bE = bounds(mo, sy.R_ref, ev["M"], W)
-        assert np.all(np.abs(obs["D"] - D_ref) <= bD + 1e-300)
+        ref_round = 4.0 * 2.0 ** -52 * np.abs(mo.lam) * np.abs(ev["M"]).sum()
+        assert np.all(np.abs(obs["D"] - D_ref) <= bD + ref_round)
         cell = np.repeat(np.arange(sy.n_cells), np.diff(sy.cell_offset))
         F_ref = ev["F_dftb"] + E_ref[cell][:, None] * ev["b"]
         assert np.all(np.abs(ev["F_total"] - F_ref) <= bE[cell][:, None] * np.abs(ev["b"]) + 1e-12)
