@@ -200,3 +200,22 @@ def test_periodic_cells_with_the_tensor_core_coupling(P):
         cell = np.repeat(np.arange(sy.n_cells), np.diff(sy.cell_offset))
         F_ref = ev["F_dftb"] + E_ref[cell][:, None] * ev["b"]
         assert np.all(np.abs(ev["F_total"] - F_ref) <= bE[cell][:, None] * np.abs(ev["b"]) + 1e-12)
+
+
+@pytest.mark.parametrize("kgrid", [(1, 1, 1), (2, 1, 1)])
+def test_largest_cell(P, kgrid):
+    """The largest periodic cell the kernels take: 42 waters (126 atoms, 252 orbitals; the limits are
+    128 atoms and 256 orbitals), at liquid density, at the Gamma point and on a 2 x 1 x 1 grid (real
+    forms of 504, the widest problem the k-grid staging holds), against the oracle."""
+    rng = np.random.default_rng(5)
+    side = 10.0 * cs.ANGSTROM * (42.0 / 33.0) ** (1.0 / 3.0)
+    sy, lat = cs.periodic_water_cells(rng, np.zeros((1, 3)), n_waters=42, side=side)
+    params = cs.load_water_params()
+    ctx = _ctx(P, sy, lat, kgrid)
+    ev = ctx.cavmd_get_eval()
+    ref = (PR.dftb_periodic(params, sy.species, sy.r, lat) if kgrid == (1, 1, 1)
+           else PR.dftb_periodic_k(params, sy.species, sy.r, lat, kgrid))
+    fs = np.abs(ref["F"]).max()
+    np.testing.assert_allclose(ev["F_dftb"], ref["F"], rtol=0, atol=1e-9 * fs)
+    np.testing.assert_allclose(ev["q_pop"], ref["q"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(ev["E_cell"][0], ref["E"], rtol=0, atol=1e-10)
