@@ -135,16 +135,23 @@ __global__ void k_features(int n_cells, const int *__restrict__ off, const int *
 //       float's 24-bit significand, so A B^T equals the FP32 products to accumulation rounding;
 //   B = the layer's BF16 weights (exact), N outputs x K, K-major core matrices.
 // L1: K = 32, N = 128 into TMEM columns 0..127; L2: K = 128, N = 128 into columns 128..255;
-// L3: K = 128, N = 16 (the 9 outputs, zero-padded) into columns 0..15, free again once L1's
-// epilogue has read them. The epilogues read TMEM (warp w of 16: lanes 32 (w mod 4) .. + 31,
-// columns 32 (w div 4) .. + 31), add the bias, apply silu and write the next layer's split operand to
-// shared memory; the last forms Zl = R^T T R for its atom. One persistent CTA per SM loads the
-// weights once; every mbarrier wait is bounded (timeout: status bit, TMEM still released).
+// L3: K = 128, N = 16 (the 9 outputs, zero-padded) into columns 128..143, which the second
+// epilogue has read in its first round. Sixteen epilogue warps read TMEM (warp w: lanes
+// 32 (w mod 4) .. + 31), add the bias, apply silu and write the next layer's split operand to
+// shared memory in four rounds of 32 columns (K chunks; warp w takes columns 8 (w div 4) + 32 c of
+// round c), and a seventeenth warp issues the MMAs: each K chunk of L2 and L3 as soon as all
+// sixteen warps have written it, so the next layer's MMAs run under the rest of the epilogue. The
+// MMA order is that of one chain per layer (K steps ascending, parts hi, mid, lo), so the sums do
+// not depend on the overlap. The next tile's inputs are loaded during the second epilogue and the
+// last layer's outputs (Zl = R^T T R per atom) are formed while the next tile's first layer runs.
+// One persistent CTA per SM loads the weights once; every mbarrier wait is bounded (timeout:
+// status bit, the MMAs in flight drained, TMEM still released).
 // Training keeps what the backward pass reads (FwdStore): the pre-activations z1, z2 atom-major,
 // and the layer inputs x, h1, h2 feature-major per tile ([tile][feature][atom of the tile]), the
 // layout in which the weight-gradient kernel stages them as K-major operands over atoms.
 constexpr int MT = 128;                              // atoms per tile = TMEM lanes
 constexpr int FWD_THREADS = 512;                     // 16 warps: four per TMEM lane quadrant
+constexpr int FWD_TC_THREADS = FWD_THREADS + 32;     // the forward: 16 epilogue warps and one MMA warp
 constexpr uint32_t LBO_A = (MT / 8) * 128;           // A operand: K-group stride (128 rows)
 constexpr uint32_t LBO_W = (NH / 8) * 128;           // W1, W2: 128 rows
 constexpr uint32_t LBO_W3 = (16 / 8) * 128;          // W3 padded to 16 rows
@@ -214,51 +221,111 @@ struct FwdStore {       // training outputs of the forward (all NULL in the time
     float *xt;          // [tile][32][128] network inputs, feature-major per tile
 };
 
-// Hidden-layer epilogue: 32 TMEM columns of this thread's atom -> z = d + b -> silu -> split A
-// operand; zg (this atom's row of z) and ht (this atom's column of the tile's activations) may be
-// NULL.
-__device__ __forceinline__ void hidden_epilogue(uint32_t taddr, int col0, const float *b, uint8_t *sa, int row,
-                                                float *zg, float *ht) {
-    float v[32];
-    tc::tmem_ld32(taddr, v);
+// Hidden-layer epilogue, one 8-column chunk of this thread's atom (the accumulator values v):
+// z = d + b -> silu -> split A operand; zg (this atom's row of z) and ht (this atom's column of the
+// tile's activations) may be NULL.
+__device__ __forceinline__ void hidden_chunk(const uint32_t (&v)[8], int col, const float *b, uint8_t *sa, int row,
+                                             float *zg, float *ht) {
+    float x[8], z[8];
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        float x[8], z[8];
+    for (int q = 0; q < 8; ++q) {
+        z[q] = __uint_as_float(v[q]) + b[col + q];
+        x[q] = silu_fast(z[q]);
+    }
+    if (zg) {
+        *reinterpret_cast<float4 *>(zg + col) = make_float4(z[0], z[1], z[2], z[3]);
+        *reinterpret_cast<float4 *>(zg + col + 4) = make_float4(z[4], z[5], z[6], z[7]);
+    }
+    if (ht)
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            z[q] = v[8 * g + q] + b[col0 + 8 * g + q];
-            x[q] = silu_fast(z[q]);
-        }
-        if (zg) {
-            *reinterpret_cast<float4 *>(zg + col0 + 8 * g) = make_float4(z[0], z[1], z[2], z[3]);
-            *reinterpret_cast<float4 *>(zg + col0 + 8 * g + 4) = make_float4(z[4], z[5], z[6], z[7]);
-        }
-        if (ht)
+        for (int q = 0; q < 8; ++q) ht[(size_t)(col + q) * MT] = x[q];
+    split_store8(sa, tc::core_offset(row, col, LBO_A), x);
+}
+
+// Eight input features of one atom (chunk c of the tile: features 8 (c / MT) .., atom c mod MT), or
+// zeros past the last atom.
+__device__ __forceinline__ void load_x8(const float *X, int n, int t0, int c, float (&x)[8]) {
+    const int g = c / MT, r = c - g * MT;
+    if (t0 + r < n) {
+        const float4 u0 = *reinterpret_cast<const float4 *>(X + (size_t)(t0 + r) * NF + 8 * g);
+        const float4 u1 = *reinterpret_cast<const float4 *>(X + (size_t)(t0 + r) * NF + 8 * g + 4);
+        x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
+        x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
+    } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) ht[(size_t)(col0 + 8 * g + q) * MT] = x[q];
-        split_store8(sa, tc::core_offset(row, col0 + 8 * g, LBO_A), x);
+        for (int q = 0; q < 8; ++q) x[q] = 0.0f;
     }
 }
 
-__global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const float *__restrict__ X,
-                                                             const float *__restrict__ R,
-                                                             const __nv_bfloat16 *__restrict__ w,
-                                                             float *__restrict__ Zl, unsigned *__restrict__ status,
-                                                             const FwdStore st) {
+// ... into the K = 32 operand of L1 (and, in training, the tile's feature-major copy).
+__device__ __forceinline__ void store_x8(uint8_t *sa, int t, int c, const float (&x)[8], float *xt) {
+    const int g = c / MT, r = c - g * MT;
+    if (xt)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) xt[((size_t)t * NF + 8 * g + q) * MT + r] = x[q];
+    split_store8(sa, tc::core_offset(r, 8 * g, LBO_A), x);
+}
+
+// K steps k0, k0 + 1 of one layer (issued by one thread), in the order of the whole chain: for each
+// K step the parts hi, mid, lo; the first product of the chain overwrites the accumulator.
+__device__ __forceinline__ void chunk_mma(uint32_t tmem_d, uint32_t sa, uint32_t sw, uint32_t lbo_w, int k0,
+                                          uint32_t idesc) {
+#pragma unroll
+    for (int k = k0; k < k0 + 2; ++k) {
+        const uint64_t bd = tc::make_desc(sw + (uint32_t)k * 2 * lbo_w, lbo_w, 128);
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+            tc::mma_bf16(tmem_d, tc::make_desc(sa + s * A_SPLIT + (uint32_t)k * 2 * LBO_A, LBO_A, 128), bd, idesc,
+                         (k > 0 || s > 0) ? 1u : 0u);
+    }
+}
+
+// Outputs of one atom: y = the L3 accumulator + b3, Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k].
+__device__ __forceinline__ void output_atom(const float (&v)[32], const float *b3, const float (&Rj)[9], float *zl) {
+    float y[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) y[o] = v[o] + b3[o];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) {
+            float s = 0.0f;
+            for (int aa = 0; aa < 3; ++aa)
+                for (int bb = 0; bb < 3; ++bb) s = fmaf(Rj[3 * aa + i] * y[3 * aa + bb], Rj[3 * bb + k], s);
+            zl[3 * i + k] = s;
+        }
+}
+
+__global__ void __launch_bounds__(FWD_TC_THREADS, 1) k_forward_tc(int n, const float *__restrict__ X,
+                                                                const float *__restrict__ R,
+                                                                const __nv_bfloat16 *__restrict__ w,
+                                                                float *__restrict__ Zl, unsigned *__restrict__ status,
+                                                                const FwdStore st) {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *sw1 = smem, *sw2 = sw1 + SW1, *sw3 = sw2 + SW2, *sa = sw3 + SW3;   // sa: [hi][mid][lo]
     float *bias = reinterpret_cast<float *>(sa + 3 * A_SPLIT);                  // b1 [128] b2 [128] b3 [16]
-    uint64_t *done = reinterpret_cast<uint64_t *>(bias + 2 * NH + 16);
-    uint32_t *slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *done = reinterpret_cast<uint64_t *>(bias + 2 * NH + 16);        // a layer's MMAs finished
+    uint64_t *chunk = done + 1;                                                // [4] K chunk c written
+    uint64_t *drain = chunk + 4;                                               // error path: MMAs in flight
+    uint32_t *slot = reinterpret_cast<uint32_t *>(drain + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool mma_warp = warp == FWD_THREADS / 32;
     if (warp == 0) tc::tmem_alloc(slot, 256);
-    if (tid == 0) tc::mbar_init(done, 1);
+    if (tid == 0) {
+        tc::mbar_init(done, 1);
+        for (int c = 0; c < 4; ++c) tc::mbar_init(&chunk[c], FWD_THREADS / 32);
+        tc::mbar_init(drain, 1);
+    }
     const uint16_t *wr = reinterpret_cast<const uint16_t *>(w);
     load_weights(sw1, wr + OFF_W1, NH, NH, NF, LBO_W);
     load_weights(sw2, wr + OFF_W2, NH, NH, NH, LBO_W);
     load_weights(sw3, wr + OFF_W3, 16, NO, NH, LBO_W3);
-    for (int e = tid; e < 2 * NH + 16; e += FWD_THREADS)
+    for (int e = tid; e < 2 * NH + 16; e += blockDim.x)
         bias[e] = e < 2 * NH ? wv(w, (e < NH ? OFF_B1 : OFF_B2 - NH) + e) : (e - 2 * NH < NO ? wv(w, OFF_B3 + e - 2 * NH) : 0.0f);
+    const int n_tiles = (n + MT - 1) / MT;
+    if (!mma_warp && (int)blockIdx.x < n_tiles) {   // the first tile's inputs
+        float x[8];
+        load_x8(X, n, blockIdx.x * MT, tid, x);
+        store_x8(sa, blockIdx.x, tid, x, st.xt);
+    }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -266,77 +333,98 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_forward_tc(int n, const floa
     const uint32_t tmem = *slot;
     const uint32_t sa_u = tc::smem_u32(sa), sw1_u = tc::smem_u32(sw1), sw2_u = tc::smem_u32(sw2),
                    sw3_u = tc::smem_u32(sw3);
-    const uint32_t quad = warp & 3, slice = warp >> 2;   // lane quadrant; 32-column slice
-    const uint32_t lanes = tmem + ((32u * quad) << 16);   // this warp's TMEM lanes
-    const int row = 32 * quad + lane;                      // this thread's atom in the tile
+    const uint32_t quad = warp & 3, part = (warp >> 2) & 3;   // lane quadrant; column part of each chunk
+    const uint32_t lanes = tmem + ((32u * quad) << 16);       // this warp's TMEM lanes
+    const int row = 32 * quad + lane;                          // this thread's atom in the tile
     const float *b1 = bias, *b2 = bias + NH, *b3 = bias + 2 * NH;
     constexpr uint32_t ID128 = tc::idesc_bf16(MT, NH), ID16 = tc::idesc_bf16(MT, 16);
-    const int n_tiles = (n + MT - 1) / MT;
-    uint32_t pd = 0u;
+    uint32_t pd = 0u, pc = 0u;   // phase parities: done (epilogue warps), chunk[c] in bit c (MMA warp)
     bool ok = true;
+    float Rp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, Rc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    int t_prev = -1;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int t0 = t * MT;
-        // input features -> A (K = 32)
-        for (int c = tid; c < MT * (NF / 8); c += FWD_THREADS) {
-            const int g = c / MT, r = c - g * MT;
-            float x[8];
-            if (t0 + r < n) {
-                const float4 u0 = *reinterpret_cast<const float4 *>(X + (size_t)(t0 + r) * NF + 8 * g);
-                const float4 u1 = *reinterpret_cast<const float4 *>(X + (size_t)(t0 + r) * NF + 8 * g + 4);
-                x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
-                x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
-            } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) x[q] = 0.0f;
-            }
-            if (st.xt)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) st.xt[((size_t)t * NF + 8 * g + q) * MT + r] = x[q];
-            split_store8(sa, tc::core_offset(r, 8 * g, LBO_A), x);
-        }
-        for (int layer = 0; layer < 3; ++layer) {
-            tc::fence_proxy_async();
-            tc::fence_before_sync();
-            __syncthreads();   // the operand is in shared memory; the previous TMEM reads are done
-            if (tid == 0) {
-                tc::fence_after_sync();
-                if (layer == 0) layer_mma(tmem, sa_u, sw1_u, LBO_W, NF, ID128);
-                else if (layer == 1) layer_mma(tmem + NH, sa_u, sw2_u, LBO_W, NH, ID128);
-                else layer_mma(tmem, sa_u, sw3_u, LBO_W3, NH, ID16);
+        const int t0 = t * MT, tn = t + gridDim.x;
+        if (mma_warp) {
+            if (lane == 0) {
+                layer_mma(tmem, sa_u, sw1_u, LBO_W, NF, ID128);   // L1, the whole chain
                 tc::mma_commit(done);
+                for (int layer = 0; layer < 2; ++layer)
+                    for (int c = 0; c < 4; ++c) {   // L2 (L3) K chunk c once the first (second) epilogue wrote it
+                        const bool g = ok && tc::mbar_wait(&chunk[c], (pc >> c) & 1u);
+                        pc ^= 1u << c;
+                        ok = g;
+                        if (!ok) continue;
+                        tc::fence_after_sync();
+                        if (layer == 0) chunk_mma(tmem + NH, sa_u, sw2_u, LBO_W, 2 * c, ID128);
+                        else chunk_mma(tmem + NH, sa_u, sw3_u, LBO_W3, 2 * c, ID16);
+                        if (c == 3) tc::mma_commit(done);
+                    }
             }
-            const bool mg = tc::mbar_wait(done, pd);
-            pd ^= 1u;
-            if (!__syncthreads_and(mg)) { ok = false; break; }
-            tc::fence_after_sync();
-            if (layer < 2) {
-                float *zb = layer == 0 ? st.z1 : st.z2;
-                float *hb = layer == 0 ? st.h1t : st.h2t;
-                hidden_epilogue(lanes + (layer == 0 ? 0 : NH) + 32 * slice, 32 * slice, layer == 0 ? b1 : b2, sa, row,
-                                zb ? zb + (size_t)(t0 + row) * NH : nullptr,
-                                hb ? hb + (size_t)t * NH * MT + row : nullptr);
-            }
-            else if (slice == 0) {   // outputs: Zl[i][k] = sum_{a,b} R[a][i] T[a][b] R[b][k]
+            __syncwarp();
+        } else {
+            if (t_prev >= 0 && part == 0) {   // outputs of the previous tile (its L3 is complete)
                 float v[32];
-                tc::tmem_ld32(lanes, v);
+                tc::tmem_ld32(lanes + NH, v);
+                if (t_prev * MT + row < n) output_atom(v, b3, Rp, Zl + (size_t)(t_prev * MT + row) * 9);
+            }
+            if (part == 0) {
                 if (t0 + row < n) {
-                    float y[NO];
 #pragma unroll
-                    for (int o = 0; o < NO; ++o) y[o] = v[o] + b3[o];
-                    const float *Rj = R + (size_t)(t0 + row) * 9;
-                    for (int i = 0; i < 3; ++i)
-                        for (int k = 0; k < 3; ++k) {
-                            float s = 0.0f;
-                            for (int aa = 0; aa < 3; ++aa)
-                                for (int bb = 0; bb < 3; ++bb) s = fmaf(Rj[3 * aa + i] * y[3 * aa + bb], Rj[3 * bb + k], s);
-                            Zl[(size_t)(t0 + row) * 9 + 3 * i + k] = s;
-                        }
+                    for (int q = 0; q < 9; ++q) Rc[q] = R[(size_t)(t0 + row) * 9 + q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) Rc[q] = 0.0f;
                 }
             }
+            float xn[8];
+            for (int layer = 0; layer < 2; ++layer) {
+                ok = tc::mbar_wait(done, pd) && ok;   // L1 (L2) finished
+                pd ^= 1u;
+                tc::fence_after_sync();
+                uint32_t v[4][8];
+                const uint32_t acc = lanes + (layer == 0 ? 0u : (uint32_t)NH) + 8 * part;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) tc::tmem_ld8_nowait(acc + 32 * c, v[c]);
+                tc::tmem_wait_ld();
+                if (layer == 1 && tn < n_tiles) load_x8(X, n, tn * MT, tid, xn);   // the next tile's inputs
+                float *zb = layer == 0 ? st.z1 : st.z2;
+                float *hb = layer == 0 ? st.h1t : st.h2t;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int col = 32 * c + 8 * part;
+                    hidden_chunk(v[c], col, layer == 0 ? b1 : b2, sa, row, zb ? zb + (size_t)(t0 + row) * NH : nullptr,
+                                 hb ? hb + (size_t)t * NH * MT + row : nullptr);
+                    tc::fence_proxy_async();   // the operand chunk is visible to the MMAs
+                    tc::fence_before_sync();   // and this round's TMEM reads are ordered before them
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&chunk[c]);
+                }
+            }
+            ok = tc::mbar_wait(done, pd) && ok;   // L3 finished: the operand buffer is free
+            pd ^= 1u;
+            tc::fence_after_sync();
+            if (tn < n_tiles) store_x8(sa, tn, tid, xn, st.xt);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Rp[q] = Rc[q];
+            t_prev = t;
         }
-        if (!ok) break;
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        tc::fence_after_sync();
     }
-    if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+    if (ok && t_prev >= 0 && !mma_warp && part == 0) {   // the last tile's outputs
+        float v[32];
+        tc::tmem_ld32(lanes + NH, v);
+        if (t_prev * MT + row < n) output_atom(v, b3, Rp, Zl + (size_t)(t_prev * MT + row) * 9);
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
+        if (mma_warp && lane == 0) {   // every MMA issued so far completes before TMEM is released
+            tc::mma_commit(drain);
+            tc::mbar_wait(drain, 0);
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
@@ -779,7 +867,7 @@ cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, cons
     if (e != cudaSuccess) return e;
     const int tiles = (n_atoms + MT - 1) / MT;
     const int grid = std::min(tiles, n_sm);
-    k_forward_tc<<<grid, FWD_THREADS, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl, status,
+    k_forward_tc<<<grid, FWD_TC_THREADS, FWD_SMEM, st>>>(n_atoms, X, R, (const __nv_bfloat16 *)w_bf16, Zl, status,
                                                     FwdStore{nullptr, nullptr, nullptr, nullptr, nullptr});
     return cudaGetLastError();
 }
@@ -861,7 +949,7 @@ int mlp_loss_grad_range(cavmd_mlp *m, int cell0, int ncells, const float *X, con
     const int a0 = 3 * cell0, na = 3 * ncells;
     const int tiles = (na + MT - 1) / MT;
     const int grid = std::min(tiles, m->n_sm);
-    k_forward_tc<<<grid, FWD_THREADS, FWD_SMEM, m->stream>>>(na, X + (size_t)a0 * NF, R + (size_t)a0 * 9, m->w,
+    k_forward_tc<<<grid, FWD_TC_THREADS, FWD_SMEM, m->stream>>>(na, X + (size_t)a0 * NF, R + (size_t)a0 * 9, m->w,
                                                              m->Zl, m->status,
                                                              FwdStore{m->z1, m->z2, m->h1t, m->h2t, m->xt});
     k_cell_tensors<<<(ncells + 127) / 128, 128, 0, m->stream>>>(ncells, m->off, m->Zl, R + (size_t)a0 * 9, Q + a0,
