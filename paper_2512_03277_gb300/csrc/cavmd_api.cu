@@ -35,7 +35,7 @@ struct cavmd_ctx {
     double pol[3] = {1, 0, 0};
     // device buffers
     DevSK *d_sk = nullptr;
-    int *d_off = nullptr, *d_species = nullptr, *d_iters = nullptr;
+    int *d_off = nullptr, *d_species = nullptr, *d_iters = nullptr, *d_acell = nullptr;
     double *d_r = nullptr, *d_p = nullptr, *d_F = nullptr, *d_b = nullptr, *d_qpop = nullptr, *d_qprev = nullptr;
     double *d_C = nullptr, *d_E = nullptr, *d_Mc = nullptr, *d_mass = nullptr, *d_imass = nullptr;
     double *d_U = nullptr, *d_k = nullptr, *d_phi = nullptr, *d_R = nullptr;
@@ -774,7 +774,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     fill_devsk(sk, &hsk);
 
     AL(c->d_sk, 1);
-    AL(c->d_off, N + 1); AL(c->d_species, NA); AL(c->d_iters, N);
+    AL(c->d_off, N + 1); AL(c->d_species, NA); AL(c->d_iters, N); AL(c->d_acell, NA);
     AL(c->d_r, 3 * NA); AL(c->d_p, 3 * NA); AL(c->d_F, 3 * NA); AL(c->d_b, 3 * NA);
     // eigenvector blocks: n_c^2 per cell; the water kernel takes every cell when all are 3-atom,
     // 6-orbital cells, the persistent generic kernel otherwise
@@ -847,6 +847,13 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     CK(cudaMemcpyAsync(c->d_sk, &hsk, sizeof(DevSK), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_off, sys->cell_offset, sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_species, sys->species, sizeof(int) * NA, cudaMemcpyHostToDevice, st));
+    {
+        std::vector<int> acell(NA);
+        for (int n = 0; n < N; ++n)
+            for (int i = sys->cell_offset[n]; i < sys->cell_offset[n + 1]; ++i) acell[i] = n;
+        CK(cudaMemcpyAsync(c->d_acell, acell.data(), sizeof(int) * NA, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));   // acell is pageable and local
+    }
     CK(cudaMemcpyAsync(c->d_r, sys->r, sizeof(double) * 3 * NA, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_p, sys->p, sizeof(double) * 3 * NA, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_mass, mass.data(), sizeof(double) * NA, cudaMemcpyHostToDevice, st));
@@ -1039,6 +1046,7 @@ int build_context(cavmd_ctx *c, const cavmd_system *sys, const cavmd_sk_tables *
     s.E1store = c->d_E1;
     s.Kx = c->tc.Kx; s.Ky2 = c->tc.Ky2; s.KY = c->tc.KY;
     s.Us = c->d_Us; s.kvec = c->d_k; s.Wk2 = c->d_Wk2; s.Wk1 = c->d_Wk1; s.w_atom = c->d_watom;
+    s.atom_cell = c->d_acell;
     s.G1store = c->d_G1; s.G1in = c->d_G1;   // all NULL with fixed mode positions
     s.G2in = c->d_G2;                          // tensor-core coupling with moving mode positions only
     s.paper = c->opt.splitting == CAVMD_SPLIT_PAPER || c->opt.splitting == CAVMD_SPLIT_STRANG;

@@ -115,6 +115,7 @@ struct StepArgs {
     const double *kvec;        // [M][3] wave vectors
     double *Wk2, *Wk1;         // [M][3] -W_a k_a of the second / first half-flow (written by k_photon)
     const double *w_atom;      // [n_atoms] m_j / m_n
+    const int *atom_cell;      // [n_atoms] the cell of each atom
     double *G1store;           // [N][3] G_n of the next first half-flow, kept for the next call
     const double *G1in;        // [N][3] G_n of the opening first half-flow (FLD_E_GIVEN)
     const double *G2in;        // [N][3] G_n of the second half-flow (FLD_E_GIVEN, tensor-core coupling)

@@ -19,7 +19,8 @@
 //           block to finish sums the per-block energy partials in block order (deterministic)
 //           and appends the energies of the synchronised state to the history ring.
 // k_kick:   the same kicks, drift and energy record when the tensor-core back product has
-//           already formed the fields: one thread per cell.
+//           already formed the fields: one thread per Cartesian component of an atom (one thread
+//           per cell with moving mode positions).
 #include <algorithm>
 
 #include "cavmd_internal.cuh"
@@ -29,7 +30,9 @@ namespace {
 constexpr int PH_THREADS = 256;
 constexpr int FLD_CELLS = 16;    // cells per block (N / 16 blocks fill every SM for N >= 2432)
 constexpr int FLD_SLICES = 16;   // mode slices: thread (cell, slice) sums every 16th mode of its cell
-constexpr int KICK_THREADS = 64;    // cells per block of the kick-only kernel
+constexpr int KICK_THREADS = 64;    // cells per block of the kick-only kernel (moving mode positions)
+constexpr int KA_THREADS = 256;     // atom components per block of the component-parallel kick
+constexpr int KA_MAX_BLOCKS = 1024; // its grid-stride launch: about one resident wave on 152 SMs
 
 __global__ void k_mode_functions(const double *__restrict__ k, const double *__restrict__ phi,
                                  const double *__restrict__ R, int M, int N, double *__restrict__ U) {
@@ -496,6 +499,73 @@ __global__ void __launch_bounds__(KICK_THREADS) k_kick(const StepArgs a, const i
     record_energies<KICK_THREADS>(a, flags, gridDim.x, scr);
 }
 
+// The kicks and the drift of k_kick with fixed mode positions, one thread per Cartesian component
+// of an atom (grid-stride over the 3 n_atoms components, so the loads and stores of p, F, b and r
+// are coalesced); the field of the atom's cell comes through the atom-to-cell index. Each thread
+// also adds the DFTB energies of the cells i, i + stride, ...; the block partials and their totals
+// are summed in a fixed order, so the energy record is deterministic. p and r are those of
+// kick_atom bit for bit.
+__global__ void __launch_bounds__(KA_THREADS) k_kick_atoms(const StepArgs a, const int flags) {
+    __shared__ double scr[6 * (KA_THREADS / 32)];
+    __shared__ bool last;
+    const int stride = gridDim.x * KA_THREADS;
+    const int n3 = 3 * a.n_atoms;
+    // distinct arrays: the loads of later iterations may be issued ahead of this one's stores
+    const double *__restrict__ F = a.F;
+    const double *__restrict__ b = a.b;
+    const double *__restrict__ im_ = a.inv_mass;
+    const double *__restrict__ E2 = a.E2in;
+    const double *__restrict__ E1 = a.E1in;
+    const int *__restrict__ acell = a.atom_cell;
+    double *__restrict__ p = a.p;
+    double *__restrict__ r = a.r;
+    double kin = 0.0, edf = 0.0;
+#pragma unroll 4
+    for (int i = blockIdx.x * KA_THREADS + threadIdx.x; i < n3; i += stride) {
+        const int j = i / 3;
+        const int n = acell[j];
+        const double im = im_[j];
+        const double f = F[i], bb = b[i];
+        double pj = p[i];
+        if (flags & FLD_SECOND) pj = fma(a.tau, f, fma(E2[n], bb, pj));
+        kin = fma(0.5 * im * pj, pj, kin);
+        if (flags & FLD_FIRST) {
+            pj = fma(a.tau, f, fma(E1[n], bb, pj));
+            r[i] = fma(a.dt * im, pj, r[i]);
+        }
+        p[i] = pj;
+    }
+    if (!(flags & FLD_ENERGY)) return;
+    for (int n = blockIdx.x * KA_THREADS + threadIdx.x; n < a.N; n += stride) edf += a.E_cell[n];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kin += __shfl_xor_sync(CAVMD_FULL_MASK, kin, o);
+        edf += __shfl_xor_sync(CAVMD_FULL_MASK, edf, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        scr[w] = kin;
+        scr[KA_THREADS / 32 + w] = edf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double k = 0.0, d = 0.0;
+        for (int i = 0; i < KA_THREADS / 32; ++i) {
+            k += scr[i];
+            d += scr[KA_THREADS / 32 + i];
+        }
+        a.e_kin_part[blockIdx.x] = k;
+        a.e_dftb_part[blockIdx.x] = d;
+        __threadfence();
+        const unsigned ticket = atomicAdd(a.done_counter, 1u);
+        last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    record_energies<KA_THREADS>(a, flags, gridDim.x, scr);
+}
+
 // k_field for moving mode positions: besides E_n of both half-flows, the position-term vectors
 // G_n = sum_a Us[a][n] Wk_a (Wk_a = -W_a k_a, written by k_photon), summed over the same 16 mode
 // slices and combined in the same fixed order; the kicks add (m_j / m_n) M_n G_n.
@@ -710,8 +780,16 @@ cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st) {
 int field_blocks(int N) { return (N + FLD_CELLS - 1) / FLD_CELLS; }   // >= the kick kernel's blocks
 
 cudaError_t launch_field(const StepArgs &a, int flags, cudaStream_t st) {
-    if (flags & FLD_E_GIVEN)
-        k_kick<<<(a.N + KICK_THREADS - 1) / KICK_THREADS, KICK_THREADS, 0, st>>>(a, flags);
+    if (flags & FLD_E_GIVEN) {
+        if (a.G1in) {
+            k_kick<<<(a.N + KICK_THREADS - 1) / KICK_THREADS, KICK_THREADS, 0, st>>>(a, flags);
+        } else {   // one resident wave at most (fewer block partials and last-block tickets), and at
+                   // most field_blocks(N) blocks: the energy partials hold that many
+            const long long need = (3LL * a.n_atoms + KA_THREADS - 1) / KA_THREADS;
+            const int blocks = (int)std::max(1LL, std::min({need, (long long)KA_MAX_BLOCKS, (long long)field_blocks(a.N)}));
+            k_kick_atoms<<<blocks, KA_THREADS, 0, st>>>(a, flags);
+        }
+    }
     else if (a.Us)
         k_field_moving<<<field_blocks(a.N), FLD_CELLS * FLD_SLICES, 0, st>>>(a, flags);
     else

@@ -26,7 +26,7 @@ constexpr int KXP = 128;          // MMA M: 2 Kx rows padded to 128
 constexpr int FWD_CELLS = 64;     // cells (K) per tile of the forward panels in HBM
 constexpr int FWD_SC = 32;        // cells (K) per forward stage: half a panel tile
 constexpr int FWD_NST = 4;        // forward stages in flight
-constexpr int FWD_THREADS = 256;  // two warps per TMEM lane quadrant in the forward fold
+constexpr int FWD_THREADS = 512;  // sixteen warps: four per TMEM lane quadrant in the forward fold
 constexpr int BACK_CELLS = 128;   // cells (N) per back tile
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
@@ -210,13 +210,14 @@ __global__ void __launch_bounds__(PCOM_THREADS) k_tc_panels_com(int N, int Kx, i
 
 // Forward Gram product, split over cells: partial[cta][i][j] = sum over the CTA's cells of A B^T.
 // Each 32-cell stage arrives by bulk copies (the BF16 hi / lo panels of A and the FP32 y-phase panel
-// of B, all pre-arranged in core-matrix order); up to FWD_NST stages are in flight. The threads scale
-// the y phases by M_n and split them into the BF16 hi / lo panels of B in shared memory, and one
-// thread issues the stage's MMAs into a fresh TMEM accumulator (two, alternating). The FP32 run of
-// an accumulator is therefore one stage: 32 cells, 6 MMAs. While the next stage's MMAs run, the
-// eight warps fold the finished accumulator into per-thread compensated FP32 sums (two-sum: the
-// rounding error of every addition is carried in a second register), so the accumulated error does
-// not grow with the number of cells a CTA owns. The partials leave as FP64 (sum + carried error).
+// of B, all pre-arranged in core-matrix order); up to FWD_NST stages are in flight. The sixteen warps
+// scale the y phases by M_n (converted and staged in shared memory one stage ahead) and split them
+// into the BF16 hi / lo panels of B in shared memory, and one thread issues the stage's MMAs into a
+// fresh TMEM accumulator (two, alternating) and the bulk copies. The FP32 run of an accumulator is
+// therefore one stage: 32 cells, 6 MMAs. While the next stage's MMAs run, the warps fold the
+// finished accumulator into per-thread compensated FP32 sums (two-sum: the rounding error of every
+// addition is carried in a second register), so the accumulated error does not grow with the
+// number of cells a CTA owns. The partials leave as FP64 (sum + carried error).
 template <int KY>
 __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total, int st_per_cta,
                                                                 const __nv_bfloat16 *__restrict__ Ahi,
@@ -230,11 +231,13 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
     constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES + S_BYTES;   // [A hi][A lo][B hi][B lo][B source]
     constexpr uint32_t LBO_A = (KXP / 8) * 128, LBO_B = (KY / 8) * 128;
     constexpr uint32_t TC = KY <= 32 ? 32 : (KY <= 64 ? 64 : 128);    // columns of one accumulator
-    constexpr int NCOL = KY / 2;                                       // columns folded per thread
+    constexpr int NGRP = KY / 8;                                       // 8-column groups of an accumulator
+    constexpr int GPT = (NGRP + 3) / 4;                                // groups folded per thread (at most)
+    constexpr int NCHUNK = KY * FWD_SC / 8;                            // split chunks: 8 cells of one row
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + FWD_NST * STAGE);   // [NST] stage data arrived
     uint64_t *done = full + FWD_NST;                                         // [NST] stage MMAs finished
     uint32_t *slot = reinterpret_cast<uint32_t *>(done + FWD_NST);
-    float *ms = reinterpret_cast<float *>(slot + 4);                         // [32] M_n of the stage (FP32)
+    float *ms = reinterpret_cast<float *>(slot + 4);                         // [2][32] M_n of two stages
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q0 = blockIdx.x * st_per_cta;
     const int nq = max(0, min(n_stage_total, q0 + st_per_cta) - q0);
@@ -245,14 +248,22 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
             tc::mbar_init(&done[s], 1);
         }
     }
+    // the dipoles of local stage i in FP32 (converted once: a conversion from FP64 runs on the FP64
+    // pipe), loaded by warp 1 a stage ahead and stored into ms[i & 1] after its fold
+    auto load_m = [&](int i) -> float {
+        const int n = (q0 + i) * FWD_SC + lane;
+        return (warp == 1 && i < nq && n < N) ? (float)__ldg(Mc + n) : 0.0f;
+    };
+    if (warp == 1) ms[lane] = load_m(0);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *slot;
     const uint32_t idesc = tc::idesc_bf16(KXP, KY);
-    // warps w and w + 4 read the same TMEM lane quadrant (w & 3), each one half of the columns
+    // warps w, w + 4, w + 8, w + 12 read the same TMEM lane quadrant (w & 3); warp part p = w / 4
+    // folds the 8-column groups p, p + 4, ...
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const int col0 = (warp >> 2) * NCOL;
+    const int part = warp >> 2;
     auto issue = [&](int i) {   // thread 0: the copies of local stage i into slot i % NST
         const int s = i % FWD_NST;
         const size_t q = (size_t)(q0 + i);
@@ -262,61 +273,49 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
         tc::bulk_g2s(st + A_BYTES, Alo + q * KXP * FWD_SC, A_BYTES, &full[s]);
         tc::bulk_g2s(st + 2 * A_BYTES + 2 * B_BYTES, Bsrc + q * KY * FWD_SC, S_BYTES, &full[s]);
     };
-    float acc_s[NCOL], acc_c[NCOL];
+    float acc_s[GPT * 8], acc_c[GPT * 8];
 #pragma unroll
-    for (int j = 0; j < NCOL; ++j) {
+    for (int j = 0; j < GPT * 8; ++j) {
         acc_s[j] = 0.0f;
         acc_c[j] = 0.0f;
     }
     // all threads: the accumulator of local stage i (TMEM buffer i & 1) into the compensated sums
     auto fold = [&](int i) {
-        const uint32_t base = tmem + lane_base + (uint32_t)((i & 1) * TC + col0);
+        const uint32_t base = tmem + lane_base + (uint32_t)((i & 1) * TC);
+        uint32_t r[GPT][8];
 #pragma unroll
-        for (int c0 = 0; c0 < NCOL; c0 += 32) {   // up to four loads in flight, then one wait
-            uint32_t r[4][8];
+        for (int g = 0; g < GPT; ++g)
+            if (part + 4 * g < NGRP) tc::tmem_ld8_nowait(base + (uint32_t)(8 * (part + 4 * g)), r[g]);
+        tc::tmem_wait_ld();
 #pragma unroll
-            for (int g = 0; g < 4; ++g)
-                if (c0 + 8 * g < NCOL) tc::tmem_ld8_nowait(base + (uint32_t)(c0 + 8 * g), r[g]);
-            tc::tmem_wait_ld();
+        for (int g = 0; g < GPT; ++g) {
+            if (part + 4 * g >= NGRP) continue;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                if (c0 + 8 * g >= NCOL) continue;
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int j = c0 + 8 * g + k;
-                    const float x = __uint_as_float(r[g][k]);
-                    const float s = acc_s[j];
-                    const float t = __fadd_rn(s, x);
-                    const float z = __fsub_rn(t, s);
-                    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));   // s + x - t exactly
-                    acc_s[j] = t;
-                    acc_c[j] = __fadd_rn(acc_c[j], e);
-                }
+            for (int k = 0; k < 8; ++k) {
+                const int j = 8 * g + k;
+                const float x = __uint_as_float(r[g][k]);
+                const float s = acc_s[j];
+                const float t = __fadd_rn(s, x);
+                const float z = __fsub_rn(t, s);
+                const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));   // s + x - t exactly
+                acc_s[j] = t;
+                acc_c[j] = __fadd_rn(acc_c[j], e);
             }
         }
     };
     int n_issued = 0;   // thread 0's count of stages whose copies were issued
     if (tid == 0)
         for (; n_issued < min(nq, FWD_NST - 1); ++n_issued) issue(n_issued);
-    bool ok = true;
+    bool ok = true, wd = true;   // wd: the last wait for a stage's MMAs (checked at the next barrier)
     int i = 0;
     for (; i < nq; ++i) {
         const int s = i % FWD_NST;
-        // stage i - 1's MMAs are done: its accumulator can be folded and its slot refilled
-        bool w = i == 0 || tc::mbar_wait(&done[(i - 1) % FWD_NST], ((i - 1) / FWD_NST) & 1);
-        if (tid == 0 && w && n_issued < nq && n_issued == i + FWD_NST - 1) issue(n_issued++);
-        w = w && tc::mbar_wait(&full[s], (i / FWD_NST) & 1);
-        const int nbase = (q0 + i) * FWD_SC;
-        if (tid < FWD_SC) {   // the stage's dipoles, converted once (a conversion from FP64 runs on the FP64 pipe)
-            const int n = nbase + tid;
-            ms[tid] = n < N ? (float)__ldg(Mc + n) : 0.0f;
-        }
-        if (!__syncthreads_and(w)) { ok = false; break; }
-        tc::fence_after_sync();
-        if (i > 0) fold(i - 1);
+        const bool w = tc::mbar_wait(&full[s], (i / FWD_NST) & 1);   // stage i's data arrived
+        if (!__syncthreads_and(w && wd)) { ok = false; break; }
         uint8_t *st = smem + s * STAGE;
         const float *bs = reinterpret_cast<const float *>(st + 2 * A_BYTES + 2 * B_BYTES);
-        for (int c = tid; c < KY * FWD_SC / 8; c += FWD_THREADS) {   // 8 consecutive cells of one row per chunk
+        const float *mi = ms + (i & 1) * FWD_SC;
+        for (int c = tid; c < NCHUNK; c += FWD_THREADS) {   // 8 consecutive cells of one row per chunk
             const int kgrp = c / KY, row = c - kgrp * KY;
             const uint32_t off = tc::core_offset(row, 8 * kgrp, LBO_B);
             const float4 v0 = *reinterpret_cast<const float4 *>(bs + off / 2);
@@ -324,13 +323,14 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
             const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
             __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) split_bf16(vv[q] * ms[8 * kgrp + q], hi[q], lo[q]);
+            for (int q = 0; q < 8; ++q) split_bf16(vv[q] * mi[8 * kgrp + q], hi[q], lo[q]);
             *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + off) = *reinterpret_cast<const uint4 *>(hi);
             *reinterpret_cast<uint4 *>(st + 2 * A_BYTES + B_BYTES + off) = *reinterpret_cast<const uint4 *>(lo);
         }
-        tc::fence_before_sync();   // the fold's TMEM reads are complete before the next MMAs reuse it
+        tc::fence_before_sync();   // the previous fold's TMEM reads are complete before MMAs reuse its buffer
         tc::fence_proxy_async();
         __syncthreads();
+        const float m_next = load_m(i + 1);   // in flight during the fold
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t sa = tc::smem_u32(st), sb = sa + 2 * A_BYTES;
@@ -346,10 +346,20 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
             }
             tc::mma_commit(&done[s]);
         }
+        __syncwarp();
+        // while stage i's MMAs run: stage i - 1's are done, so its slot is refilled (with stage
+        // i + NST - 1; at i = 0 the one slot the prologue left empty) and its accumulator folded
+        if (i > 0) wd = tc::mbar_wait(&done[(i - 1) % FWD_NST], ((i - 1) / FWD_NST) & 1);
+        if (tid == 0 && wd && n_issued < nq && n_issued == i + FWD_NST - 1) issue(n_issued++);
+        if (i > 0) {
+            tc::fence_after_sync();
+            fold(i - 1);
+        }
+        if (warp == 1) ms[((i + 1) & 1) * FWD_SC + lane] = m_next;   // read at stage i + 1, after a barrier
     }
     if (ok && nq > 0) {   // the last stage
         const bool w = tc::mbar_wait(&done[(nq - 1) % FWD_NST], ((nq - 1) / FWD_NST) & 1);
-        if (__syncthreads_and(w)) {
+        if (__syncthreads_and(w && wd)) {
             tc::fence_after_sync();
             fold(nq - 1);
         } else {
@@ -361,9 +371,14 @@ __global__ void __launch_bounds__(FWD_THREADS, 1) k_tc_forward(int n_stage_total
     }
     ok = __syncthreads_and(ok) != 0;
     if (!ok && tid == 0) atomicOr(status, (unsigned)ERRBIT_TIMEOUT);
-    double *P = partial + (size_t)blockIdx.x * KXP * KY + (size_t)(32 * (warp & 3) + lane) * KY + col0;
+    double *P = partial + (size_t)blockIdx.x * KXP * KY + (size_t)(32 * (warp & 3) + lane) * KY;
 #pragma unroll
-    for (int j = 0; j < NCOL; ++j) P[j] = ok ? (double)acc_s[j] + (double)acc_c[j] : 0.0;
+    for (int g = 0; g < GPT; ++g) {
+        if (part + 4 * g >= NGRP) continue;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            P[8 * (part + 4 * g) + k] = ok ? (double)acc_s[8 * g + k] + (double)acc_c[8 * g + k] : 0.0;
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 2 * TC);
@@ -556,7 +571,7 @@ cudaError_t set_smem(F f, size_t bytes) {
 // ---------------------------------------------------------------------------------------- host
 
 size_t tc_fwd_smem(int KY) {
-    return FWD_NST * (2 * (size_t)KXP * FWD_SC * 2 + 2 * (size_t)KY * FWD_SC * 2 + (size_t)KY * FWD_SC * 4) + 256;
+    return FWD_NST * (2 * (size_t)KXP * FWD_SC * 2 + 2 * (size_t)KY * FWD_SC * 2 + (size_t)KY * FWD_SC * 4) + 512;
 }
 int tc_fwd_stage_cells() { return FWD_SC; }
 size_t tc_back_smem(int KY) { return 4 * (size_t)KXP * KY * 2 + 2 * (size_t)BACK_CELLS * KY * 2 + 64; }
