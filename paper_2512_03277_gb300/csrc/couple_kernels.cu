@@ -28,6 +28,7 @@
 namespace {
 
 constexpr int PH_THREADS = 256;
+constexpr int PHM_THREADS = 128;   // modes per block of the one-thread-per-mode photon kernel
 constexpr int FLD_CELLS = 16;    // cells per block (N / 16 blocks fill every SM for N >= 2432)
 constexpr int FLD_SLICES = 16;   // mode slices: thread (cell, slice) sums every 16th mode of its cell
 constexpr int KICK_THREADS = 64;    // cells per block of the kick-only kernel (moving mode positions)
@@ -159,35 +160,9 @@ __device__ __forceinline__ void photon_paper_order(const StepArgs &a, int flags,
     a.pq[al] = p1;
 }
 
-__global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {
-    __shared__ double red[PH_THREADS / 32];
-    const int al = blockIdx.x;
-    double D = 0.0;
-    // PH_OPEN: the field of the synchronised state, read before the forward replaces it
-    const double D_sync = ((flags & PH_OPEN) && threadIdx.x == 0) ? a.D[al] : 0.0;
-    if (flags & PH_FORWARD) {
-        const double *u = a.U + (size_t)al * a.N;
-        double s = 0.0;
-#pragma unroll 4
-        for (int n = threadIdx.x; n < a.N; n += PH_THREADS) s = fma(u[n], a.M_cell[n], s);
-        s = block_sum_ordered(s, red);
-        if (threadIdx.x == 0) {
-            D = a.lam[al] * s;
-            a.D[al] = D;
-        }
-    } else if (flags & PH_FORWARD_G) {
-        if (threadIdx.x == 0) {   // mode (jx, jy, s) from the factorised Gram matrix
-            const int jx = al / (2 * a.Ky2), rem = al - jx * 2 * a.Ky2, jy = rem >> 1, sm = rem & 1;
-            const double *g = a.G;
-            const double v = sm == 0 ? g[jx * a.KY + jy] - g[(a.Kx + jx) * a.KY + a.Ky2 + jy]
-                                     : g[(a.Kx + jx) * a.KY + jy] + g[jx * a.KY + a.Ky2 + jy];
-            D = a.lam[al] * v;
-            a.D[al] = D;
-        }
-    } else if (threadIdx.x == 0) {
-        D = a.D[al];
-    }
-    if (threadIdx.x != 0) return;
+// Everything of k_photon after the mode's field D is known, for mode al (one thread).
+__device__ __forceinline__ void photon_mode(const StepArgs &a, const int flags, const int al, const double D,
+                                            const double D_sync) {
     const double w = a.omega[al], iw = a.inv_omega[al], lam = a.lam[al];
     const double c = a.cos_h[al], s = a.sin_h[al], omc = a.omc_h[al];
     const double cen = __dmul_rn(D, iw);
@@ -244,6 +219,44 @@ __global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const i
         a.q[al] = qs;
         a.pq[al] = ps;
     }
+}
+
+
+__global__ void __launch_bounds__(PH_THREADS) k_photon(const StepArgs a, const int flags) {
+    __shared__ double red[PH_THREADS / 32];
+    const int al = blockIdx.x;
+    double D = 0.0;
+    // PH_OPEN: the field of the synchronised state, read before the forward replaces it
+    const double D_sync = ((flags & PH_OPEN) && threadIdx.x == 0) ? a.D[al] : 0.0;
+    const double *u = a.U + (size_t)al * a.N;
+    double s = 0.0;
+#pragma unroll 4
+    for (int n = threadIdx.x; n < a.N; n += PH_THREADS) s = fma(u[n], a.M_cell[n], s);
+    s = block_sum_ordered(s, red);
+    if (threadIdx.x != 0) return;
+    D = a.lam[al] * s;
+    a.D[al] = D;
+    photon_mode(a, flags, al, D, D_sync);
+}
+
+// k_photon without the FP64 forward contraction (D from the factorised Gram matrix, or the stored
+// D): one thread per mode.
+__global__ void __launch_bounds__(PHM_THREADS) k_photon_modes(const StepArgs a, const int flags) {
+    const int al = blockIdx.x * PHM_THREADS + threadIdx.x;
+    if (al >= a.M) return;
+    const double D_sync = (flags & PH_OPEN) ? a.D[al] : 0.0;   // read before the field is replaced
+    double D;
+    if (flags & PH_FORWARD_G) {   // mode (jx, jy, s) from the factorised Gram matrix
+        const int jx = al / (2 * a.Ky2), rem = al - jx * 2 * a.Ky2, jy = rem >> 1, sm = rem & 1;
+        const double *g = a.G;
+        const double v = sm == 0 ? g[jx * a.KY + jy] - g[(a.Kx + jx) * a.KY + a.Ky2 + jy]
+                                 : g[(a.Kx + jx) * a.KY + jy] + g[jx * a.KY + a.Ky2 + jy];
+        D = a.lam[al] * v;
+        a.D[al] = D;
+    } else {
+        D = a.D[al];
+    }
+    photon_mode(a, flags, al, D, D_sync);
 }
 
 // Partial field sums over the modes a = sl, sl + FLD_SLICES, ... for cell n; the loads of u are
@@ -773,7 +786,10 @@ cudaError_t launch_field_grad_only(const double *Us, const double *W, const doub
 }
 
 cudaError_t launch_photon(const StepArgs &a, int flags, cudaStream_t st) {
-    k_photon<<<a.M, PH_THREADS, 0, st>>>(a, flags);
+    if (flags & PH_FORWARD)
+        k_photon<<<a.M, PH_THREADS, 0, st>>>(a, flags);
+    else
+        k_photon_modes<<<(a.M + PHM_THREADS - 1) / PHM_THREADS, PHM_THREADS, 0, st>>>(a, flags);
     return cudaGetLastError();
 }
 
