@@ -252,8 +252,9 @@ cudaError_t run_born(cavmd_ctx *c) {
 // Network dipole derivatives at the current positions (after the cell evaluation).
 cudaError_t run_mlp(cavmd_ctx *c) {
     PhaseScope ps(c, 3);
+    // the water kernel's cells hold 3 atoms each, at 3 n .. 3 n + 2
     cudaError_t e = launch_mlp_features(c->N, c->d_off, c->d_species, c->d_r, c->d_mlpX, c->d_mlpR, c->d_status,
-                                        c->stream);
+                                        c->stream, (c->generic || c->periodic) ? 0 : 3);
     if (e == cudaSuccess) e = launch_mlp_forward(c->n_atoms, c->d_mlpX, c->d_mlpR, c->d_mlpw, c->d_mlpZl, c->d_status, c->stream);
     if (e == cudaSuccess)
         e = launch_mlp_born(c->N, c->d_off, c->d_mlpZl, c->d_mlpR, c->d_Q, c->pol[0], c->pol[1], c->pol[2], c->d_b,

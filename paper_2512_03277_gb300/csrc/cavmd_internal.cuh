@@ -274,7 +274,7 @@ cudaError_t launch_born_assemble(int n_cells, const int *cell_offset, const doub
                                  cudaStream_t st);
 // Born-charge network pieces used by a time step
 cudaError_t launch_mlp_features(int n_cells, const int *off, const int *species, const double *r, float *X,
-                                float *R, unsigned *status, cudaStream_t st);
+                                float *R, unsigned *status, cudaStream_t st, int atoms_per_cell = 0);
 cudaError_t launch_mlp_forward(int n_atoms, const float *X, const float *R, const void *w_bf16, float *Zl,
                                unsigned *status, cudaStream_t st);
 cudaError_t prepare_mlp_forward();   // shared-memory attribute of the inference forward, once per process

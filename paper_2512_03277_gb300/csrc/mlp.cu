@@ -45,7 +45,81 @@ __device__ __forceinline__ float dsilu(float z) {
 __device__ __forceinline__ float fcut(float r) { return r < RC ? 0.5f * (cospif(r / RC) + 1.0f) : 0.0f; }
 __device__ __forceinline__ float wv(const __nv_bfloat16 *w, int i) { return __bfloat162float(w[i]); }
 
-// features (n_atoms x 32) and frames (n_atoms x 9, rows e1 e2 e3) of every atom; thread per atom
+// features x (32) and frame fr (9, rows e1 e2 e3) of atom j of the cell of atoms [a0, a1)
+__device__ __forceinline__ void atom_features(int a0, int a1, int j, const int *__restrict__ species,
+                                              const double *__restrict__ r, float (&x)[NF], float (&fr)[9],
+                                              unsigned *__restrict__ status) {
+#pragma unroll
+    for (int i = 0; i < NF; ++i) x[i] = 0.0f;
+    int k1 = -1, k2 = -1;
+    float r1 = 1e30f, r2 = 1e30f;
+    for (int k = a0; k < a1; ++k) {
+        if (k == j) continue;
+        const float dx = (float)(r[3 * k] - r[3 * j]), dy = (float)(r[3 * k + 1] - r[3 * j + 1]),
+                    dz = (float)(r[3 * k + 2] - r[3 * j + 2]);
+        const float rk = sqrtf(dx * dx + dy * dy + dz * dz);
+        if (!(rk < RC)) continue;
+        const float fc = fcut(rk);
+        const int e = species[k];   // radial channels: O (0) and H (1); every index below is constant
+        const float w0 = e == 0 ? fc : 0.0f, w1 = e == 1 ? fc : 0.0f;
+#pragma unroll
+        for (int a = 0; a < 11; ++a) {
+            const float t = rk - (0.8f + 0.7f * a);
+            const float g = __expf(-2.0f * t * t);
+            x[a] = fmaf(g, w0, x[a]);
+            x[11 + a] = fmaf(g, w1, x[11 + a]);
+        }
+        if (rk < r1 || (rk == r1 && k < k1)) { r2 = r1; k2 = k1; r1 = rk; k1 = k; }
+        else if (rk < r2 || (rk == r2 && k < k2)) { r2 = rk; k2 = k; }
+        for (int l = k + 1; l < a1; ++l) {
+            if (l == j) continue;
+            const float ex = (float)(r[3 * l] - r[3 * j]), ey = (float)(r[3 * l + 1] - r[3 * j + 1]),
+                        ez = (float)(r[3 * l + 2] - r[3 * j + 2]);
+            const float rl = sqrtf(ex * ex + ey * ey + ez * ez);
+            if (!(rl < RC)) continue;
+            const float cs = (dx * ex + dy * ey + dz * ez) / (rk * rl);
+            const float rad = __expf(-0.05f * (rk * rk + rl * rl)) * fc * fcut(rl);
+            // 2^(1-z) (1 +- cos)^z for z = 1, 2, 4, 8: powers by repeated squaring
+            const float pre[4] = {1.0f, 0.5f, 0.125f, 0.0078125f};   // 2^(1-z)
+            float pp = 1.0f + cs, pm = fmaxf(1.0f - cs, 0.0f);
+#pragma unroll
+            for (int zi = 0; zi < 4; ++zi) {
+                if (zi > 0) {
+                    pp *= pp;
+                    pm *= pm;
+                }
+                x[22 + 2 * zi] = fmaf(pre[zi] * pp, rad, x[22 + 2 * zi]);
+                x[22 + 2 * zi + 1] = fmaf(pre[zi] * pm, rad, x[22 + 2 * zi + 1]);
+            }
+        }
+    }
+    x[30] = species[j] == 0 ? 1.0f : 0.0f;
+    x[31] = species[j] == 1 ? 1.0f : 0.0f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) fr[q] = (q % 4 == 0) ? 1.0f : 0.0f;
+    if (k2 >= 0) {
+        float e1[3], v[3];
+        for (int q = 0; q < 3; ++q) {
+            e1[q] = (float)(r[3 * k1 + q] - r[3 * j + q]) / r1;
+            v[q] = (float)(r[3 * k2 + q] - r[3 * j + q]);
+        }
+        const float ve = v[0] * e1[0] + v[1] * e1[1] + v[2] * e1[2];
+        for (int q = 0; q < 3; ++q) v[q] -= ve * e1[q];
+        const float vn = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const float e2[3] = {v[0] * vn, v[1] * vn, v[2] * vn};
+        const float e3[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                             e1[0] * e2[1] - e1[1] * e2[0]};
+        for (int q = 0; q < 3; ++q) {
+            fr[q] = e1[q];
+            fr[3 + q] = e2[q];
+            fr[6 + q] = e3[q];
+        }
+    } else {
+        atomicOr(status, (unsigned)ERRBIT_NONFINITE);   // a frame needs two neighbours
+    }
+}
+
+// features (n_atoms x 32) and frames (n_atoms x 9) of every atom; thread per cell, cells of any size
 __global__ void k_features(int n_cells, const int *__restrict__ off, const int *__restrict__ species,
                            const double *__restrict__ r, float *__restrict__ X, float *__restrict__ R,
                            unsigned *__restrict__ status) {
@@ -53,77 +127,48 @@ __global__ void k_features(int n_cells, const int *__restrict__ off, const int *
     if (c >= n_cells) return;
     const int a0 = off[c], a1 = off[c + 1];
     for (int j = a0; j < a1; ++j) {
-        float x[NF];
-        for (int i = 0; i < NF; ++i) x[i] = 0.0f;
-        int k1 = -1, k2 = -1;
-        float r1 = 1e30f, r2 = 1e30f;
-        for (int k = a0; k < a1; ++k) {
-            if (k == j) continue;
-            const float dx = (float)(r[3 * k] - r[3 * j]), dy = (float)(r[3 * k + 1] - r[3 * j + 1]),
-                        dz = (float)(r[3 * k + 2] - r[3 * j + 2]);
-            const float rk = sqrtf(dx * dx + dy * dy + dz * dz);
-            if (!(rk < RC)) continue;
-            const float fc = fcut(rk);
-            const int e = species[k];   // radial channels: O (0) and H (1); every index below is constant
-            const float w0 = e == 0 ? fc : 0.0f, w1 = e == 1 ? fc : 0.0f;
-#pragma unroll
-            for (int a = 0; a < 11; ++a) {
-                const float t = rk - (0.8f + 0.7f * a);
-                const float g = __expf(-2.0f * t * t);
-                x[a] = fmaf(g, w0, x[a]);
-                x[11 + a] = fmaf(g, w1, x[11 + a]);
-            }
-            if (rk < r1 || (rk == r1 && k < k1)) { r2 = r1; k2 = k1; r1 = rk; k1 = k; }
-            else if (rk < r2 || (rk == r2 && k < k2)) { r2 = rk; k2 = k; }
-            for (int l = k + 1; l < a1; ++l) {
-                if (l == j) continue;
-                const float ex = (float)(r[3 * l] - r[3 * j]), ey = (float)(r[3 * l + 1] - r[3 * j + 1]),
-                            ez = (float)(r[3 * l + 2] - r[3 * j + 2]);
-                const float rl = sqrtf(ex * ex + ey * ey + ez * ez);
-                if (!(rl < RC)) continue;
-                const float cs = (dx * ex + dy * ey + dz * ez) / (rk * rl);
-                const float rad = __expf(-0.05f * (rk * rk + rl * rl)) * fc * fcut(rl);
-                // 2^(1-z) (1 +- cos)^z for z = 1, 2, 4, 8: powers by repeated squaring
-                const float pre[4] = {1.0f, 0.5f, 0.125f, 0.0078125f};   // 2^(1-z)
-                float pp = 1.0f + cs, pm = fmaxf(1.0f - cs, 0.0f);
-#pragma unroll
-                for (int zi = 0; zi < 4; ++zi) {
-                    if (zi > 0) {
-                        pp *= pp;
-                        pm *= pm;
-                    }
-                    x[22 + 2 * zi] = fmaf(pre[zi] * pp, rad, x[22 + 2 * zi]);
-                    x[22 + 2 * zi + 1] = fmaf(pre[zi] * pm, rad, x[22 + 2 * zi + 1]);
-                }
-            }
-        }
-        x[30] = species[j] == 0 ? 1.0f : 0.0f;
-        x[31] = species[j] == 1 ? 1.0f : 0.0f;
+        float x[NF], fr[9];
+        atom_features(a0, a1, j, species, r, x, fr, status);
         float4 *Xj = reinterpret_cast<float4 *>(X + (size_t)j * NF);
 #pragma unroll
         for (int i = 0; i < NF / 4; ++i) Xj[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
-        float fr[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        if (k2 >= 0) {
-            float e1[3], v[3];
-            for (int q = 0; q < 3; ++q) {
-                e1[q] = (float)(r[3 * k1 + q] - r[3 * j + q]) / r1;
-                v[q] = (float)(r[3 * k2 + q] - r[3 * j + q]);
-            }
-            const float ve = v[0] * e1[0] + v[1] * e1[1] + v[2] * e1[2];
-            for (int q = 0; q < 3; ++q) v[q] -= ve * e1[q];
-            const float vn = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            const float e2[3] = {v[0] * vn, v[1] * vn, v[2] * vn};
-            const float e3[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                                 e1[0] * e2[1] - e1[1] * e2[0]};
-            for (int q = 0; q < 3; ++q) {
-                fr[q] = e1[q];
-                fr[3 + q] = e2[q];
-                fr[6 + q] = e3[q];
-            }
-        } else {
-            atomicOr(status, (unsigned)ERRBIT_NONFINITE);   // a frame needs two neighbours
-        }
         for (int q = 0; q < 9; ++q) R[(size_t)j * 9 + q] = fr[q];
+    }
+}
+
+// The same for cells of 3 atoms each (water systems, atoms 3 c .. 3 c + 2), in three rounds: round
+// a forms atom a of every cell of the block, stages the rows in shared memory and writes them out
+// row by row (a warp writes one 128-byte feature row per store; a thread's own rows would be
+// 384 bytes apart from its neighbours').
+constexpr int FEAT_CELLS = 128;                 // cells (threads) per block
+constexpr int FEAT_LD = NF + 4;                 // staged row stride in floats (16-byte rows, no bank conflicts)
+__global__ void __launch_bounds__(FEAT_CELLS) k_features_w3(int n_cells, const int *__restrict__ species,
+                                                            const double *__restrict__ r, float *__restrict__ X,
+                                                            float *__restrict__ R, unsigned *__restrict__ status) {
+    __shared__ __align__(16) float sx[FEAT_CELLS * FEAT_LD];
+    __shared__ float sr[FEAT_CELLS * 9];
+    const int c0 = blockIdx.x * FEAT_CELLS, c = c0 + threadIdx.x;
+    const int nc = min(FEAT_CELLS, n_cells - c0);   // cells of this block
+    for (int at = 0; at < 3; ++at) {
+        if (c < n_cells) {
+            float x[NF], fr[9];
+            atom_features(3 * c, 3 * c + 3, 3 * c + at, species, r, x, fr, status);
+            float4 *sxj = reinterpret_cast<float4 *>(sx + threadIdx.x * FEAT_LD);
+#pragma unroll
+            for (int i = 0; i < NF / 4; ++i) sxj[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) sr[threadIdx.x * 9 + q] = fr[q];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nc * NF; i += FEAT_CELLS) {   // row i / NF: atom 3 (c0 + row) + at
+            const int row = i / NF, col = i - row * NF;
+            X[((size_t)3 * (c0 + row) + at) * NF + col] = sx[row * FEAT_LD + col];
+        }
+        for (int i = threadIdx.x; i < nc * 9; i += FEAT_CELLS) {
+            const int row = i / 9, q = i - row * 9;
+            R[((size_t)3 * (c0 + row) + at) * 9 + q] = sr[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -840,8 +885,12 @@ __global__ void k_permute_cells(int n_cells, const int *__restrict__ perm, const
 // --------------------------------------------------------------------------------------------- host
 
 cudaError_t launch_mlp_features(int n_cells, const int *off, const int *species, const double *r, float *X,
-                                float *R, unsigned *status, cudaStream_t st) {
-    k_features<<<(n_cells + 127) / 128, 128, 0, st>>>(n_cells, off, species, r, X, R, status);
+                                float *R, unsigned *status, cudaStream_t st, int atoms_per_cell) {
+    if (atoms_per_cell == 3)
+        k_features_w3<<<(n_cells + FEAT_CELLS - 1) / FEAT_CELLS, FEAT_CELLS, 0, st>>>(n_cells, species, r, X, R,
+                                                                                     status);
+    else
+        k_features<<<(n_cells + 127) / 128, 128, 0, st>>>(n_cells, off, species, r, X, R, status);
     return cudaGetLastError();
 }
 
